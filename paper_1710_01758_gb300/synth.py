@@ -1,0 +1,188 @@
+"""Seeded synthetic inputs for PI+CS reconstruction problems.
+
+This module only *simulates an acquisition*: a piecewise-constant ellipse phantom, smooth
+Gaussian-profile coil sensitivities normalised to sum(|S_c|^2) = 1 (the normalisation of the
+"Coil sensitivity maps" paragraph of the paper's Methods), Cartesian phase-encode line masks
+(Methods, "Undersampling"), and noisy undersampled k-space y_c = R (F S_c x + n_c) (the data model
+of Eq. ill0).  It holds none of the reconstruction method's arithmetic: no system matrix, no
+preconditioner, no CG, no Split Bregman.  Both the FP64 oracle and the CUDA path consume its
+arrays; neither is used to produce them.
+
+Conventions shared by every consumer:
+  * images are C-ordered ``[ny, nx]`` (2D) with x fastest;
+  * coil sensitivities are ``[Nc, ny, nx]``;
+  * the mask is ``uint8 [ny, nx]`` in DFT (unshifted) order, 1 = sampled;
+  * k-space is ``[Nc, ny, nx]`` in DFT order with zeros off the mask;
+  * F is the unitary 2D DFT (forward sign negative).
+All arrays are returned in complex128 / float64; a consumer casts them to its own precision.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+# Seeds of the two 2D workloads: seed = SEED_BASE + workload number.
+SEED_BASE = 1710017580
+
+
+def _grid(ny: int, nx: int):
+    """Pixel-centre coordinates in [-1, 1) along x and y, shaped [ny, nx]."""
+    xs = -1.0 + 2.0 * np.arange(nx) / nx
+    ys = -1.0 + 2.0 * np.arange(ny) / ny
+    return np.meshgrid(ys, xs, indexing="ij")[::-1]  # (X, Y)
+
+
+def ellipse_phantom(ny: int, nx: int, rng: np.random.Generator, n_ellipses: int = 12) -> np.ndarray:
+    """Piecewise-constant phantom: ``n_ellipses`` ellipses painted in order, each overwriting the
+    pixels it covers with an intensity drawn from U[0, 1]; background 0.  Centres U[-0.7, 0.7],
+    semi-axes U[0.05, 0.5], rotation U[0, pi).  The magnitude image is multiplied by the smooth
+    phase exp(i*pi*(a*x + b*y)), a, b ~ U[-0.5, 0.5]."""
+    X, Y = _grid(ny, nx)
+    img = np.zeros((ny, nx), np.float64)
+    for _ in range(n_ellipses):
+        cx, cy = rng.uniform(-0.7, 0.7, 2)
+        a, b = rng.uniform(0.05, 0.5, 2)
+        th = rng.uniform(0.0, math.pi)
+        val = rng.uniform(0.0, 1.0)
+        xr = (X - cx) * math.cos(th) + (Y - cy) * math.sin(th)
+        yr = -(X - cx) * math.sin(th) + (Y - cy) * math.cos(th)
+        img[(xr / a) ** 2 + (yr / b) ** 2 <= 1.0] = val
+    pa, pb = rng.uniform(-0.5, 0.5, 2)
+    return img * np.exp(1j * math.pi * (pa * X + pb * Y))
+
+
+def coil_maps(ny: int, nx: int, nc: int, rng: np.random.Generator) -> np.ndarray:
+    """Smooth complex coil sensitivities ``[nc, ny, nx]``.
+
+    Coil c sits at angle theta_c = 2*pi*c/nc + theta_0 (theta_0 ~ U[0, 2*pi/nc), one draw per
+    slice) on a ring of radius 1.2 around the field of view [-1, 1]^2, with profile
+    exp(-|r - r_c|^2 / (2 * 0.6^2)) * exp(i*theta_c).  The maps are then normalised pointwise so
+    that sum_c |S_c|^2 = 1 everywhere."""
+    X, Y = _grid(ny, nx)
+    theta0 = rng.uniform(0.0, 2.0 * math.pi / nc)
+    maps = np.empty((nc, ny, nx), np.complex128)
+    for c in range(nc):
+        th = 2.0 * math.pi * c / nc + theta0
+        xc, yc = 1.2 * math.cos(th), 1.2 * math.sin(th)
+        prof = np.exp(-((X - xc) ** 2 + (Y - yc) ** 2) / (2.0 * 0.6 ** 2))
+        maps[c] = prof * np.exp(1j * th)
+    maps /= np.sqrt(np.sum(np.abs(maps) ** 2, axis=0, keepdims=True))
+    return maps
+
+
+def line_mask(ny: int, nx: int, accel: float, n_centre: int, rng: np.random.Generator,
+              density: str = "uniform") -> np.ndarray:
+    """Cartesian mask of fully sampled readout (x) lines at random phase-encode (y) positions.
+
+    round(ny/accel) lines in total, of which the ``n_centre`` lines around k_y = 0 are always
+    taken; the rest are drawn without replacement, uniformly (``density='uniform'``) or with
+    probability proportional to (1 - |k|/k_max)^2 (``'variable'``).  Returned in DFT order."""
+    n_lines = int(round(ny / accel))
+    if not (0 < n_centre <= n_lines <= ny):
+        raise ValueError("need 0 < n_centre <= round(ny/accel) <= ny")
+    kc = np.arange(ny) - ny // 2                      # centred k_y coordinate of each slot
+    centre = np.zeros(ny, bool)
+    lo = ny // 2 - n_centre // 2
+    centre[lo:lo + n_centre] = True
+    cand = np.flatnonzero(~centre)
+    if density == "uniform":
+        p = np.ones(cand.size)
+    elif density == "variable":
+        p = (1.0 - np.abs(kc[cand]) / (ny / 2.0)) ** 2 + 1e-12
+    else:
+        raise ValueError(density)
+    pick = rng.choice(cand, size=n_lines - n_centre, replace=False, p=p / p.sum())
+    lines_centred = centre.copy()
+    lines_centred[pick] = True
+    lines = np.fft.ifftshift(lines_centred)           # centred order -> DFT order
+    return np.repeat(lines[:, None], nx, axis=1).astype(np.uint8)
+
+
+def random_mask(ny: int, nx: int, accel: float, centre: int, rng: np.random.Generator) -> np.ndarray:
+    """Fully random 2D variable-density mask (the paper's second sampling scheme): a fully
+    sampled ``centre`` x ``centre`` block plus points drawn with probability proportional to
+    (1 - r/r_max)^2, round(ny*nx/accel) points in total.  DFT order."""
+    n_pts = int(round(ny * nx / accel))
+    ky = (np.arange(ny) - ny // 2)[:, None] / (ny / 2.0)
+    kx = (np.arange(nx) - nx // 2)[None, :] / (nx / 2.0)
+    rad = np.sqrt(ky ** 2 + kx ** 2) / math.sqrt(2.0)
+    m = np.zeros((ny, nx), bool)
+    cy, cx = ny // 2 - centre // 2, nx // 2 - centre // 2
+    m[cy:cy + centre, cx:cx + centre] = True
+    cand = np.flatnonzero(~m.ravel())
+    p = (1.0 - rad.ravel()[cand]) ** 2 + 1e-12
+    pick = rng.choice(cand, size=max(0, n_pts - int(m.sum())), replace=False, p=p / p.sum())
+    m.ravel()[pick] = True
+    return np.fft.ifftshift(m).astype(np.uint8)
+
+
+def acquire(x: np.ndarray, sens: np.ndarray, mask: np.ndarray, sigma: float,
+            rng: np.random.Generator) -> np.ndarray:
+    """Simulated undersampled acquisition y_c = R (F S_c x + n_c), n_c complex Gaussian with
+    independent N(0, sigma^2) real and imaginary parts (data model of Eq. ill0)."""
+    coil_imgs = sens * x[None]
+    k = np.fft.fft2(coil_imgs, norm="ortho")
+    noise = sigma * (rng.standard_normal(k.shape) + 1j * rng.standard_normal(k.shape))
+    return (k + noise) * mask[None].astype(np.float64)
+
+
+@dataclasses.dataclass
+class Workload:
+    """A 2D PI+CS reconstruction workload (geometry, regularisation and iteration schedule)."""
+    name: str
+    ny: int
+    nx: int
+    ncoils: int
+    accel: float
+    n_centre: int
+    density: str
+    mu: float
+    lam: float
+    gam: float
+    wavelet_levels: int
+    n_outer: int
+    n_inner: int
+    pcg_tol: float
+    pcg_maxit: int
+    pcg_fixed_iters: int          # > 0: run exactly this many PCG iterations per solve
+    sigma: float = 1e-3
+    seed: int = SEED_BASE
+
+
+# 128x128, 4 coils, R=4 lines + 16 centre lines, TV only, 10 SB x 20 fixed PCG iterations.
+SMALL_128 = Workload("128x128 Nc4 R4 TV-only 10SBx20PCG", 128, 128, 4, 4.0, 16, "uniform",
+                     1.0, 0.1, 0.0, 0, 10, 1, 1e-3, 20, 20, seed=SEED_BASE + 1)
+# 256x256, 12 coils, R=4 lines + 24 centre lines, TV + 4-level Haar, 20 SB, PCG to 1e-3.
+METRIC_256 = Workload("256x256 Nc12 R4 TV+Haar4 20SB PCG-tol1e-3", 256, 256, 12, 4.0, 24, "uniform",
+                      1.0, 0.05, 0.05, 4, 20, 1, 1e-3, 200, 0, seed=SEED_BASE + 2)
+
+
+@dataclasses.dataclass
+class Slice:
+    x_true: np.ndarray    # complex128 [ny, nx]
+    sens: np.ndarray      # complex128 [Nc, ny, nx]
+    mask: np.ndarray      # uint8 [ny, nx], DFT order
+    y: np.ndarray         # complex128 [Nc, ny, nx], zeros off-mask
+
+
+def make_slice(wl: Workload, seed: int | None = None) -> Slice:
+    """One seeded slice of workload ``wl`` (seed defaults to ``wl.seed``)."""
+    rng = np.random.default_rng(wl.seed if seed is None else seed)
+    x = ellipse_phantom(wl.ny, wl.nx, rng)
+    s = coil_maps(wl.ny, wl.nx, wl.ncoils, rng)
+    m = line_mask(wl.ny, wl.nx, wl.accel, wl.n_centre, rng, wl.density)
+    y = acquire(x, s, m, wl.sigma, rng)
+    return Slice(x, s, m, y)
+
+
+def make_batch(wl: Workload, nbatch: int, seed: int | None = None) -> list[Slice]:
+    """``nbatch`` independent slices; slice i uses seed (seed or wl.seed) * 1000 + i."""
+    base = wl.seed if seed is None else seed
+    return [make_slice(wl, base * 1000 + i) for i in range(nbatch)]
+
+
+def random_complex(shape, rng: np.random.Generator) -> np.ndarray:
+    """Standard complex Gaussian test vector (real and imaginary parts N(0, 1))."""
+    return rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
