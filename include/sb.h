@@ -1,0 +1,155 @@
+/*
+ * sb.h — C ABI of a GB300 (sm_103a) library for the circulant-preconditioned conjugate-gradient
+ * solve inside Split Bregman for parallel imaging + compressed sensing MRI
+ * (Koolstra, van Gemert et al., arXiv 1710.01758).
+ *
+ * Problem (Theory, Eq. original and Eq. system):
+ *   A = mu * sum_i (R F S_i)^H (R F S_i) + lambda (D_x^H D_x + D_y^H D_y) + gamma W^H W,
+ * F the unitary 2D DFT, S_i diagonal coil sensitivities, R = diag(r) a binary k-space mask,
+ * D_x, D_y periodic first-order differences, W an orthonormal (Haar) wavelet, so W^H W = I.
+ * Preconditioner (Eq. precon, Eq. Kdiag): M^{-1} = F^H diag(k)^{-1} F with
+ * k = mu k_c + lambda k_d + gamma, k_c the diagonal of F (sum_i S_i^H F^H R F S_i) F^H.
+ *
+ * Conventions for every entry point:
+ *  - Pointers named d_* are DEVICE pointers on the device that was current at sb_plan_create;
+ *    h_* are host pointers.  The caller owns all of them.
+ *  - Complex data is interleaved complex64 (float re, float im), C order, x fastest:
+ *    an image is [nbatch][ny][nx]; coil data are [nbatch][ncoils][ny][nx].
+ *  - k-space arrays are in DFT (unshifted) order; the DFT is unitary, forward sign negative.
+ *  - All device work is enqueued on the plan's stream.  sb_apply_A and sb_apply_precond are
+ *    asynchronous; sb_set_mask, sb_pcg_solve and sb_split_bregman synchronise the stream before
+ *    they return (they report iteration counts to the host).
+ *  - Errors are returned as sb_status, never by abort; sb_plan_last_error() gives a message.
+ *    A CUDA error leaves the plan in an undefined numerical state (destroy it).
+ *  - The mask must be constant along the readout (x) axis: Cartesian phase-encode line masks,
+ *    the sampling of the paper's Methods ("Undersampling", random lines).  Other masks are
+ *    rejected with SB_ERR_UNSUPPORTED.
+ *  - Supported sizes: ndim = 2; nx, ny in {32, 64, 128, 256}; ncoils >= 1; nbatch >= 1;
+ *    wavelet_levels in [0, 6] with nx, ny divisible by 2^levels and by 16.
+ */
+#ifndef SB_H
+#define SB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SB_OK = 0,
+    SB_ERR_INVALID_ARG = 1,   /* null pointer, bad size, bad option */
+    SB_ERR_UNSUPPORTED = 2,   /* valid but not implemented (size, mask kind, precision) */
+    SB_ERR_CUDA = 3,          /* a CUDA runtime call failed; message in sb_plan_last_error */
+    SB_ERR_NOT_READY = 4,     /* coils / mask not set yet */
+    SB_ERR_NONFINITE = 5,     /* NaN or Inf met in a CG scalar (rho, p^H A p, ||r||) */
+    SB_ERR_BREAKDOWN = 6,     /* Re(p^H A p) <= 0: A not positive definite on the data */
+    SB_ERR_NOT_CONVERGED = 7, /* maxit reached before the tolerance */
+    SB_ERR_TIMEOUT = 8        /* reserved for bounded device-side waits */
+} sb_status;
+
+typedef enum { SB_PREC_FP32 = 0, SB_PREC_SPLIT_BF16 = 1, SB_PREC_SPLIT_FP16 = 2 } sb_precision;
+typedef enum { SB_PRECOND_NONE = 0, SB_PRECOND_CIRCULANT = 1, SB_PRECOND_JACOBI = 2 } sb_precond;
+
+typedef struct {
+    int ndim;               /* 2 */
+    int nx, ny, nz;         /* image size; nz = 1 */
+    int ncoils;             /* N_c */
+    int nbatch;             /* independent slices of this geometry solved together (>= 1) */
+    double mu, lambda, gamma;  /* weights of Eq. system; mu > 0, lambda >= 0, gamma >= 0 */
+    int wavelet_levels;     /* Haar levels of W used by sb_split_bregman; 0 = no wavelet term */
+    sb_precision prec;      /* SB_PREC_FP32 */
+} sb_plan_desc;
+
+typedef struct sb_plan_s* sb_plan;
+
+/* Create a plan: validates the descriptor and allocates the plan's device workspace
+ * (PCG vectors, Split Bregman fields, k^{-1}, FFT twiddles, CG scalars) on the current
+ * device.  cuda_stream: a cudaStream_t (NULL = legacy default stream).  *out receives the plan.
+ * No allocation happens after sb_set_mask. */
+sb_status sb_plan_create(const sb_plan_desc* desc, void* cuda_stream, sb_plan* out);
+
+/* Destroy a plan and free its workspace (synchronises its stream).  NULL is accepted. */
+sb_status sb_plan_destroy(sb_plan plan);
+
+/* Set the coil sensitivities S_i (Eq. ill0), complex64 [nbatch][ncoils][ny][nx].
+ * BORROWED: d_sens is read by every later operator call and must stay alive and unchanged
+ * until sb_plan_destroy or the next sb_set_coils.  Invalidates k: call sb_set_mask next. */
+sb_status sb_set_coils(sb_plan plan, const void* d_sens);
+
+/* Set the sampling mask r (R = diag(r), Eq. ill0), uint8 [nbatch][ny][nx], nonzero = sampled,
+ * DFT order, and build k of Eq. Kdiag by FFTs (Eq. diagonalelements and the k_d paragraph of
+ * "Efficient Implementation of the Preconditioner").  Requires sb_set_coils.  d_mask is read
+ * during this call only.  Synchronises the stream.  Returns SB_ERR_UNSUPPORTED if some slice's
+ * mask varies along x. */
+sb_status sb_set_mask(sb_plan plan, const uint8_t* d_mask);
+
+/* Copy k (float32 [nbatch][ny][nx], DFT order, before inversion) into d_k. */
+sb_status sb_get_k(sb_plan plan, float* d_k);
+
+/* d_y = A d_x for every slice (Eq. system).  complex64 [nbatch][ny][nx] each; d_x and d_y
+ * must not overlap.  Asynchronous. */
+sb_status sb_apply_A(sb_plan plan, const void* d_x, void* d_y);
+
+/* d_z = M^{-1} d_r = F^H diag(k)^{-1} F d_r (Eq. precon).  complex64 [nbatch][ny][nx];
+ * d_r and d_z may be equal (in place).  Asynchronous. */
+sb_status sb_apply_precond(sb_plan plan, const void* d_r, void* d_z);
+
+typedef struct {
+    double tol;          /* stop when ||b - A x|| <= tol ||b|| (recurrence residual) */
+    int maxit;           /* iteration cap (>= 1) */
+    int fixed_iters;     /* > 0: run exactly this many iterations, no tolerance test */
+    sb_precond precond;  /* SB_PRECOND_CIRCULANT or SB_PRECOND_NONE */
+} sb_pcg_opts;
+
+typedef struct {
+    int iters;           /* A applications after the initial residual */
+    double rel_resid;    /* final ||r|| / ||b|| */
+    int converged;       /* 1 if the tolerance was met (or fixed_iters ran) */
+} sb_pcg_result;
+
+/* Solve A x = b for every slice by preconditioned CG (Complexity section; standard PCG with
+ * the HPD preconditioner), warm-started from d_x.  d_b, d_x complex64 [nbatch][ny][nx];
+ * d_x is overwritten with the solution.  h_results (host, may be NULL) receives nbatch
+ * entries.  FP64 CG scalars.  Synchronises.  Returns SB_ERR_NOT_CONVERGED if any slice missed
+ * the tolerance within maxit, SB_ERR_BREAKDOWN / SB_ERR_NONFINITE on a CG breakdown. */
+sb_status sb_pcg_solve(sb_plan plan, const void* d_b, void* d_x, const sb_pcg_opts* opts,
+                       sb_pcg_result* h_results);
+
+typedef struct {
+    int n_outer;            /* Algorithm 1 outer iterations (j loop) */
+    int n_inner;            /* Algorithm 1 inner iterations (k loop) */
+    sb_pcg_opts pcg;        /* the solve of step 5 */
+    double tau_tv, tau_w;   /* shrink thresholds; <= 0 selects 1/lambda and 1/gamma */
+    int init_rss;           /* 1: x starts as the root-sum-of-squares coil combination of
+                               F^H y_i (step 1); 0: d_x holds the caller's start */
+    int* h_iters;           /* host, may be NULL: receives nbatch * n_outer * n_inner PCG
+                               iteration counts, slice-major */
+} sb_sb_opts;
+
+/* Split Bregman reconstruction (Algorithm 1) of every slice from undersampled k-space
+ * d_y (complex64 [nbatch][ncoils][ny][nx], DFT order; entries off the mask are ignored),
+ * result in d_x (complex64 [nbatch][ny][nx]).  Each inner iteration forms b (step 4), solves
+ * A x = b by PCG warm-started from x (step 5), shrinks and updates the Bregman variables
+ * (steps 6-11); each outer iteration adds the data residual back (steps 12-14).
+ * h_last (host, may be NULL) receives the last solve's result per slice.  Synchronises.
+ * Returns the first non-OK PCG status met (the reconstruction still completes). */
+sb_status sb_split_bregman(sb_plan plan, const void* d_y, void* d_x, const sb_sb_opts* opts,
+                           sb_pcg_result* h_last);
+
+/* Human-readable name of a status code (static string). */
+const char* sb_status_string(sb_status status);
+
+/* Message of the last error raised on this plan ("" if none).  Valid until the next call. */
+const char* sb_plan_last_error(sb_plan plan);
+
+/* Number of kernels this library has launched in this process (graph replays count every
+ * kernel node they run).  Instrumentation for benchmarks. */
+uint64_t sb_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SB_H */

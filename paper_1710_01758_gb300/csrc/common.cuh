@@ -1,0 +1,214 @@
+// Shared device helpers: complex arithmetic, small DFTs, the two-stage Stockham FFT that
+// keeps a transform in registers, and deterministic block / cross-CTA reductions.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sb {
+
+// ------------------------------------------------------------------ complex helpers
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+// conj(a) * b
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.x, b.y, -a.y * b.x));
+}
+// acc + conj(a) * b
+__device__ __forceinline__ float2 cfmac(float2 acc, float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, fmaf(a.y, b.y, acc.x)), fmaf(a.x, b.y, fmaf(-a.y, b.x, acc.y)));
+}
+__device__ __forceinline__ float cabs2(float2 a) { return fmaf(a.x, a.x, a.y * a.y); }
+// multiply by W4 = -i (forward) or +i (inverse)
+template <bool INV> __device__ __forceinline__ float2 mul_w4(float2 a) {
+    return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+}
+// cos(2 pi m / 16) and sin(2 pi m / 16): cos(pi/8), sin(pi/8) and sqrt(1/2) are the only
+// irrational values needed.
+__host__ __device__ constexpr float w16_cos(int m) {
+    constexpr float C1 = 0.92387953251128674f, S1 = 0.38268343236508977f, R2 = 0.70710678118654752f;
+    switch (m & 15) {
+        case 0: return 1.f;  case 1: return C1;  case 2: return R2;  case 3: return S1;
+        case 4: return 0.f;  case 5: return -S1; case 6: return -R2; case 7: return -C1;
+        case 8: return -1.f; case 9: return -C1; case 10: return -R2; case 11: return -S1;
+        case 12: return 0.f; case 13: return S1; case 14: return R2; default: return C1;
+    }
+}
+__host__ __device__ constexpr float w16_sin(int m) { return w16_cos(m - 4); }
+
+// multiply by the constant exp(-2 pi i m / 16) (forward) or its conjugate (inverse)
+template <bool INV, int M> __device__ __forceinline__ float2 mul_w16(float2 a) {
+    constexpr int m = M & 15;
+    if constexpr (m == 0) return a;
+    else if constexpr (m == 4) return mul_w4<INV>(a);
+    else if constexpr (m == 8) return make_float2(-a.x, -a.y);
+    else if constexpr (m == 12) return mul_w4<!INV>(a);
+    else {
+        constexpr float c = w16_cos(m);
+        constexpr float s = INV ? w16_sin(m) : -w16_sin(m);
+        return make_float2(fmaf(a.x, c, -a.y * s), fmaf(a.x, s, a.y * c));
+    }
+}
+
+// ------------------------------------------------------------------ small DFTs in registers
+// Unnormalised DFT of R points, forward sign negative (INV: positive), in natural order.
+template <bool INV> __device__ __forceinline__ void dft2(float2& a0, float2& a1) {
+    const float2 t = a0;
+    a0 = cadd(t, a1);
+    a1 = csub(t, a1);
+}
+
+template <bool INV> __device__ __forceinline__ void dft4(float2& a0, float2& a1, float2& a2, float2& a3) {
+    const float2 t0 = cadd(a0, a2), t1 = csub(a0, a2);
+    const float2 t2 = cadd(a1, a3), t3 = mul_w4<INV>(csub(a1, a3));
+    a0 = cadd(t0, t2);
+    a2 = csub(t0, t2);
+    a1 = cadd(t1, t3);
+    a3 = csub(t1, t3);
+}
+
+template <bool INV> __device__ __forceinline__ void dft8(float2 (&a)[8]) {
+    float2 e0 = a[0], e1 = a[2], e2 = a[4], e3 = a[6];
+    float2 o0 = a[1], o1 = a[3], o2 = a[5], o3 = a[7];
+    dft4<INV>(e0, e1, e2, e3);
+    dft4<INV>(o0, o1, o2, o3);
+    o1 = mul_w16<INV, 2>(o1);
+    o2 = mul_w16<INV, 4>(o2);
+    o3 = mul_w16<INV, 6>(o3);
+    a[0] = cadd(e0, o0); a[4] = csub(e0, o0);
+    a[1] = cadd(e1, o1); a[5] = csub(e1, o1);
+    a[2] = cadd(e2, o2); a[6] = csub(e2, o2);
+    a[3] = cadd(e3, o3); a[7] = csub(e3, o3);
+}
+
+// 16 = 4 x 4: n = 4 n1 + n2, k = k1 + 4 k2.
+template <bool INV> __device__ __forceinline__ void dft16(float2 (&a)[16]) {
+    // length-4 DFTs over n1 for each n2 (in place: a[n2 + 4 k1] holds Y[n2][k1])
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) dft4<INV>(a[n2], a[n2 + 4], a[n2 + 8], a[n2 + 12]);
+    // twiddles W16^(n2 k1)
+    a[5] = mul_w16<INV, 1>(a[5]);  a[9] = mul_w16<INV, 2>(a[9]);   a[13] = mul_w16<INV, 3>(a[13]);
+    a[6] = mul_w16<INV, 2>(a[6]);  a[10] = mul_w16<INV, 4>(a[10]); a[14] = mul_w16<INV, 6>(a[14]);
+    a[7] = mul_w16<INV, 3>(a[7]);  a[11] = mul_w16<INV, 6>(a[11]); a[15] = mul_w16<INV, 9>(a[15]);
+    // length-4 DFTs over n2 for each k1: inputs a[4 k1 + n2], outputs X[k1 + 4 k2]
+    float2 y[16];
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) {
+        // element (n2, k1) sits at a[n2 + 4 k1]
+        float2 b0 = a[4 * k1], b1 = a[1 + 4 * k1], b2 = a[2 + 4 * k1], b3 = a[3 + 4 * k1];
+        dft4<INV>(b0, b1, b2, b3);
+        y[k1] = b0; y[k1 + 4] = b1; y[k1 + 8] = b2; y[k1 + 12] = b3;
+    }
+#pragma unroll
+    for (int i = 0; i < 16; ++i) a[i] = y[i];
+}
+
+template <int R, bool INV> __device__ __forceinline__ void dftR(float2 (&a)[R]) {
+    if constexpr (R == 2) dft2<INV>(a[0], a[1]);
+    else if constexpr (R == 4) dft4<INV>(a[0], a[1], a[2], a[3]);
+    else if constexpr (R == 8) dft8<INV>(a);
+    else if constexpr (R == 16) dft16<INV>(a);
+}
+
+// ------------------------------------------------------------------ two-stage Stockham FFT
+// An N-point transform (N = 16 * R2, R2 in {2, 4, 8, 16}) is carried by T = N/16 threads;
+// thread t holds v[e] = x[t + T e], e = 0..15, and receives X[t + T e] (unnormalised DFT).
+// Stage 1 is a radix-16 butterfly on the registers; its outputs go to shared memory at
+// positions 16 t + r; stage 2 is radix R2 with twiddles W_N^{r j} read from `tw`
+// (tw[r * 16 + j] = exp(-2 pi i r j / N), conjugated for INV) and lands back in registers.
+// `idx(pos)` maps a position of this transform to its shared-memory slot.  One
+// __syncthreads() separates the two stages; callers alternate two buffers between
+// consecutive transforms so that no second barrier is needed.
+template <int N, bool INV, class Idx>
+__device__ __forceinline__ void fft_2stage(float2 (&v)[16], int t, float2* buf, Idx idx,
+                                           const float2* tw) {
+    constexpr int R2 = N / 16;
+    constexpr int T = N / 16;
+    constexpr int BF = 16 / R2;  // stage-2 butterflies per thread
+    dft16<INV>(v);
+#pragma unroll
+    for (int r = 0; r < 16; ++r) buf[idx(16 * t + r)] = v[r];
+    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < BF; ++m) {
+        const int j = t + T * m;
+        float2 a[R2];
+#pragma unroll
+        for (int r = 0; r < R2; ++r) a[r] = buf[idx(j + 16 * r)];
+#pragma unroll
+        for (int r = 1; r < R2; ++r) {
+            float2 w = tw[r * 16 + j];
+            if (INV) w.y = -w.y;
+            a[r] = cmul(a[r], w);
+        }
+        dftR<R2, INV>(a);
+#pragma unroll
+        for (int r = 0; r < R2; ++r) v[m + r * BF] = a[r];
+    }
+}
+
+// ------------------------------------------------------------------ reductions
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sum K doubles over the block in a fixed order; result valid in thread 0.
+template <int K>
+__device__ __forceinline__ void block_sum(double (&v)[K], double* scratch /* >= 32*K */) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] = warp_sum(v[k]);
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < K; ++k) scratch[wid * K + k] = v[k];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            double s = 0.0;
+            for (int w = 0; w < nw; ++w) s += scratch[w * K + k];
+            v[k] = s;
+        }
+    }
+}
+
+// Cross-CTA reduction without a second launch: every CTA of slice `b` stores its block sums
+// into part[(b * nparts + blockIdx.x) * K + k]; the last CTA to arrive (atomic ticket) sums all
+// parts of the slice in index order and returns true with the totals in `tot` (thread 0).
+// The ticket counter is reset by the last CTA, so the same counter serves the next launch.
+template <int K>
+__device__ __forceinline__ bool last_block_total(double (&v)[K], double* part, int nparts, int slot,
+                                                 unsigned* counter, double (&tot)[K], double* scratch,
+                                                 int* flag_smem) {
+    block_sum<K>(v, scratch);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) part[(size_t)slot * K + k] = v[k];
+        __threadfence();
+        const unsigned ticket = atomicAdd(counter, 1u);
+        *flag_smem = (ticket == (unsigned)nparts - 1u);
+    }
+    __syncthreads();
+    const bool last = *flag_smem != 0;
+    if (last && threadIdx.x == 0) {
+        __threadfence();
+        const double* base = part + (size_t)(slot - (slot % nparts)) * K;
+#pragma unroll
+        for (int k = 0; k < K; ++k) tot[k] = 0.0;
+        for (int i = 0; i < nparts; ++i)
+#pragma unroll
+            for (int k = 0; k < K; ++k) tot[k] += __ldcg(base + (size_t)i * K + k);
+        *counter = 0u;
+    }
+    return last;
+}
+
+}  // namespace sb

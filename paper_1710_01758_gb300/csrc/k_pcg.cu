@@ -1,0 +1,597 @@
+// Kernels of one preconditioned-CG iteration (Theory, "Complexity": one application of A and
+// one of M^{-1} per iteration) on a batch of slices.
+//
+//  k_apply_A      q = A p.  Readout-axis shortcut: with a mask constant along x,
+//                 F^H R F = (F_y^H R_y F_y) (x) I_x, so the data term needs only length-ny DFTs
+//                 along y.  One CTA owns TX full columns of one slice and loops over the
+//                 coils: S_c p -> DFT_y -> mask -> IDFT_y -> conj(S_c) . -> sum, then adds the
+//                 periodic TV stencil lambda D^H D p and gamma p, stores q and Re(p^H q).
+//  k_row_fwd      r -= alpha q, ||r||^2, then the DFT along x of r (first half of M^{-1}).
+//  k_col_precond  DFT along y, scale by 1/(k N), inverse DFT along y (middle of M^{-1});
+//                 rho = r^H M^{-1} r = sum |DFT2 r|^2 / (N k) is accumulated in k-space.
+//  k_row_inv      inverse DFT along x gives z; x += alpha p, p = z + beta p.
+//  k_vec_plain    the same CG updates without a preconditioner (z = r).
+// FP64 holds every CG scalar; vectors are complex64.  Cross-CTA sums use the last-CTA
+// pattern (common.cuh), so a CG iteration needs no extra scalar launches and no host sync.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace sb {
+namespace {
+
+constexpr int TX = 16;  // columns per CTA in column kernels
+constexpr int RY = 16;  // rows per CTA in row kernels
+
+struct ColIdx {
+    int col;
+    __device__ __forceinline__ int operator()(int pos) const { return pos * TX + col; }
+};
+template <int N>
+struct RowIdx {
+    int row;
+    __device__ __forceinline__ int operator()(int pos) const {
+        return row * (N + N / 16) + pos + (pos >> 4);
+    }
+};
+
+// ------------------------------------------------------------------------------ q = A p
+template <int NY, bool PCG>
+__global__ void __launch_bounds__(TX * NY / 16)
+k_apply_A(const float2* __restrict__ p, float2* __restrict__ q, const float2* __restrict__ sens,
+          const float* __restrict__ maskw, const float2* __restrict__ tw_g, int nx, int nc,
+          float mu, float lam, float gam, SliceState* st, Red red) {
+    constexpr int T = NY / 16;
+    constexpr int NT = TX * T;
+    const int b = blockIdx.y;
+    if (PCG && st[b].state != ST_ACTIVE) return;
+    extern __shared__ __align__(16) unsigned char smem[];
+    float2* buf0 = reinterpret_cast<float2*>(smem);
+    float2* buf1 = buf0 + NY * TX;
+    float2* tw = buf1 + NY * TX;
+    float2* halo = tw + NY;  // [2][NY]: columns x0-1 and x0+TX
+    float* mk = reinterpret_cast<float*>(halo + 2 * NY);
+    double* red_s = reinterpret_cast<double*>(mk + NY);
+    __shared__ int flag;
+
+    const int tid = threadIdx.x, col = tid % TX, t = tid / TX;
+    const int x0 = blockIdx.x * TX, x = x0 + col;
+    for (int i = tid; i < NY; i += NT) {
+        tw[i] = tw_g[i];
+        mk[i] = maskw[(size_t)b * NY + i];
+    }
+    const size_t img = (size_t)b * NY * nx;
+    float2 pv[16], acc[16];
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+        pv[e] = p[img + (size_t)(t + T * e) * nx + x];
+        acc[e] = make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    const ColIdx idx{col};
+    for (int c = 0; c < nc; ++c) {
+        const float2* S = sens + ((size_t)b * nc + c) * NY * nx;
+        float2 s[16], u[16];
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+            s[e] = __ldg(S + (size_t)(t + T * e) * nx + x);
+            u[e] = cmul(s[e], pv[e]);
+        }
+        fft_2stage<NY, false>(u, t, buf0, idx, tw);
+#pragma unroll
+        for (int e = 0; e < 16; ++e) u[e] = cscale(u[e], mk[t + T * e]);
+        fft_2stage<NY, true>(u, t, buf1, idx, tw);
+#pragma unroll
+        for (int e = 0; e < 16; ++e) acc[e] = cfmac(acc[e], s[e], u[e]);
+    }
+    // periodic 5-point stencil for lambda (D_x^H D_x + D_y^H D_y) p
+#pragma unroll
+    for (int e = 0; e < 16; ++e) buf0[idx(t + T * e)] = pv[e];
+    for (int i = tid; i < NY; i += NT) {
+        halo[i] = p[img + (size_t)i * nx + (x0 == 0 ? nx - 1 : x0 - 1)];
+        halo[NY + i] = p[img + (size_t)i * nx + (x0 + TX == nx ? 0 : x0 + TX)];
+    }
+    __syncthreads();
+    float dot = 0.f;
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+        const int y = t + T * e;
+        const float2 up = buf0[idx(y == 0 ? NY - 1 : y - 1)];
+        const float2 dn = buf0[idx(y == NY - 1 ? 0 : y + 1)];
+        const float2 lf = col > 0 ? buf0[idx(y) - 1] : halo[y];
+        const float2 rt = col < TX - 1 ? buf0[idx(y) + 1] : halo[NY + y];
+        const float tvx = 4.f * pv[e].x - up.x - dn.x - lf.x - rt.x;
+        const float tvy = 4.f * pv[e].y - up.y - dn.y - lf.y - rt.y;
+        float2 o;
+        o.x = fmaf(mu, acc[e].x, fmaf(lam, tvx, gam * pv[e].x));
+        o.y = fmaf(mu, acc[e].y, fmaf(lam, tvy, gam * pv[e].y));
+        q[img + (size_t)y * nx + x] = o;
+        dot = fmaf(pv[e].x, o.x, fmaf(pv[e].y, o.y, dot));
+    }
+    if constexpr (PCG) {
+        double v[1] = {(double)dot}, tot[1];
+        const int np = gridDim.x;
+        if (last_block_total<1>(v, red.part, np, b * np + blockIdx.x, red.counter + b, tot, red_s, &flag) &&
+            threadIdx.x == 0) {
+            SliceState& S = st[b];
+            const double pq = tot[0];
+            S.pq = pq;
+            if (!isfinite(pq) || !isfinite(S.rho)) {
+                S.state = ST_NONFINITE;
+            } else if (!(pq > 0.0)) {
+                S.state = ST_BREAKDOWN;
+            } else {
+                S.alpha = S.rho / pq;
+                S.iters += 1;
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------ row pass F_x
+// MODE 0: t = F_x(r), slices filtered by st if given.  MODE 1: r -= alpha q first (PCG step).
+template <int NX, int MODE>
+__global__ void __launch_bounds__(RY * NX / 16)
+k_row_fwd(float2* __restrict__ r, const float2* __restrict__ q, float2* __restrict__ tout,
+          const float2* __restrict__ tw_g, int ny, SliceState* st, double tol2, Red red) {
+    constexpr int T = NX / 16;
+    constexpr int NT = RY * T;
+    const int b = blockIdx.y;
+    if (st != nullptr && st[b].state != ST_ACTIVE) return;
+    extern __shared__ __align__(16) unsigned char smem[];
+    float2* buf = reinterpret_cast<float2*>(smem);
+    float2* tw = buf + RY * (NX + NX / 16);
+    double* red_s = reinterpret_cast<double*>(tw + NX);
+    __shared__ int flag;
+    const int tid = threadIdx.x, t = tid % T, row = tid / T;
+    const int y = blockIdx.x * RY + row;
+    const size_t base = ((size_t)b * ny + y) * NX;
+    for (int i = tid; i < NX; i += NT) tw[i] = tw_g[i];
+    float2 v[16];
+    float rr = 0.f;
+    if constexpr (MODE == 1) {
+        const float alpha = (float)st[b].alpha;
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+            const size_t i = base + t + T * e;
+            const float2 qq = q[i];
+            float2 rv = r[i];
+            rv.x = fmaf(-alpha, qq.x, rv.x);
+            rv.y = fmaf(-alpha, qq.y, rv.y);
+            r[i] = rv;
+            v[e] = rv;
+            rr += cabs2(rv);
+        }
+    } else {
+#pragma unroll
+        for (int e = 0; e < 16; ++e) v[e] = r[base + t + T * e];
+    }
+    __syncthreads();
+    fft_2stage<NX, false>(v, t, buf, RowIdx<NX>{row}, tw);
+#pragma unroll
+    for (int e = 0; e < 16; ++e) tout[base + t + T * e] = v[e];
+    if constexpr (MODE == 1) {
+        double vv[1] = {(double)rr}, tot[1];
+        const int np = gridDim.x;
+        if (last_block_total<1>(vv, red.part, np, b * np + blockIdx.x, red.counter + b, tot, red_s, &flag) &&
+            threadIdx.x == 0) {
+            SliceState& S = st[b];
+            S.rnorm2 = tot[0];
+            if (!isfinite(tot[0])) S.state = ST_NONFINITE;
+            else if (tot[0] <= tol2 * S.bnorm2) S.state = ST_FINISHING;
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------ column pass
+template <int NY, bool PCG>
+__global__ void __launch_bounds__(TX * NY / 16)
+k_col_precond(float2* __restrict__ tb, const float* __restrict__ invk, const float2* __restrict__ tw_g,
+              int nx, SliceState* st, int init, Red red) {
+    constexpr int T = NY / 16;
+    constexpr int NT = TX * T;
+    const int b = blockIdx.y;
+    if (PCG && st[b].state != ST_ACTIVE) return;
+    extern __shared__ __align__(16) unsigned char smem[];
+    float2* buf0 = reinterpret_cast<float2*>(smem);
+    float2* buf1 = buf0 + NY * TX;
+    float2* tw = buf1 + NY * TX;
+    double* red_s = reinterpret_cast<double*>(tw + NY);
+    __shared__ int flag;
+    const int tid = threadIdx.x, col = tid % TX, t = tid / TX;
+    const int x = blockIdx.x * TX + col;
+    for (int i = tid; i < NY; i += NT) tw[i] = tw_g[i];
+    const size_t img = (size_t)b * NY * nx;
+    float2 v[16];
+#pragma unroll
+    for (int e = 0; e < 16; ++e) v[e] = tb[img + (size_t)(t + T * e) * nx + x];
+    __syncthreads();
+    const ColIdx idx{col};
+    fft_2stage<NY, false>(v, t, buf0, idx, tw);
+    float rz = 0.f;
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+        const float w = __ldg(invk + img + (size_t)(t + T * e) * nx + x);
+        rz = fmaf(cabs2(v[e]), w, rz);
+        v[e] = cscale(v[e], w);
+    }
+    fft_2stage<NY, true>(v, t, buf1, idx, tw);
+#pragma unroll
+    for (int e = 0; e < 16; ++e) tb[img + (size_t)(t + T * e) * nx + x] = v[e];
+    if constexpr (PCG) {
+        double vv[1] = {(double)rz}, tot[1];
+        const int np = gridDim.x;
+        if (last_block_total<1>(vv, red.part, np, b * np + blockIdx.x, red.counter + b, tot, red_s, &flag) &&
+            threadIdx.x == 0) {
+            SliceState& S = st[b];
+            const double rho_new = tot[0];
+            if (!isfinite(rho_new)) {
+                S.state = ST_NONFINITE;
+            } else {
+                if (!init) S.beta = rho_new / S.rho;
+                S.rho = rho_new;
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------ row pass F_x^H
+// MODE 0: out = z.  MODE 1: p = z (CG start).  MODE 2: x += alpha p; p = z + beta p.
+template <int NX, int MODE>
+__global__ void __launch_bounds__(RY * NX / 16)
+k_row_inv(const float2* __restrict__ tb, float2* __restrict__ out, float2* __restrict__ x,
+          float2* __restrict__ p, const float2* __restrict__ tw_g, int ny, SliceState* st, Red red) {
+    constexpr int T = NX / 16;
+    constexpr int NT = RY * T;
+    const int b = blockIdx.y;
+    const int s = (MODE == 0) ? ST_ACTIVE : st[b].state;
+    if (MODE == 1 && s != ST_ACTIVE) return;
+    if (MODE == 2 && s != ST_ACTIVE && s != ST_FINISHING) return;
+    extern __shared__ __align__(16) unsigned char smem[];
+    float2* buf = reinterpret_cast<float2*>(smem);
+    float2* tw = buf + RY * (NX + NX / 16);
+    double* red_s = reinterpret_cast<double*>(tw + NX);
+    __shared__ int flag;
+    const int tid = threadIdx.x, t = tid % T, row = tid / T;
+    const int y = blockIdx.x * RY + row;
+    const size_t base = ((size_t)b * ny + y) * NX;
+    if (MODE == 2 && s == ST_FINISHING) {
+        // last step of a converged slice: x += alpha p; then mark it done
+        const float alpha = (float)st[b].alpha;
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+            const size_t i = base + t + T * e;
+            const float2 pp = p[i];
+            float2 xv = x[i];
+            xv.x = fmaf(alpha, pp.x, xv.x);
+            xv.y = fmaf(alpha, pp.y, xv.y);
+            x[i] = xv;
+        }
+        double vv[1] = {0.0}, tot[1];
+        const int np = gridDim.x;
+        if (last_block_total<1>(vv, red.part, np, b * np + blockIdx.x, red.counter + b, tot, red_s, &flag) &&
+            threadIdx.x == 0)
+            st[b].state = ST_DONE;
+        return;
+    }
+    for (int i = tid; i < NX; i += NT) tw[i] = tw_g[i];
+    float2 v[16];
+#pragma unroll
+    for (int e = 0; e < 16; ++e) v[e] = tb[base + t + T * e];
+    __syncthreads();
+    fft_2stage<NX, true>(v, t, buf, RowIdx<NX>{row}, tw);
+    if constexpr (MODE == 0) {
+#pragma unroll
+        for (int e = 0; e < 16; ++e) out[base + t + T * e] = v[e];
+    } else if constexpr (MODE == 1) {
+#pragma unroll
+        for (int e = 0; e < 16; ++e) p[base + t + T * e] = v[e];
+    } else {
+        const float alpha = (float)st[b].alpha, beta = (float)st[b].beta;
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+            const size_t i = base + t + T * e;
+            const float2 pp = p[i];
+            float2 xv = x[i];
+            xv.x = fmaf(alpha, pp.x, xv.x);
+            xv.y = fmaf(alpha, pp.y, xv.y);
+            x[i] = xv;
+            p[i] = make_float2(fmaf(beta, pp.x, v[e].x), fmaf(beta, pp.y, v[e].y));
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------ plain CG
+template <int MODE>
+__global__ void __launch_bounds__(kVecThreads)
+k_vec_plain(float2* __restrict__ x, float2* __restrict__ r, float2* __restrict__ p,
+            const float2* __restrict__ q, int n, SliceState* st, double tol2, Red red) {
+    const int b = blockIdx.y;
+    const int s = st[b].state;
+    if (MODE != 2 && s != ST_ACTIVE) return;
+    if (MODE == 2 && s != ST_ACTIVE && s != ST_FINISHING) return;
+    __shared__ double red_s[32];
+    __shared__ int flag;
+    const size_t img = (size_t)b * n;
+    const int i0 = blockIdx.x * kVecThreads * kVecPerThread + threadIdx.x;
+    float rr = 0.f;
+    if constexpr (MODE == 0) {
+#pragma unroll
+        for (int k = 0; k < kVecPerThread; ++k) {
+            const int i = i0 + k * kVecThreads;
+            if (i < n) {
+                const float2 rv = r[img + i];
+                p[img + i] = rv;
+                rr += cabs2(rv);
+            }
+        }
+    } else if constexpr (MODE == 1) {
+        const float alpha = (float)st[b].alpha;
+#pragma unroll
+        for (int k = 0; k < kVecPerThread; ++k) {
+            const int i = i0 + k * kVecThreads;
+            if (i < n) {
+                const float2 qq = q[img + i];
+                float2 rv = r[img + i];
+                rv.x = fmaf(-alpha, qq.x, rv.x);
+                rv.y = fmaf(-alpha, qq.y, rv.y);
+                r[img + i] = rv;
+                rr += cabs2(rv);
+            }
+        }
+    } else {
+        const float alpha = (float)st[b].alpha, beta = (float)st[b].beta;
+        const bool upd_p = (s == ST_ACTIVE);
+#pragma unroll
+        for (int k = 0; k < kVecPerThread; ++k) {
+            const int i = i0 + k * kVecThreads;
+            if (i < n) {
+                const float2 pp = p[img + i];
+                float2 xv = x[img + i];
+                xv.x = fmaf(alpha, pp.x, xv.x);
+                xv.y = fmaf(alpha, pp.y, xv.y);
+                x[img + i] = xv;
+                if (upd_p) {
+                    const float2 rv = r[img + i];
+                    p[img + i] = make_float2(fmaf(beta, pp.x, rv.x), fmaf(beta, pp.y, rv.y));
+                }
+            }
+        }
+    }
+    double vv[1] = {(double)rr}, tot[1];
+    const int np = gridDim.x;
+    if (last_block_total<1>(vv, red.part, np, b * np + blockIdx.x, red.counter + b, tot, red_s, &flag) &&
+        threadIdx.x == 0) {
+        SliceState& S = st[b];
+        if (MODE == 0) {
+            S.rho = tot[0];
+        } else if (MODE == 1) {
+            S.rnorm2 = tot[0];
+            if (!isfinite(tot[0])) S.state = ST_NONFINITE;
+            else if (tot[0] <= tol2 * S.bnorm2) S.state = ST_FINISHING;
+            else {
+                S.beta = tot[0] / S.rho;
+                S.rho = tot[0];
+            }
+        } else if (s == ST_FINISHING) {
+            S.state = ST_DONE;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kVecThreads)
+k_resid_init(const float2* __restrict__ bvec, const float2* __restrict__ q, float2* __restrict__ r,
+             int n, SliceState* st, double tol2, Red red) {
+    const int b = blockIdx.y;
+    __shared__ double red_s[64];
+    __shared__ int flag;
+    const size_t img = (size_t)b * n;
+    const int i0 = blockIdx.x * kVecThreads * kVecPerThread + threadIdx.x;
+    float bb = 0.f, rr = 0.f;
+#pragma unroll
+    for (int k = 0; k < kVecPerThread; ++k) {
+        const int i = i0 + k * kVecThreads;
+        if (i < n) {
+            const float2 bv = bvec[img + i], qq = q[img + i];
+            const float2 rv = csub(bv, qq);
+            r[img + i] = rv;
+            bb += cabs2(bv);
+            rr += cabs2(rv);
+        }
+    }
+    double vv[2] = {(double)bb, (double)rr}, tot[2];
+    const int np = gridDim.x;
+    if (last_block_total<2>(vv, red.part, np, b * np + blockIdx.x, red.counter + b, tot, red_s, &flag) &&
+        threadIdx.x == 0) {
+        SliceState& S = st[b];
+        S.bnorm2 = tot[0];
+        S.rnorm2 = tot[1];
+        S.iters = 0;
+        S.rho = S.alpha = S.beta = S.pq = 0.0;
+        if (!isfinite(tot[0]) || !isfinite(tot[1])) S.state = ST_NONFINITE;
+        else if (tot[0] == 0.0) S.state = ST_ZERO;
+        else if (tot[1] <= tol2 * tot[0]) S.state = ST_DONE;
+        else S.state = ST_ACTIVE;
+    }
+}
+
+__global__ void __launch_bounds__(kVecThreads)
+k_zero_rhs(float2* __restrict__ x, int n, const SliceState* st) {
+    const int b = blockIdx.y;
+    if (st[b].state != ST_ZERO) return;
+    const int i0 = blockIdx.x * kVecThreads * kVecPerThread + threadIdx.x;
+#pragma unroll
+    for (int k = 0; k < kVecPerThread; ++k) {
+        const int i = i0 + k * kVecThreads;
+        if (i < n) x[(size_t)b * n + i] = make_float2(0.f, 0.f);
+    }
+}
+
+// ------------------------------------------------------------------------------ launch helpers
+template <class K>
+cudaError_t prepare(K kernel, size_t smem) {
+    if (smem > 48 * 1024) return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return cudaSuccess;
+}
+
+template <int NY>
+size_t smem_apply_A() { return (2 * NY * TX + NY + 2 * NY) * sizeof(float2) + NY * sizeof(float) + 64 * sizeof(double); }
+template <int NY>
+size_t smem_col() { return (2 * NY * TX + NY) * sizeof(float2) + 64 * sizeof(double); }
+template <int NX>
+size_t smem_row() { return (RY * (NX + NX / 16) + NX) * sizeof(float2) + 64 * sizeof(double); }
+
+template <int NY>
+cudaError_t apply_A_n(const Dims& d, const float2* p, float2* q, const float2* sens, const float* maskw,
+                      const float2* tw, float mu, float lam, float gam, SliceState* st, Red red,
+                      cudaStream_t s) {
+    const dim3 grid(d.nx / TX, d.nb), block(TX * NY / 16);
+    const size_t sm = smem_apply_A<NY>();
+    cudaError_t e;
+    if (st) {
+        if ((e = prepare(k_apply_A<NY, true>, sm)) != cudaSuccess) return e;
+        k_apply_A<NY, true><<<grid, block, sm, s>>>(p, q, sens, maskw, tw, d.nx, d.nc, mu, lam, gam, st, red);
+    } else {
+        if ((e = prepare(k_apply_A<NY, false>, sm)) != cudaSuccess) return e;
+        k_apply_A<NY, false><<<grid, block, sm, s>>>(p, q, sens, maskw, tw, d.nx, d.nc, mu, lam, gam, st, red);
+    }
+    return cudaGetLastError();
+}
+
+template <int NX>
+cudaError_t row_fwd_n(const Dims& d, int mode, float2* r, const float2* q, float2* t, const float2* tw,
+                      SliceState* st, double tol2, Red red, cudaStream_t s) {
+    const dim3 grid(d.ny / RY, d.nb), block(RY * NX / 16);
+    const size_t sm = smem_row<NX>();
+    cudaError_t e;
+    if (mode == 1) {
+        if ((e = prepare(k_row_fwd<NX, 1>, sm)) != cudaSuccess) return e;
+        k_row_fwd<NX, 1><<<grid, block, sm, s>>>(r, q, t, tw, d.ny, st, tol2, red);
+    } else {
+        if ((e = prepare(k_row_fwd<NX, 0>, sm)) != cudaSuccess) return e;
+        k_row_fwd<NX, 0><<<grid, block, sm, s>>>(r, q, t, tw, d.ny, st, tol2, red);
+    }
+    return cudaGetLastError();
+}
+
+template <int NY>
+cudaError_t col_precond_n(const Dims& d, float2* t, const float* invk, const float2* tw, SliceState* st,
+                          int init, Red red, cudaStream_t s) {
+    const dim3 grid(d.nx / TX, d.nb), block(TX * NY / 16);
+    const size_t sm = smem_col<NY>();
+    cudaError_t e;
+    if (st) {
+        if ((e = prepare(k_col_precond<NY, true>, sm)) != cudaSuccess) return e;
+        k_col_precond<NY, true><<<grid, block, sm, s>>>(t, invk, tw, d.nx, st, init, red);
+    } else {
+        if ((e = prepare(k_col_precond<NY, false>, sm)) != cudaSuccess) return e;
+        k_col_precond<NY, false><<<grid, block, sm, s>>>(t, invk, tw, d.nx, st, init, red);
+    }
+    return cudaGetLastError();
+}
+
+template <int NX>
+cudaError_t row_inv_n(const Dims& d, int mode, const float2* t, float2* out, float2* x, float2* p,
+                      const float2* tw, SliceState* st, Red red, cudaStream_t s) {
+    const dim3 grid(d.ny / RY, d.nb), block(RY * NX / 16);
+    const size_t sm = smem_row<NX>();
+    cudaError_t e;
+    switch (mode) {
+        case 0:
+            if ((e = prepare(k_row_inv<NX, 0>, sm)) != cudaSuccess) return e;
+            k_row_inv<NX, 0><<<grid, block, sm, s>>>(t, out, x, p, tw, d.ny, st, red);
+            break;
+        case 1:
+            if ((e = prepare(k_row_inv<NX, 1>, sm)) != cudaSuccess) return e;
+            k_row_inv<NX, 1><<<grid, block, sm, s>>>(t, out, x, p, tw, d.ny, st, red);
+            break;
+        default:
+            if ((e = prepare(k_row_inv<NX, 2>, sm)) != cudaSuccess) return e;
+            k_row_inv<NX, 2><<<grid, block, sm, s>>>(t, out, x, p, tw, d.ny, st, red);
+    }
+    return cudaGetLastError();
+}
+
+dim3 vec_grid(const Dims& d) {
+    const int n = d.nx * d.ny;
+    return dim3((n + kVecThreads * kVecPerThread - 1) / (kVecThreads * kVecPerThread), d.nb);
+}
+
+}  // namespace
+
+cudaError_t launch_apply_A(const Dims& d, const float2* p, float2* q, const float2* sens, const float* maskw,
+                           const float2* tw_y, float mu, float lam, float gam, SliceState* st, Red red,
+                           cudaStream_t s) {
+#define CALL(N) apply_A_n<N>(d, p, q, sens, maskw, tw_y, mu, lam, gam, st, red, s)
+    switch (d.ny) {
+        case 32: return CALL(32);
+        case 64: return CALL(64);
+        case 128: return CALL(128);
+        case 256: return CALL(256);
+        default: return cudaErrorInvalidValue;
+    }
+#undef CALL
+}
+
+cudaError_t launch_row_fwd(const Dims& d, int mode, float2* r, const float2* q, float2* t, const float2* tw_x,
+                           SliceState* st, double tol2, Red red, cudaStream_t s) {
+#define CALL(N) row_fwd_n<N>(d, mode, r, q, t, tw_x, st, tol2, red, s)
+    switch (d.nx) {
+        case 32: return CALL(32);
+        case 64: return CALL(64);
+        case 128: return CALL(128);
+        case 256: return CALL(256);
+        default: return cudaErrorInvalidValue;
+    }
+#undef CALL
+}
+
+cudaError_t launch_col_precond(const Dims& d, float2* t, const float* invk, const float2* tw_y, SliceState* st,
+                               int init, Red red, cudaStream_t s) {
+#define CALL(N) col_precond_n<N>(d, t, invk, tw_y, st, init, red, s)
+    switch (d.ny) {
+        case 32: return CALL(32);
+        case 64: return CALL(64);
+        case 128: return CALL(128);
+        case 256: return CALL(256);
+        default: return cudaErrorInvalidValue;
+    }
+#undef CALL
+}
+
+cudaError_t launch_row_inv(const Dims& d, int mode, const float2* t, float2* out, float2* x, float2* p,
+                           const float2* tw_x, SliceState* st, Red red, cudaStream_t s) {
+#define CALL(N) row_inv_n<N>(d, mode, t, out, x, p, tw_x, st, red, s)
+    switch (d.nx) {
+        case 32: return CALL(32);
+        case 64: return CALL(64);
+        case 128: return CALL(128);
+        case 256: return CALL(256);
+        default: return cudaErrorInvalidValue;
+    }
+#undef CALL
+}
+
+cudaError_t launch_vec_plain(const Dims& d, int mode, float2* x, float2* r, float2* p, const float2* q,
+                             SliceState* st, double tol2, Red red, cudaStream_t s) {
+    const int n = d.nx * d.ny;
+    const dim3 grid = vec_grid(d);
+    switch (mode) {
+        case 0: k_vec_plain<0><<<grid, kVecThreads, 0, s>>>(x, r, p, q, n, st, tol2, red); break;
+        case 1: k_vec_plain<1><<<grid, kVecThreads, 0, s>>>(x, r, p, q, n, st, tol2, red); break;
+        default: k_vec_plain<2><<<grid, kVecThreads, 0, s>>>(x, r, p, q, n, st, tol2, red);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_resid_init(const Dims& d, const float2* b, const float2* q, float2* r, SliceState* st,
+                              double tol2, Red red, cudaStream_t s) {
+    k_resid_init<<<vec_grid(d), kVecThreads, 0, s>>>(b, q, r, d.nx * d.ny, st, tol2, red);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_zero_rhs_slices(const Dims& d, float2* x, SliceState* st, cudaStream_t s) {
+    k_zero_rhs<<<vec_grid(d), kVecThreads, 0, s>>>(x, d.nx * d.ny, st);
+    return cudaGetLastError();
+}
+
+}  // namespace sb

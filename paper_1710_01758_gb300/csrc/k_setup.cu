@@ -1,0 +1,235 @@
+// Once-per-plan kernels: mask analysis and the construction of k (Eq. Kdiag).
+//
+// k_c follows "Efficient Implementation of the Preconditioner" (Eq. diagonalelements): the
+// diagonal of sum_i C_i^H R C_i, C_i = F S_i F^H BCCB, is the circular correlation
+//   k_c[kappa] = sum_l r[l] g[l - kappa],   g = sum_i |DFT2(s_i)|^2 / N^2,
+// evaluated as k_c = IDFT2( DFT2(r) conj(DFT2(g)) ) / N with unnormalised transforms.  k_d is
+// the DFT of the first row of D_x^H D_x + D_y^H D_y, 4 - 2 cos(2 pi kx/nx) - 2 cos(2 pi ky/ny),
+// and k_w = 1.  The generic row / column FFT kernels here reuse the register-resident Stockham
+// transform of common.cuh.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace sb {
+namespace {
+
+constexpr int TX = 16;
+constexpr int RY = 16;
+
+struct ColIdx {
+    int col;
+    __device__ __forceinline__ int operator()(int pos) const { return pos * TX + col; }
+};
+template <int N>
+struct RowIdx {
+    int row;
+    __device__ __forceinline__ int operator()(int pos) const {
+        return row * (N + N / 16) + pos + (pos >> 4);
+    }
+};
+
+__global__ void k_mask_lines(const uint8_t* __restrict__ mask, int nx, int* line_val, int* line_uniform) {
+    // one CTA per (slice, line): blockIdx.x = line, blockIdx.y = slice
+    const size_t row = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
+    const uint8_t* m = mask + row * nx;
+    const int v0 = m[0] != 0;
+    int diff = 0;
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) diff |= ((m[i] != 0) != v0);
+    diff = __syncthreads_or(diff);
+    if (threadIdx.x == 0) {
+        line_val[row] = v0;
+        line_uniform[row] = !diff;
+    }
+}
+
+template <int NX, bool INV>
+__global__ void __launch_bounds__(RY * NX / 16)
+k_fft_rows(float2* __restrict__ data, int nrows_total, const float2* __restrict__ tw_g) {
+    constexpr int T = NX / 16;
+    constexpr int NT = RY * T;
+    extern __shared__ __align__(16) unsigned char smem[];
+    float2* buf = reinterpret_cast<float2*>(smem);
+    float2* tw = buf + RY * (NX + NX / 16);
+    const int tid = threadIdx.x, t = tid % T, row = tid / T;
+    const int grow = blockIdx.x * RY + row;
+    for (int i = tid; i < NX; i += NT) tw[i] = tw_g[i];
+    float2 v[16];
+    const bool ok = grow < nrows_total;
+    const size_t base = (size_t)(ok ? grow : 0) * NX;
+#pragma unroll
+    for (int e = 0; e < 16; ++e) v[e] = data[base + t + T * e];
+    __syncthreads();
+    fft_2stage<NX, INV>(v, t, buf, RowIdx<NX>{row}, tw);
+    if (ok)
+#pragma unroll
+        for (int e = 0; e < 16; ++e) data[base + t + T * e] = v[e];
+}
+
+template <int NY, bool INV>
+__global__ void __launch_bounds__(TX * NY / 16)
+k_fft_cols(float2* __restrict__ data, int nx, const float2* __restrict__ tw_g) {
+    constexpr int T = NY / 16;
+    constexpr int NT = TX * T;
+    extern __shared__ __align__(16) unsigned char smem[];
+    float2* buf = reinterpret_cast<float2*>(smem);
+    float2* tw = buf + NY * TX;
+    const int tid = threadIdx.x, col = tid % TX, t = tid / TX;
+    const int x = blockIdx.x * TX + col;
+    for (int i = tid; i < NY; i += NT) tw[i] = tw_g[i];
+    const size_t img = (size_t)blockIdx.y * NY * nx;
+    float2 v[16];
+#pragma unroll
+    for (int e = 0; e < 16; ++e) v[e] = data[img + (size_t)(t + T * e) * nx + x];
+    __syncthreads();
+    fft_2stage<NY, INV>(v, t, buf, ColIdx{col}, tw);
+#pragma unroll
+    for (int e = 0; e < 16; ++e) data[img + (size_t)(t + T * e) * nx + x] = v[e];
+}
+
+__global__ void k_coil_power(const float2* __restrict__ spec, float2* __restrict__ g, int n, int nc, double inv_n2) {
+    const int b = blockIdx.y;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double acc = 0.0;
+        for (int c = 0; c < nc; ++c) {
+            const float2 v = spec[((size_t)b * nc + c) * n + i];
+            acc += (double)v.x * v.x + (double)v.y * v.y;
+        }
+        g[(size_t)b * n + i] = make_float2((float)(acc * inv_n2), 0.f);
+    }
+}
+
+__global__ void k_mask_to_complex(const uint8_t* __restrict__ mask, float2* __restrict__ out, size_t n) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        out[i] = make_float2(mask[i] ? 1.f : 0.f, 0.f);
+}
+
+__global__ void k_mul_conj(float2* __restrict__ R, const float2* __restrict__ G, size_t n) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        R[i] = cmul(R[i], make_float2(G[i].x, -G[i].y));
+}
+
+// k = mu kc + lam kd + gam (first pass) and its per-slice maximum (non-negative floats compare
+// as integers)
+__global__ void k_form_k(const float2* __restrict__ kc_raw, int nx, int ny, float mu, float lam, float gam,
+                         float inv_n, float* __restrict__ k, unsigned* __restrict__ kmax) {
+    const int b = blockIdx.y;
+    const int n = nx * ny;
+    float local = 0.f;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int kx = i % nx, ky = i / nx;
+        const float kd = 4.f - 2.f * cospif(2.f * kx / nx) - 2.f * cospif(2.f * ky / ny);
+        const float kc = kc_raw[(size_t)b * n + i].x * inv_n;
+        const float v = fmaf(mu, kc, fmaf(lam, kd, gam));
+        k[(size_t)b * n + i] = v;
+        local = fmaxf(local, v);
+    }
+    atomicMax(kmax + b, __float_as_uint(fmaxf(local, 0.f)));
+}
+
+// clamp k below at 1e-12 max(k) and store 1/(k N), the scale that turns the unnormalised
+// DFT pair of the preconditioner into F^H diag(k)^{-1} F
+__global__ void k_clamp_invert(float* __restrict__ k, float* __restrict__ invk, int n, const unsigned* __restrict__ kmax) {
+    const int b = blockIdx.y;
+    const float floor_v = 1e-12f * __uint_as_float(kmax[b]);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const float v = fmaxf(k[(size_t)b * n + i], floor_v);
+        k[(size_t)b * n + i] = v;
+        invk[(size_t)b * n + i] = 1.f / (v * (float)n);
+    }
+}
+
+template <int NX>
+cudaError_t fft_rows_n(int ny, int nimg, float2* data, const float2* tw, bool inv, cudaStream_t s) {
+    const int rows = ny * nimg;
+    const dim3 grid((rows + RY - 1) / RY), block(RY * NX / 16);
+    const size_t sm = (RY * (NX + NX / 16) + NX) * sizeof(float2);
+    cudaError_t e;
+    if (inv) {
+        if (sm > 48 * 1024 && (e = cudaFuncSetAttribute(k_fft_rows<NX, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)) != cudaSuccess) return e;
+        k_fft_rows<NX, true><<<grid, block, sm, s>>>(data, rows, tw);
+    } else {
+        if (sm > 48 * 1024 && (e = cudaFuncSetAttribute(k_fft_rows<NX, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)) != cudaSuccess) return e;
+        k_fft_rows<NX, false><<<grid, block, sm, s>>>(data, rows, tw);
+    }
+    return cudaGetLastError();
+}
+
+template <int NY>
+cudaError_t fft_cols_n(int nx, int nimg, float2* data, const float2* tw, bool inv, cudaStream_t s) {
+    const dim3 grid(nx / TX, nimg), block(TX * NY / 16);
+    const size_t sm = (NY * TX + NY) * sizeof(float2);
+    cudaError_t e;
+    if (inv) {
+        if (sm > 48 * 1024 && (e = cudaFuncSetAttribute(k_fft_cols<NY, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)) != cudaSuccess) return e;
+        k_fft_cols<NY, true><<<grid, block, sm, s>>>(data, nx, tw);
+    } else {
+        if (sm > 48 * 1024 && (e = cudaFuncSetAttribute(k_fft_cols<NY, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)) != cudaSuccess) return e;
+        k_fft_cols<NY, false><<<grid, block, sm, s>>>(data, nx, tw);
+    }
+    return cudaGetLastError();
+}
+
+unsigned elem_blocks(size_t n) {
+    const size_t b = (n + 255) / 256;
+    return (unsigned)(b < 4096 ? b : 4096);
+}
+
+}  // namespace
+
+cudaError_t launch_mask_lines(const Dims& d, const uint8_t* mask, int* line_val, int* line_uniform, cudaStream_t s) {
+    k_mask_lines<<<dim3(d.ny, d.nb), 128, 0, s>>>(mask, d.nx, line_val, line_uniform);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fft_rows(int nx, int ny, int nimg, float2* data, const float2* tw_x, bool inv, cudaStream_t s) {
+    switch (nx) {
+        case 32: return fft_rows_n<32>(ny, nimg, data, tw_x, inv, s);
+        case 64: return fft_rows_n<64>(ny, nimg, data, tw_x, inv, s);
+        case 128: return fft_rows_n<128>(ny, nimg, data, tw_x, inv, s);
+        case 256: return fft_rows_n<256>(ny, nimg, data, tw_x, inv, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_fft_cols(int nx, int ny, int nimg, float2* data, const float2* tw_y, bool inv, cudaStream_t s) {
+    switch (ny) {
+        case 32: return fft_cols_n<32>(nx, nimg, data, tw_y, inv, s);
+        case 64: return fft_cols_n<64>(nx, nimg, data, tw_y, inv, s);
+        case 128: return fft_cols_n<128>(nx, nimg, data, tw_y, inv, s);
+        case 256: return fft_cols_n<256>(nx, nimg, data, tw_y, inv, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_coil_power(const Dims& d, const float2* data, float2* g, cudaStream_t s) {
+    const int n = d.nx * d.ny;
+    const double inv_n2 = 1.0 / ((double)n * (double)n);
+    k_coil_power<<<dim3(elem_blocks(n), d.nb), 256, 0, s>>>(data, g, n, d.nc, inv_n2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mask_to_complex(const Dims& d, const uint8_t* mask, float2* out, cudaStream_t s) {
+    const size_t n = (size_t)d.nx * d.ny * d.nb;
+    k_mask_to_complex<<<elem_blocks(n), 256, 0, s>>>(mask, out, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mul_conj(const Dims& d, float2* R, const float2* G, cudaStream_t s) {
+    const size_t n = (size_t)d.nx * d.ny * d.nb;
+    k_mul_conj<<<elem_blocks(n), 256, 0, s>>>(R, G, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finish_k(const Dims& d, const float2* kc_raw, float mu, float lam, float gam, float* k,
+                            float* invk, unsigned* kmax, cudaStream_t s) {
+    const int n = d.nx * d.ny;
+    cudaError_t e = cudaMemsetAsync(kmax, 0, sizeof(unsigned) * d.nb, s);
+    if (e != cudaSuccess) return e;
+    const dim3 grid(elem_blocks(n), d.nb);
+    k_form_k<<<grid, 256, 0, s>>>(kc_raw, d.nx, d.ny, mu, lam, gam, 1.f / n, k, kmax);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_clamp_invert<<<grid, 256, 0, s>>>(k, invk, n, kmax);
+    return cudaGetLastError();
+}
+
+}  // namespace sb

@@ -1,0 +1,133 @@
+// Internal interface between the C-ABI layer (sb_api.cu) and the CUDA kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sb {
+
+// Per-slice CG state; lives in device memory, one entry per slice of the batch.
+enum : int {
+    ST_ACTIVE = 0,     // iterating
+    ST_FINISHING = 1,  // tolerance met by the residual update of this iteration: apply x += a p
+    ST_DONE = 2,       // converged
+    ST_BREAKDOWN = 3,  // Re(p^H A p) <= 0
+    ST_NONFINITE = 4,  // NaN / Inf in a CG scalar
+    ST_ZERO = 5,       // ||b|| = 0: the solution is x = 0
+};
+
+struct SliceState {
+    double rho;     // r^H z of the current iterate
+    double alpha;   // step length of the current iteration
+    double beta;    // direction update of the current iteration
+    double bnorm2;  // ||b||^2
+    double rnorm2;  // ||r||^2 after the latest residual update
+    double pq;      // Re(p^H A p) of the current iteration
+    int state;
+    int iters;      // A applications since the initial residual
+};
+
+struct Dims {
+    int nx, ny, nc, nb;
+};
+
+// Workspace of the cross-CTA reductions: part[nb][maxparts][K] doubles, counter[nb].
+struct Red {
+    double* part;
+    unsigned* counter;
+};
+
+constexpr int kMaxParts = 1024;
+constexpr int kVecThreads = 256;
+constexpr int kVecPerThread = 8;
+
+// ------------------------------------------------------------------ PCG kernels (k_pcg.cu)
+// q = A p (readout-axis shortcut of the data term); st == nullptr: plain application;
+// otherwise PCG mode: skips inactive slices, accumulates Re(p^H q) and sets alpha = rho/pq.
+cudaError_t launch_apply_A(const Dims& d, const float2* p, float2* q, const float2* sens,
+                           const float* maskw, const float2* tw_y, float mu, float lam, float gam,
+                           SliceState* st, Red red, cudaStream_t s);
+
+// Row pass of M^{-1}: mode 0 = t = F_x(in) (no CG work); mode 1 = PCG update r -= alpha q,
+// ||r||^2, convergence test, t = F_x(r).
+cudaError_t launch_row_fwd(const Dims& d, int mode, float2* r, const float2* q, float2* t,
+                           const float2* tw_x, SliceState* st, double tol2, Red red, cudaStream_t s);
+
+// Column pass of M^{-1}: t <- F_y^H diag(invk) F_y t (in place); with st != nullptr also
+// rho_new = sum |F t|^2 invk and (init = 0) beta = rho_new / rho, rho = rho_new or
+// (init = 1) rho = rho_new.
+cudaError_t launch_col_precond(const Dims& d, float2* t, const float* invk, const float2* tw_y,
+                               SliceState* st, int init, Red red, cudaStream_t s);
+
+// Row pass back: z = F_x^H t; mode 0: out = z; mode 1 (PCG init): p = z;
+// mode 2 (PCG step): x += alpha p, p = z + beta p (FINISHING slices: x += alpha p, -> DONE).
+cudaError_t launch_row_inv(const Dims& d, int mode, const float2* t, float2* out, float2* x,
+                           float2* p, const float2* tw_x, SliceState* st, Red red, cudaStream_t s);
+
+// Preconditioner-free CG: mode 0 (init): p = r, rho = ||r||^2;
+// mode 1 (step, after q = A p): r -= alpha q, ||r||^2 test, beta = ||r||^2 / rho;
+// mode 2 (step): x += alpha p, p = r + beta p.
+cudaError_t launch_vec_plain(const Dims& d, int mode, float2* x, float2* r, float2* p,
+                             const float2* q, SliceState* st, double tol2, Red red, cudaStream_t s);
+
+// r = b - q, ||b||^2, ||r||^2, initial convergence test and state.
+cudaError_t launch_resid_init(const Dims& d, const float2* b, const float2* q, float2* r,
+                              SliceState* st, double tol2, Red red, cudaStream_t s);
+
+// x = 0 on slices whose ||b|| = 0, state -> DONE.
+cudaError_t launch_zero_rhs_slices(const Dims& d, float2* x, SliceState* st, cudaStream_t s);
+
+// ------------------------------------------------------------------ set-up kernels (k_setup.cu)
+// Per slice and phase-encode line: flag whether the mask is constant along x and its value.
+cudaError_t launch_mask_lines(const Dims& d, const uint8_t* mask, int* line_val, int* line_uniform,
+                              cudaStream_t s);
+// Generic batched unnormalised FFT of complex rows (along x) or columns (along y) of
+// [nbatch_images][ny][nx] arrays, in place; inv selects the sign.
+cudaError_t launch_fft_rows(int nx, int ny, int nimg, float2* data, const float2* tw_x, bool inv,
+                            cudaStream_t s);
+cudaError_t launch_fft_cols(int nx, int ny, int nimg, float2* data, const float2* tw_y, bool inv,
+                            cudaStream_t s);
+// g[b] = sum_c |data[b][c]|^2 / N^2 (data: [nb][nc][N], the DFTs of the sensitivities);
+// out as complex (imaginary part 0) for the next FFT.
+cudaError_t launch_coil_power(const Dims& d, const float2* data, float2* g, cudaStream_t s);
+// Pack the mask as complex: out[b][i] = (mask != 0, 0).
+cudaError_t launch_mask_to_complex(const Dims& d, const uint8_t* mask, float2* out, cudaStream_t s);
+// prod[b][i] = R[b][i] * conj(G[b][i])  (the spectra of r and g), in place in R.
+cudaError_t launch_mul_conj(const Dims& d, float2* R, const float2* G, cudaStream_t s);
+// k = mu Re(kc)/N + lam k_d + gam, clamped; invk = 1 / (k N).
+// kmax: nb words of scratch.
+cudaError_t launch_finish_k(const Dims& d, const float2* kc_unscaled, float mu, float lam,
+                            float gam, float* k, float* invk, unsigned* kmax, cudaStream_t s);
+
+// ------------------------------------------------------------------ Split Bregman (k_sb.cu)
+struct SbFields {
+    const float2* sens;
+    const float* maskw;   // [nb][ny]: 1/ny on sampled lines, 0 elsewhere
+    const int* slot;      // [nb][ny]: compact index of a sampled line, -1 elsewhere
+    float2* yt;           // [nb][nc][ms][nx]: F_x^H y^[j] on sampled lines
+    const float2* yt1;    // [nb][nc][ms][nx]: F_x^H y^[1]
+    int ms;               // slots per slice
+    const float2* bx;     // Bregman variables b_x, b_y before this update (read)
+    const float2* by;
+    float2* bx_new;       // ... after it (written; the caller swaps the two buffers)
+    float2* by_new;
+    float2* bw;           // wavelet Bregman variable, tile-local Mallat layout, in place
+    float2* g;            // lam Dx^H(dx-bx) + lam Dy^H(dy-by) + gam W^H(dw-bw)
+};
+
+// yt1[b][c][s][:] = F_x^H y[b][c][line(s)][:] (unitary).
+cudaError_t launch_ytilde(const Dims& d, const float2* y, const int* lines, int ms, float2* yt1,
+                          const float2* tw_x, cudaStream_t s);
+// x = sqrt(sum_c |F^H y_c|^2) from yt1.
+cudaError_t launch_rss(const Dims& d, const SbFields& f, float2* x, const float2* tw_y,
+                       cudaStream_t s);
+// Right-hand side and initial residual: optional outer data update yt += yt1 - R F S x,
+// b = mu sum_c S_c^H F^H yt_c + g, r = b - A x; ||b||^2, ||r||^2, state.
+cudaError_t launch_rhs(const Dims& d, const SbFields& f, int addback, const float2* x, float2* r,
+                       const float2* tw_y, float mu, float lam, float gam, SliceState* st,
+                       double tol2, Red red, cudaStream_t s);
+// Shrink + Bregman updates (steps 6-11) and the next g.
+cudaError_t launch_sb_update(const Dims& d, const SbFields& f, const float2* x, int levels,
+                             float lam, float gam, float tau_tv, float tau_w, cudaStream_t s);
+
+}  // namespace sb

@@ -1,0 +1,487 @@
+// C-ABI layer (include/sb.h): plan object, workspace, argument checks, and the host-side
+// drivers of preconditioned CG and of Split Bregman (Algorithm 1).  Every numerical step runs
+// in the kernels of k_pcg.cu, k_setup.cu and k_sb.cu; the host only sequences launches and
+// reads the per-slice CG state back to decide when to stop.
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+#include "sb.h"
+
+using namespace sb;
+
+namespace {
+
+std::atomic<uint64_t> g_launches{0};
+
+// PCG iterations enqueued between two reads of the per-slice state
+constexpr int kPollEvery = 4;
+
+bool supported_n(int n) { return n == 32 || n == 64 || n == 128 || n == 256; }
+
+}  // namespace
+
+struct sb_plan_s {
+    sb_plan_desc d{};
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    Dims dims{};
+    size_t n = 0;  // pixels per slice
+    const float2* sens = nullptr;
+    bool have_coils = false, have_mask = false;
+    std::string err;
+
+    float2* tw_x = nullptr;
+    float2* tw_y = nullptr;
+    float* maskw = nullptr;  // [nb][ny]
+    int* slot = nullptr;     // [nb][ny]
+    int* lines = nullptr;    // [nb][ms]
+    int ms = 0;
+    float* k = nullptr;      // [nb][N]
+    float* invk = nullptr;   // [nb][N]
+    float2 *r = nullptr, *p = nullptr, *q = nullptr, *tb = nullptr;
+    float2* bx[2] = {nullptr, nullptr};
+    float2* by[2] = {nullptr, nullptr};
+    float2 *bw = nullptr, *g = nullptr;
+    float2 *yt = nullptr, *yt1 = nullptr;
+    size_t yt_elems = 0;
+    SliceState* st = nullptr;
+    SliceState* h_st = nullptr;  // pinned mirror
+    double* part = nullptr;
+    unsigned* counter = nullptr;
+    unsigned* kmax = nullptr;
+};
+
+namespace {
+
+sb_status fail(sb_plan pl, sb_status s, const std::string& msg) {
+    if (pl) pl->err = msg;
+    return s;
+}
+
+sb_status cuda_fail(sb_plan pl, const char* what, cudaError_t e) {
+    return fail(pl, SB_ERR_CUDA, std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")");
+}
+
+#define SB_CK(pl, call)                                              \
+    do {                                                             \
+        cudaError_t e_ = (call);                                     \
+        if (e_ != cudaSuccess) return cuda_fail((pl), #call, e_);    \
+    } while (0)
+
+// launch helper: counts kernels
+#define SB_LAUNCH(pl, nk, call)                                      \
+    do {                                                             \
+        cudaError_t e_ = (call);                                     \
+        if (e_ != cudaSuccess) return cuda_fail((pl), #call, e_);    \
+        g_launches.fetch_add((nk), std::memory_order_relaxed);       \
+    } while (0)
+
+template <class T>
+cudaError_t dalloc(T** p, size_t count) {
+    return cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T) + 16);
+}
+
+void dfree(void* p) {
+    if (p) cudaFree(p);
+}
+
+// tw[r * 16 + j] = exp(-2 pi i r j / n), r < n/16, j < 16 (stage-2 twiddles of fft_2stage)
+std::vector<float2> twiddles(int n) {
+    std::vector<float2> t(n);
+    for (int r = 0; r < n / 16; ++r)
+        for (int j = 0; j < 16; ++j) {
+            const double a = -2.0 * M_PI * (double)r * j / n;
+            t[r * 16 + j] = make_float2((float)std::cos(a), (float)std::sin(a));
+        }
+    return t;
+}
+
+Red red_of(sb_plan pl) { return Red{pl->part, pl->counter}; }
+
+// Sequence CG from the state left by launch_resid_init / launch_rhs (r = r0, bnorm2, state).
+// Returns the worst per-slice status; fills h_results (may be null).
+sb_status pcg_run(sb_plan pl, const sb_pcg_opts& o, float2* x, sb_pcg_result* h_results, int* iters_out,
+                  int iters_stride) {
+    const Dims& d = pl->dims;
+    cudaStream_t s = pl->stream;
+    const bool fixed = o.fixed_iters > 0;
+    const double tol2 = fixed ? -1.0 : o.tol * o.tol;
+    const bool circ = o.precond == SB_PRECOND_CIRCULANT;
+    const Red red = red_of(pl);
+    const float mu = (float)pl->d.mu, lam = (float)pl->d.lambda, gam = (float)pl->d.gamma;
+
+    SB_LAUNCH(pl, 1, launch_zero_rhs_slices(d, x, pl->st, s));
+    if (circ) {
+        SB_LAUNCH(pl, 1, launch_row_fwd(d, 0, pl->r, nullptr, pl->tb, pl->tw_x, pl->st, tol2, red, s));
+        SB_LAUNCH(pl, 1, launch_col_precond(d, pl->tb, pl->invk, pl->tw_y, pl->st, 1, red, s));
+        SB_LAUNCH(pl, 1, launch_row_inv(d, 1, pl->tb, nullptr, x, pl->p, pl->tw_x, pl->st, red, s));
+    } else {
+        SB_LAUNCH(pl, 1, launch_vec_plain(d, 0, x, pl->r, pl->p, nullptr, pl->st, tol2, red, s));
+    }
+    const int nit = fixed ? o.fixed_iters : o.maxit;
+    int it = 0;
+    while (it < nit) {
+        const int g = std::min(kPollEvery, nit - it);
+        for (int i = 0; i < g; ++i) {
+            SB_LAUNCH(pl, 1, launch_apply_A(d, pl->p, pl->q, pl->sens, pl->maskw, pl->tw_y, mu, lam, gam, pl->st, red, s));
+            if (circ) {
+                SB_LAUNCH(pl, 1, launch_row_fwd(d, 1, pl->r, pl->q, pl->tb, pl->tw_x, pl->st, tol2, red, s));
+                SB_LAUNCH(pl, 1, launch_col_precond(d, pl->tb, pl->invk, pl->tw_y, pl->st, 0, red, s));
+                SB_LAUNCH(pl, 1, launch_row_inv(d, 2, pl->tb, nullptr, x, pl->p, pl->tw_x, pl->st, red, s));
+            } else {
+                SB_LAUNCH(pl, 1, launch_vec_plain(d, 1, x, pl->r, pl->p, pl->q, pl->st, tol2, red, s));
+                SB_LAUNCH(pl, 1, launch_vec_plain(d, 2, x, pl->r, pl->p, pl->q, pl->st, tol2, red, s));
+            }
+        }
+        it += g;
+        if (!fixed || it >= nit) {
+            SB_CK(pl, cudaMemcpyAsync(pl->h_st, pl->st, sizeof(SliceState) * d.nb, cudaMemcpyDeviceToHost, s));
+            SB_CK(pl, cudaStreamSynchronize(s));
+            bool running = false;
+            for (int b = 0; b < d.nb; ++b)
+                running |= (pl->h_st[b].state == ST_ACTIVE || pl->h_st[b].state == ST_FINISHING);
+            if (!running) break;
+        }
+    }
+    sb_status worst = SB_OK;
+    for (int b = 0; b < d.nb; ++b) {
+        const SliceState& S = pl->h_st[b];
+        sb_status sl = SB_OK;
+        if (S.state == ST_BREAKDOWN) sl = SB_ERR_BREAKDOWN;
+        else if (S.state == ST_NONFINITE) sl = SB_ERR_NONFINITE;
+        else if (S.state == ST_ACTIVE && !fixed) sl = SB_ERR_NOT_CONVERGED;
+        if (worst == SB_OK) worst = sl;
+        const double rel = S.bnorm2 > 0 ? std::sqrt(S.rnorm2 / S.bnorm2) : 0.0;
+        if (h_results) {
+            h_results[b].iters = S.iters;
+            h_results[b].rel_resid = rel;
+            h_results[b].converged = (sl == SB_OK) ? 1 : 0;
+        }
+        if (iters_out) iters_out[(size_t)b * iters_stride] = S.iters;
+    }
+    if (worst == SB_ERR_NOT_CONVERGED) pl->err = "PCG reached maxit before the tolerance";
+    else if (worst != SB_OK) pl->err = std::string("PCG stopped: ") + sb_status_string(worst);
+    return worst;
+}
+
+sb_status check_ready(sb_plan pl) {
+    if (!pl) return SB_ERR_INVALID_ARG;
+    if (!pl->have_coils || !pl->have_mask) return fail(pl, SB_ERR_NOT_READY, "call sb_set_coils and sb_set_mask first");
+    return SB_OK;
+}
+
+sb_status check_opts(sb_plan pl, const sb_pcg_opts* o) {
+    if (!o) return fail(pl, SB_ERR_INVALID_ARG, "null PCG options");
+    if (o->fixed_iters < 0 || (o->fixed_iters == 0 && (o->maxit < 1 || !(o->tol >= 0.0))))
+        return fail(pl, SB_ERR_INVALID_ARG, "PCG options: need fixed_iters > 0, or maxit >= 1 and tol >= 0");
+    if (o->precond != SB_PRECOND_CIRCULANT && o->precond != SB_PRECOND_NONE)
+        return fail(pl, SB_ERR_UNSUPPORTED, "preconditioner kind not implemented");
+    return SB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* sb_status_string(sb_status s) {
+    switch (s) {
+        case SB_OK: return "SB_OK";
+        case SB_ERR_INVALID_ARG: return "SB_ERR_INVALID_ARG";
+        case SB_ERR_UNSUPPORTED: return "SB_ERR_UNSUPPORTED";
+        case SB_ERR_CUDA: return "SB_ERR_CUDA";
+        case SB_ERR_NOT_READY: return "SB_ERR_NOT_READY";
+        case SB_ERR_NONFINITE: return "SB_ERR_NONFINITE";
+        case SB_ERR_BREAKDOWN: return "SB_ERR_BREAKDOWN";
+        case SB_ERR_NOT_CONVERGED: return "SB_ERR_NOT_CONVERGED";
+        case SB_ERR_TIMEOUT: return "SB_ERR_TIMEOUT";
+    }
+    return "SB_ERR_UNKNOWN";
+}
+
+const char* sb_plan_last_error(sb_plan pl) { return pl ? pl->err.c_str() : "null plan"; }
+
+uint64_t sb_kernel_launches(void) { return g_launches.load(); }
+
+sb_status sb_plan_create(const sb_plan_desc* desc, void* cuda_stream, sb_plan* out) {
+    if (!desc || !out) return SB_ERR_INVALID_ARG;
+    *out = nullptr;
+    const sb_plan_desc& d = *desc;
+    if (d.ndim != 2 || (d.nz != 1 && d.nz != 0) || d.ncoils < 1 || d.nbatch < 1 || !(d.mu > 0.0) ||
+        !(d.lambda >= 0.0) || !(d.gamma >= 0.0) || d.wavelet_levels < 0)
+        return SB_ERR_INVALID_ARG;
+    if (!supported_n(d.nx) || !supported_n(d.ny) || d.wavelet_levels > 4 || d.prec != SB_PREC_FP32)
+        return SB_ERR_UNSUPPORTED;
+    sb_plan pl = new (std::nothrow) sb_plan_s();
+    if (!pl) return SB_ERR_INVALID_ARG;
+    pl->d = d;
+    pl->d.nz = 1;
+    pl->stream = static_cast<cudaStream_t>(cuda_stream);
+    pl->dims = Dims{d.nx, d.ny, d.ncoils, d.nbatch};
+    pl->n = (size_t)d.nx * d.ny;
+    const size_t nb = d.nbatch, n = pl->n;
+    cudaError_t e = cudaGetDevice(&pl->device);
+    auto bail = [&](const char* what) {
+        sb_status s = cuda_fail(pl, what, e);
+        fprintf(stderr, "sb_plan_create: %s\n", pl->err.c_str());
+        sb_plan_destroy(pl);
+        return s;
+    };
+    if (e != cudaSuccess) return bail("cudaGetDevice");
+#define ALLOC(ptr, count) \
+    if ((e = dalloc(&(ptr), (count))) != cudaSuccess) return bail("cudaMalloc " #ptr);
+    ALLOC(pl->tw_x, d.nx);
+    ALLOC(pl->tw_y, d.ny);
+    ALLOC(pl->maskw, nb * d.ny);
+    ALLOC(pl->slot, nb * d.ny);
+    ALLOC(pl->k, nb * n);
+    ALLOC(pl->invk, nb * n);
+    ALLOC(pl->r, nb * n);
+    ALLOC(pl->p, nb * n);
+    ALLOC(pl->q, nb * n);
+    ALLOC(pl->tb, nb * n);
+    ALLOC(pl->st, nb);
+    ALLOC(pl->part, nb * kMaxParts * 2);
+    ALLOC(pl->counter, nb);
+    ALLOC(pl->kmax, nb);
+#undef ALLOC
+    if ((e = cudaMallocHost(reinterpret_cast<void**>(&pl->h_st), sizeof(SliceState) * nb)) != cudaSuccess)
+        return bail("cudaMallocHost");
+    const std::vector<float2> tx = twiddles(d.nx), ty = twiddles(d.ny);
+    if ((e = cudaMemcpy(pl->tw_x, tx.data(), sizeof(float2) * d.nx, cudaMemcpyHostToDevice)) != cudaSuccess)
+        return bail("cudaMemcpy twiddles");
+    if ((e = cudaMemcpy(pl->tw_y, ty.data(), sizeof(float2) * d.ny, cudaMemcpyHostToDevice)) != cudaSuccess)
+        return bail("cudaMemcpy twiddles");
+    if ((e = cudaMemset(pl->counter, 0, sizeof(unsigned) * nb)) != cudaSuccess) return bail("cudaMemset");
+    if ((e = cudaMemset(pl->st, 0, sizeof(SliceState) * nb)) != cudaSuccess) return bail("cudaMemset");
+    *out = pl;
+    return SB_OK;
+}
+
+sb_status sb_plan_destroy(sb_plan pl) {
+    if (!pl) return SB_OK;
+    if (pl->stream) cudaStreamSynchronize(pl->stream);
+    else cudaDeviceSynchronize();
+    for (void* p : {(void*)pl->tw_x, (void*)pl->tw_y, (void*)pl->maskw, (void*)pl->slot, (void*)pl->lines,
+                    (void*)pl->k, (void*)pl->invk, (void*)pl->r, (void*)pl->p, (void*)pl->q, (void*)pl->tb,
+                    (void*)pl->bx[0], (void*)pl->bx[1], (void*)pl->by[0], (void*)pl->by[1], (void*)pl->bw,
+                    (void*)pl->g, (void*)pl->yt, (void*)pl->yt1, (void*)pl->st, (void*)pl->part,
+                    (void*)pl->counter, (void*)pl->kmax})
+        dfree(p);
+    if (pl->h_st) cudaFreeHost(pl->h_st);
+    delete pl;
+    return SB_OK;
+}
+
+sb_status sb_set_coils(sb_plan pl, const void* d_sens) {
+    if (!pl || !d_sens) return fail(pl, SB_ERR_INVALID_ARG, "null plan or sensitivities");
+    pl->sens = static_cast<const float2*>(d_sens);
+    pl->have_coils = true;
+    pl->have_mask = false;  // k depends on the coils: rebuilt by sb_set_mask
+    return SB_OK;
+}
+
+sb_status sb_set_mask(sb_plan pl, const uint8_t* d_mask) {
+    if (!pl || !d_mask) return fail(pl, SB_ERR_INVALID_ARG, "null plan or mask");
+    if (!pl->have_coils) return fail(pl, SB_ERR_NOT_READY, "call sb_set_coils before sb_set_mask");
+    const Dims& d = pl->dims;
+    const size_t nb = d.nb, n = pl->n;
+    cudaStream_t s = pl->stream;
+    // 1. line structure of the mask
+    int *lv = nullptr, *lu = nullptr;
+    SB_CK(pl, dalloc(&lv, nb * d.ny));
+    SB_CK(pl, dalloc(&lu, nb * d.ny));
+    SB_LAUNCH(pl, 1, launch_mask_lines(d, d_mask, lv, lu, s));
+    std::vector<int> hv(nb * d.ny), hu(nb * d.ny);
+    SB_CK(pl, cudaMemcpyAsync(hv.data(), lv, sizeof(int) * hv.size(), cudaMemcpyDeviceToHost, s));
+    SB_CK(pl, cudaMemcpyAsync(hu.data(), lu, sizeof(int) * hu.size(), cudaMemcpyDeviceToHost, s));
+    SB_CK(pl, cudaStreamSynchronize(s));
+    dfree(lv);
+    dfree(lu);
+    for (size_t i = 0; i < hu.size(); ++i)
+        if (!hu[i]) return fail(pl, SB_ERR_UNSUPPORTED, "mask varies along the readout (x) axis");
+    int ms = 1;
+    for (size_t b = 0; b < nb; ++b) {
+        int c = 0;
+        for (int y = 0; y < d.ny; ++y) c += hv[b * d.ny + y] != 0;
+        ms = std::max(ms, c);
+    }
+    std::vector<float> hw(nb * d.ny);
+    std::vector<int> hs(nb * d.ny), hl(nb * ms, -1);
+    for (size_t b = 0; b < nb; ++b) {
+        int c = 0;
+        for (int y = 0; y < d.ny; ++y) {
+            const bool on = hv[b * d.ny + y] != 0;
+            hw[b * d.ny + y] = on ? 1.0f / d.ny : 0.0f;
+            hs[b * d.ny + y] = on ? c : -1;
+            if (on) hl[b * ms + c++] = y;
+        }
+    }
+    if (ms != pl->ms) {
+        dfree(pl->lines);
+        pl->lines = nullptr;
+        SB_CK(pl, dalloc(&pl->lines, nb * ms));
+    }
+    pl->ms = ms;
+    SB_CK(pl, cudaMemcpyAsync(pl->maskw, hw.data(), sizeof(float) * hw.size(), cudaMemcpyHostToDevice, s));
+    SB_CK(pl, cudaMemcpyAsync(pl->slot, hs.data(), sizeof(int) * hs.size(), cudaMemcpyHostToDevice, s));
+    SB_CK(pl, cudaMemcpyAsync(pl->lines, hl.data(), sizeof(int) * hl.size(), cudaMemcpyHostToDevice, s));
+
+    // 2. k = mu k_c + lam k_d + gam by FFTs (Eq. Kdiag, Eq. diagonalelements)
+    float2 *spec = nullptr, *gb = nullptr, *rb = nullptr;
+    SB_CK(pl, dalloc(&spec, nb * d.nc * n));
+    SB_CK(pl, dalloc(&gb, nb * n));
+    SB_CK(pl, dalloc(&rb, nb * n));
+    const int nimg_c = d.nb * d.nc;
+    SB_CK(pl, cudaMemcpyAsync(spec, pl->sens, sizeof(float2) * nb * d.nc * n, cudaMemcpyDeviceToDevice, s));
+    SB_LAUNCH(pl, 1, launch_fft_rows(d.nx, d.ny, nimg_c, spec, pl->tw_x, false, s));
+    SB_LAUNCH(pl, 1, launch_fft_cols(d.nx, d.ny, nimg_c, spec, pl->tw_y, false, s));
+    SB_LAUNCH(pl, 1, launch_coil_power(d, spec, gb, s));
+    SB_LAUNCH(pl, 1, launch_mask_to_complex(d, d_mask, rb, s));
+    SB_LAUNCH(pl, 1, launch_fft_rows(d.nx, d.ny, d.nb, gb, pl->tw_x, false, s));
+    SB_LAUNCH(pl, 1, launch_fft_cols(d.nx, d.ny, d.nb, gb, pl->tw_y, false, s));
+    SB_LAUNCH(pl, 1, launch_fft_rows(d.nx, d.ny, d.nb, rb, pl->tw_x, false, s));
+    SB_LAUNCH(pl, 1, launch_fft_cols(d.nx, d.ny, d.nb, rb, pl->tw_y, false, s));
+    SB_LAUNCH(pl, 1, launch_mul_conj(d, rb, gb, s));
+    SB_LAUNCH(pl, 1, launch_fft_rows(d.nx, d.ny, d.nb, rb, pl->tw_x, true, s));
+    SB_LAUNCH(pl, 1, launch_fft_cols(d.nx, d.ny, d.nb, rb, pl->tw_y, true, s));
+    SB_LAUNCH(pl, 2, launch_finish_k(d, rb, (float)pl->d.mu, (float)pl->d.lambda, (float)pl->d.gamma, pl->k,
+                                     pl->invk, pl->kmax, s));
+    SB_CK(pl, cudaStreamSynchronize(s));
+    dfree(spec);
+    dfree(gb);
+    dfree(rb);
+
+    // 3. Split Bregman workspace sized by the number of sampled lines
+    const size_t yt_elems = nb * d.nc * (size_t)ms * d.nx;
+    if (yt_elems != pl->yt_elems) {
+        dfree(pl->yt);
+        dfree(pl->yt1);
+        pl->yt = pl->yt1 = nullptr;
+        SB_CK(pl, dalloc(&pl->yt, yt_elems));
+        SB_CK(pl, dalloc(&pl->yt1, yt_elems));
+        pl->yt_elems = yt_elems;
+    }
+    if (!pl->g) {
+        SB_CK(pl, dalloc(&pl->bx[0], nb * n));
+        SB_CK(pl, dalloc(&pl->bx[1], nb * n));
+        SB_CK(pl, dalloc(&pl->by[0], nb * n));
+        SB_CK(pl, dalloc(&pl->by[1], nb * n));
+        SB_CK(pl, dalloc(&pl->bw, nb * n));
+        SB_CK(pl, dalloc(&pl->g, nb * n));
+    }
+    pl->have_mask = true;
+    return SB_OK;
+}
+
+sb_status sb_get_k(sb_plan pl, float* d_k) {
+    if (sb_status s = check_ready(pl)) return s;
+    if (!d_k) return fail(pl, SB_ERR_INVALID_ARG, "null output");
+    SB_CK(pl, cudaMemcpyAsync(d_k, pl->k, sizeof(float) * pl->n * pl->dims.nb, cudaMemcpyDeviceToDevice, pl->stream));
+    return SB_OK;
+}
+
+sb_status sb_apply_A(sb_plan pl, const void* d_x, void* d_y) {
+    if (sb_status s = check_ready(pl)) return s;
+    if (!d_x || !d_y || d_x == d_y) return fail(pl, SB_ERR_INVALID_ARG, "need distinct non-null x and y");
+    SB_LAUNCH(pl, 1, launch_apply_A(pl->dims, static_cast<const float2*>(d_x), static_cast<float2*>(d_y), pl->sens,
+                                    pl->maskw, pl->tw_y, (float)pl->d.mu, (float)pl->d.lambda, (float)pl->d.gamma,
+                                    nullptr, red_of(pl), pl->stream));
+    return SB_OK;
+}
+
+sb_status sb_apply_precond(sb_plan pl, const void* d_r, void* d_z) {
+    if (sb_status s = check_ready(pl)) return s;
+    if (!d_r || !d_z) return fail(pl, SB_ERR_INVALID_ARG, "null vector");
+    const Dims& d = pl->dims;
+    const Red red = red_of(pl);
+    SB_LAUNCH(pl, 1, launch_row_fwd(d, 0, const_cast<float2*>(static_cast<const float2*>(d_r)), nullptr, pl->tb,
+                                    pl->tw_x, nullptr, 0.0, red, pl->stream));
+    SB_LAUNCH(pl, 1, launch_col_precond(d, pl->tb, pl->invk, pl->tw_y, nullptr, 0, red, pl->stream));
+    SB_LAUNCH(pl, 1, launch_row_inv(d, 0, pl->tb, static_cast<float2*>(d_z), nullptr, nullptr, pl->tw_x, nullptr,
+                                    red, pl->stream));
+    return SB_OK;
+}
+
+sb_status sb_pcg_solve(sb_plan pl, const void* d_b, void* d_x, const sb_pcg_opts* o, sb_pcg_result* h_results) {
+    if (sb_status s = check_ready(pl)) return s;
+    if (sb_status s = check_opts(pl, o)) return s;
+    if (!d_b || !d_x || d_b == d_x) return fail(pl, SB_ERR_INVALID_ARG, "need distinct non-null b and x");
+    const Dims& d = pl->dims;
+    float2* x = static_cast<float2*>(d_x);
+    const double tol2 = o->fixed_iters > 0 ? -1.0 : o->tol * o->tol;
+    SB_LAUNCH(pl, 1, launch_apply_A(d, x, pl->q, pl->sens, pl->maskw, pl->tw_y, (float)pl->d.mu,
+                                    (float)pl->d.lambda, (float)pl->d.gamma, nullptr, red_of(pl), pl->stream));
+    SB_LAUNCH(pl, 1, launch_resid_init(d, static_cast<const float2*>(d_b), pl->q, pl->r, pl->st, tol2, red_of(pl),
+                                       pl->stream));
+    return pcg_run(pl, *o, x, h_results, nullptr, 0);
+}
+
+sb_status sb_split_bregman(sb_plan pl, const void* d_y, void* d_x, const sb_sb_opts* o, sb_pcg_result* h_last) {
+    if (sb_status s = check_ready(pl)) return s;
+    if (!o || !d_y || !d_x) return fail(pl, SB_ERR_INVALID_ARG, "null argument");
+    if (o->n_outer < 1 || o->n_inner < 1) return fail(pl, SB_ERR_INVALID_ARG, "n_outer and n_inner must be >= 1");
+    if (sb_status s = check_opts(pl, &o->pcg)) return s;
+    const Dims& d = pl->dims;
+    const size_t nb = d.nb, n = pl->n;
+    cudaStream_t s = pl->stream;
+    float2* x = static_cast<float2*>(d_x);
+    const float mu = (float)pl->d.mu, lam = (float)pl->d.lambda, gam = (float)pl->d.gamma;
+    const float tau_tv = o->tau_tv > 0 ? (float)o->tau_tv : (lam > 0 ? 1.0f / lam : INFINITY);
+    const float tau_w = o->tau_w > 0 ? (float)o->tau_w : (gam > 0 ? 1.0f / gam : INFINITY);
+    const double tol2 = o->pcg.fixed_iters > 0 ? -1.0 : o->pcg.tol * o->pcg.tol;
+    const int levels = pl->d.wavelet_levels;
+    const int nsolve = o->n_outer * o->n_inner;
+
+    SB_LAUNCH(pl, 1, launch_ytilde(d, static_cast<const float2*>(d_y), pl->lines, pl->ms, pl->yt1, pl->tw_x, s));
+    SB_CK(pl, cudaMemcpyAsync(pl->yt, pl->yt1, sizeof(float2) * pl->yt_elems, cudaMemcpyDeviceToDevice, s));
+    int cur = 0;
+    SB_CK(pl, cudaMemsetAsync(pl->bx[0], 0, sizeof(float2) * nb * n, s));
+    SB_CK(pl, cudaMemsetAsync(pl->by[0], 0, sizeof(float2) * nb * n, s));
+    SB_CK(pl, cudaMemsetAsync(pl->bw, 0, sizeof(float2) * nb * n, s));
+    SB_CK(pl, cudaMemsetAsync(pl->g, 0, sizeof(float2) * nb * n, s));
+    auto fields = [&]() {
+        SbFields f;
+        f.sens = pl->sens;
+        f.maskw = pl->maskw;
+        f.slot = pl->slot;
+        f.yt = pl->yt;
+        f.yt1 = pl->yt1;
+        f.ms = pl->ms;
+        f.bx = pl->bx[cur];
+        f.by = pl->by[cur];
+        f.bx_new = pl->bx[cur ^ 1];
+        f.by_new = pl->by[cur ^ 1];
+        f.bw = pl->bw;
+        f.g = pl->g;
+        return f;
+    };
+    if (o->init_rss) SB_LAUNCH(pl, 1, launch_rss(d, fields(), x, pl->tw_y, s));
+
+    sb_status first_err = SB_OK;
+    std::vector<int> iters(nb * nsolve, 0);
+    int solve = 0;
+    for (int j = 0; j < o->n_outer; ++j) {
+        for (int k = 0; k < o->n_inner; ++k, ++solve) {
+            const int addback = (j > 0 && k == 0);
+            SB_LAUNCH(pl, 1, launch_rhs(d, fields(), addback, x, pl->r, pl->tw_y, mu, lam, gam, pl->st, tol2,
+                                        red_of(pl), s));
+            sb_status ps = pcg_run(pl, o->pcg, x, h_last, iters.data() + solve, nsolve);
+            if (ps != SB_OK && first_err == SB_OK) first_err = ps;
+            const bool last = (j == o->n_outer - 1) && (k == o->n_inner - 1);
+            if (!last) {
+                SB_LAUNCH(pl, 1, launch_sb_update(d, fields(), x, levels, lam, gam, tau_tv, tau_w, s));
+                if (lam != 0.f) cur ^= 1;
+            }
+        }
+    }
+    SB_CK(pl, cudaStreamSynchronize(s));
+    if (o->h_iters) std::memcpy(o->h_iters, iters.data(), sizeof(int) * iters.size());
+    return first_err;
+}
+
+}  // extern "C"

@@ -1,0 +1,227 @@
+"""Python binding of the C ABI in ``include/sb.h`` (ctypes; argument marshalling only).
+
+Every function here forwards to ``lib/libsbpcg.so`` with the same name.  Device arrays are
+passed as raw device pointers (``torch.Tensor.data_ptr()`` of contiguous complex64 / uint8 /
+float32 CUDA tensors); nothing is computed in Python.  If the library has not been built the
+import of this module raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "lib", "libsbpcg.so")
+
+# sb_status
+SB_OK = 0
+SB_ERR_INVALID_ARG = 1
+SB_ERR_UNSUPPORTED = 2
+SB_ERR_CUDA = 3
+SB_ERR_NOT_READY = 4
+SB_ERR_NONFINITE = 5
+SB_ERR_BREAKDOWN = 6
+SB_ERR_NOT_CONVERGED = 7
+SB_ERR_TIMEOUT = 8
+# sb_precision
+SB_PREC_FP32 = 0
+SB_PREC_SPLIT_BF16 = 1
+SB_PREC_SPLIT_FP16 = 2
+# sb_precond
+SB_PRECOND_NONE = 0
+SB_PRECOND_CIRCULANT = 1
+SB_PRECOND_JACOBI = 2
+
+
+class sb_plan_desc(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("ncoils", ctypes.c_int), ("nbatch", ctypes.c_int), ("mu", ctypes.c_double),
+                ("lambda_", ctypes.c_double), ("gamma", ctypes.c_double), ("wavelet_levels", ctypes.c_int),
+                ("prec", ctypes.c_int)]
+
+
+class sb_pcg_opts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("maxit", ctypes.c_int), ("fixed_iters", ctypes.c_int),
+                ("precond", ctypes.c_int)]
+
+
+class sb_pcg_result(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("rel_resid", ctypes.c_double), ("converged", ctypes.c_int)]
+
+
+class sb_sb_opts(ctypes.Structure):
+    _fields_ = [("n_outer", ctypes.c_int), ("n_inner", ctypes.c_int), ("pcg", sb_pcg_opts),
+                ("tau_tv", ctypes.c_double), ("tau_w", ctypes.c_double), ("init_rss", ctypes.c_int),
+                ("h_iters", ctypes.POINTER(ctypes.c_int))]
+
+
+# (name, restype, argtypes) of every exported entry point
+_P = ctypes.c_void_p
+SIGNATURES = [
+    ("sb_plan_create", ctypes.c_int, [ctypes.POINTER(sb_plan_desc), _P, ctypes.POINTER(_P)]),
+    ("sb_plan_destroy", ctypes.c_int, [_P]),
+    ("sb_set_coils", ctypes.c_int, [_P, _P]),
+    ("sb_set_mask", ctypes.c_int, [_P, _P]),
+    ("sb_get_k", ctypes.c_int, [_P, _P]),
+    ("sb_apply_A", ctypes.c_int, [_P, _P, _P]),
+    ("sb_apply_precond", ctypes.c_int, [_P, _P, _P]),
+    ("sb_pcg_solve", ctypes.c_int, [_P, _P, _P, ctypes.POINTER(sb_pcg_opts), ctypes.POINTER(sb_pcg_result)]),
+    ("sb_split_bregman", ctypes.c_int, [_P, _P, _P, ctypes.POINTER(sb_sb_opts), ctypes.POINTER(sb_pcg_result)]),
+    ("sb_status_string", ctypes.c_char_p, [ctypes.c_int]),
+    ("sb_plan_last_error", ctypes.c_char_p, [_P]),
+    ("sb_kernel_launches", ctypes.c_uint64, []),
+]
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with __graft_entry__.build() "
+                           "(the CUDA library is required; there is no fallback)")
+    lib = ctypes.CDLL(path)
+    for name, res, args in SIGNATURES:
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = load()
+
+
+class SbError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{status_string(status)}: {msg}")
+        self.status = status
+
+
+def status_string(status: int) -> str:
+    return _lib.sb_status_string(status).decode()
+
+
+def kernel_launches() -> int:
+    return int(_lib.sb_kernel_launches())
+
+
+def _check(status: int, plan=None, allow=()):
+    if status != SB_OK and status not in allow:
+        msg = _lib.sb_plan_last_error(plan).decode() if plan else ""
+        raise SbError(status, msg)
+    return status
+
+
+def plan_desc(nx, ny, ncoils, nbatch, mu, lam, gam, wavelet_levels, prec=SB_PREC_FP32) -> sb_plan_desc:
+    return sb_plan_desc(2, nx, ny, 1, ncoils, nbatch, mu, lam, gam, wavelet_levels, prec)
+
+
+def sb_plan_create(desc: sb_plan_desc, stream: int = 0) -> int:
+    out = _P()
+    _check(_lib.sb_plan_create(ctypes.byref(desc), _P(stream), ctypes.byref(out)))
+    return out.value
+
+
+def sb_plan_destroy(plan: int) -> None:
+    _check(_lib.sb_plan_destroy(_P(plan)))
+
+
+def sb_set_coils(plan: int, d_sens: int) -> None:
+    _check(_lib.sb_set_coils(_P(plan), _P(d_sens)), plan)
+
+
+def sb_set_mask(plan: int, d_mask: int) -> None:
+    _check(_lib.sb_set_mask(_P(plan), _P(d_mask)), plan)
+
+
+def sb_get_k(plan: int, d_k: int) -> None:
+    _check(_lib.sb_get_k(_P(plan), _P(d_k)), plan)
+
+
+def sb_apply_A(plan: int, d_x: int, d_y: int) -> None:
+    _check(_lib.sb_apply_A(_P(plan), _P(d_x), _P(d_y)), plan)
+
+
+def sb_apply_precond(plan: int, d_r: int, d_z: int) -> None:
+    _check(_lib.sb_apply_precond(_P(plan), _P(d_r), _P(d_z)), plan)
+
+
+def pcg_opts(tol=1e-3, maxit=200, fixed_iters=0, precond=SB_PRECOND_CIRCULANT) -> sb_pcg_opts:
+    return sb_pcg_opts(tol, maxit, fixed_iters, precond)
+
+
+def sb_pcg_solve(plan: int, d_b: int, d_x: int, opts: sb_pcg_opts, nbatch: int, allow=(SB_ERR_NOT_CONVERGED,)):
+    """Returns (status, [(iters, rel_resid, converged)] per slice)."""
+    res = (sb_pcg_result * nbatch)()
+    st = _check(_lib.sb_pcg_solve(_P(plan), _P(d_b), _P(d_x), ctypes.byref(opts), res), plan, allow)
+    return st, [(r.iters, r.rel_resid, bool(r.converged)) for r in res]
+
+
+def sb_split_bregman(plan: int, d_y: int, d_x: int, n_outer: int, n_inner: int, pcg: sb_pcg_opts, nbatch: int,
+                     tau_tv: float = 0.0, tau_w: float = 0.0, init_rss: bool = True,
+                     allow=(SB_ERR_NOT_CONVERGED,)):
+    """Returns (status, iters[nbatch][n_outer * n_inner], last results per slice)."""
+    nsolve = n_outer * n_inner
+    iters = (ctypes.c_int * (nbatch * nsolve))()
+    opts = sb_sb_opts(n_outer, n_inner, pcg, tau_tv, tau_w, 1 if init_rss else 0,
+                      ctypes.cast(iters, ctypes.POINTER(ctypes.c_int)))
+    last = (sb_pcg_result * nbatch)()
+    st = _check(_lib.sb_split_bregman(_P(plan), _P(d_y), _P(d_x), ctypes.byref(opts), last), plan, allow)
+    it = [[iters[b * nsolve + i] for i in range(nsolve)] for b in range(nbatch)]
+    return st, it, [(r.iters, r.rel_resid, bool(r.converged)) for r in last]
+
+
+class Plan:
+    """Owns an sb_plan and the device tensors it borrows (torch CUDA tensors)."""
+
+    def __init__(self, nx, ny, ncoils, nbatch, mu, lam, gam, wavelet_levels, stream=None):
+        import torch
+        self.torch = torch
+        self.nbatch = nbatch
+        self.shape = (nbatch, ny, nx)
+        s = stream if stream is not None else torch.cuda.current_stream()
+        self.stream = s
+        self.handle = sb_plan_create(plan_desc(nx, ny, ncoils, nbatch, mu, lam, gam, wavelet_levels), s.cuda_stream)
+        self._sens = None
+
+    def close(self):
+        if self.handle:
+            sb_plan_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _c64(self, t):
+        assert t.is_cuda and t.dtype == self.torch.complex64 and t.is_contiguous()
+        return t.data_ptr()
+
+    def set_coils(self, sens):
+        self._sens = sens  # borrowed by the plan: keep it alive
+        sb_set_coils(self.handle, self._c64(sens))
+
+    def set_mask(self, mask):
+        assert mask.is_cuda and mask.dtype == self.torch.uint8 and mask.is_contiguous()
+        sb_set_mask(self.handle, mask.data_ptr())
+
+    def k(self):
+        out = self.torch.empty(self.shape, dtype=self.torch.float32, device="cuda")
+        sb_get_k(self.handle, out.data_ptr())
+        return out
+
+    def apply_A(self, x, y=None):
+        y = self.torch.empty_like(x) if y is None else y
+        sb_apply_A(self.handle, self._c64(x), self._c64(y))
+        return y
+
+    def apply_precond(self, r, z=None):
+        z = self.torch.empty_like(r) if z is None else z
+        sb_apply_precond(self.handle, self._c64(r), self._c64(z))
+        return z
+
+    def pcg_solve(self, b, x, **kw):
+        return sb_pcg_solve(self.handle, self._c64(b), self._c64(x), pcg_opts(**kw), self.nbatch)
+
+    def split_bregman(self, y, x, n_outer, n_inner=1, tau_tv=0.0, tau_w=0.0, init_rss=True, **pcg_kw):
+        return sb_split_bregman(self.handle, self._c64(y), self._c64(x), n_outer, n_inner, pcg_opts(**pcg_kw),
+                                self.nbatch, tau_tv, tau_w, init_rss)

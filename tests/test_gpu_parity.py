@@ -1,0 +1,222 @@
+"""GPU parity: the CUDA library (through its C ABI) against the FP64 oracle on the same seeded
+inputs.  Tolerances: one operator application <= 1e-5 relative L2; a fixed PCG / Split Bregman
+schedule <= 1e-4 relative L2 on the image (complex64 vectors, FP64 CG scalars)."""
+import numpy as np
+import pytest
+
+from oracle import operators, pcg, precond, split_bregman as sb_oracle
+from paper_1710_01758_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+OP_TOL = 1e-5
+IMG_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def torch():
+    t = pytest.importorskip("torch")
+    if not t.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return t
+
+
+@pytest.fixture(scope="module")
+def sbm(torch):
+    from paper_1710_01758_gb300 import sb
+    return sb
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def to_dev(torch, a, dtype=None):
+    if dtype is None:
+        dtype = torch.complex64 if np.iscomplexobj(a) else torch.float32
+    return torch.from_numpy(np.ascontiguousarray(a)).to(dtype).cuda()
+
+
+def problem(nx, ny, nc, nb, seed, accel=4.0, n_centre=4):
+    rng = np.random.default_rng(seed)
+    sens = np.stack([synth.coil_maps(ny, nx, nc, rng) for _ in range(nb)])
+    mask = np.stack([synth.line_mask(ny, nx, accel, min(n_centre, int(round(ny / accel))), rng)
+                     for _ in range(nb)])
+    return sens, mask, rng
+
+
+def make_plan(sbm, torch, sens, mask, mu, lam, gam, levels=0):
+    nb, nc, ny, nx = sens.shape
+    plan = sbm.Plan(nx, ny, nc, nb, mu, lam, gam, levels)
+    s_dev = to_dev(torch, sens)
+    plan.set_coils(s_dev)
+    plan.set_mask(torch.from_numpy(mask).cuda())
+    return plan
+
+
+SHAPES = [(32, 64, 3, 2), (64, 32, 2, 3), (128, 128, 4, 1), (256, 256, 12, 1), (256, 128, 5, 2)]
+
+
+@pytest.mark.parametrize("nx,ny,nc,nb", SHAPES)
+def test_apply_A(torch, sbm, nx, ny, nc, nb):
+    sens, mask, rng = problem(nx, ny, nc, nb, seed=nx * 7 + ny + nc)
+    mu, lam, gam = 1.0, 0.05, 0.05
+    plan = make_plan(sbm, torch, sens, mask, mu, lam, gam)
+    x = synth.random_complex((nb, ny, nx), rng)
+    q = plan.apply_A(to_dev(torch, x)).cpu().numpy()
+    for b in range(nb):
+        ref = operators.apply_A(x[b], sens[b], mask[b], mu, lam, gam, 2)
+        assert rel(q[b], ref) <= OP_TOL
+
+
+@pytest.mark.parametrize("nx,ny,nc,nb", SHAPES)
+def test_k_and_precond(torch, sbm, nx, ny, nc, nb):
+    sens, mask, rng = problem(nx, ny, nc, nb, seed=nx + ny * 3 + nc)
+    mu, lam, gam = 1.0, 0.05, 0.05
+    plan = make_plan(sbm, torch, sens, mask, mu, lam, gam)
+    kg = plan.k().cpu().numpy()
+    r = synth.random_complex((nb, ny, nx), rng)
+    z = plan.apply_precond(to_dev(torch, r)).cpu().numpy()
+    for b in range(nb):
+        kref = precond.k_diag(sens[b], mask[b], mu, lam, gam, 2)
+        assert np.max(np.abs(kg[b] - kref)) <= OP_TOL * np.max(kref)
+        zref = precond.apply_precond(r[b], kref, 2)
+        assert rel(z[b], zref) <= OP_TOL
+
+
+def test_precond_in_place_and_edge_masks(torch, sbm):
+    # a single sampled line, full sampling, and one coil
+    nx = ny = 64
+    rng = np.random.default_rng(5)
+    sens = np.stack([synth.coil_maps(ny, nx, 1, rng), synth.coil_maps(ny, nx, 1, rng)])
+    mask = np.zeros((2, ny, nx), np.uint8)
+    mask[0, 3] = 1
+    mask[1] = 1
+    plan = make_plan(sbm, torch, sens, mask, 1.0, 0.1, 0.02)
+    r = synth.random_complex((2, ny, nx), rng)
+    rd = to_dev(torch, r)
+    plan.apply_precond(rd, rd)
+    x = synth.random_complex((2, ny, nx), rng)
+    q = plan.apply_A(to_dev(torch, x)).cpu().numpy()
+    for b in range(2):
+        kref = precond.k_diag(sens[b], mask[b], 1.0, 0.1, 0.02, 2)
+        assert rel(rd[b].cpu().numpy(), precond.apply_precond(r[b], kref, 2)) <= OP_TOL
+        assert rel(q[b], operators.apply_A(x[b], sens[b], mask[b], 1.0, 0.1, 0.02, 2)) <= OP_TOL
+
+
+@pytest.mark.parametrize("kind", ["circulant", "none"])
+def test_pcg_fixed_iterations(torch, sbm, kind):
+    nx, ny, nc, nb = 128, 128, 4, 2
+    sens, mask, rng = problem(nx, ny, nc, nb, seed=21)
+    mu, lam, gam = 1.0, 0.05, 0.05
+    plan = make_plan(sbm, torch, sens, mask, mu, lam, gam)
+    b = synth.random_complex((nb, ny, nx), rng)
+    x0 = synth.random_complex((nb, ny, nx), rng) * 0.1
+    xd = to_dev(torch, x0)
+    pc = sbm.SB_PRECOND_CIRCULANT if kind == "circulant" else sbm.SB_PRECOND_NONE
+    st, res = plan.pcg_solve(to_dev(torch, b), xd, fixed_iters=12, precond=pc)
+    assert st == sbm.SB_OK and all(r[0] == 12 for r in res)
+    xg = xd.cpu().numpy()
+    for i in range(nb):
+        A = lambda v: operators.apply_A(v, sens[i], mask[i], mu, lam, gam, 2)  # noqa: E731
+        k = precond.k_diag(sens[i], mask[i], mu, lam, gam, 2)
+        M = (lambda v: precond.apply_precond(v, k, 2)) if kind == "circulant" else None
+        ref = pcg.pcg(A, b[i], x0[i], M, fixed_iters=12)
+        assert rel(xg[i], ref.x) <= IMG_TOL
+
+
+@pytest.mark.parametrize("kind", ["circulant", "none"])
+def test_pcg_tolerance_iteration_counts(torch, sbm, kind):
+    nx, ny, nc, nb = 256, 256, 8, 2
+    sens, mask, rng = problem(nx, ny, nc, nb, seed=33, n_centre=16)
+    mu, lam, gam = 1e-3, 4e-3, 1e-3        # the paper's parameter set 1
+    plan = make_plan(sbm, torch, sens, mask, mu, lam, gam)
+    b = synth.random_complex((nb, ny, nx), rng)
+    xd = torch.zeros((nb, ny, nx), dtype=torch.complex64, device="cuda")
+    pc = sbm.SB_PRECOND_CIRCULANT if kind == "circulant" else sbm.SB_PRECOND_NONE
+    st, res = plan.pcg_solve(to_dev(torch, b), xd, tol=1e-3, maxit=300, precond=pc)
+    assert st == sbm.SB_OK
+    xg = xd.cpu().numpy()
+    for i in range(nb):
+        A = lambda v: operators.apply_A(v, sens[i], mask[i], mu, lam, gam, 2)  # noqa: E731
+        k = precond.k_diag(sens[i], mask[i], mu, lam, gam, 2)
+        M = (lambda v: precond.apply_precond(v, k, 2)) if kind == "circulant" else None
+        ref = pcg.pcg(A, b[i], np.zeros((ny, nx), complex), M, tol=1e-3, maxit=300)
+        assert abs(res[i][0] - ref.iters) <= 1, (res[i], ref.iters)
+        assert res[i][1] <= 1e-3 and res[i][2]
+        assert rel(xg[i], ref.x) <= 2e-3
+
+
+def test_pcg_zero_rhs_and_converged_start(torch, sbm):
+    nx = ny = 64
+    sens, mask, rng = problem(nx, ny, 2, 2, seed=3)
+    plan = make_plan(sbm, torch, sens, mask, 1.0, 0.05, 0.05)
+    b = np.zeros((2, ny, nx), complex)
+    b[1] = synth.random_complex((ny, nx), rng)
+    xd = to_dev(torch, synth.random_complex((2, ny, nx), rng))
+    st, res = plan.pcg_solve(to_dev(torch, b), xd, tol=1e-3, maxit=100)
+    assert st == sbm.SB_OK
+    assert res[0][0] == 0 and res[0][2] and not torch.any(xd[0]).item()
+    # restart from the converged solution: zero iterations
+    st, res2 = plan.pcg_solve(to_dev(torch, b), xd, tol=1e-2, maxit=100)
+    assert res2[1][0] == 0
+
+
+def run_sb_both(torch, sbm, wl, nb, seed, tau=0.0, fixed=20, levels=None, n_outer=None):
+    levels = wl.wavelet_levels if levels is None else levels
+    n_outer = wl.n_outer if n_outer is None else n_outer
+    slices = [synth.make_slice(wl, seed * 1000 + i) for i in range(nb)]
+    sens = np.stack([s.sens for s in slices])
+    mask = np.stack([s.mask for s in slices])
+    y = np.stack([s.y for s in slices])
+    plan = make_plan(sbm, torch, sens, mask, wl.mu, wl.lam, wl.gam, levels)
+    xd = torch.zeros((nb, wl.ny, wl.nx), dtype=torch.complex64, device="cuda")
+    st, iters, _ = plan.split_bregman(to_dev(torch, y), xd, n_outer, wl.n_inner, tau_tv=tau, tau_w=tau,
+                                      fixed_iters=fixed, tol=wl.pcg_tol, maxit=wl.pcg_maxit)
+    assert st == sbm.SB_OK
+    xg = xd.cpu().numpy()
+    refs = [sb_oracle.split_bregman(s.y, s.sens, s.mask, wl.mu, wl.lam, wl.gam, levels, 2, n_outer,
+                                    wl.n_inner, wl.pcg_tol, wl.pcg_maxit, fixed, "circulant",
+                                    tau if tau > 0 else None, tau if tau > 0 else None) for s in slices]
+    return xg, refs, iters
+
+
+def test_split_bregman_small_config(torch, sbm):
+    # 128x128, 4 coils, TV only, 10 SB x 20 fixed PCG iterations
+    wl = synth.SMALL_128
+    xg, refs, _ = run_sb_both(torch, sbm, wl, 1, wl.seed, fixed=wl.pcg_fixed_iters)
+    assert rel(xg[0], refs[0].x) <= IMG_TOL
+
+
+@pytest.mark.parametrize("tau", [0.0, 0.02])
+def test_split_bregman_tv_haar_active_shrink(torch, sbm, tau):
+    wl = synth.Workload("64x64 Nc6 TV+Haar", 64, 64, 6, 4.0, 8, "uniform", 1.0, 0.05, 0.05, 4, 6, 1,
+                        1e-3, 100, 0, seed=91)
+    xg, refs, _ = run_sb_both(torch, sbm, wl, 2, wl.seed, tau=tau, fixed=15)
+    for b in range(2):
+        assert rel(xg[b], refs[b].x) <= IMG_TOL
+
+
+def test_split_bregman_inner_loops_and_levels(torch, sbm):
+    wl = synth.Workload("64x32 Nc3 TV+Haar2 inner2", 32, 64, 3, 4.0, 4, "uniform", 1.0, 0.1, 0.05, 2, 3, 2,
+                        1e-3, 100, 0, seed=17)
+    xg, refs, _ = run_sb_both(torch, sbm, wl, 1, wl.seed, tau=0.03, fixed=10)
+    assert rel(xg[0], refs[0].x) <= IMG_TOL
+
+
+def test_unsupported_inputs(torch, sbm):
+    with pytest.raises(sbm.SbError) as ei:
+        sbm.Plan(48, 64, 2, 1, 1.0, 0.1, 0.1, 0)
+    assert ei.value.status == sbm.SB_ERR_UNSUPPORTED
+    nx = ny = 32
+    sens, mask, rng = problem(nx, ny, 2, 1, seed=1)
+    plan = sbm.Plan(nx, ny, 2, 1, 1.0, 0.1, 0.1, 0)
+    plan.set_coils(to_dev(torch, sens))
+    bad = mask.copy()
+    bad[0, 0, 5] ^= 1                       # breaks the line structure
+    with pytest.raises(sbm.SbError) as ei:
+        plan.set_mask(torch.from_numpy(bad).cuda())
+    assert ei.value.status == sbm.SB_ERR_UNSUPPORTED
+    with pytest.raises(sbm.SbError) as ei:  # k was not built: operators refuse
+        plan.apply_A(to_dev(torch, np.zeros((1, ny, nx), complex)))
+    assert ei.value.status == sbm.SB_ERR_NOT_READY
