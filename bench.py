@@ -1,0 +1,366 @@
+#!/usr/bin/env python
+"""Throughput of batched PI+CS reconstruction with circulant-preconditioned PCG inside Split
+Bregman (arXiv 1710.01758) on one node.
+
+Workload (one "step"): a batch of independent 256x256 slices, 12 coils each, Cartesian line
+masks at R = 4 with 24 fully sampled centre lines, TV + 4-level Haar, mu = 1, lambda = gamma =
+0.05, 20 Split Bregman iterations with PCG to relative residual 1e-3.  A step runs the whole
+hot path: k construction from the coils and mask (sb_set_mask), then Split Bregman
+(sb_split_bregman: right-hand sides, PCG solves, shrink / Bregman updates, data add-back).
+Inputs are seeded synthetic phantoms, coil maps and masks, resident in HBM before timing; the
+batch (about 0.9 GB of coil maps and k-space) is larger than L2.
+
+Metric: PCG iterations per second summed over the batch (value) and reconstructions per second;
+the dominant kernel's achieved HBM bandwidth against the measured peak; the image error against
+the FP64 oracle.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU (torchrun): each rank reconstructs its own batch (weak scaling, no collective on the
+data path); rank 0 prints one JSON line with the max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "PCG iters/s and recon/s at 256²×12 coils; HBM GB/s vs peak; err vs FP64"
+UNIT = "PCG iter/s"
+DEFAULT_BATCH = 64
+HBM_FALLBACK_GBS = 6800.0
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--batch", type=int, default=DEFAULT_BATCH)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while active."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = sorted(float(r[1]) for r in rows if r[1].replace(".", "").isdigit())
+        smax = max((float(r[2]) for r in rows if r[2].replace(".", "").isdigit()), default=None)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": smax, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def make_inputs(wl, nbatch, seed):
+    import numpy as np
+    from paper_1710_01758_gb300 import synth
+    slices = synth.make_batch(wl, nbatch, seed)
+    sens = np.ascontiguousarray(np.stack([s.sens for s in slices]).astype(np.complex64))
+    mask = np.ascontiguousarray(np.stack([s.mask for s in slices]))
+    y = np.ascontiguousarray(np.stack([s.y for s in slices]).astype(np.complex64))
+    return slices, sens, mask, y
+
+
+def oracle_recon(wl, s, n_outer=None):
+    """The FP64 oracle on one slice; returns (x, total PCG iterations, seconds)."""
+    from oracle import split_bregman as sbo
+    t0 = time.perf_counter()
+    r = sbo.split_bregman(s.y, s.sens, s.mask, wl.mu, wl.lam, wl.gam, wl.wavelet_levels, 2,
+                          wl.n_outer if n_outer is None else n_outer, wl.n_inner, wl.pcg_tol, wl.pcg_maxit)
+    return r.x, int(sum(r.iters)), time.perf_counter() - t0
+
+
+def host_threads():
+    try:
+        import threadpoolctl
+        info = threadpoolctl.threadpool_info()
+        return max([i.get("num_threads", 1) for i in info] + [1])
+    except Exception:
+        return 1
+
+
+def workload_config(wl, nbatch, extra=None):
+    cfg = {"workload": f"{nbatch} x [{wl.name}]", "nx": wl.nx, "ny": wl.ny, "ncoils": wl.ncoils,
+           "batch_slices": nbatch, "accel": wl.accel, "centre_lines": wl.n_centre, "mu": wl.mu,
+           "lambda": wl.lam, "gamma": wl.gam, "haar_levels": wl.wavelet_levels, "n_outer": wl.n_outer,
+           "n_inner": wl.n_inner, "pcg_tol": wl.pcg_tol, "precond": "circulant",
+           "l2": "inputs larger than L2 (coil maps + k-space of the batch)"}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+# --------------------------------------------------------------------------------- reference arm
+def run_reference(args):
+    """The FP64 oracle, as it stands, timed on the host cores on a bounded sample of the workload
+    (one slice, the first 4 Split Bregman iterations, per step)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from paper_1710_01758_gb300 import synth
+    wl = synth.METRIC_256
+    s = synth.make_slice(wl, wl.seed * 1000)
+    n_outer = 4
+    for _ in range(args.warmup):
+        oracle_recon(wl, s, n_outer)
+    iters, secs = 0, 0.0
+    for _ in range(args.steps):
+        _, it, t = oracle_recon(wl, s, n_outer)
+        iters += it
+        secs += t
+    value = iters / secs
+    cores = host_threads()
+    sample = f"1 slice x first {n_outer} of {wl.n_outer} Split Bregman iterations per step"
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": workload_config(wl, 1, {"sample": sample}),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------------- our arm
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_1710_01758_gb300 import build as build_mod
+    build_mod.build()
+    from paper_1710_01758_gb300 import sb, synth
+
+    wl = synth.METRIC_256
+    B = args.batch
+    t0 = time.perf_counter()
+    slices, sens_h, mask_h, y_h = make_inputs(wl, B, wl.seed + 7919 * rank)
+    log(f"[bench] rank {rank}: generated {B} slices in {time.perf_counter() - t0:.1f}s")
+    dev = torch.device("cuda", local)
+    d_sens = torch.from_numpy(sens_h).to(dev)
+    d_mask = torch.from_numpy(mask_h).to(dev)
+    d_y = torch.from_numpy(y_h).to(dev)
+    x = torch.zeros((B, wl.ny, wl.nx), dtype=torch.complex64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    plan = sb.Plan(wl.nx, wl.ny, wl.ncoils, B, wl.mu, wl.lam, wl.gam, wl.wavelet_levels, stream=stream)
+
+    def step(ys=d_y, ss=d_sens, ms=d_mask, xx=x):
+        plan.set_coils(ss)
+        plan.set_mask(ms)
+        st, iters, _ = plan.split_bregman(ys, xx, wl.n_outer, wl.n_inner, tol=wl.pcg_tol, maxit=wl.pcg_maxit)
+        if st != sb.SB_OK:
+            raise RuntimeError(f"split_bregman: {sb.status_string(st)}")
+        return int(sum(sum(i) for i in iters)), iters
+
+    for _ in range(args.warmup):
+        step()
+    plan.set_timing((1 << sb.SB_KCLASS_COUNT) - 1)
+    sampler = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    launches0 = sb.kernel_launches()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    total_iters = 0
+    iters_last = None
+    for _ in range(args.steps):
+        it, iters_last = step()
+        total_iters += it
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    launches = sb.kernel_launches() - launches0
+    clocks = sampler.stop()
+    if dist:
+        dist.barrier()
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    timing = {sb.KCLASS_NAMES[c]: plan.timing(c) for c in range(sb.SB_KCLASS_COUNT)}
+    plan.set_timing(0)
+    total_all = total_iters
+    elapsed_max = elapsed
+    if dist:
+        t = torch.tensor([elapsed, float(total_iters)], dtype=torch.float64, device=dev)
+        tmax = t.clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        elapsed_max, total_all = float(tmax[0]), int(t[1])
+    value = total_all / elapsed_max
+    recon_per_s = args.steps * B * world / elapsed_max
+
+    # dominant kernel: q = A p; algorithmic bytes per slice-iteration = p + S read, q written
+    n = wl.nx * wl.ny
+    bytes_per_slice_iter = (2 + wl.ncoils) * 8 * n
+    k1_launches, k1_ms = timing["apply_A"]
+    k1_bytes = total_iters * bytes_per_slice_iter
+    peak, peak_kind = peaks()
+    achieved = (k1_bytes / (k1_ms / 1e3) / 1e9) if k1_ms > 0 else None
+    all_ms = sum(v[1] for v in timing.values())
+    breakdown = {k: {"launches": v[0], "ms": round(v[1], 3), "share": round(v[1] / all_ms, 4) if all_ms else None}
+                 for k, v in timing.items()}
+    # whole PCG iteration (q = A p, the three preconditioner passes, vector updates) bytes
+    pcg_classes = ["apply_A", "precond_row_fwd", "precond_col", "precond_row_inv"]
+    pcg_ms = sum(timing[k][1] for k in pcg_classes)
+    bytes_pcg_iter = (2 + wl.ncoils) * 8 * n + 4 * 8 * n + (2 * 8 + 4) * n + 5 * 8 * n
+
+    # untimed diagnostics (rank 0): preconditioned vs plain CG iteration counts on a sub-batch,
+    # image error vs the FP64 oracle, the oracle's own throughput
+    extra = {}
+    if rank == 0:
+        nsub = min(8, B)
+        sub = sb.Plan(wl.nx, wl.ny, wl.ncoils, nsub, wl.mu, wl.lam, wl.gam, wl.wavelet_levels, stream=stream)
+        sub.set_coils(d_sens[:nsub].contiguous())
+        sub.set_mask(d_mask[:nsub].contiguous())
+        xs = torch.zeros((nsub, wl.ny, wl.nx), dtype=torch.complex64, device=dev)
+        _, it_plain, _ = sub.split_bregman(d_y[:nsub].contiguous(), xs, wl.n_outer, wl.n_inner, tol=wl.pcg_tol,
+                                           maxit=wl.pcg_maxit, precond=sb.SB_PRECOND_NONE)
+        sub.close()
+        it_pre = iters_last[:nsub]
+        extra["pcg_iters_per_solve"] = {
+            "circulant": round(float(np.mean(it_pre)), 3), "plain_cg": round(float(np.mean(it_plain)), 3),
+            "reduction": round(float(np.sum(it_plain)) / max(1, float(np.sum(it_pre))), 3),
+            "first_solve": [round(float(np.mean([i[0] for i in it_plain])), 2),
+                            round(float(np.mean([i[0] for i in it_pre])), 2)],
+            "slices": nsub}
+        if not args.no_cpu_baseline:
+            x_or, it_or, t_or = oracle_recon(wl, slices[0])
+            xg = x[0].cpu().numpy()
+            extra["err_vs_fp64"] = float(np.linalg.norm(xg - x_or) / np.linalg.norm(x_or))
+            extra["cpu_baseline"] = {"value": it_or / t_or, "unit": UNIT, "cores": host_threads(), "kind": "oracle",
+                                     "sample": "slice 0 of the batch, full 20-iteration Split Bregman, FP64 numpy"}
+
+    # end to end through the public API with host buffers (pinned), copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        hs = torch.from_numpy(sens_h).pin_memory()
+        hm = torch.from_numpy(mask_h).pin_memory()
+        hy = torch.from_numpy(y_h).pin_memory()
+        hx = torch.empty((B, wl.ny, wl.nx), dtype=torch.complex64).pin_memory()
+        h2d = hs.numel() * 8 + hm.numel() + hy.numel() * 8
+        d2h = hx.numel() * 8
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        e2e_iters = 0
+        for _ in range(args.steps):
+            d_sens.copy_(hs, non_blocking=True)
+            d_mask.copy_(hm, non_blocking=True)
+            d_y.copy_(hy, non_blocking=True)
+            it, _ = step()
+            e2e_iters += it
+            hx.copy_(x, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e_el = e0.elapsed_time(e1) / 1e3
+        if dist:
+            t = torch.tensor([e_el, float(e2e_iters)], dtype=torch.float64, device=dev)
+            tmax = t.clone()
+            dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+            dist.all_reduce(t, op=dist.ReduceOp.SUM)
+            e_el, e2e_iters = float(tmax[0]), int(t[1])
+        e2e = {"value": e2e_iters / e_el, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+    plan.close()
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1e3 * elapsed_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "fp32", "scalars": "fp64", "data": "synthetic",
+                "config": workload_config(wl, B, {"parallelism": f"{world} ranks x independent batches"}),
+                "recon_per_s": recon_per_s,
+                "pcg_iters_per_step": total_all / args.steps,
+                "roofline": {"bound": "hbm", "kernel": "k_apply_A (q = A p)",
+                             "achieved": achieved, "peak": peak, "unit": "GB/s",
+                             "frac": (achieved / peak) if achieved else None, "traffic": None,
+                             "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
+                             else "fallback",
+                             "algorithmic_bytes_per_slice_iter": bytes_per_slice_iter,
+                             "launches": k1_launches, "mean_launch_us": 1e3 * k1_ms / max(1, k1_launches)},
+                "pcg_iteration_gbs": (total_iters * bytes_pcg_iter / (pcg_ms / 1e3) / 1e9) if pcg_ms else None,
+                "kernel_time_breakdown": breakdown,
+                "gpu_launches": int(launches),
+                "clocks": clocks, "e2e": e2e}
+        line.update(extra)
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -148,6 +148,26 @@ const char* sb_plan_last_error(sb_plan plan);
  * kernel node they run).  Instrumentation for benchmarks. */
 uint64_t sb_kernel_launches(void);
 
+/* Kernel classes for the event timer below. */
+typedef enum {
+    SB_KCLASS_APPLY_A = 0,       /* q = A p (data term by DFTs along y, TV stencil, gamma p) */
+    SB_KCLASS_PRECOND_ROW_FWD = 1,  /* r -= alpha q, ||r||^2, DFT along x */
+    SB_KCLASS_PRECOND_COL = 2,   /* DFT along y, k^{-1}, inverse DFT along y, r^H z */
+    SB_KCLASS_PRECOND_ROW_INV = 3,  /* inverse DFT along x, x and p updates */
+    SB_KCLASS_RHS = 4,           /* Split Bregman right-hand side + initial residual */
+    SB_KCLASS_SB_UPDATE = 5,     /* shrink, Bregman updates, Haar analysis / synthesis */
+    SB_KCLASS_VEC = 6,           /* preconditioner-free CG vector updates */
+    SB_KCLASS_OTHER = 7,         /* set-up: k construction, mask analysis, y transform, RSS */
+    SB_KCLASS_COUNT = 8
+} sb_kernel_class;
+
+/* Event timer (instrumentation).  With bit c of class_mask set, the plan records a CUDA event
+ * pair on its stream around every launch of kernel class c, and accumulates the elapsed times
+ * whenever it synchronises.  sb_plan_get_timing synchronises the stream and returns the number
+ * of timed launches and their summed duration (ms) since the last sb_plan_set_timing. */
+sb_status sb_plan_set_timing(sb_plan plan, unsigned class_mask);
+sb_status sb_plan_get_timing(sb_plan plan, int kernel_class, uint64_t* launches, double* total_ms);
+
 #ifdef __cplusplus
 }
 #endif

@@ -15,11 +15,12 @@
 // pattern (common.cuh), so a CG iteration needs no extra scalar launches and no host sync.
 #include "common.cuh"
 #include "kernels.h"
+#include "tma.cuh"
 
 namespace sb {
 namespace {
 
-constexpr int TX = 16;  // columns per CTA in column kernels
+constexpr int TX = kColTile;  // columns per CTA in column kernels
 constexpr int RY = 16;  // rows per CTA in row kernels
 
 struct ColIdx {
@@ -35,26 +36,43 @@ struct RowIdx {
 };
 
 // ------------------------------------------------------------------------------ q = A p
+// The coil tiles S_c[:, x0:x0+TX] stream through a two-stage shared-memory pipeline filled by
+// TMA (one elected thread issues cp.async.bulk.tensor.2d per tile): while coil c is
+// transformed, coil c+1 is in flight.  p stays in registers for the whole coil loop.
 template <int NY, bool PCG>
-__global__ void __launch_bounds__(TX * NY / 16)
-k_apply_A(const float2* __restrict__ p, float2* __restrict__ q, const float2* __restrict__ sens,
-          const float* __restrict__ maskw, const float2* __restrict__ tw_g, int nx, int nc,
-          float mu, float lam, float gam, SliceState* st, Red red) {
+__global__ void __launch_bounds__(TX * NY / 16, 2)
+k_apply_A(const __grid_constant__ CUtensorMap smap, const float2* __restrict__ p, float2* __restrict__ q,
+          const float* __restrict__ maskw, const float2* __restrict__ tw_g, int nx, int nc, float mu, float lam,
+          float gam, SliceState* st, Red red) {
     constexpr int T = NY / 16;
     constexpr int NT = TX * T;
+    constexpr uint32_t kTileBytes = NY * TX * sizeof(float2);
     const int b = blockIdx.y;
     if (PCG && st[b].state != ST_ACTIVE) return;
-    extern __shared__ __align__(16) unsigned char smem[];
-    float2* buf0 = reinterpret_cast<float2*>(smem);
-    float2* buf1 = buf0 + NY * TX;
-    float2* tw = buf1 + NY * TX;
-    float2* halo = tw + NY;  // [2][NY]: columns x0-1 and x0+TX
+    extern __shared__ __align__(128) unsigned char smem[];
+    float2* sbuf = reinterpret_cast<float2*>(smem);  // [2][NY * TX] coil tiles (TMA destinations)
+    float2* xbuf = sbuf + 2 * NY * TX;                // [NY * TX] FFT exchange, then the p tile
+    float2* tw = xbuf + NY * TX;
+    float2* halo = tw + NY;                           // [2][NY]: columns x0-1 and x0+TX
     float* mk = reinterpret_cast<float*>(halo + 2 * NY);
     double* red_s = reinterpret_cast<double*>(mk + NY);
+    __shared__ __align__(8) uint64_t bars[2];
     __shared__ int flag;
 
     const int tid = threadIdx.x, col = tid % TX, t = tid / TX;
     const int x0 = blockIdx.x * TX, x = x0 + col;
+    if (tid == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    if (tid == 0) {
+        for (int c = 0; c < 2 && c < nc; ++c) {
+            mbar_arrive_expect_tx(&bars[c], kTileBytes);
+            tma_load_2d(sbuf + c * NY * TX, &smap, 2 * x0, (b * nc + c) * NY, &bars[c]);
+        }
+    }
     for (int i = tid; i < NY; i += NT) {
         tw[i] = tw_g[i];
         mk[i] = maskw[(size_t)b * NY + i];
@@ -69,23 +87,28 @@ k_apply_A(const float2* __restrict__ p, float2* __restrict__ q, const float2* __
     __syncthreads();
     const ColIdx idx{col};
     for (int c = 0; c < nc; ++c) {
-        const float2* S = sens + ((size_t)b * nc + c) * NY * nx;
-        float2 s[16], u[16];
+        const int stage = c & 1;
+        mbar_wait(&bars[stage], (c >> 1) & 1, red.err);
+        const float2* S = sbuf + stage * NY * TX;
+        float2 u[16];
 #pragma unroll
-        for (int e = 0; e < 16; ++e) {
-            s[e] = __ldg(S + (size_t)(t + T * e) * nx + x);
-            u[e] = cmul(s[e], pv[e]);
-        }
-        fft_2stage<NY, false>(u, t, buf0, idx, tw);
+        for (int e = 0; e < 16; ++e) u[e] = cmul(S[idx(t + T * e)], pv[e]);
+        fft_2stage<NY, false>(u, t, xbuf, idx, tw);
 #pragma unroll
         for (int e = 0; e < 16; ++e) u[e] = cscale(u[e], mk[t + T * e]);
-        fft_2stage<NY, true>(u, t, buf1, idx, tw);
+        __syncthreads();  // forward transform done with xbuf
+        fft_2stage<NY, true>(u, t, xbuf, idx, tw);
 #pragma unroll
-        for (int e = 0; e < 16; ++e) acc[e] = cfmac(acc[e], s[e], u[e]);
+        for (int e = 0; e < 16; ++e) acc[e] = cfmac(acc[e], S[idx(t + T * e)], u[e]);
+        __syncthreads();  // every thread is done with this stage's tile and with xbuf
+        if (tid == 0 && c + 2 < nc) {
+            mbar_arrive_expect_tx(&bars[stage], kTileBytes);
+            tma_load_2d(sbuf + stage * NY * TX, &smap, 2 * x0, (b * nc + c + 2) * NY, &bars[stage]);
+        }
     }
     // periodic 5-point stencil for lambda (D_x^H D_x + D_y^H D_y) p
 #pragma unroll
-    for (int e = 0; e < 16; ++e) buf0[idx(t + T * e)] = pv[e];
+    for (int e = 0; e < 16; ++e) xbuf[idx(t + T * e)] = pv[e];
     for (int i = tid; i < NY; i += NT) {
         halo[i] = p[img + (size_t)i * nx + (x0 == 0 ? nx - 1 : x0 - 1)];
         halo[NY + i] = p[img + (size_t)i * nx + (x0 + TX == nx ? 0 : x0 + TX)];
@@ -95,10 +118,10 @@ k_apply_A(const float2* __restrict__ p, float2* __restrict__ q, const float2* __
 #pragma unroll
     for (int e = 0; e < 16; ++e) {
         const int y = t + T * e;
-        const float2 up = buf0[idx(y == 0 ? NY - 1 : y - 1)];
-        const float2 dn = buf0[idx(y == NY - 1 ? 0 : y + 1)];
-        const float2 lf = col > 0 ? buf0[idx(y) - 1] : halo[y];
-        const float2 rt = col < TX - 1 ? buf0[idx(y) + 1] : halo[NY + y];
+        const float2 up = xbuf[idx(y == 0 ? NY - 1 : y - 1)];
+        const float2 dn = xbuf[idx(y == NY - 1 ? 0 : y + 1)];
+        const float2 lf = col > 0 ? xbuf[idx(y) - 1] : halo[y];
+        const float2 rt = col < TX - 1 ? xbuf[idx(y) + 1] : halo[NY + y];
         const float tvx = 4.f * pv[e].x - up.x - dn.x - lf.x - rt.x;
         const float tvy = 4.f * pv[e].y - up.y - dn.y - lf.y - rt.y;
         float2 o;
@@ -137,7 +160,7 @@ k_row_fwd(float2* __restrict__ r, const float2* __restrict__ q, float2* __restri
     constexpr int NT = RY * T;
     const int b = blockIdx.y;
     if (st != nullptr && st[b].state != ST_ACTIVE) return;
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(128) unsigned char smem[];
     float2* buf = reinterpret_cast<float2*>(smem);
     float2* tw = buf + RY * (NX + NX / 16);
     double* red_s = reinterpret_cast<double*>(tw + NX);
@@ -191,7 +214,7 @@ k_col_precond(float2* __restrict__ tb, const float* __restrict__ invk, const flo
     constexpr int NT = TX * T;
     const int b = blockIdx.y;
     if (PCG && st[b].state != ST_ACTIVE) return;
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(128) unsigned char smem[];
     float2* buf0 = reinterpret_cast<float2*>(smem);
     float2* buf1 = buf0 + NY * TX;
     float2* tw = buf1 + NY * TX;
@@ -246,7 +269,7 @@ k_row_inv(const float2* __restrict__ tb, float2* __restrict__ out, float2* __res
     const int s = (MODE == 0) ? ST_ACTIVE : st[b].state;
     if (MODE == 1 && s != ST_ACTIVE) return;
     if (MODE == 2 && s != ST_ACTIVE && s != ST_FINISHING) return;
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(128) unsigned char smem[];
     float2* buf = reinterpret_cast<float2*>(smem);
     float2* tw = buf + RY * (NX + NX / 16);
     double* red_s = reinterpret_cast<double*>(tw + NX);
@@ -434,14 +457,14 @@ cudaError_t prepare(K kernel, size_t smem) {
 }
 
 template <int NY>
-size_t smem_apply_A() { return (2 * NY * TX + NY + 2 * NY) * sizeof(float2) + NY * sizeof(float) + 64 * sizeof(double); }
+size_t smem_apply_A() { return (3 * NY * TX + NY + 2 * NY) * sizeof(float2) + NY * sizeof(float) + 64 * sizeof(double); }
 template <int NY>
 size_t smem_col() { return (2 * NY * TX + NY) * sizeof(float2) + 64 * sizeof(double); }
 template <int NX>
 size_t smem_row() { return (RY * (NX + NX / 16) + NX) * sizeof(float2) + 64 * sizeof(double); }
 
 template <int NY>
-cudaError_t apply_A_n(const Dims& d, const float2* p, float2* q, const float2* sens, const float* maskw,
+cudaError_t apply_A_n(const Dims& d, const CUtensorMap& smap, const float2* p, float2* q, const float* maskw,
                       const float2* tw, float mu, float lam, float gam, SliceState* st, Red red,
                       cudaStream_t s) {
     const dim3 grid(d.nx / TX, d.nb), block(TX * NY / 16);
@@ -449,10 +472,10 @@ cudaError_t apply_A_n(const Dims& d, const float2* p, float2* q, const float2* s
     cudaError_t e;
     if (st) {
         if ((e = prepare(k_apply_A<NY, true>, sm)) != cudaSuccess) return e;
-        k_apply_A<NY, true><<<grid, block, sm, s>>>(p, q, sens, maskw, tw, d.nx, d.nc, mu, lam, gam, st, red);
+        k_apply_A<NY, true><<<grid, block, sm, s>>>(smap, p, q, maskw, tw, d.nx, d.nc, mu, lam, gam, st, red);
     } else {
         if ((e = prepare(k_apply_A<NY, false>, sm)) != cudaSuccess) return e;
-        k_apply_A<NY, false><<<grid, block, sm, s>>>(p, q, sens, maskw, tw, d.nx, d.nc, mu, lam, gam, st, red);
+        k_apply_A<NY, false><<<grid, block, sm, s>>>(smap, p, q, maskw, tw, d.nx, d.nc, mu, lam, gam, st, red);
     }
     return cudaGetLastError();
 }
@@ -518,10 +541,10 @@ dim3 vec_grid(const Dims& d) {
 
 }  // namespace
 
-cudaError_t launch_apply_A(const Dims& d, const float2* p, float2* q, const float2* sens, const float* maskw,
+cudaError_t launch_apply_A(const Dims& d, const CUtensorMap& smap, const float2* p, float2* q, const float* maskw,
                            const float2* tw_y, float mu, float lam, float gam, SliceState* st, Red red,
                            cudaStream_t s) {
-#define CALL(N) apply_A_n<N>(d, p, q, sens, maskw, tw_y, mu, lam, gam, st, red, s)
+#define CALL(N) apply_A_n<N>(d, smap, p, q, maskw, tw_y, mu, lam, gam, st, red, s)
     switch (d.ny) {
         case 32: return CALL(32);
         case 64: return CALL(64);

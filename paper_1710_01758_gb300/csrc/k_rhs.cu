@@ -1,0 +1,201 @@
+// Right-hand side of Eq. system (step 4 of Algorithm 1) fused with the outer data update
+// (steps 12-14) and the initial PCG residual.
+//
+// Per column tile of one slice and per coil c (yt = F_x^H y on the sampled lines, see k_sb.cu):
+//   u   = R_y F_y (S_c x)                      forward DFT along y, kept on sampled lines
+//   yt  = yt + yt1 - u                         outer update (ADDBACK), written back
+//   b  += S_c^H F_y^H yt                       inverse DFT
+//   r  += S_c^H F_y^H (yt - u)                 inverse DFT: data term of b - A x
+// then b = mu b + g, r = mu r + g - lambda D^H D x - gamma x, with ||b||^2, ||r||^2 and the
+// initial convergence test in the last CTA of the slice.  The coil tile S_c and the compact
+// rows of yt and yt1 arrive by TMA into a two-stage shared-memory pipeline (coil c + 1 in
+// flight while coil c is transformed).
+#include "common.cuh"
+#include "kernels.h"
+#include "tma.cuh"
+
+namespace sb {
+namespace {
+
+constexpr int TX = kColTile;
+
+struct ColIdx {
+    int col;
+    __device__ __forceinline__ int operator()(int pos) const { return pos * TX + col; }
+};
+
+template <int NY, bool ADDBACK>
+__global__ void __launch_bounds__(TX * NY / 16, 1)
+k_rhs(const __grid_constant__ CUtensorMap smap, const __grid_constant__ CUtensorMap ymap,
+      const __grid_constant__ CUtensorMap y1map, SbFields f, int nx, int nc, const float2* __restrict__ xin,
+      float2* __restrict__ r, const float2* __restrict__ tw_g, float mu, float lam, float gam, SliceState* st,
+      double tol2, Red red) {
+    constexpr int T = NY / 16;
+    constexpr int NT = TX * T;
+    const int b = blockIdx.y;
+    const int ms = f.ms;
+    const uint32_t sbytes = NY * TX * sizeof(float2);
+    const uint32_t ybytes = ms * TX * sizeof(float2);
+    const uint32_t stage_bytes = sbytes + (ADDBACK ? 2u : 1u) * ybytes;
+    const int stage_elems = (NY + 2 * ms) * TX;
+    extern __shared__ __align__(128) unsigned char smem[];
+    float2* stages = reinterpret_cast<float2*>(smem);  // [2][S tile | yt rows | yt1 rows]
+    float2* xbuf = stages + 2 * stage_elems;            // FFT exchange, then the x tile
+    float2* tw = xbuf + NY * TX;
+    float2* halo = tw + NY;
+    int* sl = reinterpret_cast<int*>(halo + 2 * NY);
+    double* red_s = reinterpret_cast<double*>(sl + NY);
+    __shared__ __align__(8) uint64_t bars[2];
+    __shared__ int flag;
+
+    const int tid = threadIdx.x, col = tid % TX, t = tid / TX;
+    const int x0 = blockIdx.x * TX, xg = x0 + col;
+    auto issue = [&](int c, int stage) {
+        float2* dst = stages + stage * stage_elems;
+        mbar_arrive_expect_tx(&bars[stage], stage_bytes);
+        tma_load_2d(dst, &smap, 2 * x0, (b * nc + c) * NY, &bars[stage]);
+        tma_load_2d(dst + NY * TX, &ymap, 2 * x0, (b * nc + c) * ms, &bars[stage]);
+        if (ADDBACK) tma_load_2d(dst + (NY + ms) * TX, &y1map, 2 * x0, (b * nc + c) * ms, &bars[stage]);
+    };
+    if (tid == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    if (tid == 0)
+        for (int c = 0; c < 2 && c < nc; ++c) issue(c, c);
+    for (int i = tid; i < NY; i += NT) {
+        tw[i] = tw_g[i];
+        sl[i] = f.slot[(size_t)b * NY + i];
+    }
+    const size_t img = (size_t)b * NY * nx;
+    float2 xv[16], bacc[16], racc[16];
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+        xv[e] = xin[img + (size_t)(t + T * e) * nx + xg];
+        bacc[e] = racc[e] = make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    const ColIdx idx{col};
+    const float sc = rsqrtf((float)NY);
+    for (int c = 0; c < nc; ++c) {
+        const int stage = c & 1;
+        mbar_wait(&bars[stage], (c >> 1) & 1, red.err);
+        const float2* S = stages + stage * stage_elems;
+        const float2* Yt = S + NY * TX;
+        const float2* Y1 = Yt + ms * TX;
+        const size_t ybase = ((size_t)b * nc + c) * ms * nx;
+        float2 u[16], v1[16];
+#pragma unroll
+        for (int e = 0; e < 16; ++e) u[e] = cmul(S[idx(t + T * e)], xv[e]);
+        fft_2stage<NY, false>(u, t, xbuf, idx, tw);
+        // u <- R F S x on sampled lines (unitary scale); v1 <- y^[j] after the outer update
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+            const int s = sl[t + T * e];
+            if (s >= 0) {
+                const float2 tt = cscale(u[e], sc);
+                float2 yv = Yt[s * TX + col];
+                if (ADDBACK) {
+                    yv = csub(cadd(yv, Y1[s * TX + col]), tt);
+                    f.yt[ybase + (size_t)s * nx + xg] = yv;
+                }
+                v1[e] = yv;
+                u[e] = csub(yv, tt);
+            } else {
+                v1[e] = make_float2(0.f, 0.f);
+                u[e] = make_float2(0.f, 0.f);
+            }
+        }
+        __syncthreads();
+        fft_2stage<NY, true>(v1, t, xbuf, idx, tw);
+#pragma unroll
+        for (int e = 0; e < 16; ++e) bacc[e] = cfmac(bacc[e], S[idx(t + T * e)], cscale(v1[e], sc));
+        __syncthreads();
+        fft_2stage<NY, true>(u, t, xbuf, idx, tw);
+#pragma unroll
+        for (int e = 0; e < 16; ++e) racc[e] = cfmac(racc[e], S[idx(t + T * e)], cscale(u[e], sc));
+        __syncthreads();  // this stage's tiles and xbuf are free
+        if (tid == 0 && c + 2 < nc) issue(c + 2, stage);
+    }
+    // b = mu bacc + g ;  r = mu racc + g - lam D^H D x - gam x
+#pragma unroll
+    for (int e = 0; e < 16; ++e) xbuf[idx(t + T * e)] = xv[e];
+    for (int i = tid; i < NY; i += NT) {
+        halo[i] = xin[img + (size_t)i * nx + (x0 == 0 ? nx - 1 : x0 - 1)];
+        halo[NY + i] = xin[img + (size_t)i * nx + (x0 + TX == nx ? 0 : x0 + TX)];
+    }
+    __syncthreads();
+    float bb = 0.f, rr = 0.f;
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+        const int yy = t + T * e;
+        const size_t gi = img + (size_t)yy * nx + xg;
+        const float2 gv = f.g[gi];
+        const float2 up = xbuf[idx(yy == 0 ? NY - 1 : yy - 1)];
+        const float2 dn = xbuf[idx(yy == NY - 1 ? 0 : yy + 1)];
+        const float2 lf = col > 0 ? xbuf[idx(yy) - 1] : halo[yy];
+        const float2 rt = col < TX - 1 ? xbuf[idx(yy) + 1] : halo[NY + yy];
+        const float tvx = 4.f * xv[e].x - up.x - dn.x - lf.x - rt.x;
+        const float tvy = 4.f * xv[e].y - up.y - dn.y - lf.y - rt.y;
+        const float2 bvec = make_float2(fmaf(mu, bacc[e].x, gv.x), fmaf(mu, bacc[e].y, gv.y));
+        float2 rv;
+        rv.x = fmaf(mu, racc[e].x, gv.x) - fmaf(lam, tvx, gam * xv[e].x);
+        rv.y = fmaf(mu, racc[e].y, gv.y) - fmaf(lam, tvy, gam * xv[e].y);
+        r[gi] = rv;
+        bb += cabs2(bvec);
+        rr += cabs2(rv);
+    }
+    double vv[2] = {(double)bb, (double)rr}, tot[2];
+    const int np = gridDim.x;
+    if (last_block_total<2>(vv, red.part, np, b * np + blockIdx.x, red.counter + b, tot, red_s, &flag) &&
+        threadIdx.x == 0) {
+        SliceState& S = st[b];
+        S.bnorm2 = tot[0];
+        S.rnorm2 = tot[1];
+        S.iters = 0;
+        S.rho = S.alpha = S.beta = S.pq = 0.0;
+        if (!isfinite(tot[0]) || !isfinite(tot[1])) S.state = ST_NONFINITE;
+        else if (tot[0] == 0.0) S.state = ST_ZERO;
+        else if (tot[1] <= tol2 * tot[0]) S.state = ST_DONE;
+        else S.state = ST_ACTIVE;
+    }
+}
+
+template <int NY, bool AB>
+cudaError_t rhs_n(const Dims& d, const CUtensorMap& smap, const CUtensorMap& ymap, const CUtensorMap& y1map,
+                  const SbFields& f, const float2* x, float2* r, const float2* tw, float mu, float lam, float gam,
+                  SliceState* st, double tol2, Red red, cudaStream_t s) {
+    const size_t sm = rhs_smem_bytes(NY, f.ms);
+    cudaError_t e = cudaFuncSetAttribute(k_rhs<NY, AB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    k_rhs<NY, AB><<<dim3(d.nx / TX, d.nb), TX * NY / 16, sm, s>>>(smap, ymap, y1map, f, d.nx, d.nc, x, r, tw, mu,
+                                                                   lam, gam, st, tol2, red);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t rhs_smem_bytes(int ny, int ms) {
+    return (2 * (size_t)(ny + 2 * ms) * TX + (size_t)ny * TX + 3 * (size_t)ny) * sizeof(float2) +
+           ny * sizeof(int) + 64 * sizeof(double);
+}
+
+cudaError_t launch_rhs(const Dims& d, const CUtensorMap& smap, const CUtensorMap& ymap, const CUtensorMap& y1map,
+                       const SbFields& f, int addback, const float2* x, float2* r, const float2* tw_y, float mu,
+                       float lam, float gam, SliceState* st, double tol2, Red red, cudaStream_t s) {
+#define CALL(N)                                                                                        \
+    return addback ? rhs_n<N, true>(d, smap, ymap, y1map, f, x, r, tw_y, mu, lam, gam, st, tol2, red, s) \
+                   : rhs_n<N, false>(d, smap, ymap, y1map, f, x, r, tw_y, mu, lam, gam, st, tol2, red, s);
+    switch (d.ny) {
+        case 32: CALL(32)
+        case 64: CALL(64)
+        case 128: CALL(128)
+        case 256: CALL(256)
+        default: return cudaErrorInvalidValue;
+    }
+#undef CALL
+}
+
+}  // namespace sb

@@ -8,9 +8,7 @@
 //
 //  k_ytilde     yt1 = F_x^H y on the sampled lines (once per reconstruction).
 //  k_rss        x = sqrt(sum_i |F^H y_i|^2) (step 1).
-//  k_rhs        [outer update yt += yt1 - R F S x], b = mu sum S^H F^H yt + g (step 4), and the
-//               initial PCG residual r = b - A x in the same pass (A x's data term reuses the
-//               forward transform R F S x of the outer update).
+//  (the right-hand side and initial residual kernel is in k_rhs.cu)
 //  k_sb_update  steps 6-11 on a 16x16 tile: TV shrink + Bregman updates, Haar analysis,
 //               wavelet shrink + Bregman update, Haar synthesis, and the next
 //               g = lam (D_x^H(d_x-b_x) + D_y^H(d_y-b_y)) + gam W^H(d_w-b_w).
@@ -42,7 +40,7 @@ k_ytilde(const float2* __restrict__ y, const int* __restrict__ lines, int ny, in
          float2* __restrict__ yt1, const float2* __restrict__ tw_g) {
     constexpr int T = NX / 16;
     constexpr int NT = RY * T;
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(128) unsigned char smem[];
     float2* buf = reinterpret_cast<float2*>(smem);
     float2* tw = buf + RY * (NX + NX / 16);
     const int tid = threadIdx.x, t = tid % T, row = tid / T;
@@ -75,7 +73,7 @@ k_rss(SbFields f, int nx, int nc, float2* __restrict__ x, const float2* __restri
     constexpr int T = NY / 16;
     constexpr int NT = TX * T;
     const int b = blockIdx.y;
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(128) unsigned char smem[];
     float2* buf0 = reinterpret_cast<float2*>(smem);
     float2* buf1 = buf0 + NY * TX;
     float2* tw = buf1 + NY * TX;
@@ -107,119 +105,6 @@ k_rss(SbFields f, int nx, int nc, float2* __restrict__ x, const float2* __restri
 #pragma unroll
     for (int e = 0; e < 16; ++e)
         x[((size_t)b * NY + t + T * e) * nx + xg] = make_float2(sqrtf(acc[e]), 0.f);
-}
-
-// ------------------------------------------------------------------ right-hand side + r0
-template <int NY, bool ADDBACK>
-__global__ void __launch_bounds__(TX * NY / 16)
-k_rhs(SbFields f, int nx, int nc, const float2* __restrict__ xin, float2* __restrict__ r,
-      const float2* __restrict__ tw_g, float mu, float lam, float gam, SliceState* st, double tol2, Red red) {
-    constexpr int T = NY / 16;
-    constexpr int NT = TX * T;
-    const int b = blockIdx.y;
-    extern __shared__ __align__(16) unsigned char smem[];
-    float2* buf0 = reinterpret_cast<float2*>(smem);
-    float2* buf1 = buf0 + NY * TX;
-    float2* tw = buf1 + NY * TX;
-    float2* halo = tw + NY;
-    int* sl = reinterpret_cast<int*>(halo + 2 * NY);
-    double* red_s = reinterpret_cast<double*>(sl + NY);
-    __shared__ int flag;
-    const int tid = threadIdx.x, col = tid % TX, t = tid / TX;
-    const int x0 = blockIdx.x * TX, xg = x0 + col;
-    for (int i = tid; i < NY; i += NT) {
-        tw[i] = tw_g[i];
-        sl[i] = f.slot[(size_t)b * NY + i];
-    }
-    const size_t img = (size_t)b * NY * nx;
-    float2 xv[16], bacc[16], racc[16];
-#pragma unroll
-    for (int e = 0; e < 16; ++e) {
-        xv[e] = xin[img + (size_t)(t + T * e) * nx + xg];
-        bacc[e] = racc[e] = make_float2(0.f, 0.f);
-    }
-    __syncthreads();
-    const ColIdx idx{col};
-    const float sc = rsqrtf((float)NY);
-    int nf = 0;  // transforms done: buffer parity
-    for (int c = 0; c < nc; ++c) {
-        const float2* S = f.sens + ((size_t)b * nc + c) * NY * nx;
-        const size_t ybase = ((size_t)b * nc + c) * f.ms * nx;
-        float2 u[16], v1[16];
-#pragma unroll
-        for (int e = 0; e < 16; ++e) u[e] = cmul(__ldg(S + (size_t)(t + T * e) * nx + xg), xv[e]);
-        fft_2stage<NY, false>(u, t, (nf++ & 1) ? buf1 : buf0, idx, tw);
-        // u <- R F S x on sampled lines (unitary scale); v1 <- the data y^[j] (after the update)
-#pragma unroll
-        for (int e = 0; e < 16; ++e) {
-            const int s = sl[t + T * e];
-            if (s >= 0) {
-                const size_t yi = ybase + (size_t)s * nx + xg;
-                const float2 tt = cscale(u[e], sc);
-                float2 yv = f.yt[yi];
-                if (ADDBACK) {
-                    yv = csub(cadd(yv, f.yt1[yi]), tt);
-                    f.yt[yi] = yv;
-                }
-                v1[e] = yv;
-                u[e] = csub(yv, tt);  // data residual y - R F S x
-            } else {
-                v1[e] = make_float2(0.f, 0.f);
-                u[e] = make_float2(0.f, 0.f);
-            }
-        }
-        fft_2stage<NY, true>(v1, t, (nf++ & 1) ? buf1 : buf0, idx, tw);
-        fft_2stage<NY, true>(u, t, (nf++ & 1) ? buf1 : buf0, idx, tw);
-#pragma unroll
-        for (int e = 0; e < 16; ++e) {
-            const float2 s = __ldg(S + (size_t)(t + T * e) * nx + xg);
-            bacc[e] = cfmac(bacc[e], s, cscale(v1[e], sc));
-            racc[e] = cfmac(racc[e], s, cscale(u[e], sc));
-        }
-    }
-    // b = mu bacc + g ;  r = mu racc + g - lam D^H D x - gam x
-    __syncthreads();  // all transforms finished with both buffers
-#pragma unroll
-    for (int e = 0; e < 16; ++e) buf0[idx(t + T * e)] = xv[e];
-    for (int i = tid; i < NY; i += NT) {
-        halo[i] = xin[img + (size_t)i * nx + (x0 == 0 ? nx - 1 : x0 - 1)];
-        halo[NY + i] = xin[img + (size_t)i * nx + (x0 + TX == nx ? 0 : x0 + TX)];
-    }
-    __syncthreads();
-    float bb = 0.f, rr = 0.f;
-#pragma unroll
-    for (int e = 0; e < 16; ++e) {
-        const int yy = t + T * e;
-        const size_t gi = img + (size_t)yy * nx + xg;
-        const float2 gv = f.g[gi];
-        const float2 up = buf0[idx(yy == 0 ? NY - 1 : yy - 1)];
-        const float2 dn = buf0[idx(yy == NY - 1 ? 0 : yy + 1)];
-        const float2 lf = col > 0 ? buf0[idx(yy) - 1] : halo[yy];
-        const float2 rt = col < TX - 1 ? buf0[idx(yy) + 1] : halo[NY + yy];
-        const float tvx = 4.f * xv[e].x - up.x - dn.x - lf.x - rt.x;
-        const float tvy = 4.f * xv[e].y - up.y - dn.y - lf.y - rt.y;
-        const float2 bvec = make_float2(fmaf(mu, bacc[e].x, gv.x), fmaf(mu, bacc[e].y, gv.y));
-        float2 rv;
-        rv.x = fmaf(mu, racc[e].x, gv.x) - fmaf(lam, tvx, gam * xv[e].x);
-        rv.y = fmaf(mu, racc[e].y, gv.y) - fmaf(lam, tvy, gam * xv[e].y);
-        r[gi] = rv;
-        bb += cabs2(bvec);
-        rr += cabs2(rv);
-    }
-    double vv[2] = {(double)bb, (double)rr}, tot[2];
-    const int np = gridDim.x;
-    if (last_block_total<2>(vv, red.part, np, b * np + blockIdx.x, red.counter + b, tot, red_s, &flag) &&
-        threadIdx.x == 0) {
-        SliceState& S = st[b];
-        S.bnorm2 = tot[0];
-        S.rnorm2 = tot[1];
-        S.iters = 0;
-        S.rho = S.alpha = S.beta = S.pq = 0.0;
-        if (!isfinite(tot[0]) || !isfinite(tot[1])) S.state = ST_NONFINITE;
-        else if (tot[0] == 0.0) S.state = ST_ZERO;
-        else if (tot[1] <= tol2 * tot[0]) S.state = ST_DONE;
-        else S.state = ST_ACTIVE;
-    }
 }
 
 // ------------------------------------------------------------------ steps 6-11 on a 16x16 tile
@@ -375,40 +260,6 @@ cudaError_t launch_rss(const Dims& d, const SbFields& f, float2* x, const float2
         case 128: CALL(128)
         case 256: CALL(256)
         default: return cudaErrorInvalidValue;
-    }
-#undef CALL
-}
-
-cudaError_t launch_rhs(const Dims& d, const SbFields& f, int addback, const float2* x, float2* r, const float2* tw_y,
-                       float mu, float lam, float gam, SliceState* st, double tol2, Red red, cudaStream_t s) {
-    const dim3 grid(d.nx / TX, d.nb);
-    cudaError_t e;
-#define CALL(N, AB)                                                                                              \
-    {                                                                                                            \
-        const size_t sm = (2 * N * TX + N + 2 * N) * sizeof(float2) + N * sizeof(int) + 64 * sizeof(double);     \
-        if (sm > 48 * 1024 &&                                                                                    \
-            (e = cudaFuncSetAttribute(k_rhs<N, AB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)) !=   \
-                cudaSuccess)                                                                                     \
-            return e;                                                                                            \
-        k_rhs<N, AB><<<grid, TX * N / 16, sm, s>>>(f, d.nx, d.nc, x, r, tw_y, mu, lam, gam, st, tol2, red);      \
-        return cudaGetLastError();                                                                               \
-    }
-    if (addback) {
-        switch (d.ny) {
-            case 32: CALL(32, true)
-            case 64: CALL(64, true)
-            case 128: CALL(128, true)
-            case 256: CALL(256, true)
-            default: return cudaErrorInvalidValue;
-        }
-    } else {
-        switch (d.ny) {
-            case 32: CALL(32, false)
-            case 64: CALL(64, false)
-            case 128: CALL(128, false)
-            case 256: CALL(256, false)
-            default: return cudaErrorInvalidValue;
-        }
     }
 #undef CALL
 }

@@ -47,7 +47,7 @@ __global__ void __launch_bounds__(RY * NX / 16)
 k_fft_rows(float2* __restrict__ data, int nrows_total, const float2* __restrict__ tw_g) {
     constexpr int T = NX / 16;
     constexpr int NT = RY * T;
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(128) unsigned char smem[];
     float2* buf = reinterpret_cast<float2*>(smem);
     float2* tw = buf + RY * (NX + NX / 16);
     const int tid = threadIdx.x, t = tid % T, row = tid / T;
@@ -70,7 +70,7 @@ __global__ void __launch_bounds__(TX * NY / 16)
 k_fft_cols(float2* __restrict__ data, int nx, const float2* __restrict__ tw_g) {
     constexpr int T = NY / 16;
     constexpr int NT = TX * T;
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(128) unsigned char smem[];
     float2* buf = reinterpret_cast<float2*>(smem);
     float2* tw = buf + NY * TX;
     const int tid = threadIdx.x, col = tid % TX, t = tid / TX;

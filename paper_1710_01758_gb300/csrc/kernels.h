@@ -1,10 +1,14 @@
 // Internal interface between the C-ABI layer (sb_api.cu) and the CUDA kernels.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 namespace sb {
+
+// Columns per CTA of the column kernels; the TMA box of a coil tile is kColTile x ny.
+constexpr int kColTile = 16;
 
 // Per-slice CG state; lives in device memory, one entry per slice of the batch.
 enum : int {
@@ -31,10 +35,12 @@ struct Dims {
     int nx, ny, nc, nb;
 };
 
-// Workspace of the cross-CTA reductions: part[nb][maxparts][K] doubles, counter[nb].
+// Workspace of the cross-CTA reductions: part[nb][maxparts][K] doubles, counter[nb]; err is
+// the device error word (bit kErrTmaTimeout: a bounded TMA wait gave up).
 struct Red {
     double* part;
     unsigned* counter;
+    unsigned* err;
 };
 
 constexpr int kMaxParts = 1024;
@@ -44,7 +50,8 @@ constexpr int kVecPerThread = 8;
 // ------------------------------------------------------------------ PCG kernels (k_pcg.cu)
 // q = A p (readout-axis shortcut of the data term); st == nullptr: plain application;
 // otherwise PCG mode: skips inactive slices, accumulates Re(p^H q) and sets alpha = rho/pq.
-cudaError_t launch_apply_A(const Dims& d, const float2* p, float2* q, const float2* sens,
+// smap: TMA map of the sensitivities viewed as float32 [nb*nc*ny][2*nx], box [ny][2*kColTile].
+cudaError_t launch_apply_A(const Dims& d, const CUtensorMap& smap, const float2* p, float2* q,
                            const float* maskw, const float2* tw_y, float mu, float lam, float gam,
                            SliceState* st, Red red, cudaStream_t s);
 
@@ -123,9 +130,14 @@ cudaError_t launch_rss(const Dims& d, const SbFields& f, float2* x, const float2
                        cudaStream_t s);
 // Right-hand side and initial residual: optional outer data update yt += yt1 - R F S x,
 // b = mu sum_c S_c^H F^H yt_c + g, r = b - A x; ||b||^2, ||r||^2, state.
-cudaError_t launch_rhs(const Dims& d, const SbFields& f, int addback, const float2* x, float2* r,
-                       const float2* tw_y, float mu, float lam, float gam, SliceState* st,
+// smap: as for launch_apply_A; ymap / y1map: TMA maps of yt / yt1 viewed as float32
+// [nb*nc*ms][2*nx] with box [ms][2*kColTile].
+cudaError_t launch_rhs(const Dims& d, const CUtensorMap& smap, const CUtensorMap& ymap,
+                       const CUtensorMap& y1map, const SbFields& f, int addback, const float2* x,
+                       float2* r, const float2* tw_y, float mu, float lam, float gam, SliceState* st,
                        double tol2, Red red, cudaStream_t s);
+// Shared memory the right-hand-side kernel needs for ny and ms (bytes).
+size_t rhs_smem_bytes(int ny, int ms);
 // Shrink + Bregman updates (steps 6-11) and the next g.
 cudaError_t launch_sb_update(const Dims& d, const SbFields& f, const float2* x, int levels,
                              float lam, float gam, float tau_tv, float tau_w, cudaStream_t s);

@@ -54,6 +54,24 @@ struct sb_plan_s {
     double* part = nullptr;
     unsigned* counter = nullptr;
     unsigned* kmax = nullptr;
+    unsigned* derr = nullptr;  // device error word
+    unsigned h_err = 0;
+    CUtensorMap smap;         // TMA map of the sensitivities
+    CUtensorMap ymap, y1map;  // TMA maps of yt and yt1
+    // k construction scratch (kept after the first sb_set_mask so later calls do not allocate)
+    float2 *spec = nullptr, *gb = nullptr, *rb = nullptr;
+    int *line_val = nullptr, *line_uni = nullptr;
+
+    // event timer per kernel class
+    struct Pending {
+        int cls;
+        cudaEvent_t a, b;
+    };
+    unsigned tmask = 0;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<Pending> pending;
+    uint64_t tcount[SB_KCLASS_COUNT] = {};
+    double tms[SB_KCLASS_COUNT] = {};
 };
 
 namespace {
@@ -73,11 +91,57 @@ sb_status cuda_fail(sb_plan pl, const char* what, cudaError_t e) {
         if (e_ != cudaSuccess) return cuda_fail((pl), #call, e_);    \
     } while (0)
 
-// launch helper: counts kernels
-#define SB_LAUNCH(pl, nk, call)                                      \
+cudaEvent_t timer_begin(sb_plan pl, int cls) {
+    if (!(pl->tmask & (1u << cls))) return nullptr;
+    cudaEvent_t a = nullptr;
+    if (!pl->ev_pool.empty()) {
+        a = pl->ev_pool.back();
+        pl->ev_pool.pop_back();
+    } else if (cudaEventCreate(&a) != cudaSuccess) {
+        return nullptr;
+    }
+    if (cudaEventRecord(a, pl->stream) != cudaSuccess) {
+        pl->ev_pool.push_back(a);
+        return nullptr;
+    }
+    return a;
+}
+
+void timer_end(sb_plan pl, int cls, cudaEvent_t a) {
+    if (!a) return;
+    cudaEvent_t b = nullptr;
+    if (!pl->ev_pool.empty()) {
+        b = pl->ev_pool.back();
+        pl->ev_pool.pop_back();
+    } else if (cudaEventCreate(&b) != cudaSuccess) {
+        pl->ev_pool.push_back(a);
+        return;
+    }
+    cudaEventRecord(b, pl->stream);
+    pl->pending.push_back({cls, a, b});
+}
+
+// accumulate the recorded event pairs; call only after the stream has been synchronised
+void timer_harvest(sb_plan pl) {
+    for (const auto& p : pl->pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+            pl->tms[p.cls] += ms;
+            pl->tcount[p.cls] += 1;
+        }
+        pl->ev_pool.push_back(p.a);
+        pl->ev_pool.push_back(p.b);
+    }
+    pl->pending.clear();
+}
+
+// launch helper: counts kernels and, when enabled for the class, times them with events
+#define SB_LAUNCH(pl, cls, nk, call)                                 \
     do {                                                             \
+        cudaEvent_t ta_ = timer_begin((pl), (cls));                  \
         cudaError_t e_ = (call);                                     \
         if (e_ != cudaSuccess) return cuda_fail((pl), #call, e_);    \
+        timer_end((pl), (cls), ta_);                                 \
         g_launches.fetch_add((nk), std::memory_order_relaxed);       \
     } while (0)
 
@@ -101,7 +165,25 @@ std::vector<float2> twiddles(int n) {
     return t;
 }
 
-Red red_of(sb_plan pl) { return Red{pl->part, pl->counter}; }
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// the driver's tensor-map encoder, resolved once through the runtime (no link against libcuda)
+EncodeTiledFn tensor_map_encoder() {
+    static EncodeTiledFn fn = []() -> EncodeTiledFn {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return nullptr;
+        return reinterpret_cast<EncodeTiledFn>(p);
+    }();
+    return fn;
+}
+
+Red red_of(sb_plan pl) { return Red{pl->part, pl->counter, pl->derr}; }
 
 // Sequence CG from the state left by launch_resid_init / launch_rhs (r = r0, bnorm2, state).
 // Returns the worst per-slice status; fills h_results (may be null).
@@ -115,33 +197,36 @@ sb_status pcg_run(sb_plan pl, const sb_pcg_opts& o, float2* x, sb_pcg_result* h_
     const Red red = red_of(pl);
     const float mu = (float)pl->d.mu, lam = (float)pl->d.lambda, gam = (float)pl->d.gamma;
 
-    SB_LAUNCH(pl, 1, launch_zero_rhs_slices(d, x, pl->st, s));
+    SB_LAUNCH(pl, SB_KCLASS_VEC, 1, launch_zero_rhs_slices(d, x, pl->st, s));
     if (circ) {
-        SB_LAUNCH(pl, 1, launch_row_fwd(d, 0, pl->r, nullptr, pl->tb, pl->tw_x, pl->st, tol2, red, s));
-        SB_LAUNCH(pl, 1, launch_col_precond(d, pl->tb, pl->invk, pl->tw_y, pl->st, 1, red, s));
-        SB_LAUNCH(pl, 1, launch_row_inv(d, 1, pl->tb, nullptr, x, pl->p, pl->tw_x, pl->st, red, s));
+        SB_LAUNCH(pl, SB_KCLASS_PRECOND_ROW_FWD, 1, launch_row_fwd(d, 0, pl->r, nullptr, pl->tb, pl->tw_x, pl->st, tol2, red, s));
+        SB_LAUNCH(pl, SB_KCLASS_PRECOND_COL, 1, launch_col_precond(d, pl->tb, pl->invk, pl->tw_y, pl->st, 1, red, s));
+        SB_LAUNCH(pl, SB_KCLASS_PRECOND_ROW_INV, 1, launch_row_inv(d, 1, pl->tb, nullptr, x, pl->p, pl->tw_x, pl->st, red, s));
     } else {
-        SB_LAUNCH(pl, 1, launch_vec_plain(d, 0, x, pl->r, pl->p, nullptr, pl->st, tol2, red, s));
+        SB_LAUNCH(pl, SB_KCLASS_VEC, 1, launch_vec_plain(d, 0, x, pl->r, pl->p, nullptr, pl->st, tol2, red, s));
     }
     const int nit = fixed ? o.fixed_iters : o.maxit;
     int it = 0;
     while (it < nit) {
         const int g = std::min(kPollEvery, nit - it);
         for (int i = 0; i < g; ++i) {
-            SB_LAUNCH(pl, 1, launch_apply_A(d, pl->p, pl->q, pl->sens, pl->maskw, pl->tw_y, mu, lam, gam, pl->st, red, s));
+            SB_LAUNCH(pl, SB_KCLASS_APPLY_A, 1, launch_apply_A(d, pl->smap, pl->p, pl->q, pl->maskw, pl->tw_y, mu, lam, gam, pl->st, red, s));
             if (circ) {
-                SB_LAUNCH(pl, 1, launch_row_fwd(d, 1, pl->r, pl->q, pl->tb, pl->tw_x, pl->st, tol2, red, s));
-                SB_LAUNCH(pl, 1, launch_col_precond(d, pl->tb, pl->invk, pl->tw_y, pl->st, 0, red, s));
-                SB_LAUNCH(pl, 1, launch_row_inv(d, 2, pl->tb, nullptr, x, pl->p, pl->tw_x, pl->st, red, s));
+                SB_LAUNCH(pl, SB_KCLASS_PRECOND_ROW_FWD, 1, launch_row_fwd(d, 1, pl->r, pl->q, pl->tb, pl->tw_x, pl->st, tol2, red, s));
+                SB_LAUNCH(pl, SB_KCLASS_PRECOND_COL, 1, launch_col_precond(d, pl->tb, pl->invk, pl->tw_y, pl->st, 0, red, s));
+                SB_LAUNCH(pl, SB_KCLASS_PRECOND_ROW_INV, 1, launch_row_inv(d, 2, pl->tb, nullptr, x, pl->p, pl->tw_x, pl->st, red, s));
             } else {
-                SB_LAUNCH(pl, 1, launch_vec_plain(d, 1, x, pl->r, pl->p, pl->q, pl->st, tol2, red, s));
-                SB_LAUNCH(pl, 1, launch_vec_plain(d, 2, x, pl->r, pl->p, pl->q, pl->st, tol2, red, s));
+                SB_LAUNCH(pl, SB_KCLASS_VEC, 1, launch_vec_plain(d, 1, x, pl->r, pl->p, pl->q, pl->st, tol2, red, s));
+                SB_LAUNCH(pl, SB_KCLASS_VEC, 1, launch_vec_plain(d, 2, x, pl->r, pl->p, pl->q, pl->st, tol2, red, s));
             }
         }
         it += g;
         if (!fixed || it >= nit) {
             SB_CK(pl, cudaMemcpyAsync(pl->h_st, pl->st, sizeof(SliceState) * d.nb, cudaMemcpyDeviceToHost, s));
+            SB_CK(pl, cudaMemcpyAsync(&pl->h_err, pl->derr, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
             SB_CK(pl, cudaStreamSynchronize(s));
+            timer_harvest(pl);
+            if (pl->h_err) return fail(pl, SB_ERR_TIMEOUT, "a bounded device wait gave up (TMA tile never arrived)");
             bool running = false;
             for (int b = 0; b < d.nb; ++b)
                 running |= (pl->h_st[b].state == ST_ACTIVE || pl->h_st[b].state == ST_FINISHING);
@@ -248,6 +333,7 @@ sb_status sb_plan_create(const sb_plan_desc* desc, void* cuda_stream, sb_plan* o
     ALLOC(pl->part, nb * kMaxParts * 2);
     ALLOC(pl->counter, nb);
     ALLOC(pl->kmax, nb);
+    ALLOC(pl->derr, 1);
 #undef ALLOC
     if ((e = cudaMallocHost(reinterpret_cast<void**>(&pl->h_st), sizeof(SliceState) * nb)) != cudaSuccess)
         return bail("cudaMallocHost");
@@ -257,6 +343,7 @@ sb_status sb_plan_create(const sb_plan_desc* desc, void* cuda_stream, sb_plan* o
     if ((e = cudaMemcpy(pl->tw_y, ty.data(), sizeof(float2) * d.ny, cudaMemcpyHostToDevice)) != cudaSuccess)
         return bail("cudaMemcpy twiddles");
     if ((e = cudaMemset(pl->counter, 0, sizeof(unsigned) * nb)) != cudaSuccess) return bail("cudaMemset");
+    if ((e = cudaMemset(pl->derr, 0, sizeof(unsigned))) != cudaSuccess) return bail("cudaMemset");
     if ((e = cudaMemset(pl->st, 0, sizeof(SliceState) * nb)) != cudaSuccess) return bail("cudaMemset");
     *out = pl;
     return SB_OK;
@@ -270,15 +357,35 @@ sb_status sb_plan_destroy(sb_plan pl) {
                     (void*)pl->k, (void*)pl->invk, (void*)pl->r, (void*)pl->p, (void*)pl->q, (void*)pl->tb,
                     (void*)pl->bx[0], (void*)pl->bx[1], (void*)pl->by[0], (void*)pl->by[1], (void*)pl->bw,
                     (void*)pl->g, (void*)pl->yt, (void*)pl->yt1, (void*)pl->st, (void*)pl->part,
-                    (void*)pl->counter, (void*)pl->kmax})
+                    (void*)pl->counter, (void*)pl->kmax, (void*)pl->derr, (void*)pl->spec, (void*)pl->gb, (void*)pl->rb,
+                    (void*)pl->line_val, (void*)pl->line_uni})
         dfree(p);
     if (pl->h_st) cudaFreeHost(pl->h_st);
+    for (const auto& pe : pl->pending) {
+        cudaEventDestroy(pe.a);
+        cudaEventDestroy(pe.b);
+    }
+    for (cudaEvent_t e : pl->ev_pool) cudaEventDestroy(e);
     delete pl;
     return SB_OK;
 }
 
 sb_status sb_set_coils(sb_plan pl, const void* d_sens) {
     if (!pl || !d_sens) return fail(pl, SB_ERR_INVALID_ARG, "null plan or sensitivities");
+    if (reinterpret_cast<uintptr_t>(d_sens) % 16 != 0)
+        return fail(pl, SB_ERR_INVALID_ARG, "sensitivities must be 16-byte aligned");
+    const Dims& d = pl->dims;
+    auto encode = tensor_map_encoder();
+    if (!encode) return fail(pl, SB_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
+    // float32 view [nb*nc*ny][2*nx]; box = ny rows x 2*kColTile floats (one coil tile)
+    const cuuint64_t gdim[2] = {(cuuint64_t)2 * d.nx, (cuuint64_t)d.nb * d.nc * d.ny};
+    const cuuint64_t gstride[1] = {(cuuint64_t)2 * d.nx * sizeof(float)};
+    const cuuint32_t box[2] = {(cuuint32_t)2 * kColTile, (cuuint32_t)d.ny};
+    const cuuint32_t estride[2] = {1, 1};
+    const CUresult cr = encode(&pl->smap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(d_sens), gdim,
+                               gstride, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (cr != CUDA_SUCCESS) return fail(pl, SB_ERR_CUDA, "cuTensorMapEncodeTiled failed for the sensitivities");
     pl->sens = static_cast<const float2*>(d_sens);
     pl->have_coils = true;
     pl->have_mask = false;  // k depends on the coils: rebuilt by sb_set_mask
@@ -291,17 +398,21 @@ sb_status sb_set_mask(sb_plan pl, const uint8_t* d_mask) {
     const Dims& d = pl->dims;
     const size_t nb = d.nb, n = pl->n;
     cudaStream_t s = pl->stream;
+    // scratch of the k construction, allocated once per plan
+    if (!pl->spec) {
+        SB_CK(pl, dalloc(&pl->line_val, nb * d.ny));
+        SB_CK(pl, dalloc(&pl->line_uni, nb * d.ny));
+        SB_CK(pl, dalloc(&pl->spec, nb * d.nc * n));
+        SB_CK(pl, dalloc(&pl->gb, nb * n));
+        SB_CK(pl, dalloc(&pl->rb, nb * n));
+    }
     // 1. line structure of the mask
-    int *lv = nullptr, *lu = nullptr;
-    SB_CK(pl, dalloc(&lv, nb * d.ny));
-    SB_CK(pl, dalloc(&lu, nb * d.ny));
-    SB_LAUNCH(pl, 1, launch_mask_lines(d, d_mask, lv, lu, s));
+    int *lv = pl->line_val, *lu = pl->line_uni;
+    SB_LAUNCH(pl, SB_KCLASS_OTHER, 1, launch_mask_lines(d, d_mask, lv, lu, s));
     std::vector<int> hv(nb * d.ny), hu(nb * d.ny);
     SB_CK(pl, cudaMemcpyAsync(hv.data(), lv, sizeof(int) * hv.size(), cudaMemcpyDeviceToHost, s));
     SB_CK(pl, cudaMemcpyAsync(hu.data(), lu, sizeof(int) * hu.size(), cudaMemcpyDeviceToHost, s));
     SB_CK(pl, cudaStreamSynchronize(s));
-    dfree(lv);
-    dfree(lu);
     for (size_t i = 0; i < hu.size(); ++i)
         if (!hu[i]) return fail(pl, SB_ERR_UNSUPPORTED, "mask varies along the readout (x) axis");
     int ms = 1;
@@ -332,29 +443,24 @@ sb_status sb_set_mask(sb_plan pl, const uint8_t* d_mask) {
     SB_CK(pl, cudaMemcpyAsync(pl->lines, hl.data(), sizeof(int) * hl.size(), cudaMemcpyHostToDevice, s));
 
     // 2. k = mu k_c + lam k_d + gam by FFTs (Eq. Kdiag, Eq. diagonalelements)
-    float2 *spec = nullptr, *gb = nullptr, *rb = nullptr;
-    SB_CK(pl, dalloc(&spec, nb * d.nc * n));
-    SB_CK(pl, dalloc(&gb, nb * n));
-    SB_CK(pl, dalloc(&rb, nb * n));
+    float2 *spec = pl->spec, *gb = pl->gb, *rb = pl->rb;
     const int nimg_c = d.nb * d.nc;
     SB_CK(pl, cudaMemcpyAsync(spec, pl->sens, sizeof(float2) * nb * d.nc * n, cudaMemcpyDeviceToDevice, s));
-    SB_LAUNCH(pl, 1, launch_fft_rows(d.nx, d.ny, nimg_c, spec, pl->tw_x, false, s));
-    SB_LAUNCH(pl, 1, launch_fft_cols(d.nx, d.ny, nimg_c, spec, pl->tw_y, false, s));
-    SB_LAUNCH(pl, 1, launch_coil_power(d, spec, gb, s));
-    SB_LAUNCH(pl, 1, launch_mask_to_complex(d, d_mask, rb, s));
-    SB_LAUNCH(pl, 1, launch_fft_rows(d.nx, d.ny, d.nb, gb, pl->tw_x, false, s));
-    SB_LAUNCH(pl, 1, launch_fft_cols(d.nx, d.ny, d.nb, gb, pl->tw_y, false, s));
-    SB_LAUNCH(pl, 1, launch_fft_rows(d.nx, d.ny, d.nb, rb, pl->tw_x, false, s));
-    SB_LAUNCH(pl, 1, launch_fft_cols(d.nx, d.ny, d.nb, rb, pl->tw_y, false, s));
-    SB_LAUNCH(pl, 1, launch_mul_conj(d, rb, gb, s));
-    SB_LAUNCH(pl, 1, launch_fft_rows(d.nx, d.ny, d.nb, rb, pl->tw_x, true, s));
-    SB_LAUNCH(pl, 1, launch_fft_cols(d.nx, d.ny, d.nb, rb, pl->tw_y, true, s));
-    SB_LAUNCH(pl, 2, launch_finish_k(d, rb, (float)pl->d.mu, (float)pl->d.lambda, (float)pl->d.gamma, pl->k,
+    SB_LAUNCH(pl, SB_KCLASS_OTHER, 1, launch_fft_rows(d.nx, d.ny, nimg_c, spec, pl->tw_x, false, s));
+    SB_LAUNCH(pl, SB_KCLASS_OTHER, 1, launch_fft_cols(d.nx, d.ny, nimg_c, spec, pl->tw_y, false, s));
+    SB_LAUNCH(pl, SB_KCLASS_OTHER, 1, launch_coil_power(d, spec, gb, s));
+    SB_LAUNCH(pl, SB_KCLASS_OTHER, 1, launch_mask_to_complex(d, d_mask, rb, s));
+    SB_LAUNCH(pl, SB_KCLASS_OTHER, 1, launch_fft_rows(d.nx, d.ny, d.nb, gb, pl->tw_x, false, s));
+    SB_LAUNCH(pl, SB_KCLASS_OTHER, 1, launch_fft_cols(d.nx, d.ny, d.nb, gb, pl->tw_y, false, s));
+    SB_LAUNCH(pl, SB_KCLASS_OTHER, 1, launch_fft_rows(d.nx, d.ny, d.nb, rb, pl->tw_x, false, s));
+    SB_LAUNCH(pl, SB_KCLASS_OTHER, 1, launch_fft_cols(d.nx, d.ny, d.nb, rb, pl->tw_y, false, s));
+    SB_LAUNCH(pl, SB_KCLASS_OTHER, 1, launch_mul_conj(d, rb, gb, s));
+    SB_LAUNCH(pl, SB_KCLASS_OTHER, 1, launch_fft_rows(d.nx, d.ny, d.nb, rb, pl->tw_x, true, s));
+    SB_LAUNCH(pl, SB_KCLASS_OTHER, 1, launch_fft_cols(d.nx, d.ny, d.nb, rb, pl->tw_y, true, s));
+    SB_LAUNCH(pl, SB_KCLASS_OTHER, 2, launch_finish_k(d, rb, (float)pl->d.mu, (float)pl->d.lambda, (float)pl->d.gamma, pl->k,
                                      pl->invk, pl->kmax, s));
     SB_CK(pl, cudaStreamSynchronize(s));
-    dfree(spec);
-    dfree(gb);
-    dfree(rb);
+    timer_harvest(pl);
 
     // 3. Split Bregman workspace sized by the number of sampled lines
     const size_t yt_elems = nb * d.nc * (size_t)ms * d.nx;
@@ -365,6 +471,23 @@ sb_status sb_set_mask(sb_plan pl, const uint8_t* d_mask) {
         SB_CK(pl, dalloc(&pl->yt, yt_elems));
         SB_CK(pl, dalloc(&pl->yt1, yt_elems));
         pl->yt_elems = yt_elems;
+    }
+    {
+        // TMA maps of the compact k-space rows: float32 [nb*nc*ms][2*nx], box = ms rows x one tile
+        auto encode = tensor_map_encoder();
+        if (!encode) return fail(pl, SB_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
+        const cuuint64_t gdim[2] = {(cuuint64_t)2 * d.nx, (cuuint64_t)nb * d.nc * ms};
+        const cuuint64_t gstride[1] = {(cuuint64_t)2 * d.nx * sizeof(float)};
+        const cuuint32_t box[2] = {(cuuint32_t)2 * kColTile, (cuuint32_t)ms};
+        const cuuint32_t estride[2] = {1, 1};
+        for (int which = 0; which < 2; ++which) {
+            CUtensorMap* m = which ? &pl->y1map : &pl->ymap;
+            void* base = which ? (void*)pl->yt1 : (void*)pl->yt;
+            if (encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, gdim, gstride, box, estride,
+                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+                return fail(pl, SB_ERR_CUDA, "cuTensorMapEncodeTiled failed for the k-space rows");
+        }
     }
     if (!pl->g) {
         SB_CK(pl, dalloc(&pl->bx[0], nb * n));
@@ -388,7 +511,7 @@ sb_status sb_get_k(sb_plan pl, float* d_k) {
 sb_status sb_apply_A(sb_plan pl, const void* d_x, void* d_y) {
     if (sb_status s = check_ready(pl)) return s;
     if (!d_x || !d_y || d_x == d_y) return fail(pl, SB_ERR_INVALID_ARG, "need distinct non-null x and y");
-    SB_LAUNCH(pl, 1, launch_apply_A(pl->dims, static_cast<const float2*>(d_x), static_cast<float2*>(d_y), pl->sens,
+    SB_LAUNCH(pl, SB_KCLASS_APPLY_A, 1, launch_apply_A(pl->dims, pl->smap, static_cast<const float2*>(d_x), static_cast<float2*>(d_y),
                                     pl->maskw, pl->tw_y, (float)pl->d.mu, (float)pl->d.lambda, (float)pl->d.gamma,
                                     nullptr, red_of(pl), pl->stream));
     return SB_OK;
@@ -399,10 +522,10 @@ sb_status sb_apply_precond(sb_plan pl, const void* d_r, void* d_z) {
     if (!d_r || !d_z) return fail(pl, SB_ERR_INVALID_ARG, "null vector");
     const Dims& d = pl->dims;
     const Red red = red_of(pl);
-    SB_LAUNCH(pl, 1, launch_row_fwd(d, 0, const_cast<float2*>(static_cast<const float2*>(d_r)), nullptr, pl->tb,
+    SB_LAUNCH(pl, SB_KCLASS_PRECOND_ROW_FWD, 1, launch_row_fwd(d, 0, const_cast<float2*>(static_cast<const float2*>(d_r)), nullptr, pl->tb,
                                     pl->tw_x, nullptr, 0.0, red, pl->stream));
-    SB_LAUNCH(pl, 1, launch_col_precond(d, pl->tb, pl->invk, pl->tw_y, nullptr, 0, red, pl->stream));
-    SB_LAUNCH(pl, 1, launch_row_inv(d, 0, pl->tb, static_cast<float2*>(d_z), nullptr, nullptr, pl->tw_x, nullptr,
+    SB_LAUNCH(pl, SB_KCLASS_PRECOND_COL, 1, launch_col_precond(d, pl->tb, pl->invk, pl->tw_y, nullptr, 0, red, pl->stream));
+    SB_LAUNCH(pl, SB_KCLASS_PRECOND_ROW_INV, 1, launch_row_inv(d, 0, pl->tb, static_cast<float2*>(d_z), nullptr, nullptr, pl->tw_x, nullptr,
                                     red, pl->stream));
     return SB_OK;
 }
@@ -414,9 +537,9 @@ sb_status sb_pcg_solve(sb_plan pl, const void* d_b, void* d_x, const sb_pcg_opts
     const Dims& d = pl->dims;
     float2* x = static_cast<float2*>(d_x);
     const double tol2 = o->fixed_iters > 0 ? -1.0 : o->tol * o->tol;
-    SB_LAUNCH(pl, 1, launch_apply_A(d, x, pl->q, pl->sens, pl->maskw, pl->tw_y, (float)pl->d.mu,
+    SB_LAUNCH(pl, SB_KCLASS_APPLY_A, 1, launch_apply_A(d, pl->smap, x, pl->q, pl->maskw, pl->tw_y, (float)pl->d.mu,
                                     (float)pl->d.lambda, (float)pl->d.gamma, nullptr, red_of(pl), pl->stream));
-    SB_LAUNCH(pl, 1, launch_resid_init(d, static_cast<const float2*>(d_b), pl->q, pl->r, pl->st, tol2, red_of(pl),
+    SB_LAUNCH(pl, SB_KCLASS_VEC, 1, launch_resid_init(d, static_cast<const float2*>(d_b), pl->q, pl->r, pl->st, tol2, red_of(pl),
                                        pl->stream));
     return pcg_run(pl, *o, x, h_results, nullptr, 0);
 }
@@ -436,8 +559,10 @@ sb_status sb_split_bregman(sb_plan pl, const void* d_y, void* d_x, const sb_sb_o
     const double tol2 = o->pcg.fixed_iters > 0 ? -1.0 : o->pcg.tol * o->pcg.tol;
     const int levels = pl->d.wavelet_levels;
     const int nsolve = o->n_outer * o->n_inner;
+    if (rhs_smem_bytes(d.ny, pl->ms) > 227 * 1024)
+        return fail(pl, SB_ERR_UNSUPPORTED, "too many sampled lines for the shared-memory pipeline of this size");
 
-    SB_LAUNCH(pl, 1, launch_ytilde(d, static_cast<const float2*>(d_y), pl->lines, pl->ms, pl->yt1, pl->tw_x, s));
+    SB_LAUNCH(pl, SB_KCLASS_OTHER, 1, launch_ytilde(d, static_cast<const float2*>(d_y), pl->lines, pl->ms, pl->yt1, pl->tw_x, s));
     SB_CK(pl, cudaMemcpyAsync(pl->yt, pl->yt1, sizeof(float2) * pl->yt_elems, cudaMemcpyDeviceToDevice, s));
     int cur = 0;
     SB_CK(pl, cudaMemsetAsync(pl->bx[0], 0, sizeof(float2) * nb * n, s));
@@ -460,7 +585,7 @@ sb_status sb_split_bregman(sb_plan pl, const void* d_y, void* d_x, const sb_sb_o
         f.g = pl->g;
         return f;
     };
-    if (o->init_rss) SB_LAUNCH(pl, 1, launch_rss(d, fields(), x, pl->tw_y, s));
+    if (o->init_rss) SB_LAUNCH(pl, SB_KCLASS_OTHER, 1, launch_rss(d, fields(), x, pl->tw_y, s));
 
     sb_status first_err = SB_OK;
     std::vector<int> iters(nb * nsolve, 0);
@@ -468,20 +593,43 @@ sb_status sb_split_bregman(sb_plan pl, const void* d_y, void* d_x, const sb_sb_o
     for (int j = 0; j < o->n_outer; ++j) {
         for (int k = 0; k < o->n_inner; ++k, ++solve) {
             const int addback = (j > 0 && k == 0);
-            SB_LAUNCH(pl, 1, launch_rhs(d, fields(), addback, x, pl->r, pl->tw_y, mu, lam, gam, pl->st, tol2,
-                                        red_of(pl), s));
+            SB_LAUNCH(pl, SB_KCLASS_RHS, 1, launch_rhs(d, pl->smap, pl->ymap, pl->y1map, fields(), addback, x, pl->r,
+                                                       pl->tw_y, mu, lam, gam, pl->st, tol2, red_of(pl), s));
             sb_status ps = pcg_run(pl, o->pcg, x, h_last, iters.data() + solve, nsolve);
             if (ps != SB_OK && first_err == SB_OK) first_err = ps;
             const bool last = (j == o->n_outer - 1) && (k == o->n_inner - 1);
             if (!last) {
-                SB_LAUNCH(pl, 1, launch_sb_update(d, fields(), x, levels, lam, gam, tau_tv, tau_w, s));
+                SB_LAUNCH(pl, SB_KCLASS_SB_UPDATE, 1, launch_sb_update(d, fields(), x, levels, lam, gam, tau_tv, tau_w, s));
                 if (lam != 0.f) cur ^= 1;
             }
         }
     }
     SB_CK(pl, cudaStreamSynchronize(s));
+    timer_harvest(pl);
     if (o->h_iters) std::memcpy(o->h_iters, iters.data(), sizeof(int) * iters.size());
     return first_err;
+}
+
+sb_status sb_plan_set_timing(sb_plan pl, unsigned class_mask) {
+    if (!pl) return SB_ERR_INVALID_ARG;
+    SB_CK(pl, pl->stream ? cudaStreamSynchronize(pl->stream) : cudaDeviceSynchronize());
+    timer_harvest(pl);
+    pl->tmask = class_mask;
+    for (int c = 0; c < SB_KCLASS_COUNT; ++c) {
+        pl->tcount[c] = 0;
+        pl->tms[c] = 0.0;
+    }
+    return SB_OK;
+}
+
+sb_status sb_plan_get_timing(sb_plan pl, int kernel_class, uint64_t* launches, double* total_ms) {
+    if (!pl || kernel_class < 0 || kernel_class >= SB_KCLASS_COUNT || !launches || !total_ms)
+        return fail(pl, SB_ERR_INVALID_ARG, "bad timing query");
+    SB_CK(pl, pl->stream ? cudaStreamSynchronize(pl->stream) : cudaDeviceSynchronize());
+    timer_harvest(pl);
+    *launches = pl->tcount[kernel_class];
+    *total_ms = pl->tms[kernel_class];
+    return SB_OK;
 }
 
 }  // extern "C"

@@ -70,7 +70,23 @@ SIGNATURES = [
     ("sb_status_string", ctypes.c_char_p, [ctypes.c_int]),
     ("sb_plan_last_error", ctypes.c_char_p, [_P]),
     ("sb_kernel_launches", ctypes.c_uint64, []),
+    ("sb_plan_set_timing", ctypes.c_int, [_P, ctypes.c_uint]),
+    ("sb_plan_get_timing", ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_uint64),
+                                          ctypes.POINTER(ctypes.c_double)]),
 ]
+
+# sb_kernel_class
+SB_KCLASS_APPLY_A = 0
+SB_KCLASS_PRECOND_ROW_FWD = 1
+SB_KCLASS_PRECOND_COL = 2
+SB_KCLASS_PRECOND_ROW_INV = 3
+SB_KCLASS_RHS = 4
+SB_KCLASS_SB_UPDATE = 5
+SB_KCLASS_VEC = 6
+SB_KCLASS_OTHER = 7
+SB_KCLASS_COUNT = 8
+KCLASS_NAMES = ["apply_A", "precond_row_fwd", "precond_col", "precond_row_inv", "rhs", "sb_update", "vec",
+                "other"]
 
 
 def load(path: str = LIB_PATH) -> ctypes.CDLL:
@@ -168,6 +184,18 @@ def sb_split_bregman(plan: int, d_y: int, d_x: int, n_outer: int, n_inner: int, 
     return st, it, [(r.iters, r.rel_resid, bool(r.converged)) for r in last]
 
 
+def sb_plan_set_timing(plan: int, class_mask: int) -> None:
+    _check(_lib.sb_plan_set_timing(_P(plan), class_mask), plan)
+
+
+def sb_plan_get_timing(plan: int, kernel_class: int):
+    """(launches, total_ms) of the kernel class since sb_plan_set_timing."""
+    n = ctypes.c_uint64()
+    ms = ctypes.c_double()
+    _check(_lib.sb_plan_get_timing(_P(plan), kernel_class, ctypes.byref(n), ctypes.byref(ms)), plan)
+    return int(n.value), float(ms.value)
+
+
 class Plan:
     """Owns an sb_plan and the device tensors it borrows (torch CUDA tensors)."""
 
@@ -221,6 +249,12 @@ class Plan:
 
     def pcg_solve(self, b, x, **kw):
         return sb_pcg_solve(self.handle, self._c64(b), self._c64(x), pcg_opts(**kw), self.nbatch)
+
+    def set_timing(self, class_mask: int):
+        sb_plan_set_timing(self.handle, class_mask)
+
+    def timing(self, kernel_class: int):
+        return sb_plan_get_timing(self.handle, kernel_class)
 
     def split_bregman(self, y, x, n_outer, n_inner=1, tau_tv=0.0, tau_w=0.0, init_rss=True, **pcg_kw):
         return sb_split_bregman(self.handle, self._c64(y), self._c64(x), n_outer, n_inner, pcg_opts(**pcg_kw),
