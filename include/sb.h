@@ -138,6 +138,22 @@ typedef struct {
 sb_status sb_split_bregman(sb_plan plan, const void* d_y, void* d_x, const sb_sb_opts* opts,
                            sb_pcg_result* h_last);
 
+/* d_z = F^H diag(d_k)^{-1} F d_r, like sb_apply_precond, but without a plan and without any
+ * device allocation, for callers that cannot call cudaMalloc when they apply the
+ * preconditioner (fixed memory budgets after start-up, plugins handed only pre-allocated
+ * buffers, hosts whose framework owns the memory pool).  The paper has no counterpart; this is
+ * a deployment variant of the same operation.
+ *   d_r, d_z: complex64 [nbatch][ny][nx] (may be equal); d_k: float32 [nbatch][ny][nx], the
+ *   diagonal k as returned by sb_get_k; cuda_stream: a cudaStream_t (NULL = legacy stream).
+ *   nx, ny in {32, 64, 128, 256}; nbatch * ny * nx <= 1048576, else SB_ERR_INVALID_ARG.
+ * The intermediate lives in one fixed 8 MiB device array that this library defines and every
+ * GPU using it keeps until the process exits.  The first call on a device sets that array up
+ * (resolves its address, writes the DFT twiddle tables with a synchronous copy), so make it
+ * before any stream capture.  All calls share the array: calls whose kernels overlap on the
+ * GPU race with each other and must be ordered by the caller.  Asynchronous after set-up. */
+sb_status sb_apply_precond_noalloc(const void* d_r, const float* d_k, void* d_z, int nx, int ny,
+                                   int nbatch, void* cuda_stream);
+
 /* Human-readable name of a status code (static string). */
 const char* sb_status_string(sb_status status);
 

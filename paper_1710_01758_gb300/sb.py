@@ -70,6 +70,7 @@ SIGNATURES = [
     ("sb_status_string", ctypes.c_char_p, [ctypes.c_int]),
     ("sb_plan_last_error", ctypes.c_char_p, [_P]),
     ("sb_kernel_launches", ctypes.c_uint64, []),
+    ("sb_apply_precond_noalloc", ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P]),
     ("sb_plan_set_timing", ctypes.c_int, [_P, ctypes.c_uint]),
     ("sb_plan_get_timing", ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_uint64),
                                           ctypes.POINTER(ctypes.c_double)]),
@@ -182,6 +183,11 @@ def sb_split_bregman(plan: int, d_y: int, d_x: int, n_outer: int, n_inner: int, 
     st = _check(_lib.sb_split_bregman(_P(plan), _P(d_y), _P(d_x), ctypes.byref(opts), last), plan, allow)
     it = [[iters[b * nsolve + i] for i in range(nsolve)] for b in range(nbatch)]
     return st, it, [(r.iters, r.rel_resid, bool(r.converged)) for r in last]
+
+
+def sb_apply_precond_noalloc(d_r: int, d_k: int, d_z: int, nx: int, ny: int, nbatch: int, stream: int = 0) -> None:
+    """Plan-free, allocation-free M^{-1} r (see include/sb.h)."""
+    _check(_lib.sb_apply_precond_noalloc(_P(d_r), _P(d_k), _P(d_z), nx, ny, nbatch, _P(stream)))
 
 
 def sb_plan_set_timing(plan: int, class_mask: int) -> None:
