@@ -58,8 +58,13 @@ typedef struct {
     int ncoils;             /* N_c */
     int nbatch;             /* independent slices of this geometry solved together (>= 1) */
     double mu, lambda, gamma;  /* weights of Eq. system; mu > 0, lambda >= 0, gamma >= 0 */
-    int wavelet_levels;     /* Haar levels of W used by sb_split_bregman; 0 = no wavelet term */
+    int wavelet_levels;     /* Haar levels of W used by sb_split_bregman; 0 = identity W */
     sb_precision prec;      /* SB_PREC_FP32 */
+    int groups;             /* sb_pcg_solve / sb_split_bregman run the batch as this many
+                               contiguous slice groups, each on its own stream driven by its own
+                               host thread, so that one group's work fills the GPU while another
+                               waits on its convergence test; 0 = automatic (nbatch / 8, at most
+                               4, at least 1); clamped to [1, nbatch] */
 } sb_plan_desc;
 
 typedef struct sb_plan_s* sb_plan;

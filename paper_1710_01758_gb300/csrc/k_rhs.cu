@@ -4,12 +4,14 @@
 // Per column tile of one slice and per coil c (yt = F_x^H y on the sampled lines, see k_sb.cu):
 //   u   = R_y F_y (S_c x)                      forward DFT along y, kept on sampled lines
 //   yt  = yt + yt1 - u                         outer update (ADDBACK), written back
-//   b  += S_c^H F_y^H yt                       inverse DFT
-//   r  += S_c^H F_y^H (yt - u)                 inverse DFT: data term of b - A x
-// then b = mu b + g, r = mu r + g - lambda D^H D x - gamma x, with ||b||^2, ||r||^2 and the
-// initial convergence test in the last CTA of the slice.  The coil tile S_c and the compact
-// rows of yt and yt1 arrive by TMA into a two-stage shared-memory pipeline (coil c + 1 in
-// flight while coil c is transformed).
+//   e  += S_c^H F_y^H (yt - u)                 inverse DFT: data term of b - A x
+// With B(y) = sum_c S_c^H F^H R y_c (linear) the data term of b is bd = B(y^[j]); the outer
+// update y^[j+1] = y^[j] + y^[1] - R F S x gives bd' = bd + bd1 - B(R F S x), and the pass
+// computes e = bd' - B(R F S x), so bd' = (e + bd + bd1) / 2 exactly, without a second
+// inverse transform per coil.  Then b = mu bd' + g, r = mu e + g - lambda D^H D x - gamma x,
+// with ||b||^2, ||r||^2 and the initial convergence test in the last CTA of the slice.  The
+// coil tile S_c and the compact rows of yt and yt1 arrive by TMA into a two-stage
+// shared-memory pipeline (coil c + 1 in flight while coil c is transformed).
 #include "common.cuh"
 #include "kernels.h"
 #include "tma.cuh"
@@ -70,11 +72,11 @@ k_rhs(const __grid_constant__ CUtensorMap smap, const __grid_constant__ CUtensor
         sl[i] = f.slot[(size_t)b * NY + i];
     }
     const size_t img = (size_t)b * NY * nx;
-    float2 xv[16], bacc[16], racc[16];
+    float2 xv[16], racc[16];
 #pragma unroll
     for (int e = 0; e < 16; ++e) {
         xv[e] = xin[img + (size_t)(t + T * e) * nx + xg];
-        bacc[e] = racc[e] = make_float2(0.f, 0.f);
+        racc[e] = make_float2(0.f, 0.f);
     }
     __syncthreads();
     const ColIdx idx{col};
@@ -86,11 +88,12 @@ k_rhs(const __grid_constant__ CUtensorMap smap, const __grid_constant__ CUtensor
         const float2* Yt = S + NY * TX;
         const float2* Y1 = Yt + ms * TX;
         const size_t ybase = ((size_t)b * nc + c) * ms * nx;
-        float2 u[16], v1[16];
+        float2 u[16];
 #pragma unroll
         for (int e = 0; e < 16; ++e) u[e] = cmul(S[idx(t + T * e)], xv[e]);
         fft_2stage<NY, false>(u, t, xbuf, idx, tw);
-        // u <- R F S x on sampled lines (unitary scale); v1 <- y^[j] after the outer update
+        // on sampled lines: tt = R F S x (unitary scale), yv = y^[j] after the outer update,
+        // u <- yv - tt; zero elsewhere
 #pragma unroll
         for (int e = 0; e < 16; ++e) {
             const int s = sl[t + T * e];
@@ -101,17 +104,11 @@ k_rhs(const __grid_constant__ CUtensorMap smap, const __grid_constant__ CUtensor
                     yv = csub(cadd(yv, Y1[s * TX + col]), tt);
                     f.yt[ybase + (size_t)s * nx + xg] = yv;
                 }
-                v1[e] = yv;
                 u[e] = csub(yv, tt);
             } else {
-                v1[e] = make_float2(0.f, 0.f);
                 u[e] = make_float2(0.f, 0.f);
             }
         }
-        __syncthreads();
-        fft_2stage<NY, true>(v1, t, xbuf, idx, tw);
-#pragma unroll
-        for (int e = 0; e < 16; ++e) bacc[e] = cfmac(bacc[e], S[idx(t + T * e)], cscale(v1[e], sc));
         __syncthreads();
         fft_2stage<NY, true>(u, t, xbuf, idx, tw);
 #pragma unroll
@@ -119,7 +116,8 @@ k_rhs(const __grid_constant__ CUtensorMap smap, const __grid_constant__ CUtensor
         __syncthreads();  // this stage's tiles and xbuf are free
         if (tid == 0 && c + 2 < nc) issue(c + 2, stage);
     }
-    // b = mu bacc + g ;  r = mu racc + g - lam D^H D x - gam x
+    // bd' = (racc + bd + bd1) / 2 after an outer update (else bd' = bd);
+    // b = mu bd' + g ;  r = mu racc + g - lam D^H D x - gam x
 #pragma unroll
     for (int e = 0; e < 16; ++e) xbuf[idx(t + T * e)] = xv[e];
     for (int i = tid; i < NY; i += NT) {
@@ -139,7 +137,13 @@ k_rhs(const __grid_constant__ CUtensorMap smap, const __grid_constant__ CUtensor
         const float2 rt = col < TX - 1 ? xbuf[idx(yy) + 1] : halo[NY + yy];
         const float tvx = 4.f * xv[e].x - up.x - dn.x - lf.x - rt.x;
         const float tvy = 4.f * xv[e].y - up.y - dn.y - lf.y - rt.y;
-        const float2 bvec = make_float2(fmaf(mu, bacc[e].x, gv.x), fmaf(mu, bacc[e].y, gv.y));
+        float2 bdv = f.bd[gi];
+        if (ADDBACK) {
+            const float2 b1 = f.bd1[gi];
+            bdv = make_float2(0.5f * (racc[e].x + bdv.x + b1.x), 0.5f * (racc[e].y + bdv.y + b1.y));
+            f.bd[gi] = bdv;
+        }
+        const float2 bvec = make_float2(fmaf(mu, bdv.x, gv.x), fmaf(mu, bdv.y, gv.y));
         float2 rv;
         rv.x = fmaf(mu, racc[e].x, gv.x) - fmaf(lam, tvx, gam * xv[e].x);
         rv.y = fmaf(mu, racc[e].y, gv.y) - fmaf(lam, tvy, gam * xv[e].y);

@@ -7,11 +7,10 @@
 // exactly like the data term of A.
 //
 //  k_ytilde     yt1 = F_x^H y on the sampled lines (once per reconstruction).
-//  k_rss        x = sqrt(sum_i |F^H y_i|^2) (step 1).
+//  k_rss        x = sqrt(sum_i |F^H y_i|^2) (step 1) and the data term of b for y^[1],
+//               bd1 = sum_i S_i^H F^H y_i^[1], from the same inverse transforms.
 //  (the right-hand side and initial residual kernel is in k_rhs.cu)
-//  k_sb_update  steps 6-11 on a 16x16 tile: TV shrink + Bregman updates, Haar analysis,
-//               wavelet shrink + Bregman update, Haar synthesis, and the next
-//               g = lam (D_x^H(d_x-b_x) + D_y^H(d_y-b_y)) + gam W^H(d_w-b_w).
+//  (steps 6-11, shrink and Bregman updates, are in k_sbupd.cu)
 #include "common.cuh"
 #include "kernels.h"
 
@@ -69,7 +68,7 @@ k_ytilde(const float2* __restrict__ y, const int* __restrict__ lines, int ny, in
 // ------------------------------------------------------------------ root-sum-of-squares start
 template <int NY>
 __global__ void __launch_bounds__(TX * NY / 16)
-k_rss(SbFields f, int nx, int nc, float2* __restrict__ x, const float2* __restrict__ tw_g) {
+k_rss(SbFields f, int nx, int nc, float2* __restrict__ x, int write_x, const float2* __restrict__ tw_g) {
     constexpr int T = NY / 16;
     constexpr int NT = TX * T;
     const int b = blockIdx.y;
@@ -86,12 +85,17 @@ k_rss(SbFields f, int nx, int nc, float2* __restrict__ x, const float2* __restri
     }
     __syncthreads();
     float acc[16];
+    float2 bda[16];
 #pragma unroll
-    for (int e = 0; e < 16; ++e) acc[e] = 0.f;
+    for (int e = 0; e < 16; ++e) {
+        acc[e] = 0.f;
+        bda[e] = make_float2(0.f, 0.f);
+    }
     const ColIdx idx{col};
     const float sc = rsqrtf((float)NY);
     for (int c = 0; c < nc; ++c) {
         const float2* Y = f.yt1 + ((size_t)b * nc + c) * f.ms * nx;
+        const float2* S = f.sens + ((size_t)b * nc + c) * NY * nx;
         float2 v[16];
 #pragma unroll
         for (int e = 0; e < 16; ++e) {
@@ -100,115 +104,19 @@ k_rss(SbFields f, int nx, int nc, float2* __restrict__ x, const float2* __restri
         }
         fft_2stage<NY, true>(v, t, (c & 1) ? buf1 : buf0, idx, tw);
 #pragma unroll
-        for (int e = 0; e < 16; ++e) acc[e] += cabs2(v[e]) * (sc * sc);
+        for (int e = 0; e < 16; ++e) {
+            const float2 ci = cscale(v[e], sc);  // coil image F^H y_c
+            acc[e] += cabs2(ci);
+            bda[e] = cfmac(bda[e], __ldg(S + (size_t)(t + T * e) * nx + xg), ci);
+        }
     }
 #pragma unroll
-    for (int e = 0; e < 16; ++e)
-        x[((size_t)b * NY + t + T * e) * nx + xg] = make_float2(sqrtf(acc[e]), 0.f);
-}
-
-// ------------------------------------------------------------------ steps 6-11 on a 16x16 tile
-__device__ __forceinline__ float2 shrink(float2 z, float t) {
-    const float m = sqrtf(cabs2(z));
-    const float s = m > t ? (m - t) / m : 0.f;
-    return cscale(z, s);
-}
-
-// One orthonormal Haar level on the leading `n` x `n` corner of a 16x16 tile (Mallat layout):
-// along x, then along y.  inverse: along y, then along x.
-__device__ void haar_level(float2 (*w)[16], int n, bool inverse) {
-    const int tid = threadIdx.x;
-    const int ry = tid / 16, cx = tid % 16;
-    const float h = 0.70710678118654752f;
-    const int half = n / 2;
-    for (int pass = 0; pass < 2; ++pass) {
-        const bool along_x = inverse ? (pass == 1) : (pass == 0);
-        float2 o = make_float2(0.f, 0.f);
-        const bool act = ry < n && cx < n;
-        if (act) {
-            const int i = along_x ? cx : ry;
-            if (!inverse) {
-                const int j = (i < half) ? i : i - half;
-                const float2 a = along_x ? w[ry][2 * j] : w[2 * j][cx];
-                const float2 c = along_x ? w[ry][2 * j + 1] : w[2 * j + 1][cx];
-                o = (i < half) ? cscale(cadd(a, c), h) : cscale(csub(a, c), h);
-            } else {
-                const int j = i >> 1;
-                const float2 lo = along_x ? w[ry][j] : w[j][cx];
-                const float2 hi = along_x ? w[ry][j + half] : w[j + half][cx];
-                o = (i & 1) ? cscale(csub(lo, hi), h) : cscale(cadd(lo, hi), h);
-            }
-        }
-        __syncthreads();
-        if (act) w[ry][cx] = o;
-        __syncthreads();
+    for (int e = 0; e < 16; ++e) {
+        const size_t gi = ((size_t)b * NY + t + T * e) * nx + xg;
+        f.bd1[gi] = bda[e];
+        f.bd[gi] = bda[e];
+        if (write_x) x[gi] = make_float2(sqrtf(acc[e]), 0.f);
     }
-}
-
-__global__ void __launch_bounds__(256)
-k_sb_update(SbFields f, int nx, int ny, const float2* __restrict__ x, int levels, float lam, float gam,
-            float tau_tv, float tau_w) {
-    __shared__ float2 xs[18][18];   // x with a one-pixel periodic halo
-    __shared__ float2 ux[17][17];   // d_x - b_x (new) on the tile and its +1 halo
-    __shared__ float2 uy[17][17];
-    __shared__ float2 w[16][16];
-    const int b = blockIdx.z;
-    const int y0 = blockIdx.y * 16, x0 = blockIdx.x * 16;
-    const int tid = threadIdx.x;
-    const size_t img = (size_t)b * ny * nx;
-    for (int i = tid; i < 18 * 18; i += 256) {
-        const int ly = i / 18, lx = i % 18;
-        const int gy = (y0 - 1 + ly + ny) % ny, gx = (x0 - 1 + lx + nx) % nx;
-        xs[ly][lx] = x[img + (size_t)gy * nx + gx];
-    }
-    __syncthreads();
-    const int ty = tid / 16, tx = tid % 16;
-    const size_t own = img + (size_t)(y0 + ty) * nx + x0 + tx;
-    float2 gout = make_float2(0.f, 0.f);
-    if (lam != 0.f) {
-        // u = d - b (new) on the tile and its +1 halo; the halo cells belong to neighbouring
-        // tiles, whose CTAs write their new b into the other buffer, so reading the old
-        // buffer here is race-free
-        for (int i = tid; i < 17 * 17; i += 256) {
-            const int ly = i / 17, lx = i % 17;
-            const int gy = (y0 + ly) % ny, gx = (x0 + lx) % nx;
-            const size_t gi = img + (size_t)gy * nx + gx;
-            const float2 xc = xs[ly + 1][lx + 1];
-            const float2 dxv = csub(xc, xs[ly + 1][lx]);   // D_x x
-            const float2 dyv = csub(xc, xs[ly][lx + 1]);   // D_y x
-            const float2 bxv = f.bx[gi], byv = f.by[gi];
-            const float2 dx = shrink(cadd(dxv, bxv), tau_tv);
-            const float2 dy = shrink(cadd(dyv, byv), tau_tv);
-            const float2 bxn = csub(cadd(bxv, dxv), dx);
-            const float2 byn = csub(cadd(byv, dyv), dy);
-            ux[ly][lx] = csub(dx, bxn);
-            uy[ly][lx] = csub(dy, byn);
-            if (ly < 16 && lx < 16) {
-                f.bx_new[gi] = bxn;
-                f.by_new[gi] = byn;
-            }
-        }
-        __syncthreads();
-        const float2 tvx = csub(ux[ty][tx], ux[ty][tx + 1]);
-        const float2 tvy = csub(uy[ty][tx], uy[ty + 1][tx]);
-        gout = cscale(cadd(tvx, tvy), lam);
-    }
-    if (gam != 0.f) {  // levels == 0: W is the identity
-        w[ty][tx] = xs[ty + 1][tx + 1];
-        __syncthreads();
-        for (int l = 0, n = 16; l < levels; ++l, n >>= 1) haar_level(w, n, false);
-        const float2 wc = w[ty][tx];
-        const float2 bwv = f.bw[own];
-        const float2 dw = shrink(cadd(wc, bwv), tau_w);
-        const float2 bwn = csub(cadd(bwv, wc), dw);
-        f.bw[own] = bwn;
-        __syncthreads();
-        w[ty][tx] = csub(dw, bwn);
-        __syncthreads();
-        for (int l = levels - 1; l >= 0; --l) haar_level(w, 16 >> l, true);
-        gout = cadd(gout, cscale(w[ty][tx], gam));
-    }
-    f.g[own] = gout;
 }
 
 template <int NX>
@@ -241,7 +149,8 @@ cudaError_t launch_ytilde(const Dims& d, const float2* y, const int* lines, int 
 #undef CALL
 }
 
-cudaError_t launch_rss(const Dims& d, const SbFields& f, float2* x, const float2* tw_y, cudaStream_t s) {
+cudaError_t launch_rss(const Dims& d, const SbFields& f, float2* x, int write_x, const float2* tw_y,
+                       cudaStream_t s) {
     const dim3 grid(d.nx / TX, d.nb);
     cudaError_t e;
 #define CALL(N)                                                                                            \
@@ -251,7 +160,7 @@ cudaError_t launch_rss(const Dims& d, const SbFields& f, float2* x, const float2
             (e = cudaFuncSetAttribute(k_rss<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)) != \
                 cudaSuccess)                                                                               \
             return e;                                                                                      \
-        k_rss<N><<<grid, TX * N / 16, sm, s>>>(f, d.nx, d.nc, x, tw_y);                                    \
+        k_rss<N><<<grid, TX * N / 16, sm, s>>>(f, d.nx, d.nc, x, write_x, tw_y);                           \
         return cudaGetLastError();                                                                         \
     }
     switch (d.ny) {
@@ -262,13 +171,6 @@ cudaError_t launch_rss(const Dims& d, const SbFields& f, float2* x, const float2
         default: return cudaErrorInvalidValue;
     }
 #undef CALL
-}
-
-cudaError_t launch_sb_update(const Dims& d, const SbFields& f, const float2* x, int levels, float lam, float gam,
-                             float tau_tv, float tau_w, cudaStream_t s) {
-    const dim3 grid(d.nx / 16, d.ny / 16, d.nb);
-    k_sb_update<<<grid, 256, 0, s>>>(f, d.nx, d.ny, x, levels, lam, gam, tau_tv, tau_w);
-    return cudaGetLastError();
 }
 
 }  // namespace sb

@@ -120,16 +120,19 @@ struct SbFields {
     float2* by_new;
     float2* bw;           // wavelet Bregman variable, tile-local Mallat layout, in place
     float2* g;            // lam Dx^H(dx-bx) + lam Dy^H(dy-by) + gam W^H(dw-bw)
+    float2* bd;           // [nb][N]: data term of b for the current y^[j]: sum_c S_c^H F^H R y_c^[j]
+    float2* bd1;          // [nb][N]: the same for y^[1]
 };
 
 // yt1[b][c][s][:] = F_x^H y[b][c][line(s)][:] (unitary).
 cudaError_t launch_ytilde(const Dims& d, const float2* y, const int* lines, int ms, float2* yt1,
                           const float2* tw_x, cudaStream_t s);
-// x = sqrt(sum_c |F^H y_c|^2) from yt1.
-cudaError_t launch_rss(const Dims& d, const SbFields& f, float2* x, const float2* tw_y,
+// Start of Algorithm 1 from yt1: bd1 = bd = sum_c S_c^H F^H y_c and, if write_x,
+// x = sqrt(sum_c |F^H y_c|^2).
+cudaError_t launch_rss(const Dims& d, const SbFields& f, float2* x, int write_x, const float2* tw_y,
                        cudaStream_t s);
 // Right-hand side and initial residual: optional outer data update yt += yt1 - R F S x,
-// b = mu sum_c S_c^H F^H yt_c + g, r = b - A x; ||b||^2, ||r||^2, state.
+// b = mu bd + g with bd advanced by linearity, r = b - A x; ||b||^2, ||r||^2, state.
 // smap: as for launch_apply_A; ymap / y1map: TMA maps of yt / yt1 viewed as float32
 // [nb*nc*ms][2*nx] with box [ms][2*kColTile].
 cudaError_t launch_rhs(const Dims& d, const CUtensorMap& smap, const CUtensorMap& ymap,

@@ -1,12 +1,21 @@
 // C-ABI layer (include/sb.h): plan object, workspace, argument checks, and the host-side
 // drivers of preconditioned CG and of Split Bregman (Algorithm 1).  Every numerical step runs
-// in the kernels of k_pcg.cu, k_setup.cu and k_sb.cu; the host only sequences launches and
-// reads the per-slice CG state back to decide when to stop.
+// in the kernels of k_*.cu; the host only sequences launches and reads the per-slice CG state
+// back to decide when to stop.
+//
+// Execution contexts: the batch is split into contiguous slice groups, each with its own stream
+// and its own host thread for sb_pcg_solve and sb_split_bregman.  Slices converge after
+// different numbers of PCG iterations; within one group the later iterations run with few
+// active slices, and the concurrent groups fill the GPU meanwhile.  The groups fork from and
+// join back into the plan's stream, so callers see ordinary stream-ordered calls.
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "kernels.h"
@@ -23,7 +32,30 @@ constexpr int kPollEvery = 4;
 
 bool supported_n(int n) { return n == 32 || n == 64 || n == 128 || n == 256; }
 
+struct Pending {
+    int cls;
+    cudaEvent_t a, b;
+};
+
 }  // namespace
+
+// A contiguous range of slices [b0, b0 + d.nb) driven on one stream.
+struct Exec {
+    sb_plan pl = nullptr;
+    int b0 = 0;
+    Dims d{};
+    cudaStream_t s = nullptr;
+    bool own_stream = false;
+    CUtensorMap smap{}, ymap{}, y1map{};  // TMA maps whose first row belongs to slice b0
+    SliceState* st = nullptr;             // device state of the range
+    SliceState* h_st = nullptr;           // pinned mirror of the range
+    Red red{};
+    unsigned h_err = 0;
+    std::string err;
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> ev_pool;
+    cudaEvent_t join = nullptr;
+};
 
 struct sb_plan_s {
     sb_plan_desc d{};
@@ -47,6 +79,7 @@ struct sb_plan_s {
     float2* bx[2] = {nullptr, nullptr};
     float2* by[2] = {nullptr, nullptr};
     float2 *bw = nullptr, *g = nullptr;
+    float2 *bd = nullptr, *bd1 = nullptr;  // data term of b for y^[j] and for y^[1]
     float2 *yt = nullptr, *yt1 = nullptr;
     size_t yt_elems = 0;
     SliceState* st = nullptr;
@@ -55,21 +88,17 @@ struct sb_plan_s {
     unsigned* counter = nullptr;
     unsigned* kmax = nullptr;
     unsigned* derr = nullptr;  // device error word
-    unsigned h_err = 0;
-    CUtensorMap smap;         // TMA map of the sensitivities
-    CUtensorMap ymap, y1map;  // TMA maps of yt and yt1
     // k construction scratch (kept after the first sb_set_mask so later calls do not allocate)
     float2 *spec = nullptr, *gb = nullptr, *rb = nullptr;
     int *line_val = nullptr, *line_uni = nullptr;
 
-    // event timer per kernel class
-    struct Pending {
-        int cls;
-        cudaEvent_t a, b;
-    };
+    Exec whole;                 // the full batch on the plan's stream
+    std::vector<Exec> groups;   // concurrent slice groups
+    cudaEvent_t fork = nullptr;
+
+    // event timer per kernel class (totals over all contexts)
     unsigned tmask = 0;
-    std::vector<cudaEvent_t> ev_pool;
-    std::vector<Pending> pending;
+    std::mutex tmu;
     uint64_t tcount[SB_KCLASS_COUNT] = {};
     double tms[SB_KCLASS_COUNT] = {};
 };
@@ -81,68 +110,87 @@ sb_status fail(sb_plan pl, sb_status s, const std::string& msg) {
     return s;
 }
 
-sb_status cuda_fail(sb_plan pl, const char* what, cudaError_t e) {
-    return fail(pl, SB_ERR_CUDA, std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")");
+sb_status xfail(Exec& ex, sb_status s, const std::string& msg) {
+    ex.err = msg;
+    return s;
 }
 
-#define SB_CK(pl, call)                                              \
-    do {                                                             \
-        cudaError_t e_ = (call);                                     \
-        if (e_ != cudaSuccess) return cuda_fail((pl), #call, e_);    \
+std::string cuda_msg(const char* what, cudaError_t e) {
+    return std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+}
+
+#define SB_CK(pl, call)                                                            \
+    do {                                                                           \
+        cudaError_t e_ = (call);                                                   \
+        if (e_ != cudaSuccess) return fail((pl), SB_ERR_CUDA, cuda_msg(#call, e_)); \
     } while (0)
 
-cudaEvent_t timer_begin(sb_plan pl, int cls) {
-    if (!(pl->tmask & (1u << cls))) return nullptr;
+#define SB_XCK(ex, call)                                                             \
+    do {                                                                             \
+        cudaError_t e_ = (call);                                                     \
+        if (e_ != cudaSuccess) return xfail((ex), SB_ERR_CUDA, cuda_msg(#call, e_)); \
+    } while (0)
+
+cudaEvent_t timer_begin(Exec& ex, int cls) {
+    if (!(ex.pl->tmask & (1u << cls))) return nullptr;
     cudaEvent_t a = nullptr;
-    if (!pl->ev_pool.empty()) {
-        a = pl->ev_pool.back();
-        pl->ev_pool.pop_back();
+    if (!ex.ev_pool.empty()) {
+        a = ex.ev_pool.back();
+        ex.ev_pool.pop_back();
     } else if (cudaEventCreate(&a) != cudaSuccess) {
         return nullptr;
     }
-    if (cudaEventRecord(a, pl->stream) != cudaSuccess) {
-        pl->ev_pool.push_back(a);
+    if (cudaEventRecord(a, ex.s) != cudaSuccess) {
+        ex.ev_pool.push_back(a);
         return nullptr;
     }
     return a;
 }
 
-void timer_end(sb_plan pl, int cls, cudaEvent_t a) {
+void timer_end(Exec& ex, int cls, cudaEvent_t a) {
     if (!a) return;
     cudaEvent_t b = nullptr;
-    if (!pl->ev_pool.empty()) {
-        b = pl->ev_pool.back();
-        pl->ev_pool.pop_back();
+    if (!ex.ev_pool.empty()) {
+        b = ex.ev_pool.back();
+        ex.ev_pool.pop_back();
     } else if (cudaEventCreate(&b) != cudaSuccess) {
-        pl->ev_pool.push_back(a);
+        ex.ev_pool.push_back(a);
         return;
     }
-    cudaEventRecord(b, pl->stream);
-    pl->pending.push_back({cls, a, b});
+    cudaEventRecord(b, ex.s);
+    ex.pending.push_back({cls, a, b});
 }
 
-// accumulate the recorded event pairs; call only after the stream has been synchronised
-void timer_harvest(sb_plan pl) {
-    for (const auto& p : pl->pending) {
+// accumulate the recorded event pairs; call only after ex.s has been synchronised
+void timer_harvest(Exec& ex) {
+    if (ex.pending.empty()) return;
+    double ms_c[SB_KCLASS_COUNT] = {};
+    uint64_t n_c[SB_KCLASS_COUNT] = {};
+    for (const auto& p : ex.pending) {
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
-            pl->tms[p.cls] += ms;
-            pl->tcount[p.cls] += 1;
+            ms_c[p.cls] += ms;
+            n_c[p.cls] += 1;
         }
-        pl->ev_pool.push_back(p.a);
-        pl->ev_pool.push_back(p.b);
+        ex.ev_pool.push_back(p.a);
+        ex.ev_pool.push_back(p.b);
     }
-    pl->pending.clear();
+    ex.pending.clear();
+    std::lock_guard<std::mutex> lock(ex.pl->tmu);
+    for (int c = 0; c < SB_KCLASS_COUNT; ++c) {
+        ex.pl->tms[c] += ms_c[c];
+        ex.pl->tcount[c] += n_c[c];
+    }
 }
 
 // launch helper: counts kernels and, when enabled for the class, times them with events
-#define SB_LAUNCH(pl, cls, nk, call)                                 \
-    do {                                                             \
-        cudaEvent_t ta_ = timer_begin((pl), (cls));                  \
-        cudaError_t e_ = (call);                                     \
-        if (e_ != cudaSuccess) return cuda_fail((pl), #call, e_);    \
-        timer_end((pl), (cls), ta_);                                 \
-        g_launches.fetch_add((nk), std::memory_order_relaxed);       \
+#define SB_LAUNCH(ex, cls, nk, call)                                               \
+    do {                                                                           \
+        cudaEvent_t ta_ = timer_begin((ex), (cls));                                \
+        cudaError_t e_ = (call);                                                   \
+        if (e_ != cudaSuccess) return xfail((ex), SB_ERR_CUDA, cuda_msg(#call, e_)); \
+        timer_end((ex), (cls), ta_);                                               \
+        g_launches.fetch_add((nk), std::memory_order_relaxed);                     \
     } while (0)
 
 template <class T>
@@ -183,74 +231,109 @@ EncodeTiledFn tensor_map_encoder() {
     return fn;
 }
 
-Red red_of(sb_plan pl) { return Red{pl->part, pl->counter, pl->derr}; }
+// float32 view [rows][2 nx] of complex rows starting at base; box = box_rows x one column tile
+bool encode_rows(CUtensorMap* m, const void* base, int nx, size_t rows, int box_rows) {
+    auto encode = tensor_map_encoder();
+    if (!encode) return false;
+    const cuuint64_t gdim[2] = {(cuuint64_t)2 * nx, (cuuint64_t)rows};
+    const cuuint64_t gstride[1] = {(cuuint64_t)2 * nx * sizeof(float)};
+    const cuuint32_t box[2] = {(cuuint32_t)2 * kColTile, (cuuint32_t)box_rows};
+    const cuuint32_t estride[2] = {1, 1};
+    return encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), gdim, gstride, box, estride,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
 
-// Sequence CG from the state left by launch_resid_init / launch_rhs (r = r0, bnorm2, state).
-// Returns the worst per-slice status; fills h_results (may be null).
-sb_status pcg_run(sb_plan pl, const sb_pcg_opts& o, float2* x, sb_pcg_result* h_results, int* iters_out,
+void bind_exec(sb_plan pl, Exec& ex, int b0, int nb, cudaStream_t s) {
+    ex.pl = pl;
+    ex.b0 = b0;
+    ex.d = Dims{pl->dims.nx, pl->dims.ny, pl->dims.nc, nb};
+    ex.s = s;
+    ex.st = pl->st + b0;
+    ex.h_st = pl->h_st + b0;
+    ex.red = Red{pl->part + (size_t)b0 * kMaxParts * 2, pl->counter + b0, pl->derr};
+}
+
+// pointer to slice b0 of an array whose slices hold `per` elements
+template <class T>
+T* at(T* base, const Exec& ex, size_t per) {
+    return base + (size_t)ex.b0 * per;
+}
+
+// Sequence CG on the context's slices from the state left by launch_resid_init / launch_rhs
+// (r = r0, bnorm2, state).  x and the result arrays are the full-batch ones.
+sb_status pcg_run(Exec& ex, const sb_pcg_opts& o, float2* x_full, sb_pcg_result* h_results, int* iters_out,
                   int iters_stride) {
-    const Dims& d = pl->dims;
-    cudaStream_t s = pl->stream;
+    sb_plan pl = ex.pl;
+    const Dims& d = ex.d;
+    const size_t n = pl->n;
+    cudaStream_t s = ex.s;
     const bool fixed = o.fixed_iters > 0;
     const double tol2 = fixed ? -1.0 : o.tol * o.tol;
     const bool circ = o.precond == SB_PRECOND_CIRCULANT;
-    const Red red = red_of(pl);
+    const Red red = ex.red;
     const float mu = (float)pl->d.mu, lam = (float)pl->d.lambda, gam = (float)pl->d.gamma;
+    float2* x = at(x_full, ex, n);
+    float2 *r = at(pl->r, ex, n), *p = at(pl->p, ex, n), *q = at(pl->q, ex, n), *tb = at(pl->tb, ex, n);
+    const float* invk = at(pl->invk, ex, n);
+    const float* maskw = at(pl->maskw, ex, (size_t)d.ny);
 
-    SB_LAUNCH(pl, SB_KCLASS_VEC, 1, launch_zero_rhs_slices(d, x, pl->st, s));
+    SB_LAUNCH(ex, SB_KCLASS_VEC, 1, launch_zero_rhs_slices(d, x, ex.st, s));
     if (circ) {
-        SB_LAUNCH(pl, SB_KCLASS_PRECOND_ROW_FWD, 1, launch_row_fwd(d, 0, pl->r, nullptr, pl->tb, pl->tw_x, pl->st, tol2, red, s));
-        SB_LAUNCH(pl, SB_KCLASS_PRECOND_COL, 1, launch_col_precond(d, pl->tb, pl->invk, pl->tw_y, pl->st, 1, red, s));
-        SB_LAUNCH(pl, SB_KCLASS_PRECOND_ROW_INV, 1, launch_row_inv(d, 1, pl->tb, nullptr, x, pl->p, pl->tw_x, pl->st, red, s));
+        SB_LAUNCH(ex, SB_KCLASS_PRECOND_ROW_FWD, 1, launch_row_fwd(d, 0, r, nullptr, tb, pl->tw_x, ex.st, tol2, red, s));
+        SB_LAUNCH(ex, SB_KCLASS_PRECOND_COL, 1, launch_col_precond(d, tb, invk, pl->tw_y, ex.st, 1, red, s));
+        SB_LAUNCH(ex, SB_KCLASS_PRECOND_ROW_INV, 1, launch_row_inv(d, 1, tb, nullptr, x, p, pl->tw_x, ex.st, red, s));
     } else {
-        SB_LAUNCH(pl, SB_KCLASS_VEC, 1, launch_vec_plain(d, 0, x, pl->r, pl->p, nullptr, pl->st, tol2, red, s));
+        SB_LAUNCH(ex, SB_KCLASS_VEC, 1, launch_vec_plain(d, 0, x, r, p, nullptr, ex.st, tol2, red, s));
     }
     const int nit = fixed ? o.fixed_iters : o.maxit;
     int it = 0;
     while (it < nit) {
         const int g = std::min(kPollEvery, nit - it);
         for (int i = 0; i < g; ++i) {
-            SB_LAUNCH(pl, SB_KCLASS_APPLY_A, 1, launch_apply_A(d, pl->smap, pl->p, pl->q, pl->maskw, pl->tw_y, mu, lam, gam, pl->st, red, s));
+            SB_LAUNCH(ex, SB_KCLASS_APPLY_A, 1,
+                      launch_apply_A(d, ex.smap, p, q, maskw, pl->tw_y, mu, lam, gam, ex.st, red, s));
             if (circ) {
-                SB_LAUNCH(pl, SB_KCLASS_PRECOND_ROW_FWD, 1, launch_row_fwd(d, 1, pl->r, pl->q, pl->tb, pl->tw_x, pl->st, tol2, red, s));
-                SB_LAUNCH(pl, SB_KCLASS_PRECOND_COL, 1, launch_col_precond(d, pl->tb, pl->invk, pl->tw_y, pl->st, 0, red, s));
-                SB_LAUNCH(pl, SB_KCLASS_PRECOND_ROW_INV, 1, launch_row_inv(d, 2, pl->tb, nullptr, x, pl->p, pl->tw_x, pl->st, red, s));
+                SB_LAUNCH(ex, SB_KCLASS_PRECOND_ROW_FWD, 1, launch_row_fwd(d, 1, r, q, tb, pl->tw_x, ex.st, tol2, red, s));
+                SB_LAUNCH(ex, SB_KCLASS_PRECOND_COL, 1, launch_col_precond(d, tb, invk, pl->tw_y, ex.st, 0, red, s));
+                SB_LAUNCH(ex, SB_KCLASS_PRECOND_ROW_INV, 1, launch_row_inv(d, 2, tb, nullptr, x, p, pl->tw_x, ex.st, red, s));
             } else {
-                SB_LAUNCH(pl, SB_KCLASS_VEC, 1, launch_vec_plain(d, 1, x, pl->r, pl->p, pl->q, pl->st, tol2, red, s));
-                SB_LAUNCH(pl, SB_KCLASS_VEC, 1, launch_vec_plain(d, 2, x, pl->r, pl->p, pl->q, pl->st, tol2, red, s));
+                SB_LAUNCH(ex, SB_KCLASS_VEC, 1, launch_vec_plain(d, 1, x, r, p, q, ex.st, tol2, red, s));
+                SB_LAUNCH(ex, SB_KCLASS_VEC, 1, launch_vec_plain(d, 2, x, r, p, q, ex.st, tol2, red, s));
             }
         }
         it += g;
         if (!fixed || it >= nit) {
-            SB_CK(pl, cudaMemcpyAsync(pl->h_st, pl->st, sizeof(SliceState) * d.nb, cudaMemcpyDeviceToHost, s));
-            SB_CK(pl, cudaMemcpyAsync(&pl->h_err, pl->derr, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
-            SB_CK(pl, cudaStreamSynchronize(s));
-            timer_harvest(pl);
-            if (pl->h_err) return fail(pl, SB_ERR_TIMEOUT, "a bounded device wait gave up (TMA tile never arrived)");
+            SB_XCK(ex, cudaMemcpyAsync(ex.h_st, ex.st, sizeof(SliceState) * d.nb, cudaMemcpyDeviceToHost, s));
+            SB_XCK(ex, cudaMemcpyAsync(&ex.h_err, pl->derr, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+            SB_XCK(ex, cudaStreamSynchronize(s));
+            timer_harvest(ex);
+            if (ex.h_err) return xfail(ex, SB_ERR_TIMEOUT, "a bounded device wait gave up (TMA tile never arrived)");
             bool running = false;
             for (int b = 0; b < d.nb; ++b)
-                running |= (pl->h_st[b].state == ST_ACTIVE || pl->h_st[b].state == ST_FINISHING);
+                running |= (ex.h_st[b].state == ST_ACTIVE || ex.h_st[b].state == ST_FINISHING);
             if (!running) break;
         }
     }
     sb_status worst = SB_OK;
     for (int b = 0; b < d.nb; ++b) {
-        const SliceState& S = pl->h_st[b];
+        const SliceState& S = ex.h_st[b];
         sb_status sl = SB_OK;
         if (S.state == ST_BREAKDOWN) sl = SB_ERR_BREAKDOWN;
         else if (S.state == ST_NONFINITE) sl = SB_ERR_NONFINITE;
         else if (S.state == ST_ACTIVE && !fixed) sl = SB_ERR_NOT_CONVERGED;
         if (worst == SB_OK) worst = sl;
         const double rel = S.bnorm2 > 0 ? std::sqrt(S.rnorm2 / S.bnorm2) : 0.0;
+        const int gb = ex.b0 + b;
         if (h_results) {
-            h_results[b].iters = S.iters;
-            h_results[b].rel_resid = rel;
-            h_results[b].converged = (sl == SB_OK) ? 1 : 0;
+            h_results[gb].iters = S.iters;
+            h_results[gb].rel_resid = rel;
+            h_results[gb].converged = (sl == SB_OK) ? 1 : 0;
         }
-        if (iters_out) iters_out[(size_t)b * iters_stride] = S.iters;
+        if (iters_out) iters_out[(size_t)gb * iters_stride] = S.iters;
     }
-    if (worst == SB_ERR_NOT_CONVERGED) pl->err = "PCG reached maxit before the tolerance";
-    else if (worst != SB_OK) pl->err = std::string("PCG stopped: ") + sb_status_string(worst);
+    if (worst == SB_ERR_NOT_CONVERGED) ex.err = "PCG reached maxit before the tolerance";
+    else if (worst != SB_OK) ex.err = std::string("PCG stopped: ") + sb_status_string(worst);
     return worst;
 }
 
@@ -267,6 +350,110 @@ sb_status check_opts(sb_plan pl, const sb_pcg_opts* o) {
     if (o->precond != SB_PRECOND_CIRCULANT && o->precond != SB_PRECOND_NONE)
         return fail(pl, SB_ERR_UNSUPPORTED, "preconditioner kind not implemented");
     return SB_OK;
+}
+
+// Run fn(exec) for every slice group concurrently (one host thread per extra group), forking
+// from and joining back into the plan's stream.  Returns the first non-OK status in group order.
+template <class Fn>
+sb_status run_groups(sb_plan pl, Fn fn) {
+    const int G = (int)pl->groups.size();
+    if (G == 1) {
+        Exec& ex = pl->groups[0];
+        sb_status st = fn(ex);
+        if (st != SB_OK) pl->err = ex.err;
+        return st;
+    }
+    SB_CK(pl, cudaEventRecord(pl->fork, pl->stream));
+    for (Exec& ex : pl->groups) SB_CK(pl, cudaStreamWaitEvent(ex.s, pl->fork, 0));
+    std::vector<sb_status> status(G, SB_OK);
+    std::vector<std::thread> threads;
+    for (int gi = 1; gi < G; ++gi)
+        threads.emplace_back([&, gi]() {
+            cudaSetDevice(pl->device);
+            status[gi] = fn(pl->groups[gi]);
+        });
+    status[0] = fn(pl->groups[0]);
+    for (auto& t : threads) t.join();
+    for (Exec& ex : pl->groups) {
+        SB_CK(pl, cudaEventRecord(ex.join, ex.s));
+        SB_CK(pl, cudaStreamWaitEvent(pl->stream, ex.join, 0));
+    }
+    for (int gi = 0; gi < G; ++gi)
+        if (status[gi] != SB_OK) {
+            pl->err = pl->groups[gi].err;
+            return status[gi];
+        }
+    return SB_OK;
+}
+
+// Algorithm 1 on one slice group.
+sb_status sb_run(Exec& ex, const sb_sb_opts& o, const float2* y_full, float2* x_full, sb_pcg_result* h_last,
+                 int* iters) {
+    sb_plan pl = ex.pl;
+    const Dims& d = ex.d;
+    const size_t nb = d.nb, n = pl->n, ms = pl->ms;
+    cudaStream_t s = ex.s;
+    float2* x = at(x_full, ex, n);
+    const float mu = (float)pl->d.mu, lam = (float)pl->d.lambda, gam = (float)pl->d.gamma;
+    const float tau_tv = o.tau_tv > 0 ? (float)o.tau_tv : (lam > 0 ? 1.0f / lam : INFINITY);
+    const float tau_w = o.tau_w > 0 ? (float)o.tau_w : (gam > 0 ? 1.0f / gam : INFINITY);
+    const double tol2 = o.pcg.fixed_iters > 0 ? -1.0 : o.pcg.tol * o.pcg.tol;
+    const int levels = pl->d.wavelet_levels;
+    const int nsolve = o.n_outer * o.n_inner;
+    const size_t yrow = (size_t)d.nc * ms * d.nx;  // yt elements per slice
+
+    SB_LAUNCH(ex, SB_KCLASS_OTHER, 1,
+              launch_ytilde(d, at(y_full, ex, (size_t)d.nc * n), at(pl->lines, ex, ms), (int)ms, at(pl->yt1, ex, yrow),
+                            pl->tw_x, s));
+    SB_XCK(ex, cudaMemcpyAsync(at(pl->yt, ex, yrow), at(pl->yt1, ex, yrow), sizeof(float2) * nb * yrow,
+                               cudaMemcpyDeviceToDevice, s));
+    int cur = 0;
+    SB_XCK(ex, cudaMemsetAsync(at(pl->bx[0], ex, n), 0, sizeof(float2) * nb * n, s));
+    SB_XCK(ex, cudaMemsetAsync(at(pl->by[0], ex, n), 0, sizeof(float2) * nb * n, s));
+    SB_XCK(ex, cudaMemsetAsync(at(pl->bw, ex, n), 0, sizeof(float2) * nb * n, s));
+    SB_XCK(ex, cudaMemsetAsync(at(pl->g, ex, n), 0, sizeof(float2) * nb * n, s));
+    auto fields = [&]() {
+        SbFields f;
+        f.sens = at(pl->sens, ex, (size_t)d.nc * n);
+        f.maskw = at(pl->maskw, ex, (size_t)d.ny);
+        f.slot = at(pl->slot, ex, (size_t)d.ny);
+        f.yt = at(pl->yt, ex, yrow);
+        f.yt1 = at(pl->yt1, ex, yrow);
+        f.ms = (int)ms;
+        f.bx = at(pl->bx[cur], ex, n);
+        f.by = at(pl->by[cur], ex, n);
+        f.bx_new = at(pl->bx[cur ^ 1], ex, n);
+        f.by_new = at(pl->by[cur ^ 1], ex, n);
+        f.bw = at(pl->bw, ex, n);
+        f.g = at(pl->g, ex, n);
+        f.bd = at(pl->bd, ex, n);
+        f.bd1 = at(pl->bd1, ex, n);
+        return f;
+    };
+    SB_LAUNCH(ex, SB_KCLASS_OTHER, 1, launch_rss(d, fields(), x, o.init_rss ? 1 : 0, pl->tw_y, s));
+
+    sb_status first_err = SB_OK;
+    int solve = 0;
+    float2* r = at(pl->r, ex, n);
+    for (int j = 0; j < o.n_outer; ++j) {
+        for (int k = 0; k < o.n_inner; ++k, ++solve) {
+            const int addback = (j > 0 && k == 0);
+            SB_LAUNCH(ex, SB_KCLASS_RHS, 1,
+                      launch_rhs(d, ex.smap, ex.ymap, ex.y1map, fields(), addback, x, r, pl->tw_y, mu, lam, gam, ex.st,
+                                 tol2, ex.red, s));
+            sb_status ps = pcg_run(ex, o.pcg, x_full, h_last, iters + solve, nsolve);
+            if (ps == SB_ERR_TIMEOUT || ps == SB_ERR_CUDA) return ps;
+            if (ps != SB_OK && first_err == SB_OK) first_err = ps;
+            const bool last = (j == o.n_outer - 1) && (k == o.n_inner - 1);
+            if (!last) {
+                SB_LAUNCH(ex, SB_KCLASS_SB_UPDATE, 1, launch_sb_update(d, fields(), x, levels, lam, gam, tau_tv, tau_w, s));
+                if (lam != 0.f) cur ^= 1;
+            }
+        }
+    }
+    SB_XCK(ex, cudaStreamSynchronize(s));
+    timer_harvest(ex);
+    return first_err;
 }
 
 }  // namespace
@@ -297,7 +484,7 @@ sb_status sb_plan_create(const sb_plan_desc* desc, void* cuda_stream, sb_plan* o
     *out = nullptr;
     const sb_plan_desc& d = *desc;
     if (d.ndim != 2 || (d.nz != 1 && d.nz != 0) || d.ncoils < 1 || d.nbatch < 1 || !(d.mu > 0.0) ||
-        !(d.lambda >= 0.0) || !(d.gamma >= 0.0) || d.wavelet_levels < 0)
+        !(d.lambda >= 0.0) || !(d.gamma >= 0.0) || d.wavelet_levels < 0 || d.groups < 0)
         return SB_ERR_INVALID_ARG;
     if (!supported_n(d.nx) || !supported_n(d.ny) || d.wavelet_levels > 4 || d.prec != SB_PREC_FP32)
         return SB_ERR_UNSUPPORTED;
@@ -311,10 +498,10 @@ sb_status sb_plan_create(const sb_plan_desc* desc, void* cuda_stream, sb_plan* o
     const size_t nb = d.nbatch, n = pl->n;
     cudaError_t e = cudaGetDevice(&pl->device);
     auto bail = [&](const char* what) {
-        sb_status s = cuda_fail(pl, what, e);
+        pl->err = cuda_msg(what, e);
         fprintf(stderr, "sb_plan_create: %s\n", pl->err.c_str());
         sb_plan_destroy(pl);
-        return s;
+        return SB_ERR_CUDA;
     };
     if (e != cudaSuccess) return bail("cudaGetDevice");
 #define ALLOC(ptr, count) \
@@ -345,6 +532,26 @@ sb_status sb_plan_create(const sb_plan_desc* desc, void* cuda_stream, sb_plan* o
     if ((e = cudaMemset(pl->counter, 0, sizeof(unsigned) * nb)) != cudaSuccess) return bail("cudaMemset");
     if ((e = cudaMemset(pl->derr, 0, sizeof(unsigned))) != cudaSuccess) return bail("cudaMemset");
     if ((e = cudaMemset(pl->st, 0, sizeof(SliceState) * nb)) != cudaSuccess) return bail("cudaMemset");
+
+    // execution contexts
+    bind_exec(pl, pl->whole, 0, (int)nb, pl->stream);
+    int G = d.groups > 0 ? d.groups : std::max(1, std::min(4, (int)nb / 8));
+    G = std::max(1, std::min(G, (int)nb));
+    pl->groups.resize(G);
+    for (int gi = 0; gi < G; ++gi) {
+        const int b0 = (int)(nb * gi / G), b1 = (int)(nb * (gi + 1) / G);
+        cudaStream_t s = pl->stream;
+        if (G > 1) {
+            if ((e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking)) != cudaSuccess)
+                return bail("cudaStreamCreateWithFlags");
+            pl->groups[gi].own_stream = true;
+            if ((e = cudaEventCreateWithFlags(&pl->groups[gi].join, cudaEventDisableTiming)) != cudaSuccess)
+                return bail("cudaEventCreate");
+        }
+        bind_exec(pl, pl->groups[gi], b0, b1 - b0, s);
+    }
+    if (G > 1 && (e = cudaEventCreateWithFlags(&pl->fork, cudaEventDisableTiming)) != cudaSuccess)
+        return bail("cudaEventCreate");
     *out = pl;
     return SB_OK;
 }
@@ -356,16 +563,26 @@ sb_status sb_plan_destroy(sb_plan pl) {
     for (void* p : {(void*)pl->tw_x, (void*)pl->tw_y, (void*)pl->maskw, (void*)pl->slot, (void*)pl->lines,
                     (void*)pl->k, (void*)pl->invk, (void*)pl->r, (void*)pl->p, (void*)pl->q, (void*)pl->tb,
                     (void*)pl->bx[0], (void*)pl->bx[1], (void*)pl->by[0], (void*)pl->by[1], (void*)pl->bw,
-                    (void*)pl->g, (void*)pl->yt, (void*)pl->yt1, (void*)pl->st, (void*)pl->part,
-                    (void*)pl->counter, (void*)pl->kmax, (void*)pl->derr, (void*)pl->spec, (void*)pl->gb, (void*)pl->rb,
-                    (void*)pl->line_val, (void*)pl->line_uni})
+                    (void*)pl->g, (void*)pl->bd, (void*)pl->bd1, (void*)pl->yt, (void*)pl->yt1, (void*)pl->st,
+                    (void*)pl->part, (void*)pl->counter, (void*)pl->kmax, (void*)pl->derr, (void*)pl->spec,
+                    (void*)pl->gb, (void*)pl->rb, (void*)pl->line_val, (void*)pl->line_uni})
         dfree(p);
     if (pl->h_st) cudaFreeHost(pl->h_st);
-    for (const auto& pe : pl->pending) {
-        cudaEventDestroy(pe.a);
-        cudaEventDestroy(pe.b);
-    }
-    for (cudaEvent_t e : pl->ev_pool) cudaEventDestroy(e);
+    auto release = [](Exec& ex) {
+        for (const auto& pe : ex.pending) {
+            cudaEventDestroy(pe.a);
+            cudaEventDestroy(pe.b);
+        }
+        for (cudaEvent_t e : ex.ev_pool) cudaEventDestroy(e);
+        if (ex.join) cudaEventDestroy(ex.join);
+        if (ex.own_stream) {
+            cudaStreamSynchronize(ex.s);
+            cudaStreamDestroy(ex.s);
+        }
+    };
+    release(pl->whole);
+    for (Exec& ex : pl->groups) release(ex);
+    if (pl->fork) cudaEventDestroy(pl->fork);
     delete pl;
     return SB_OK;
 }
@@ -375,17 +592,14 @@ sb_status sb_set_coils(sb_plan pl, const void* d_sens) {
     if (reinterpret_cast<uintptr_t>(d_sens) % 16 != 0)
         return fail(pl, SB_ERR_INVALID_ARG, "sensitivities must be 16-byte aligned");
     const Dims& d = pl->dims;
-    auto encode = tensor_map_encoder();
-    if (!encode) return fail(pl, SB_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
-    // float32 view [nb*nc*ny][2*nx]; box = ny rows x 2*kColTile floats (one coil tile)
-    const cuuint64_t gdim[2] = {(cuuint64_t)2 * d.nx, (cuuint64_t)d.nb * d.nc * d.ny};
-    const cuuint64_t gstride[1] = {(cuuint64_t)2 * d.nx * sizeof(float)};
-    const cuuint32_t box[2] = {(cuuint32_t)2 * kColTile, (cuuint32_t)d.ny};
-    const cuuint32_t estride[2] = {1, 1};
-    const CUresult cr = encode(&pl->smap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(d_sens), gdim,
-                               gstride, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (cr != CUDA_SUCCESS) return fail(pl, SB_ERR_CUDA, "cuTensorMapEncodeTiled failed for the sensitivities");
+    const size_t per = (size_t)d.nc * pl->n;
+    auto enc = [&](Exec& ex) {
+        return encode_rows(&ex.smap, static_cast<const float2*>(d_sens) + (size_t)ex.b0 * per, d.nx,
+                           (size_t)ex.d.nb * d.nc * d.ny, d.ny);
+    };
+    bool ok = enc(pl->whole);
+    for (Exec& ex : pl->groups) ok = ok && enc(ex);
+    if (!ok) return fail(pl, SB_ERR_CUDA, "cuTensorMapEncodeTiled failed for the sensitivities");
     pl->sens = static_cast<const float2*>(d_sens);
     pl->have_coils = true;
     pl->have_mask = false;  // k depends on the coils: rebuilt by sb_set_mask
@@ -395,6 +609,7 @@ sb_status sb_set_coils(sb_plan pl, const void* d_sens) {
 sb_status sb_set_mask(sb_plan pl, const uint8_t* d_mask) {
     if (!pl || !d_mask) return fail(pl, SB_ERR_INVALID_ARG, "null plan or mask");
     if (!pl->have_coils) return fail(pl, SB_ERR_NOT_READY, "call sb_set_coils before sb_set_mask");
+    Exec& ex = pl->whole;
     const Dims& d = pl->dims;
     const size_t nb = d.nb, n = pl->n;
     cudaStream_t s = pl->stream;
@@ -408,7 +623,12 @@ sb_status sb_set_mask(sb_plan pl, const uint8_t* d_mask) {
     }
     // 1. line structure of the mask
     int *lv = pl->line_val, *lu = pl->line_uni;
-    SB_LAUNCH(pl, SB_KCLASS_OTHER, 1, launch_mask_lines(d, d_mask, lv, lu, s));
+    sb_status st = SB_OK;
+    auto step = [&]() -> sb_status {
+        SB_LAUNCH(ex, SB_KCLASS_OTHER, 1, launch_mask_lines(d, d_mask, lv, lu, s));
+        return SB_OK;
+    };
+    if ((st = step()) != SB_OK) return fail(pl, st, ex.err);
     std::vector<int> hv(nb * d.ny), hu(nb * d.ny);
     SB_CK(pl, cudaMemcpyAsync(hv.data(), lv, sizeof(int) * hv.size(), cudaMemcpyDeviceToHost, s));
     SB_CK(pl, cudaMemcpyAsync(hu.data(), lu, sizeof(int) * hu.size(), cudaMemcpyDeviceToHost, s));
@@ -446,21 +666,26 @@ sb_status sb_set_mask(sb_plan pl, const uint8_t* d_mask) {
     float2 *spec = pl->spec, *gb = pl->gb, *rb = pl->rb;
     const int nimg_c = d.nb * d.nc;
     SB_CK(pl, cudaMemcpyAsync(spec, pl->sens, sizeof(float2) * nb * d.nc * n, cudaMemcpyDeviceToDevice, s));
-    SB_LAUNCH(pl, SB_KCLASS_OTHER, 1, launch_fft_rows(d.nx, d.ny, nimg_c, spec, pl->tw_x, false, s));
-    SB_LAUNCH(pl, SB_KCLASS_OTHER, 1, launch_fft_cols(d.nx, d.ny, nimg_c, spec, pl->tw_y, false, s));
-    SB_LAUNCH(pl, SB_KCLASS_OTHER, 1, launch_coil_power(d, spec, gb, s));
-    SB_LAUNCH(pl, SB_KCLASS_OTHER, 1, launch_mask_to_complex(d, d_mask, rb, s));
-    SB_LAUNCH(pl, SB_KCLASS_OTHER, 1, launch_fft_rows(d.nx, d.ny, d.nb, gb, pl->tw_x, false, s));
-    SB_LAUNCH(pl, SB_KCLASS_OTHER, 1, launch_fft_cols(d.nx, d.ny, d.nb, gb, pl->tw_y, false, s));
-    SB_LAUNCH(pl, SB_KCLASS_OTHER, 1, launch_fft_rows(d.nx, d.ny, d.nb, rb, pl->tw_x, false, s));
-    SB_LAUNCH(pl, SB_KCLASS_OTHER, 1, launch_fft_cols(d.nx, d.ny, d.nb, rb, pl->tw_y, false, s));
-    SB_LAUNCH(pl, SB_KCLASS_OTHER, 1, launch_mul_conj(d, rb, gb, s));
-    SB_LAUNCH(pl, SB_KCLASS_OTHER, 1, launch_fft_rows(d.nx, d.ny, d.nb, rb, pl->tw_x, true, s));
-    SB_LAUNCH(pl, SB_KCLASS_OTHER, 1, launch_fft_cols(d.nx, d.ny, d.nb, rb, pl->tw_y, true, s));
-    SB_LAUNCH(pl, SB_KCLASS_OTHER, 2, launch_finish_k(d, rb, (float)pl->d.mu, (float)pl->d.lambda, (float)pl->d.gamma, pl->k,
-                                     pl->invk, pl->kmax, s));
+    auto build_k = [&]() -> sb_status {
+        SB_LAUNCH(ex, SB_KCLASS_OTHER, 1, launch_fft_rows(d.nx, d.ny, nimg_c, spec, pl->tw_x, false, s));
+        SB_LAUNCH(ex, SB_KCLASS_OTHER, 1, launch_fft_cols(d.nx, d.ny, nimg_c, spec, pl->tw_y, false, s));
+        SB_LAUNCH(ex, SB_KCLASS_OTHER, 1, launch_coil_power(d, spec, gb, s));
+        SB_LAUNCH(ex, SB_KCLASS_OTHER, 1, launch_mask_to_complex(d, d_mask, rb, s));
+        SB_LAUNCH(ex, SB_KCLASS_OTHER, 1, launch_fft_rows(d.nx, d.ny, d.nb, gb, pl->tw_x, false, s));
+        SB_LAUNCH(ex, SB_KCLASS_OTHER, 1, launch_fft_cols(d.nx, d.ny, d.nb, gb, pl->tw_y, false, s));
+        SB_LAUNCH(ex, SB_KCLASS_OTHER, 1, launch_fft_rows(d.nx, d.ny, d.nb, rb, pl->tw_x, false, s));
+        SB_LAUNCH(ex, SB_KCLASS_OTHER, 1, launch_fft_cols(d.nx, d.ny, d.nb, rb, pl->tw_y, false, s));
+        SB_LAUNCH(ex, SB_KCLASS_OTHER, 1, launch_mul_conj(d, rb, gb, s));
+        SB_LAUNCH(ex, SB_KCLASS_OTHER, 1, launch_fft_rows(d.nx, d.ny, d.nb, rb, pl->tw_x, true, s));
+        SB_LAUNCH(ex, SB_KCLASS_OTHER, 1, launch_fft_cols(d.nx, d.ny, d.nb, rb, pl->tw_y, true, s));
+        SB_LAUNCH(ex, SB_KCLASS_OTHER, 2,
+                  launch_finish_k(d, rb, (float)pl->d.mu, (float)pl->d.lambda, (float)pl->d.gamma, pl->k, pl->invk,
+                                  pl->kmax, s));
+        return SB_OK;
+    };
+    if ((st = build_k()) != SB_OK) return fail(pl, st, ex.err);
     SB_CK(pl, cudaStreamSynchronize(s));
-    timer_harvest(pl);
+    timer_harvest(ex);
 
     // 3. Split Bregman workspace sized by the number of sampled lines
     const size_t yt_elems = nb * d.nc * (size_t)ms * d.nx;
@@ -472,29 +697,23 @@ sb_status sb_set_mask(sb_plan pl, const uint8_t* d_mask) {
         SB_CK(pl, dalloc(&pl->yt1, yt_elems));
         pl->yt_elems = yt_elems;
     }
-    {
-        // TMA maps of the compact k-space rows: float32 [nb*nc*ms][2*nx], box = ms rows x one tile
-        auto encode = tensor_map_encoder();
-        if (!encode) return fail(pl, SB_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
-        const cuuint64_t gdim[2] = {(cuuint64_t)2 * d.nx, (cuuint64_t)nb * d.nc * ms};
-        const cuuint64_t gstride[1] = {(cuuint64_t)2 * d.nx * sizeof(float)};
-        const cuuint32_t box[2] = {(cuuint32_t)2 * kColTile, (cuuint32_t)ms};
-        const cuuint32_t estride[2] = {1, 1};
-        for (int which = 0; which < 2; ++which) {
-            CUtensorMap* m = which ? &pl->y1map : &pl->ymap;
-            void* base = which ? (void*)pl->yt1 : (void*)pl->yt;
-            if (encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, gdim, gstride, box, estride,
-                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-                return fail(pl, SB_ERR_CUDA, "cuTensorMapEncodeTiled failed for the k-space rows");
-        }
-    }
+    const size_t yrow = (size_t)d.nc * ms * d.nx;
+    auto enc = [&](Exec& e2) {
+        const size_t rows = (size_t)e2.d.nb * d.nc * ms;
+        return encode_rows(&e2.ymap, pl->yt + e2.b0 * yrow, d.nx, rows, ms) &&
+               encode_rows(&e2.y1map, pl->yt1 + e2.b0 * yrow, d.nx, rows, ms);
+    };
+    bool ok = enc(pl->whole);
+    for (Exec& e2 : pl->groups) ok = ok && enc(e2);
+    if (!ok) return fail(pl, SB_ERR_CUDA, "cuTensorMapEncodeTiled failed for the k-space rows");
     if (!pl->g) {
         SB_CK(pl, dalloc(&pl->bx[0], nb * n));
         SB_CK(pl, dalloc(&pl->bx[1], nb * n));
         SB_CK(pl, dalloc(&pl->by[0], nb * n));
         SB_CK(pl, dalloc(&pl->by[1], nb * n));
         SB_CK(pl, dalloc(&pl->bw, nb * n));
+        SB_CK(pl, dalloc(&pl->bd, nb * n));
+        SB_CK(pl, dalloc(&pl->bd1, nb * n));
         SB_CK(pl, dalloc(&pl->g, nb * n));
     }
     pl->have_mask = true;
@@ -511,37 +730,56 @@ sb_status sb_get_k(sb_plan pl, float* d_k) {
 sb_status sb_apply_A(sb_plan pl, const void* d_x, void* d_y) {
     if (sb_status s = check_ready(pl)) return s;
     if (!d_x || !d_y || d_x == d_y) return fail(pl, SB_ERR_INVALID_ARG, "need distinct non-null x and y");
-    SB_LAUNCH(pl, SB_KCLASS_APPLY_A, 1, launch_apply_A(pl->dims, pl->smap, static_cast<const float2*>(d_x), static_cast<float2*>(d_y),
-                                    pl->maskw, pl->tw_y, (float)pl->d.mu, (float)pl->d.lambda, (float)pl->d.gamma,
-                                    nullptr, red_of(pl), pl->stream));
-    return SB_OK;
+    Exec& ex = pl->whole;
+    auto go = [&]() -> sb_status {
+        SB_LAUNCH(ex, SB_KCLASS_APPLY_A, 1,
+                  launch_apply_A(pl->dims, ex.smap, static_cast<const float2*>(d_x), static_cast<float2*>(d_y),
+                                 pl->maskw, pl->tw_y, (float)pl->d.mu, (float)pl->d.lambda, (float)pl->d.gamma,
+                                 nullptr, ex.red, pl->stream));
+        return SB_OK;
+    };
+    sb_status st = go();
+    return st == SB_OK ? st : fail(pl, st, ex.err);
 }
 
 sb_status sb_apply_precond(sb_plan pl, const void* d_r, void* d_z) {
     if (sb_status s = check_ready(pl)) return s;
     if (!d_r || !d_z) return fail(pl, SB_ERR_INVALID_ARG, "null vector");
+    Exec& ex = pl->whole;
     const Dims& d = pl->dims;
-    const Red red = red_of(pl);
-    SB_LAUNCH(pl, SB_KCLASS_PRECOND_ROW_FWD, 1, launch_row_fwd(d, 0, const_cast<float2*>(static_cast<const float2*>(d_r)), nullptr, pl->tb,
-                                    pl->tw_x, nullptr, 0.0, red, pl->stream));
-    SB_LAUNCH(pl, SB_KCLASS_PRECOND_COL, 1, launch_col_precond(d, pl->tb, pl->invk, pl->tw_y, nullptr, 0, red, pl->stream));
-    SB_LAUNCH(pl, SB_KCLASS_PRECOND_ROW_INV, 1, launch_row_inv(d, 0, pl->tb, static_cast<float2*>(d_z), nullptr, nullptr, pl->tw_x, nullptr,
-                                    red, pl->stream));
-    return SB_OK;
+    auto go = [&]() -> sb_status {
+        SB_LAUNCH(ex, SB_KCLASS_PRECOND_ROW_FWD, 1,
+                  launch_row_fwd(d, 0, const_cast<float2*>(static_cast<const float2*>(d_r)), nullptr, pl->tb, pl->tw_x,
+                                 nullptr, 0.0, ex.red, pl->stream));
+        SB_LAUNCH(ex, SB_KCLASS_PRECOND_COL, 1,
+                  launch_col_precond(d, pl->tb, pl->invk, pl->tw_y, nullptr, 0, ex.red, pl->stream));
+        SB_LAUNCH(ex, SB_KCLASS_PRECOND_ROW_INV, 1,
+                  launch_row_inv(d, 0, pl->tb, static_cast<float2*>(d_z), nullptr, nullptr, pl->tw_x, nullptr, ex.red,
+                                 pl->stream));
+        return SB_OK;
+    };
+    sb_status st = go();
+    return st == SB_OK ? st : fail(pl, st, ex.err);
 }
 
 sb_status sb_pcg_solve(sb_plan pl, const void* d_b, void* d_x, const sb_pcg_opts* o, sb_pcg_result* h_results) {
     if (sb_status s = check_ready(pl)) return s;
     if (sb_status s = check_opts(pl, o)) return s;
     if (!d_b || !d_x || d_b == d_x) return fail(pl, SB_ERR_INVALID_ARG, "need distinct non-null b and x");
-    const Dims& d = pl->dims;
-    float2* x = static_cast<float2*>(d_x);
+    float2* x_full = static_cast<float2*>(d_x);
+    const float2* b_full = static_cast<const float2*>(d_b);
     const double tol2 = o->fixed_iters > 0 ? -1.0 : o->tol * o->tol;
-    SB_LAUNCH(pl, SB_KCLASS_APPLY_A, 1, launch_apply_A(d, pl->smap, x, pl->q, pl->maskw, pl->tw_y, (float)pl->d.mu,
-                                    (float)pl->d.lambda, (float)pl->d.gamma, nullptr, red_of(pl), pl->stream));
-    SB_LAUNCH(pl, SB_KCLASS_VEC, 1, launch_resid_init(d, static_cast<const float2*>(d_b), pl->q, pl->r, pl->st, tol2, red_of(pl),
-                                       pl->stream));
-    return pcg_run(pl, *o, x, h_results, nullptr, 0);
+    return run_groups(pl, [&](Exec& ex) -> sb_status {
+        const size_t n = pl->n;
+        float2* x = at(x_full, ex, n);
+        float2* q = at(pl->q, ex, n);
+        SB_LAUNCH(ex, SB_KCLASS_APPLY_A, 1,
+                  launch_apply_A(ex.d, ex.smap, x, q, at(pl->maskw, ex, (size_t)ex.d.ny), pl->tw_y, (float)pl->d.mu,
+                                 (float)pl->d.lambda, (float)pl->d.gamma, nullptr, ex.red, ex.s));
+        SB_LAUNCH(ex, SB_KCLASS_VEC, 1,
+                  launch_resid_init(ex.d, at(b_full, ex, n), q, at(pl->r, ex, n), ex.st, tol2, ex.red, ex.s));
+        return pcg_run(ex, *o, x_full, h_results, nullptr, 0);
+    });
 }
 
 sb_status sb_split_bregman(sb_plan pl, const void* d_y, void* d_x, const sb_sb_opts* o, sb_pcg_result* h_last) {
@@ -549,71 +787,26 @@ sb_status sb_split_bregman(sb_plan pl, const void* d_y, void* d_x, const sb_sb_o
     if (!o || !d_y || !d_x) return fail(pl, SB_ERR_INVALID_ARG, "null argument");
     if (o->n_outer < 1 || o->n_inner < 1) return fail(pl, SB_ERR_INVALID_ARG, "n_outer and n_inner must be >= 1");
     if (sb_status s = check_opts(pl, &o->pcg)) return s;
-    const Dims& d = pl->dims;
-    const size_t nb = d.nb, n = pl->n;
-    cudaStream_t s = pl->stream;
-    float2* x = static_cast<float2*>(d_x);
-    const float mu = (float)pl->d.mu, lam = (float)pl->d.lambda, gam = (float)pl->d.gamma;
-    const float tau_tv = o->tau_tv > 0 ? (float)o->tau_tv : (lam > 0 ? 1.0f / lam : INFINITY);
-    const float tau_w = o->tau_w > 0 ? (float)o->tau_w : (gam > 0 ? 1.0f / gam : INFINITY);
-    const double tol2 = o->pcg.fixed_iters > 0 ? -1.0 : o->pcg.tol * o->pcg.tol;
-    const int levels = pl->d.wavelet_levels;
-    const int nsolve = o->n_outer * o->n_inner;
-    if (rhs_smem_bytes(d.ny, pl->ms) > 227 * 1024)
+    if (rhs_smem_bytes(pl->dims.ny, pl->ms) > 227 * 1024)
         return fail(pl, SB_ERR_UNSUPPORTED, "too many sampled lines for the shared-memory pipeline of this size");
-
-    SB_LAUNCH(pl, SB_KCLASS_OTHER, 1, launch_ytilde(d, static_cast<const float2*>(d_y), pl->lines, pl->ms, pl->yt1, pl->tw_x, s));
-    SB_CK(pl, cudaMemcpyAsync(pl->yt, pl->yt1, sizeof(float2) * pl->yt_elems, cudaMemcpyDeviceToDevice, s));
-    int cur = 0;
-    SB_CK(pl, cudaMemsetAsync(pl->bx[0], 0, sizeof(float2) * nb * n, s));
-    SB_CK(pl, cudaMemsetAsync(pl->by[0], 0, sizeof(float2) * nb * n, s));
-    SB_CK(pl, cudaMemsetAsync(pl->bw, 0, sizeof(float2) * nb * n, s));
-    SB_CK(pl, cudaMemsetAsync(pl->g, 0, sizeof(float2) * nb * n, s));
-    auto fields = [&]() {
-        SbFields f;
-        f.sens = pl->sens;
-        f.maskw = pl->maskw;
-        f.slot = pl->slot;
-        f.yt = pl->yt;
-        f.yt1 = pl->yt1;
-        f.ms = pl->ms;
-        f.bx = pl->bx[cur];
-        f.by = pl->by[cur];
-        f.bx_new = pl->bx[cur ^ 1];
-        f.by_new = pl->by[cur ^ 1];
-        f.bw = pl->bw;
-        f.g = pl->g;
-        return f;
-    };
-    if (o->init_rss) SB_LAUNCH(pl, SB_KCLASS_OTHER, 1, launch_rss(d, fields(), x, pl->tw_y, s));
-
-    sb_status first_err = SB_OK;
-    std::vector<int> iters(nb * nsolve, 0);
-    int solve = 0;
-    for (int j = 0; j < o->n_outer; ++j) {
-        for (int k = 0; k < o->n_inner; ++k, ++solve) {
-            const int addback = (j > 0 && k == 0);
-            SB_LAUNCH(pl, SB_KCLASS_RHS, 1, launch_rhs(d, pl->smap, pl->ymap, pl->y1map, fields(), addback, x, pl->r,
-                                                       pl->tw_y, mu, lam, gam, pl->st, tol2, red_of(pl), s));
-            sb_status ps = pcg_run(pl, o->pcg, x, h_last, iters.data() + solve, nsolve);
-            if (ps != SB_OK && first_err == SB_OK) first_err = ps;
-            const bool last = (j == o->n_outer - 1) && (k == o->n_inner - 1);
-            if (!last) {
-                SB_LAUNCH(pl, SB_KCLASS_SB_UPDATE, 1, launch_sb_update(d, fields(), x, levels, lam, gam, tau_tv, tau_w, s));
-                if (lam != 0.f) cur ^= 1;
-            }
-        }
+    const int nsolve = o->n_outer * o->n_inner;
+    std::vector<int> iters((size_t)pl->dims.nb * nsolve, 0);
+    const float2* y = static_cast<const float2*>(d_y);
+    float2* x = static_cast<float2*>(d_x);
+    sb_status st = run_groups(pl, [&](Exec& ex) { return sb_run(ex, *o, y, x, h_last, iters.data()); });
+    if (st != SB_ERR_CUDA && st != SB_ERR_TIMEOUT) {
+        SB_CK(pl, cudaStreamSynchronize(pl->stream));
+        if (o->h_iters) std::memcpy(o->h_iters, iters.data(), sizeof(int) * iters.size());
     }
-    SB_CK(pl, cudaStreamSynchronize(s));
-    timer_harvest(pl);
-    if (o->h_iters) std::memcpy(o->h_iters, iters.data(), sizeof(int) * iters.size());
-    return first_err;
+    return st;
 }
 
 sb_status sb_plan_set_timing(sb_plan pl, unsigned class_mask) {
     if (!pl) return SB_ERR_INVALID_ARG;
     SB_CK(pl, pl->stream ? cudaStreamSynchronize(pl->stream) : cudaDeviceSynchronize());
-    timer_harvest(pl);
+    timer_harvest(pl->whole);
+    for (Exec& ex : pl->groups) timer_harvest(ex);
+    std::lock_guard<std::mutex> lock(pl->tmu);
     pl->tmask = class_mask;
     for (int c = 0; c < SB_KCLASS_COUNT; ++c) {
         pl->tcount[c] = 0;
@@ -626,7 +819,9 @@ sb_status sb_plan_get_timing(sb_plan pl, int kernel_class, uint64_t* launches, d
     if (!pl || kernel_class < 0 || kernel_class >= SB_KCLASS_COUNT || !launches || !total_ms)
         return fail(pl, SB_ERR_INVALID_ARG, "bad timing query");
     SB_CK(pl, pl->stream ? cudaStreamSynchronize(pl->stream) : cudaDeviceSynchronize());
-    timer_harvest(pl);
+    timer_harvest(pl->whole);
+    for (Exec& ex : pl->groups) timer_harvest(ex);
+    std::lock_guard<std::mutex> lock(pl->tmu);
     *launches = pl->tcount[kernel_class];
     *total_ms = pl->tms[kernel_class];
     return SB_OK;

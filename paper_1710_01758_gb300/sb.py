@@ -37,7 +37,7 @@ class sb_plan_desc(ctypes.Structure):
     _fields_ = [("ndim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
                 ("ncoils", ctypes.c_int), ("nbatch", ctypes.c_int), ("mu", ctypes.c_double),
                 ("lambda_", ctypes.c_double), ("gamma", ctypes.c_double), ("wavelet_levels", ctypes.c_int),
-                ("prec", ctypes.c_int)]
+                ("prec", ctypes.c_int), ("groups", ctypes.c_int)]
 
 
 class sb_pcg_opts(ctypes.Structure):
@@ -126,8 +126,8 @@ def _check(status: int, plan=None, allow=()):
     return status
 
 
-def plan_desc(nx, ny, ncoils, nbatch, mu, lam, gam, wavelet_levels, prec=SB_PREC_FP32) -> sb_plan_desc:
-    return sb_plan_desc(2, nx, ny, 1, ncoils, nbatch, mu, lam, gam, wavelet_levels, prec)
+def plan_desc(nx, ny, ncoils, nbatch, mu, lam, gam, wavelet_levels, prec=SB_PREC_FP32, groups=0) -> sb_plan_desc:
+    return sb_plan_desc(2, nx, ny, 1, ncoils, nbatch, mu, lam, gam, wavelet_levels, prec, groups)
 
 
 def sb_plan_create(desc: sb_plan_desc, stream: int = 0) -> int:
@@ -205,14 +205,15 @@ def sb_plan_get_timing(plan: int, kernel_class: int):
 class Plan:
     """Owns an sb_plan and the device tensors it borrows (torch CUDA tensors)."""
 
-    def __init__(self, nx, ny, ncoils, nbatch, mu, lam, gam, wavelet_levels, stream=None):
+    def __init__(self, nx, ny, ncoils, nbatch, mu, lam, gam, wavelet_levels, stream=None, groups=0):
         import torch
         self.torch = torch
         self.nbatch = nbatch
         self.shape = (nbatch, ny, nx)
         s = stream if stream is not None else torch.cuda.current_stream()
         self.stream = s
-        self.handle = sb_plan_create(plan_desc(nx, ny, ncoils, nbatch, mu, lam, gam, wavelet_levels), s.cuda_stream)
+        self.handle = sb_plan_create(plan_desc(nx, ny, ncoils, nbatch, mu, lam, gam, wavelet_levels, groups=groups),
+                                     s.cuda_stream)
         self._sens = None
 
     def close(self):

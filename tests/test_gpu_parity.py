@@ -204,6 +204,40 @@ def test_split_bregman_inner_loops_and_levels(torch, sbm):
     assert rel(xg[0], refs[0].x) <= IMG_TOL
 
 
+def test_concurrent_groups_are_bitwise_identical(torch, sbm):
+    # slices are independent: running the batch as 3 concurrent groups must give exactly the
+    # result of one group, and both must match the oracle
+    wl = synth.Workload("64x64 Nc4 TV+Haar groups", 64, 64, 4, 4.0, 8, "uniform", 1.0, 0.05, 0.05, 3, 3, 1,
+                        1e-3, 100, 0, seed=5)
+    nb = 5
+    slices = [synth.make_slice(wl, 77 * 1000 + i) for i in range(nb)]
+    sens = to_dev(torch, np.stack([s.sens for s in slices]))
+    mask = torch.from_numpy(np.stack([s.mask for s in slices])).cuda()
+    y = to_dev(torch, np.stack([s.y for s in slices]))
+    out = []
+    for groups in (1, 3):
+        plan = sbm.Plan(wl.nx, wl.ny, wl.ncoils, nb, wl.mu, wl.lam, wl.gam, wl.wavelet_levels, groups=groups)
+        plan.set_coils(sens)
+        plan.set_mask(mask)
+        x = torch.zeros((nb, wl.ny, wl.nx), dtype=torch.complex64, device="cuda")
+        st, iters, _ = plan.split_bregman(y, x, wl.n_outer, tol=wl.pcg_tol, maxit=wl.pcg_maxit)
+        assert st == sbm.SB_OK
+        b = to_dev(torch, synth.random_complex((nb, wl.ny, wl.nx), np.random.default_rng(1)))
+        xs = torch.zeros_like(b)
+        st2, res = plan.pcg_solve(b, xs, tol=1e-4, maxit=100)
+        assert st2 == sbm.SB_OK
+        out.append((x.cpu().numpy(), iters, xs.cpu().numpy(), [r[0] for r in res]))
+        plan.close()
+    assert np.array_equal(out[0][0], out[1][0]) and out[0][1] == out[1][1]
+    assert np.array_equal(out[0][2], out[1][2]) and out[0][3] == out[1][3]
+    for i in (0, nb - 1):
+        s = slices[i]
+        ref = sb_oracle.split_bregman(s.y, s.sens, s.mask, wl.mu, wl.lam, wl.gam, wl.wavelet_levels, 2, wl.n_outer,
+                                      1, wl.pcg_tol, wl.pcg_maxit)
+        assert rel(out[1][0][i], ref.x) <= 5e-3
+        assert all(abs(a - b) <= 1 for a, b in zip(out[1][1][i], ref.iters))
+
+
 def test_unsupported_inputs(torch, sbm):
     with pytest.raises(sbm.SbError) as ei:
         sbm.Plan(48, 64, 2, 1, 1.0, 0.1, 0.1, 0)
