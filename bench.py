@@ -38,9 +38,10 @@ METRIC = "PCG iters/s and recon/s at 256²×12 coils; HBM GB/s vs peak; err vs F
 UNIT = "PCG iter/s"
 DEFAULT_BATCH = 64
 HBM_FALLBACK_GBS = 6800.0
-# DRAM bytes (read + write) of one k_apply_A launch over the full 64-slice batch, from the ncu
-# capture summarised in profiles/ (None until a capture of the current kernel exists)
-TRAFFIC_K1 = None
+# DRAM bytes (read + write) of one k_apply_A launch over the full 64-slice batch: the ncu capture
+# of profiles/k_apply_A_256x256x12_b32.md (32 slices: 227.49 MB read + 9.21 MB written) scaled by
+# the slices processed.  Set to None whenever the kernel changes until it is captured again.
+TRAFFIC_K1 = 2 * (227.49e6 + 9.21e6)
 
 
 def log(*a):
@@ -113,6 +114,22 @@ class ClockSampler:
         reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
         return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": smax, "reasons": reasons,
                 "samples": len(rows)}
+
+
+def rank_seed(seed: int, rank: int) -> int:
+    """Seed of rank `rank`'s batch: every rank reconstructs its own independent slices (weak
+    scaling over ranks, no data exchanged); rank 0 uses the workload's own seed."""
+    return seed + 7919 * rank
+
+
+def reduce_over_ranks(dist, device, elapsed: float, units: int):
+    """(max over ranks of the elapsed time, sum over ranks of the work units)."""
+    import torch
+    t = torch.tensor([elapsed, float(units)], dtype=torch.float64, device=device)
+    tmax = t.clone()
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(tmax[0]), int(round(float(t[1])))
 
 
 def make_inputs(wl, nbatch, seed):
@@ -205,7 +222,7 @@ def run_ours(args):
     wl = synth.METRIC_256
     B = args.batch
     t0 = time.perf_counter()
-    slices, sens_h, mask_h, y_h = make_inputs(wl, B, wl.seed + 7919 * rank)
+    slices, sens_h, mask_h, y_h = make_inputs(wl, B, rank_seed(wl.seed, rank))
     log(f"[bench] rank {rank}: generated {B} slices in {time.perf_counter() - t0:.1f}s")
     dev = torch.device("cuda", local)
     d_sens = torch.from_numpy(sens_h).to(dev)
@@ -252,11 +269,7 @@ def run_ours(args):
     total_all = total_iters
     elapsed_max = elapsed
     if dist:
-        t = torch.tensor([elapsed, float(total_iters)], dtype=torch.float64, device=dev)
-        tmax = t.clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        elapsed_max, total_all = float(tmax[0]), int(t[1])
+        elapsed_max, total_all = reduce_over_ranks(dist, dev, elapsed, total_iters)
     value = total_all / elapsed_max
     recon_per_s = args.steps * B * world / elapsed_max
 
@@ -338,11 +351,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         e_el = e0.elapsed_time(e1) / 1e3
         if dist:
-            t = torch.tensor([e_el, float(e2e_iters)], dtype=torch.float64, device=dev)
-            tmax = t.clone()
-            dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-            dist.all_reduce(t, op=dist.ReduceOp.SUM)
-            e_el, e2e_iters = float(tmax[0]), int(t[1])
+            e_el, e2e_iters = reduce_over_ranks(dist, dev, e_el, e2e_iters)
         e2e = {"value": e2e_iters / e_el, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
     plan.close()
