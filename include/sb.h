@@ -24,8 +24,8 @@
  *  - The mask must be constant along the readout (x) axis: Cartesian phase-encode line masks,
  *    the sampling of the paper's Methods ("Undersampling", random lines).  Other masks are
  *    rejected with SB_ERR_UNSUPPORTED.
- *  - Supported sizes: ndim = 2; nx, ny in {32, 64, 128, 256}; ncoils >= 1; nbatch >= 1;
- *    wavelet_levels in [0, 6] with nx, ny divisible by 2^levels and by 16.
+ *  - Supported sizes: ndim = 2; nx, ny in {32, 64, 128, 256, 512}; ncoils >= 1; nbatch >= 1;
+ *    wavelet_levels in [0, 5] (Haar blocks stay inside the 32 x 32 update tiles).
  */
 #ifndef SB_H
 #define SB_H
@@ -105,7 +105,8 @@ typedef struct {
     double tol;          /* stop when ||b - A x|| <= tol ||b|| (recurrence residual) */
     int maxit;           /* iteration cap (>= 1) */
     int fixed_iters;     /* > 0: run exactly this many iterations, no tolerance test */
-    sb_precond precond;  /* SB_PRECOND_CIRCULANT or SB_PRECOND_NONE */
+    sb_precond precond;  /* SB_PRECOND_CIRCULANT (Eq. precon), SB_PRECOND_NONE (plain CG) or
+                            SB_PRECOND_JACOBI (diag(A)^{-1}, the comparison of the Results) */
 } sb_pcg_opts;
 
 typedef struct {

@@ -151,6 +151,109 @@ __device__ __forceinline__ void fft_2stage(float2 (&v)[16], int t, float2* buf, 
     }
 }
 
+// The same transform with a caller-supplied barrier between the two stages (for transforms
+// whose threads are a subset of the CTA).
+template <int N, bool INV, class Idx, class Bar>
+__device__ __forceinline__ void fft_2stage_bar(float2 (&v)[16], int t, float2* buf, Idx idx, const float2* tw,
+                                               Bar bar) {
+    constexpr int R2 = N / 16;
+    constexpr int T = N / 16;
+    constexpr int BF = 16 / R2;
+    dft16<INV>(v);
+#pragma unroll
+    for (int r = 0; r < 16; ++r) buf[idx(16 * t + r)] = v[r];
+    bar();
+#pragma unroll
+    for (int m = 0; m < BF; ++m) {
+        const int j = t + T * m;
+        float2 a[R2];
+#pragma unroll
+        for (int r = 0; r < R2; ++r) a[r] = buf[idx(j + 16 * r)];
+#pragma unroll
+        for (int r = 1; r < R2; ++r) {
+            float2 w = tw[r * 16 + j];
+            if (INV) w.y = -w.y;
+            a[r] = cmul(a[r], w);
+        }
+        dftR<R2, INV>(a);
+#pragma unroll
+        for (int r = 0; r < R2; ++r) v[m + r * BF] = a[r];
+    }
+}
+
+// Three-stage transform for N = 16 * 16 * R3 (N = 512: R3 = 2), T = N / 16 threads per
+// transform, the same register layout (thread t holds x[t + T e] in and X[t + T e] out).
+// Stage 1: radix 16 on registers; stage 2: radix 16 over the 256-point sub-transforms (span 16,
+// twiddles tw[r * 16 + k] = W_256^{r k}); stage 3: radix R3 (span 256, twiddles tw[256 + k] =
+// W_N^{k}) back into registers.  Both exchanges go through `buf`; `bar()` separates every
+// write phase from the following reads and the stage-2 reads from the stage-2 writes.
+template <int N, bool INV, class Idx, class Bar>
+__device__ __forceinline__ void fft_3stage_bar(float2 (&v)[16], int t, float2* buf, Idx idx, const float2* tw,
+                                               Bar bar) {
+    constexpr int T = N / 16;
+    constexpr int R3 = N / 256;
+    constexpr int BF3 = 16 / R3;  // stage-3 butterflies per thread
+    static_assert(N == 256 * R3 && T * R3 == 16 * R3 * (T / 16), "N = 16 * 16 * R3");
+    // stage 1: Ns = 1, butterfly j = t, inputs x[t + T r], outputs y[16 t + r]
+    dft16<INV>(v);
+#pragma unroll
+    for (int r = 0; r < 16; ++r) buf[idx(16 * t + r)] = v[r];
+    bar();
+    // stage 2: Ns = 16, butterfly j = t, k = t % 16, inputs x[t + T r], outputs
+    // y[(t / 16) * 256 + k + 16 r]
+    {
+        const int k = t & 15;
+        float2 a[16];
+#pragma unroll
+        for (int r = 0; r < 16; ++r) a[r] = buf[idx(t + T * r)];
+#pragma unroll
+        for (int r = 1; r < 16; ++r) {
+            float2 w = tw[r * 16 + k];
+            if (INV) w.y = -w.y;
+            a[r] = cmul(a[r], w);
+        }
+        dft16<INV>(a);
+        bar();  // every stage-2 read is done before the stage-2 writes
+        const int base = (t >> 4) * 256 + k;
+#pragma unroll
+        for (int r = 0; r < 16; ++r) buf[idx(base + 16 * r)] = a[r];
+    }
+    bar();
+    // stage 3: Ns = 256, butterflies j = t + T m, k = j, inputs x[j + 256 r], outputs y[j + 256 r]
+#pragma unroll
+    for (int m = 0; m < BF3; ++m) {
+        const int j = t + T * m;
+        float2 a[R3];
+#pragma unroll
+        for (int r = 0; r < R3; ++r) a[r] = buf[idx(j + 256 * r)];
+#pragma unroll
+        for (int r = 1; r < R3; ++r) {
+            float2 w = tw[256 + (r * j) % 256];
+            if (INV) w.y = -w.y;
+            a[r] = cmul(a[r], w);
+        }
+        dftR<R3, INV>(a);
+#pragma unroll
+        for (int r = 0; r < R3; ++r) v[m + r * BF3] = a[r];
+    }
+}
+
+// Size dispatch: two stages up to N = 256, three for N = 512.
+template <int N, bool INV, class Idx, class Bar>
+__device__ __forceinline__ void fft_bar(float2 (&v)[16], int t, float2* buf, Idx idx, const float2* tw, Bar bar) {
+    if constexpr (N <= 256) fft_2stage_bar<N, INV>(v, t, buf, idx, tw, bar);
+    else fft_3stage_bar<N, INV>(v, t, buf, idx, tw, bar);
+}
+
+struct CtaBar {
+    __device__ __forceinline__ void operator()() const { __syncthreads(); }
+};
+
+template <int N, bool INV, class Idx>
+__device__ __forceinline__ void fft(float2 (&v)[16], int t, float2* buf, Idx idx, const float2* tw) {
+    fft_bar<N, INV>(v, t, buf, idx, tw, CtaBar{});
+}
+
 // ------------------------------------------------------------------ reductions
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll

@@ -1,21 +1,16 @@
 // Kernels of one preconditioned-CG iteration (Theory, "Complexity": one application of A and
 // one of M^{-1} per iteration) on a batch of slices.
 //
-//  k_apply_A      q = A p.  Readout-axis shortcut: with a mask constant along x,
-//                 F^H R F = (F_y^H R_y F_y) (x) I_x, so the data term needs only length-ny DFTs
-//                 along y.  One CTA owns TX full columns of one slice and loops over the
-//                 coils: S_c p -> DFT_y -> mask -> IDFT_y -> conj(S_c) . -> sum, then adds the
-//                 periodic TV stencil lambda D^H D p and gamma p, stores q and Re(p^H q).
+//  (q = A p is in k_applyA.cu)
 //  k_row_fwd      r -= alpha q, ||r||^2, then the DFT along x of r (first half of M^{-1}).
 //  k_col_precond  DFT along y, scale by 1/(k N), inverse DFT along y (middle of M^{-1});
 //                 rho = r^H M^{-1} r = sum |DFT2 r|^2 / (N k) is accumulated in k-space.
 //  k_row_inv      inverse DFT along x gives z; x += alpha p, p = z + beta p.
-//  k_vec_plain    the same CG updates without a preconditioner (z = r).
+//  k_vec_plain    the same CG updates with z = r (no preconditioner) or z = r / diag(A) (Jacobi).
 // FP64 holds every CG scalar; vectors are complex64.  Cross-CTA sums use the last-CTA
 // pattern (common.cuh), so a CG iteration needs no extra scalar launches and no host sync.
 #include "common.cuh"
 #include "kernels.h"
-#include "tma.cuh"
 
 namespace sb {
 namespace {
@@ -34,121 +29,6 @@ struct RowIdx {
         return row * (N + N / 16) + pos + (pos >> 4);
     }
 };
-
-// ------------------------------------------------------------------------------ q = A p
-// The coil tiles S_c[:, x0:x0+TX] stream through a two-stage shared-memory pipeline filled by
-// TMA (one elected thread issues cp.async.bulk.tensor.2d per tile): while coil c is
-// transformed, coil c+1 is in flight.  p stays in registers for the whole coil loop.
-template <int NY, bool PCG>
-__global__ void __launch_bounds__(TX * NY / 16, 2)
-k_apply_A(const __grid_constant__ CUtensorMap smap, const float2* __restrict__ p, float2* __restrict__ q,
-          const float* __restrict__ maskw, const float2* __restrict__ tw_g, int nx, int nc, float mu, float lam,
-          float gam, SliceState* st, Red red) {
-    constexpr int T = NY / 16;
-    constexpr int NT = TX * T;
-    constexpr uint32_t kTileBytes = NY * TX * sizeof(float2);
-    const int b = blockIdx.y;
-    if (PCG && st[b].state != ST_ACTIVE) return;
-    extern __shared__ __align__(128) unsigned char smem[];
-    float2* sbuf = reinterpret_cast<float2*>(smem);  // [2][NY * TX] coil tiles (TMA destinations)
-    float2* xbuf = sbuf + 2 * NY * TX;                // [NY * TX] FFT exchange, then the p tile
-    float2* tw = xbuf + NY * TX;
-    float2* halo = tw + NY;                           // [2][NY]: columns x0-1 and x0+TX
-    float* mk = reinterpret_cast<float*>(halo + 2 * NY);
-    double* red_s = reinterpret_cast<double*>(mk + NY);
-    __shared__ __align__(8) uint64_t bars[2];
-    __shared__ int flag;
-
-    const int tid = threadIdx.x, col = tid % TX, t = tid / TX;
-    const int x0 = blockIdx.x * TX, x = x0 + col;
-    if (tid == 0) {
-        mbar_init(&bars[0], 1);
-        mbar_init(&bars[1], 1);
-        mbar_init_fence();
-    }
-    __syncthreads();
-    if (tid == 0) {
-        for (int c = 0; c < 2 && c < nc; ++c) {
-            mbar_arrive_expect_tx(&bars[c], kTileBytes);
-            tma_load_2d(sbuf + c * NY * TX, &smap, 2 * x0, (b * nc + c) * NY, &bars[c]);
-        }
-    }
-    for (int i = tid; i < NY; i += NT) {
-        tw[i] = tw_g[i];
-        mk[i] = maskw[(size_t)b * NY + i];
-    }
-    const size_t img = (size_t)b * NY * nx;
-    float2 pv[16], acc[16];
-#pragma unroll
-    for (int e = 0; e < 16; ++e) {
-        pv[e] = p[img + (size_t)(t + T * e) * nx + x];
-        acc[e] = make_float2(0.f, 0.f);
-    }
-    __syncthreads();
-    const ColIdx idx{col};
-    for (int c = 0; c < nc; ++c) {
-        const int stage = c & 1;
-        mbar_wait(&bars[stage], (c >> 1) & 1, red.err);
-        const float2* S = sbuf + stage * NY * TX;
-        float2 u[16];
-#pragma unroll
-        for (int e = 0; e < 16; ++e) u[e] = cmul(S[idx(t + T * e)], pv[e]);
-        fft_2stage<NY, false>(u, t, xbuf, idx, tw);
-#pragma unroll
-        for (int e = 0; e < 16; ++e) u[e] = cscale(u[e], mk[t + T * e]);
-        __syncthreads();  // forward transform done with xbuf
-        fft_2stage<NY, true>(u, t, xbuf, idx, tw);
-#pragma unroll
-        for (int e = 0; e < 16; ++e) acc[e] = cfmac(acc[e], S[idx(t + T * e)], u[e]);
-        __syncthreads();  // every thread is done with this stage's tile and with xbuf
-        if (tid == 0 && c + 2 < nc) {
-            mbar_arrive_expect_tx(&bars[stage], kTileBytes);
-            tma_load_2d(sbuf + stage * NY * TX, &smap, 2 * x0, (b * nc + c + 2) * NY, &bars[stage]);
-        }
-    }
-    // periodic 5-point stencil for lambda (D_x^H D_x + D_y^H D_y) p
-#pragma unroll
-    for (int e = 0; e < 16; ++e) xbuf[idx(t + T * e)] = pv[e];
-    for (int i = tid; i < NY; i += NT) {
-        halo[i] = p[img + (size_t)i * nx + (x0 == 0 ? nx - 1 : x0 - 1)];
-        halo[NY + i] = p[img + (size_t)i * nx + (x0 + TX == nx ? 0 : x0 + TX)];
-    }
-    __syncthreads();
-    float dot = 0.f;
-#pragma unroll
-    for (int e = 0; e < 16; ++e) {
-        const int y = t + T * e;
-        const float2 up = xbuf[idx(y == 0 ? NY - 1 : y - 1)];
-        const float2 dn = xbuf[idx(y == NY - 1 ? 0 : y + 1)];
-        const float2 lf = col > 0 ? xbuf[idx(y) - 1] : halo[y];
-        const float2 rt = col < TX - 1 ? xbuf[idx(y) + 1] : halo[NY + y];
-        const float tvx = 4.f * pv[e].x - up.x - dn.x - lf.x - rt.x;
-        const float tvy = 4.f * pv[e].y - up.y - dn.y - lf.y - rt.y;
-        float2 o;
-        o.x = fmaf(mu, acc[e].x, fmaf(lam, tvx, gam * pv[e].x));
-        o.y = fmaf(mu, acc[e].y, fmaf(lam, tvy, gam * pv[e].y));
-        q[img + (size_t)y * nx + x] = o;
-        dot = fmaf(pv[e].x, o.x, fmaf(pv[e].y, o.y, dot));
-    }
-    if constexpr (PCG) {
-        double v[1] = {(double)dot}, tot[1];
-        const int np = gridDim.x;
-        if (last_block_total<1>(v, red.part, np, b * np + blockIdx.x, red.counter + b, tot, red_s, &flag) &&
-            threadIdx.x == 0) {
-            SliceState& S = st[b];
-            const double pq = tot[0];
-            S.pq = pq;
-            if (!isfinite(pq) || !isfinite(S.rho)) {
-                S.state = ST_NONFINITE;
-            } else if (!(pq > 0.0)) {
-                S.state = ST_BREAKDOWN;
-            } else {
-                S.alpha = S.rho / pq;
-                S.iters += 1;
-            }
-        }
-    }
-}
 
 // ------------------------------------------------------------------------------ row pass F_x
 // MODE 0: t = F_x(r), slices filtered by st if given.  MODE 1: r -= alpha q first (PCG step).
@@ -189,7 +69,7 @@ k_row_fwd(float2* __restrict__ r, const float2* __restrict__ q, float2* __restri
         for (int e = 0; e < 16; ++e) v[e] = r[base + t + T * e];
     }
     __syncthreads();
-    fft_2stage<NX, false>(v, t, buf, RowIdx<NX>{row}, tw);
+    fft<NX, false>(v, t, buf, RowIdx<NX>{row}, tw);
 #pragma unroll
     for (int e = 0; e < 16; ++e) tout[base + t + T * e] = v[e];
     if constexpr (MODE == 1) {
@@ -229,7 +109,7 @@ k_col_precond(float2* __restrict__ tb, const float* __restrict__ invk, const flo
     for (int e = 0; e < 16; ++e) v[e] = tb[img + (size_t)(t + T * e) * nx + x];
     __syncthreads();
     const ColIdx idx{col};
-    fft_2stage<NY, false>(v, t, buf0, idx, tw);
+    fft<NY, false>(v, t, buf0, idx, tw);
     float rz = 0.f;
 #pragma unroll
     for (int e = 0; e < 16; ++e) {
@@ -237,7 +117,7 @@ k_col_precond(float2* __restrict__ tb, const float* __restrict__ invk, const flo
         rz = fmaf(cabs2(v[e]), w, rz);
         v[e] = cscale(v[e], w);
     }
-    fft_2stage<NY, true>(v, t, buf1, idx, tw);
+    fft<NY, true>(v, t, buf1, idx, tw);
 #pragma unroll
     for (int e = 0; e < 16; ++e) tb[img + (size_t)(t + T * e) * nx + x] = v[e];
     if constexpr (PCG) {
@@ -301,7 +181,7 @@ k_row_inv(const float2* __restrict__ tb, float2* __restrict__ out, float2* __res
 #pragma unroll
     for (int e = 0; e < 16; ++e) v[e] = tb[base + t + T * e];
     __syncthreads();
-    fft_2stage<NX, true>(v, t, buf, RowIdx<NX>{row}, tw);
+    fft<NX, true>(v, t, buf, RowIdx<NX>{row}, tw);
     if constexpr (MODE == 0) {
 #pragma unroll
         for (int e = 0; e < 16; ++e) out[base + t + T * e] = v[e];
@@ -323,28 +203,30 @@ k_row_inv(const float2* __restrict__ tb, float2* __restrict__ out, float2* __res
     }
 }
 
-// ------------------------------------------------------------------------------ plain CG
+// ------------------------------------------------------------------------------ CG without
+// the circulant preconditioner: z = w r with w = 1 (plain CG) or w = 1 / diag(A) (Jacobi)
 template <int MODE>
 __global__ void __launch_bounds__(kVecThreads)
 k_vec_plain(float2* __restrict__ x, float2* __restrict__ r, float2* __restrict__ p,
-            const float2* __restrict__ q, int n, SliceState* st, double tol2, Red red) {
+            const float2* __restrict__ q, const float* __restrict__ w, int n, SliceState* st, double tol2, Red red) {
     const int b = blockIdx.y;
     const int s = st[b].state;
     if (MODE != 2 && s != ST_ACTIVE) return;
     if (MODE == 2 && s != ST_ACTIVE && s != ST_FINISHING) return;
-    __shared__ double red_s[32];
+    __shared__ double red_s[64];
     __shared__ int flag;
     const size_t img = (size_t)b * n;
     const int i0 = blockIdx.x * kVecThreads * kVecPerThread + threadIdx.x;
-    float rr = 0.f;
+    float rr = 0.f, rz = 0.f;
     if constexpr (MODE == 0) {
 #pragma unroll
         for (int k = 0; k < kVecPerThread; ++k) {
             const int i = i0 + k * kVecThreads;
             if (i < n) {
                 const float2 rv = r[img + i];
-                p[img + i] = rv;
-                rr += cabs2(rv);
+                const float wv = w ? w[img + i] : 1.f;
+                p[img + i] = cscale(rv, wv);
+                rz += wv * cabs2(rv);
             }
         }
     } else if constexpr (MODE == 1) {
@@ -358,7 +240,9 @@ k_vec_plain(float2* __restrict__ x, float2* __restrict__ r, float2* __restrict__
                 rv.x = fmaf(-alpha, qq.x, rv.x);
                 rv.y = fmaf(-alpha, qq.y, rv.y);
                 r[img + i] = rv;
-                rr += cabs2(rv);
+                const float a2 = cabs2(rv);
+                rr += a2;
+                rz += (w ? w[img + i] : 1.f) * a2;
             }
         }
     } else {
@@ -374,26 +258,26 @@ k_vec_plain(float2* __restrict__ x, float2* __restrict__ r, float2* __restrict__
                 xv.y = fmaf(alpha, pp.y, xv.y);
                 x[img + i] = xv;
                 if (upd_p) {
-                    const float2 rv = r[img + i];
-                    p[img + i] = make_float2(fmaf(beta, pp.x, rv.x), fmaf(beta, pp.y, rv.y));
+                    const float2 zv = cscale(r[img + i], w ? w[img + i] : 1.f);
+                    p[img + i] = make_float2(fmaf(beta, pp.x, zv.x), fmaf(beta, pp.y, zv.y));
                 }
             }
         }
     }
-    double vv[1] = {(double)rr}, tot[1];
+    double vv[2] = {(double)rr, (double)rz}, tot[2];
     const int np = gridDim.x;
-    if (last_block_total<1>(vv, red.part, np, b * np + blockIdx.x, red.counter + b, tot, red_s, &flag) &&
+    if (last_block_total<2>(vv, red.part, np, b * np + blockIdx.x, red.counter + b, tot, red_s, &flag) &&
         threadIdx.x == 0) {
         SliceState& S = st[b];
         if (MODE == 0) {
-            S.rho = tot[0];
+            S.rho = tot[1];
         } else if (MODE == 1) {
             S.rnorm2 = tot[0];
-            if (!isfinite(tot[0])) S.state = ST_NONFINITE;
+            if (!isfinite(tot[0]) || !isfinite(tot[1])) S.state = ST_NONFINITE;
             else if (tot[0] <= tol2 * S.bnorm2) S.state = ST_FINISHING;
             else {
-                S.beta = tot[0] / S.rho;
-                S.rho = tot[0];
+                S.beta = tot[1] / S.rho;
+                S.rho = tot[1];
             }
         } else if (s == ST_FINISHING) {
             S.state = ST_DONE;
@@ -457,28 +341,9 @@ cudaError_t prepare(K kernel, size_t smem) {
 }
 
 template <int NY>
-size_t smem_apply_A() { return (3 * NY * TX + NY + 2 * NY) * sizeof(float2) + NY * sizeof(float) + 64 * sizeof(double); }
-template <int NY>
 size_t smem_col() { return (2 * NY * TX + NY) * sizeof(float2) + 64 * sizeof(double); }
 template <int NX>
 size_t smem_row() { return (RY * (NX + NX / 16) + NX) * sizeof(float2) + 64 * sizeof(double); }
-
-template <int NY>
-cudaError_t apply_A_n(const Dims& d, const CUtensorMap& smap, const float2* p, float2* q, const float* maskw,
-                      const float2* tw, float mu, float lam, float gam, SliceState* st, Red red,
-                      cudaStream_t s) {
-    const dim3 grid(d.nx / TX, d.nb), block(TX * NY / 16);
-    const size_t sm = smem_apply_A<NY>();
-    cudaError_t e;
-    if (st) {
-        if ((e = prepare(k_apply_A<NY, true>, sm)) != cudaSuccess) return e;
-        k_apply_A<NY, true><<<grid, block, sm, s>>>(smap, p, q, maskw, tw, d.nx, d.nc, mu, lam, gam, st, red);
-    } else {
-        if ((e = prepare(k_apply_A<NY, false>, sm)) != cudaSuccess) return e;
-        k_apply_A<NY, false><<<grid, block, sm, s>>>(smap, p, q, maskw, tw, d.nx, d.nc, mu, lam, gam, st, red);
-    }
-    return cudaGetLastError();
-}
 
 template <int NX>
 cudaError_t row_fwd_n(const Dims& d, int mode, float2* r, const float2* q, float2* t, const float2* tw,
@@ -541,20 +406,6 @@ dim3 vec_grid(const Dims& d) {
 
 }  // namespace
 
-cudaError_t launch_apply_A(const Dims& d, const CUtensorMap& smap, const float2* p, float2* q, const float* maskw,
-                           const float2* tw_y, float mu, float lam, float gam, SliceState* st, Red red,
-                           cudaStream_t s) {
-#define CALL(N) apply_A_n<N>(d, smap, p, q, maskw, tw_y, mu, lam, gam, st, red, s)
-    switch (d.ny) {
-        case 32: return CALL(32);
-        case 64: return CALL(64);
-        case 128: return CALL(128);
-        case 256: return CALL(256);
-        default: return cudaErrorInvalidValue;
-    }
-#undef CALL
-}
-
 cudaError_t launch_row_fwd(const Dims& d, int mode, float2* r, const float2* q, float2* t, const float2* tw_x,
                            SliceState* st, double tol2, Red red, cudaStream_t s) {
 #define CALL(N) row_fwd_n<N>(d, mode, r, q, t, tw_x, st, tol2, red, s)
@@ -563,6 +414,7 @@ cudaError_t launch_row_fwd(const Dims& d, int mode, float2* r, const float2* q, 
         case 64: return CALL(64);
         case 128: return CALL(128);
         case 256: return CALL(256);
+        case 512: return CALL(512);
         default: return cudaErrorInvalidValue;
     }
 #undef CALL
@@ -576,6 +428,7 @@ cudaError_t launch_col_precond(const Dims& d, float2* t, const float* invk, cons
         case 64: return CALL(64);
         case 128: return CALL(128);
         case 256: return CALL(256);
+        case 512: return CALL(512);
         default: return cudaErrorInvalidValue;
     }
 #undef CALL
@@ -589,19 +442,20 @@ cudaError_t launch_row_inv(const Dims& d, int mode, const float2* t, float2* out
         case 64: return CALL(64);
         case 128: return CALL(128);
         case 256: return CALL(256);
+        case 512: return CALL(512);
         default: return cudaErrorInvalidValue;
     }
 #undef CALL
 }
 
 cudaError_t launch_vec_plain(const Dims& d, int mode, float2* x, float2* r, float2* p, const float2* q,
-                             SliceState* st, double tol2, Red red, cudaStream_t s) {
+                             const float* w, SliceState* st, double tol2, Red red, cudaStream_t s) {
     const int n = d.nx * d.ny;
     const dim3 grid = vec_grid(d);
     switch (mode) {
-        case 0: k_vec_plain<0><<<grid, kVecThreads, 0, s>>>(x, r, p, q, n, st, tol2, red); break;
-        case 1: k_vec_plain<1><<<grid, kVecThreads, 0, s>>>(x, r, p, q, n, st, tol2, red); break;
-        default: k_vec_plain<2><<<grid, kVecThreads, 0, s>>>(x, r, p, q, n, st, tol2, red);
+        case 0: k_vec_plain<0><<<grid, kVecThreads, 0, s>>>(x, r, p, q, w, n, st, tol2, red); break;
+        case 1: k_vec_plain<1><<<grid, kVecThreads, 0, s>>>(x, r, p, q, w, n, st, tol2, red); break;
+        default: k_vec_plain<2><<<grid, kVecThreads, 0, s>>>(x, r, p, q, w, n, st, tol2, red);
     }
     return cudaGetLastError();
 }

@@ -26,6 +26,10 @@ struct ColIdx {
     __device__ __forceinline__ int operator()(int pos) const { return pos * TX + col; }
 };
 
+// pipeline stages: two up to ny = 256, one at ny = 512 (shared memory)
+template <int NY>
+constexpr int kRhsStages = NY <= 256 ? 2 : 1;
+
 template <int NY, bool ADDBACK>
 __global__ void __launch_bounds__(TX * NY / 16, 1)
 k_rhs(const __grid_constant__ CUtensorMap smap, const __grid_constant__ CUtensorMap ymap,
@@ -34,15 +38,17 @@ k_rhs(const __grid_constant__ CUtensorMap smap, const __grid_constant__ CUtensor
       double tol2, Red red) {
     constexpr int T = NY / 16;
     constexpr int NT = TX * T;
+    constexpr int NST = kRhsStages<NY>;
+    constexpr int SBOX = NY < 256 ? NY : 256;  // rows per TMA box of a coil tile
     const int b = blockIdx.y;
-    const int ms = f.ms;
+    const int ms = f.ms;  // <= 256: one box of compact rows
     const uint32_t sbytes = NY * TX * sizeof(float2);
     const uint32_t ybytes = ms * TX * sizeof(float2);
     const uint32_t stage_bytes = sbytes + (ADDBACK ? 2u : 1u) * ybytes;
     const int stage_elems = (NY + 2 * ms) * TX;
     extern __shared__ __align__(128) unsigned char smem[];
-    float2* stages = reinterpret_cast<float2*>(smem);  // [2][S tile | yt rows | yt1 rows]
-    float2* xbuf = stages + 2 * stage_elems;            // FFT exchange, then the x tile
+    float2* stages = reinterpret_cast<float2*>(smem);  // [NST][S tile | yt rows | yt1 rows]
+    float2* xbuf = stages + NST * stage_elems;          // FFT exchange, then the x tile
     float2* tw = xbuf + NY * TX;
     float2* halo = tw + NY;
     int* sl = reinterpret_cast<int*>(halo + 2 * NY);
@@ -55,7 +61,8 @@ k_rhs(const __grid_constant__ CUtensorMap smap, const __grid_constant__ CUtensor
     auto issue = [&](int c, int stage) {
         float2* dst = stages + stage * stage_elems;
         mbar_arrive_expect_tx(&bars[stage], stage_bytes);
-        tma_load_2d(dst, &smap, 2 * x0, (b * nc + c) * NY, &bars[stage]);
+#pragma unroll
+        for (int r0 = 0; r0 < NY; r0 += SBOX) tma_load_2d(dst + r0 * TX, &smap, 2 * x0, (b * nc + c) * NY + r0, &bars[stage]);
         tma_load_2d(dst + NY * TX, &ymap, 2 * x0, (b * nc + c) * ms, &bars[stage]);
         if (ADDBACK) tma_load_2d(dst + (NY + ms) * TX, &y1map, 2 * x0, (b * nc + c) * ms, &bars[stage]);
     };
@@ -66,7 +73,7 @@ k_rhs(const __grid_constant__ CUtensorMap smap, const __grid_constant__ CUtensor
     }
     __syncthreads();
     if (tid == 0)
-        for (int c = 0; c < 2 && c < nc; ++c) issue(c, c);
+        for (int c = 0; c < NST && c < nc; ++c) issue(c, c);
     for (int i = tid; i < NY; i += NT) {
         tw[i] = tw_g[i];
         sl[i] = f.slot[(size_t)b * NY + i];
@@ -82,8 +89,8 @@ k_rhs(const __grid_constant__ CUtensorMap smap, const __grid_constant__ CUtensor
     const ColIdx idx{col};
     const float sc = rsqrtf((float)NY);
     for (int c = 0; c < nc; ++c) {
-        const int stage = c & 1;
-        mbar_wait(&bars[stage], (c >> 1) & 1, red.err);
+        const int stage = c % NST;
+        mbar_wait(&bars[stage], (c / NST) & 1, red.err);
         const float2* S = stages + stage * stage_elems;
         const float2* Yt = S + NY * TX;
         const float2* Y1 = Yt + ms * TX;
@@ -91,7 +98,7 @@ k_rhs(const __grid_constant__ CUtensorMap smap, const __grid_constant__ CUtensor
         float2 u[16];
 #pragma unroll
         for (int e = 0; e < 16; ++e) u[e] = cmul(S[idx(t + T * e)], xv[e]);
-        fft_2stage<NY, false>(u, t, xbuf, idx, tw);
+        fft<NY, false>(u, t, xbuf, idx, tw);
         // on sampled lines: tt = R F S x (unitary scale), yv = y^[j] after the outer update,
         // u <- yv - tt; zero elsewhere
 #pragma unroll
@@ -110,11 +117,11 @@ k_rhs(const __grid_constant__ CUtensorMap smap, const __grid_constant__ CUtensor
             }
         }
         __syncthreads();
-        fft_2stage<NY, true>(u, t, xbuf, idx, tw);
+        fft<NY, true>(u, t, xbuf, idx, tw);
 #pragma unroll
         for (int e = 0; e < 16; ++e) racc[e] = cfmac(racc[e], S[idx(t + T * e)], cscale(u[e], sc));
         __syncthreads();  // this stage's tiles and xbuf are free
-        if (tid == 0 && c + 2 < nc) issue(c + 2, stage);
+        if (tid == 0 && c + NST < nc) issue(c + NST, stage);
     }
     // bd' = (racc + bd + bd1) / 2 after an outer update (else bd' = bd);
     // b = mu bd' + g ;  r = mu racc + g - lam D^H D x - gam x
@@ -182,7 +189,8 @@ cudaError_t rhs_n(const Dims& d, const CUtensorMap& smap, const CUtensorMap& yma
 }  // namespace
 
 size_t rhs_smem_bytes(int ny, int ms) {
-    return (2 * (size_t)(ny + 2 * ms) * TX + (size_t)ny * TX + 3 * (size_t)ny) * sizeof(float2) +
+    const size_t nst = ny <= 256 ? 2 : 1;
+    return (nst * (size_t)(ny + 2 * ms) * TX + (size_t)ny * TX + 3 * (size_t)ny) * sizeof(float2) +
            ny * sizeof(int) + 64 * sizeof(double);
 }
 
@@ -197,6 +205,7 @@ cudaError_t launch_rhs(const Dims& d, const CUtensorMap& smap, const CUtensorMap
         case 64: CALL(64)
         case 128: CALL(128)
         case 256: CALL(256)
+        case 512: CALL(512)
         default: return cudaErrorInvalidValue;
     }
 #undef CALL

@@ -58,7 +58,7 @@ k_ytilde(const float2* __restrict__ y, const int* __restrict__ lines, int ny, in
         for (int e = 0; e < 16; ++e) v[e] = make_float2(0.f, 0.f);
     }
     __syncthreads();
-    fft_2stage<NX, true>(v, t, buf, RowIdx<NX>{row}, tw);
+    fft<NX, true>(v, t, buf, RowIdx<NX>{row}, tw);
     const float sc = rsqrtf((float)NX);
     if (ok)
 #pragma unroll
@@ -102,7 +102,7 @@ k_rss(SbFields f, int nx, int nc, float2* __restrict__ x, int write_x, const flo
             const int s = sl[t + T * e];
             v[e] = s >= 0 ? Y[(size_t)s * nx + xg] : make_float2(0.f, 0.f);
         }
-        fft_2stage<NY, true>(v, t, (c & 1) ? buf1 : buf0, idx, tw);
+        fft<NY, true>(v, t, (c & 1) ? buf1 : buf0, idx, tw);
 #pragma unroll
         for (int e = 0; e < 16; ++e) {
             const float2 ci = cscale(v[e], sc);  // coil image F^H y_c
@@ -144,6 +144,7 @@ cudaError_t launch_ytilde(const Dims& d, const float2* y, const int* lines, int 
         case 64: CALL(64)
         case 128: CALL(128)
         case 256: CALL(256)
+        case 512: CALL(512)
         default: return cudaErrorInvalidValue;
     }
 #undef CALL
@@ -168,6 +169,7 @@ cudaError_t launch_rss(const Dims& d, const SbFields& f, float2* x, int write_x,
         case 64: CALL(64)
         case 128: CALL(128)
         case 256: CALL(256)
+        case 512: CALL(512)
         default: return cudaErrorInvalidValue;
     }
 #undef CALL

@@ -59,7 +59,7 @@ k_fft_rows(float2* __restrict__ data, int nrows_total, const float2* __restrict_
 #pragma unroll
     for (int e = 0; e < 16; ++e) v[e] = data[base + t + T * e];
     __syncthreads();
-    fft_2stage<NX, INV>(v, t, buf, RowIdx<NX>{row}, tw);
+    fft<NX, INV>(v, t, buf, RowIdx<NX>{row}, tw);
     if (ok)
 #pragma unroll
         for (int e = 0; e < 16; ++e) data[base + t + T * e] = v[e];
@@ -81,7 +81,7 @@ k_fft_cols(float2* __restrict__ data, int nx, const float2* __restrict__ tw_g) {
 #pragma unroll
     for (int e = 0; e < 16; ++e) v[e] = data[img + (size_t)(t + T * e) * nx + x];
     __syncthreads();
-    fft_2stage<NY, INV>(v, t, buf, ColIdx{col}, tw);
+    fft<NY, INV>(v, t, buf, ColIdx{col}, tw);
 #pragma unroll
     for (int e = 0; e < 16; ++e) data[img + (size_t)(t + T * e) * nx + x] = v[e];
 }
@@ -138,6 +138,28 @@ __global__ void k_clamp_invert(float* __restrict__ k, float* __restrict__ invk, 
     }
 }
 
+// Jacobi: w = 1 / diag(A), diag(A)_j = mu (nnz(r)/N) sum_c |S_c[j]|^2 + 4 lam + gam
+// ((S^H F^H R F S)_jj = |s_j|^2 (F^H R F)_jj = |s_j|^2 nnz(r)/N; each D_a^H D_a adds 2)
+__global__ void k_jacobi_diag(const float2* __restrict__ sens, const float* __restrict__ maskw, int n, int ny, int nc,
+                              float mu, float lam, float gam, float* __restrict__ w) {
+    const int b = blockIdx.y;
+    __shared__ float frac_s;
+    if (threadIdx.x < 32) {
+        float s = 0.f;  // maskw holds 1/ny on sampled lines: its sum is nnz(r)/N
+        for (int y = threadIdx.x; y < ny; y += 32) s += maskw[(size_t)b * ny + y];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (threadIdx.x == 0) frac_s = s;
+    }
+    __syncthreads();
+    const float frac = frac_s;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        float p = 0.f;
+        for (int c = 0; c < nc; ++c) p += cabs2(sens[((size_t)b * nc + c) * n + i]);
+        w[(size_t)b * n + i] = 1.f / fmaf(mu * frac, p, 4.f * lam + gam);
+    }
+}
+
 template <int NX>
 cudaError_t fft_rows_n(int ny, int nimg, float2* data, const float2* tw, bool inv, cudaStream_t s) {
     const int rows = ny * nimg;
@@ -187,6 +209,7 @@ cudaError_t launch_fft_rows(int nx, int ny, int nimg, float2* data, const float2
         case 64: return fft_rows_n<64>(ny, nimg, data, tw_x, inv, s);
         case 128: return fft_rows_n<128>(ny, nimg, data, tw_x, inv, s);
         case 256: return fft_rows_n<256>(ny, nimg, data, tw_x, inv, s);
+        case 512: return fft_rows_n<512>(ny, nimg, data, tw_x, inv, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -197,6 +220,7 @@ cudaError_t launch_fft_cols(int nx, int ny, int nimg, float2* data, const float2
         case 64: return fft_cols_n<64>(nx, nimg, data, tw_y, inv, s);
         case 128: return fft_cols_n<128>(nx, nimg, data, tw_y, inv, s);
         case 256: return fft_cols_n<256>(nx, nimg, data, tw_y, inv, s);
+        case 512: return fft_cols_n<512>(nx, nimg, data, tw_y, inv, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -217,6 +241,13 @@ cudaError_t launch_mask_to_complex(const Dims& d, const uint8_t* mask, float2* o
 cudaError_t launch_mul_conj(const Dims& d, float2* R, const float2* G, cudaStream_t s) {
     const size_t n = (size_t)d.nx * d.ny * d.nb;
     k_mul_conj<<<elem_blocks(n), 256, 0, s>>>(R, G, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_jacobi_diag(const Dims& d, const float2* sens, const float* maskw, float mu, float lam, float gam,
+                               float* w, cudaStream_t s) {
+    const int n = d.nx * d.ny;
+    k_jacobi_diag<<<dim3(elem_blocks(n), d.nb), 256, 0, s>>>(sens, maskw, n, d.ny, d.nc, mu, lam, gam, w);
     return cudaGetLastError();
 }
 

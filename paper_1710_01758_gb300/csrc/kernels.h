@@ -71,11 +71,15 @@ cudaError_t launch_col_precond(const Dims& d, float2* t, const float* invk, cons
 cudaError_t launch_row_inv(const Dims& d, int mode, const float2* t, float2* out, float2* x,
                            float2* p, const float2* tw_x, SliceState* st, Red red, cudaStream_t s);
 
-// Preconditioner-free CG: mode 0 (init): p = r, rho = ||r||^2;
-// mode 1 (step, after q = A p): r -= alpha q, ||r||^2 test, beta = ||r||^2 / rho;
-// mode 2 (step): x += alpha p, p = r + beta p.
+// CG with a diagonal preconditioner z = w r (w == nullptr: w = 1, plain CG; else w = 1 / diag(A),
+// Jacobi): mode 0 (init): p = z, rho = r^H z; mode 1 (step, after q = A p): r -= alpha q,
+// ||r||^2 test, beta = r^H z / rho; mode 2 (step): x += alpha p, p = z + beta p.
 cudaError_t launch_vec_plain(const Dims& d, int mode, float2* x, float2* r, float2* p,
-                             const float2* q, SliceState* st, double tol2, Red red, cudaStream_t s);
+                             const float2* q, const float* w, SliceState* st, double tol2, Red red,
+                             cudaStream_t s);
+// w = 1 / (mu nnz(r)/N sum_c |S_c|^2 + 4 lambda + gamma): the inverse diagonal of A (Jacobi).
+cudaError_t launch_jacobi_diag(const Dims& d, const float2* sens, const float* maskw, float mu, float lam,
+                               float gam, float* w, cudaStream_t s);
 
 // r = b - q, ||b||^2, ||r||^2, initial convergence test and state.
 cudaError_t launch_resid_init(const Dims& d, const float2* b, const float2* q, float2* r,

@@ -30,7 +30,7 @@ std::atomic<uint64_t> g_launches{0};
 // PCG iterations enqueued between two reads of the per-slice state
 constexpr int kPollEvery = 4;
 
-bool supported_n(int n) { return n == 32 || n == 64 || n == 128 || n == 256; }
+bool supported_n(int n) { return n == 32 || n == 64 || n == 128 || n == 256 || n == 512; }
 
 struct Pending {
     int cls;
@@ -47,6 +47,7 @@ struct Exec {
     cudaStream_t s = nullptr;
     bool own_stream = false;
     CUtensorMap smap{}, ymap{}, y1map{};  // TMA maps whose first row belongs to slice b0
+    CUtensorMap smap_sw{};                // coil tiles with the 128-byte swizzle (q = A p)
     SliceState* st = nullptr;             // device state of the range
     SliceState* h_st = nullptr;           // pinned mirror of the range
     Red red{};
@@ -75,6 +76,7 @@ struct sb_plan_s {
     int ms = 0;
     float* k = nullptr;      // [nb][N]
     float* invk = nullptr;   // [nb][N]
+    float* jw = nullptr;     // [nb][N] 1 / diag(A) (Jacobi)
     float2 *r = nullptr, *p = nullptr, *q = nullptr, *tb = nullptr;
     float2* bx[2] = {nullptr, nullptr};
     float2* by[2] = {nullptr, nullptr};
@@ -202,14 +204,21 @@ void dfree(void* p) {
     if (p) cudaFree(p);
 }
 
-// tw[r * 16 + j] = exp(-2 pi i r j / n), r < n/16, j < 16 (stage-2 twiddles of fft_2stage)
+// Twiddle tables of the register-resident transforms (common.cuh), computed in double:
+// n <= 256: tw[r * 16 + j] = exp(-2 pi i r j / n), r < n/16, j < 16 (the second stage);
+// n = 512: tw[r * 16 + k] = exp(-2 pi i r k / 256) (second stage), tw[256 + k] =
+// exp(-2 pi i k / 512), k < 256 (third stage).
 std::vector<float2> twiddles(int n) {
     std::vector<float2> t(n);
-    for (int r = 0; r < n / 16; ++r)
-        for (int j = 0; j < 16; ++j) {
-            const double a = -2.0 * M_PI * (double)r * j / n;
-            t[r * 16 + j] = make_float2((float)std::cos(a), (float)std::sin(a));
-        }
+    auto w = [](double num, double den) {
+        const double a = -2.0 * M_PI * num / den;
+        return make_float2((float)std::cos(a), (float)std::sin(a));
+    };
+    const int m = n <= 256 ? n : 256;
+    for (int r = 0; r < m / 16; ++r)
+        for (int j = 0; j < 16; ++j) t[r * 16 + j] = w((double)r * j, m);
+    if (n > 256)
+        for (int k = 0; k < 256; ++k) t[256 + k] = w(k, n);
     return t;
 }
 
@@ -232,7 +241,7 @@ EncodeTiledFn tensor_map_encoder() {
 }
 
 // float32 view [rows][2 nx] of complex rows starting at base; box = box_rows x one column tile
-bool encode_rows(CUtensorMap* m, const void* base, int nx, size_t rows, int box_rows) {
+bool encode_rows(CUtensorMap* m, const void* base, int nx, size_t rows, int box_rows, bool swizzle = false) {
     auto encode = tensor_map_encoder();
     if (!encode) return false;
     const cuuint64_t gdim[2] = {(cuuint64_t)2 * nx, (cuuint64_t)rows};
@@ -240,8 +249,8 @@ bool encode_rows(CUtensorMap* m, const void* base, int nx, size_t rows, int box_
     const cuuint32_t box[2] = {(cuuint32_t)2 * kColTile, (cuuint32_t)box_rows};
     const cuuint32_t estride[2] = {1, 1};
     return encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), gdim, gstride, box, estride,
-                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 void bind_exec(sb_plan pl, Exec& ex, int b0, int nb, cudaStream_t s) {
@@ -271,6 +280,7 @@ sb_status pcg_run(Exec& ex, const sb_pcg_opts& o, float2* x_full, sb_pcg_result*
     const bool fixed = o.fixed_iters > 0;
     const double tol2 = fixed ? -1.0 : o.tol * o.tol;
     const bool circ = o.precond == SB_PRECOND_CIRCULANT;
+    const float* w = o.precond == SB_PRECOND_JACOBI ? at(pl->jw, ex, n) : nullptr;
     const Red red = ex.red;
     const float mu = (float)pl->d.mu, lam = (float)pl->d.lambda, gam = (float)pl->d.gamma;
     float2* x = at(x_full, ex, n);
@@ -284,7 +294,7 @@ sb_status pcg_run(Exec& ex, const sb_pcg_opts& o, float2* x_full, sb_pcg_result*
         SB_LAUNCH(ex, SB_KCLASS_PRECOND_COL, 1, launch_col_precond(d, tb, invk, pl->tw_y, ex.st, 1, red, s));
         SB_LAUNCH(ex, SB_KCLASS_PRECOND_ROW_INV, 1, launch_row_inv(d, 1, tb, nullptr, x, p, pl->tw_x, ex.st, red, s));
     } else {
-        SB_LAUNCH(ex, SB_KCLASS_VEC, 1, launch_vec_plain(d, 0, x, r, p, nullptr, ex.st, tol2, red, s));
+        SB_LAUNCH(ex, SB_KCLASS_VEC, 1, launch_vec_plain(d, 0, x, r, p, nullptr, w, ex.st, tol2, red, s));
     }
     const int nit = fixed ? o.fixed_iters : o.maxit;
     int it = 0;
@@ -292,14 +302,14 @@ sb_status pcg_run(Exec& ex, const sb_pcg_opts& o, float2* x_full, sb_pcg_result*
         const int g = std::min(kPollEvery, nit - it);
         for (int i = 0; i < g; ++i) {
             SB_LAUNCH(ex, SB_KCLASS_APPLY_A, 1,
-                      launch_apply_A(d, ex.smap, p, q, maskw, pl->tw_y, mu, lam, gam, ex.st, red, s));
+                      launch_apply_A(d, ex.smap_sw, p, q, maskw, pl->tw_y, mu, lam, gam, ex.st, red, s));
             if (circ) {
                 SB_LAUNCH(ex, SB_KCLASS_PRECOND_ROW_FWD, 1, launch_row_fwd(d, 1, r, q, tb, pl->tw_x, ex.st, tol2, red, s));
                 SB_LAUNCH(ex, SB_KCLASS_PRECOND_COL, 1, launch_col_precond(d, tb, invk, pl->tw_y, ex.st, 0, red, s));
                 SB_LAUNCH(ex, SB_KCLASS_PRECOND_ROW_INV, 1, launch_row_inv(d, 2, tb, nullptr, x, p, pl->tw_x, ex.st, red, s));
             } else {
-                SB_LAUNCH(ex, SB_KCLASS_VEC, 1, launch_vec_plain(d, 1, x, r, p, q, ex.st, tol2, red, s));
-                SB_LAUNCH(ex, SB_KCLASS_VEC, 1, launch_vec_plain(d, 2, x, r, p, q, ex.st, tol2, red, s));
+                SB_LAUNCH(ex, SB_KCLASS_VEC, 1, launch_vec_plain(d, 1, x, r, p, q, w, ex.st, tol2, red, s));
+                SB_LAUNCH(ex, SB_KCLASS_VEC, 1, launch_vec_plain(d, 2, x, r, p, q, w, ex.st, tol2, red, s));
             }
         }
         it += g;
@@ -347,7 +357,7 @@ sb_status check_opts(sb_plan pl, const sb_pcg_opts* o) {
     if (!o) return fail(pl, SB_ERR_INVALID_ARG, "null PCG options");
     if (o->fixed_iters < 0 || (o->fixed_iters == 0 && (o->maxit < 1 || !(o->tol >= 0.0))))
         return fail(pl, SB_ERR_INVALID_ARG, "PCG options: need fixed_iters > 0, or maxit >= 1 and tol >= 0");
-    if (o->precond != SB_PRECOND_CIRCULANT && o->precond != SB_PRECOND_NONE)
+    if (o->precond != SB_PRECOND_CIRCULANT && o->precond != SB_PRECOND_NONE && o->precond != SB_PRECOND_JACOBI)
         return fail(pl, SB_ERR_UNSUPPORTED, "preconditioner kind not implemented");
     return SB_OK;
 }
@@ -486,7 +496,7 @@ sb_status sb_plan_create(const sb_plan_desc* desc, void* cuda_stream, sb_plan* o
     if (d.ndim != 2 || (d.nz != 1 && d.nz != 0) || d.ncoils < 1 || d.nbatch < 1 || !(d.mu > 0.0) ||
         !(d.lambda >= 0.0) || !(d.gamma >= 0.0) || d.wavelet_levels < 0 || d.groups < 0)
         return SB_ERR_INVALID_ARG;
-    if (!supported_n(d.nx) || !supported_n(d.ny) || d.wavelet_levels > 4 || d.prec != SB_PREC_FP32)
+    if (!supported_n(d.nx) || !supported_n(d.ny) || d.wavelet_levels > 5 || d.prec != SB_PREC_FP32)
         return SB_ERR_UNSUPPORTED;
     sb_plan pl = new (std::nothrow) sb_plan_s();
     if (!pl) return SB_ERR_INVALID_ARG;
@@ -565,7 +575,7 @@ sb_status sb_plan_destroy(sb_plan pl) {
                     (void*)pl->bx[0], (void*)pl->bx[1], (void*)pl->by[0], (void*)pl->by[1], (void*)pl->bw,
                     (void*)pl->g, (void*)pl->bd, (void*)pl->bd1, (void*)pl->yt, (void*)pl->yt1, (void*)pl->st,
                     (void*)pl->part, (void*)pl->counter, (void*)pl->kmax, (void*)pl->derr, (void*)pl->spec,
-                    (void*)pl->gb, (void*)pl->rb, (void*)pl->line_val, (void*)pl->line_uni})
+                    (void*)pl->gb, (void*)pl->rb, (void*)pl->line_val, (void*)pl->line_uni, (void*)pl->jw})
         dfree(p);
     if (pl->h_st) cudaFreeHost(pl->h_st);
     auto release = [](Exec& ex) {
@@ -594,8 +604,10 @@ sb_status sb_set_coils(sb_plan pl, const void* d_sens) {
     const Dims& d = pl->dims;
     const size_t per = (size_t)d.nc * pl->n;
     auto enc = [&](Exec& ex) {
-        return encode_rows(&ex.smap, static_cast<const float2*>(d_sens) + (size_t)ex.b0 * per, d.nx,
-                           (size_t)ex.d.nb * d.nc * d.ny, d.ny);
+        const float2* base = static_cast<const float2*>(d_sens) + (size_t)ex.b0 * per;
+        const size_t rows = (size_t)ex.d.nb * d.nc * d.ny;
+        const int box = std::min(d.ny, 256);  // a TMA box spans at most 256 rows
+        return encode_rows(&ex.smap, base, d.nx, rows, box) && encode_rows(&ex.smap_sw, base, d.nx, rows, box, true);
     };
     bool ok = enc(pl->whole);
     for (Exec& ex : pl->groups) ok = ok && enc(ex);
@@ -620,6 +632,7 @@ sb_status sb_set_mask(sb_plan pl, const uint8_t* d_mask) {
         SB_CK(pl, dalloc(&pl->spec, nb * d.nc * n));
         SB_CK(pl, dalloc(&pl->gb, nb * n));
         SB_CK(pl, dalloc(&pl->rb, nb * n));
+        SB_CK(pl, dalloc(&pl->jw, nb * n));
     }
     // 1. line structure of the mask
     int *lv = pl->line_val, *lu = pl->line_uni;
@@ -681,6 +694,9 @@ sb_status sb_set_mask(sb_plan pl, const uint8_t* d_mask) {
         SB_LAUNCH(ex, SB_KCLASS_OTHER, 2,
                   launch_finish_k(d, rb, (float)pl->d.mu, (float)pl->d.lambda, (float)pl->d.gamma, pl->k, pl->invk,
                                   pl->kmax, s));
+        SB_LAUNCH(ex, SB_KCLASS_OTHER, 1,
+                  launch_jacobi_diag(d, pl->sens, pl->maskw, (float)pl->d.mu, (float)pl->d.lambda, (float)pl->d.gamma,
+                                     pl->jw, s));
         return SB_OK;
     };
     if ((st = build_k()) != SB_OK) return fail(pl, st, ex.err);
@@ -700,6 +716,7 @@ sb_status sb_set_mask(sb_plan pl, const uint8_t* d_mask) {
     const size_t yrow = (size_t)d.nc * ms * d.nx;
     auto enc = [&](Exec& e2) {
         const size_t rows = (size_t)e2.d.nb * d.nc * ms;
+        if (ms > 256) return true;  // no compact-row maps: sb_split_bregman refuses this mask
         return encode_rows(&e2.ymap, pl->yt + e2.b0 * yrow, d.nx, rows, ms) &&
                encode_rows(&e2.y1map, pl->yt1 + e2.b0 * yrow, d.nx, rows, ms);
     };
@@ -733,7 +750,7 @@ sb_status sb_apply_A(sb_plan pl, const void* d_x, void* d_y) {
     Exec& ex = pl->whole;
     auto go = [&]() -> sb_status {
         SB_LAUNCH(ex, SB_KCLASS_APPLY_A, 1,
-                  launch_apply_A(pl->dims, ex.smap, static_cast<const float2*>(d_x), static_cast<float2*>(d_y),
+                  launch_apply_A(pl->dims, ex.smap_sw, static_cast<const float2*>(d_x), static_cast<float2*>(d_y),
                                  pl->maskw, pl->tw_y, (float)pl->d.mu, (float)pl->d.lambda, (float)pl->d.gamma,
                                  nullptr, ex.red, pl->stream));
         return SB_OK;
@@ -774,7 +791,7 @@ sb_status sb_pcg_solve(sb_plan pl, const void* d_b, void* d_x, const sb_pcg_opts
         float2* x = at(x_full, ex, n);
         float2* q = at(pl->q, ex, n);
         SB_LAUNCH(ex, SB_KCLASS_APPLY_A, 1,
-                  launch_apply_A(ex.d, ex.smap, x, q, at(pl->maskw, ex, (size_t)ex.d.ny), pl->tw_y, (float)pl->d.mu,
+                  launch_apply_A(ex.d, ex.smap_sw, x, q, at(pl->maskw, ex, (size_t)ex.d.ny), pl->tw_y, (float)pl->d.mu,
                                  (float)pl->d.lambda, (float)pl->d.gamma, nullptr, ex.red, ex.s));
         SB_LAUNCH(ex, SB_KCLASS_VEC, 1,
                   launch_resid_init(ex.d, at(b_full, ex, n), q, at(pl->r, ex, n), ex.st, tol2, ex.red, ex.s));
@@ -787,7 +804,7 @@ sb_status sb_split_bregman(sb_plan pl, const void* d_y, void* d_x, const sb_sb_o
     if (!o || !d_y || !d_x) return fail(pl, SB_ERR_INVALID_ARG, "null argument");
     if (o->n_outer < 1 || o->n_inner < 1) return fail(pl, SB_ERR_INVALID_ARG, "n_outer and n_inner must be >= 1");
     if (sb_status s = check_opts(pl, &o->pcg)) return s;
-    if (rhs_smem_bytes(pl->dims.ny, pl->ms) > 227 * 1024)
+    if (pl->ms > 256 || rhs_smem_bytes(pl->dims.ny, pl->ms) > 227 * 1024)
         return fail(pl, SB_ERR_UNSUPPORTED, "too many sampled lines for the shared-memory pipeline of this size");
     const int nsolve = o->n_outer * o->n_inner;
     std::vector<int> iters((size_t)pl->dims.nb * nsolve, 0);

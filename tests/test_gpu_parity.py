@@ -27,6 +27,15 @@ def sbm(torch):
     return sb
 
 
+def oracle_M(kind, sens, mask, mu, lam, gam, k):
+    if kind == "circulant":
+        return lambda v: precond.apply_precond(v, k, 2)
+    if kind == "jacobi":
+        jd = precond.jacobi_diag(sens, mask, mu, lam, gam, 2)
+        return lambda v: v / jd
+    return None
+
+
 def rel(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
@@ -54,7 +63,8 @@ def make_plan(sbm, torch, sens, mask, mu, lam, gam, levels=0):
     return plan
 
 
-SHAPES = [(32, 64, 3, 2), (64, 32, 2, 3), (128, 128, 4, 1), (256, 256, 12, 1), (256, 128, 5, 2)]
+SHAPES = [(32, 64, 3, 2), (64, 32, 2, 3), (128, 128, 4, 1), (256, 256, 12, 1), (256, 128, 5, 2),
+          (512, 512, 32, 1), (512, 128, 3, 2)]
 
 
 @pytest.mark.parametrize("nx,ny,nc,nb", SHAPES)
@@ -104,7 +114,7 @@ def test_precond_in_place_and_edge_masks(torch, sbm):
         assert rel(q[b], operators.apply_A(x[b], sens[b], mask[b], 1.0, 0.1, 0.02, 2)) <= OP_TOL
 
 
-@pytest.mark.parametrize("kind", ["circulant", "none"])
+@pytest.mark.parametrize("kind", ["circulant", "none", "jacobi"])
 def test_pcg_fixed_iterations(torch, sbm, kind):
     nx, ny, nc, nb = 128, 128, 4, 2
     sens, mask, rng = problem(nx, ny, nc, nb, seed=21)
@@ -113,19 +123,19 @@ def test_pcg_fixed_iterations(torch, sbm, kind):
     b = synth.random_complex((nb, ny, nx), rng)
     x0 = synth.random_complex((nb, ny, nx), rng) * 0.1
     xd = to_dev(torch, x0)
-    pc = sbm.SB_PRECOND_CIRCULANT if kind == "circulant" else sbm.SB_PRECOND_NONE
+    pc = {"circulant": sbm.SB_PRECOND_CIRCULANT, "none": sbm.SB_PRECOND_NONE, "jacobi": sbm.SB_PRECOND_JACOBI}[kind]
     st, res = plan.pcg_solve(to_dev(torch, b), xd, fixed_iters=12, precond=pc)
     assert st == sbm.SB_OK and all(r[0] == 12 for r in res)
     xg = xd.cpu().numpy()
     for i in range(nb):
         A = lambda v: operators.apply_A(v, sens[i], mask[i], mu, lam, gam, 2)  # noqa: E731
         k = precond.k_diag(sens[i], mask[i], mu, lam, gam, 2)
-        M = (lambda v: precond.apply_precond(v, k, 2)) if kind == "circulant" else None
+        M = oracle_M(kind, sens[i], mask[i], mu, lam, gam, k)
         ref = pcg.pcg(A, b[i], x0[i], M, fixed_iters=12)
         assert rel(xg[i], ref.x) <= IMG_TOL
 
 
-@pytest.mark.parametrize("kind", ["circulant", "none"])
+@pytest.mark.parametrize("kind", ["circulant", "none", "jacobi"])
 def test_pcg_tolerance_iteration_counts(torch, sbm, kind):
     nx, ny, nc, nb = 256, 256, 8, 2
     sens, mask, rng = problem(nx, ny, nc, nb, seed=33, n_centre=16)
@@ -133,14 +143,14 @@ def test_pcg_tolerance_iteration_counts(torch, sbm, kind):
     plan = make_plan(sbm, torch, sens, mask, mu, lam, gam)
     b = synth.random_complex((nb, ny, nx), rng)
     xd = torch.zeros((nb, ny, nx), dtype=torch.complex64, device="cuda")
-    pc = sbm.SB_PRECOND_CIRCULANT if kind == "circulant" else sbm.SB_PRECOND_NONE
+    pc = {"circulant": sbm.SB_PRECOND_CIRCULANT, "none": sbm.SB_PRECOND_NONE, "jacobi": sbm.SB_PRECOND_JACOBI}[kind]
     st, res = plan.pcg_solve(to_dev(torch, b), xd, tol=1e-3, maxit=300, precond=pc)
     assert st == sbm.SB_OK
     xg = xd.cpu().numpy()
     for i in range(nb):
         A = lambda v: operators.apply_A(v, sens[i], mask[i], mu, lam, gam, 2)  # noqa: E731
         k = precond.k_diag(sens[i], mask[i], mu, lam, gam, 2)
-        M = (lambda v: precond.apply_precond(v, k, 2)) if kind == "circulant" else None
+        M = oracle_M(kind, sens[i], mask[i], mu, lam, gam, k)
         ref = pcg.pcg(A, b[i], np.zeros((ny, nx), complex), M, tol=1e-3, maxit=300)
         assert abs(res[i][0] - ref.iters) <= 1, (res[i], ref.iters)
         assert res[i][1] <= 1e-3 and res[i][2]
@@ -242,6 +252,9 @@ def test_unsupported_inputs(torch, sbm):
     with pytest.raises(sbm.SbError) as ei:
         sbm.Plan(48, 64, 2, 1, 1.0, 0.1, 0.1, 0)
     assert ei.value.status == sbm.SB_ERR_UNSUPPORTED
+    with pytest.raises(sbm.SbError) as ei:  # Haar blocks larger than the update tiles
+        sbm.Plan(64, 64, 2, 1, 1.0, 0.1, 0.1, 6)
+    assert ei.value.status == sbm.SB_ERR_UNSUPPORTED
     nx = ny = 32
     sens, mask, rng = problem(nx, ny, 2, 1, seed=1)
     plan = sbm.Plan(nx, ny, 2, 1, 1.0, 0.1, 0.1, 0)
@@ -254,3 +267,52 @@ def test_unsupported_inputs(torch, sbm):
     with pytest.raises(sbm.SbError) as ei:  # k was not built: operators refuse
         plan.apply_A(to_dev(torch, np.zeros((1, ny, nx), complex)))
     assert ei.value.status == sbm.SB_ERR_NOT_READY
+
+
+def test_parameter_sets_preconditioner_comparison(torch, sbm):
+    # The comparison of the Results on synthetic data: for the paper's parameter sets 1-3 the
+    # circulant preconditioner needs fewer PCG iterations than plain CG, and Jacobi needs the
+    # same number as plain CG (normalised coils make diag(A) constant).  GPU counts match the
+    # oracle's within one iteration.
+    nx = ny = 128
+    nb, nc = 2, 8
+    sens, mask, rng = problem(nx, ny, nc, nb, seed=404, n_centre=12)
+    b = synth.random_complex((nb, ny, nx), rng)
+    sets = [(1e-3, 4e-3, 1e-3), (1e-2, 4e-3, 1e-3), (1e-3, 4e-3, 4e-3)]
+    for mu, lam, gam in sets:
+        plan = make_plan(sbm, torch, sens, mask, mu, lam, gam)
+        counts = {}
+        for kind, pc in [("circulant", sbm.SB_PRECOND_CIRCULANT), ("none", sbm.SB_PRECOND_NONE),
+                         ("jacobi", sbm.SB_PRECOND_JACOBI)]:
+            xd = torch.zeros((nb, ny, nx), dtype=torch.complex64, device="cuda")
+            st, res = plan.pcg_solve(to_dev(torch, b), xd, tol=1e-3, maxit=500, precond=pc)
+            assert st == sbm.SB_OK
+            counts[kind] = [r[0] for r in res]
+            for i in range(nb):
+                A = lambda v: operators.apply_A(v, sens[i], mask[i], mu, lam, gam, 2)  # noqa: E731
+                k = precond.k_diag(sens[i], mask[i], mu, lam, gam, 2)
+                ref = pcg.pcg(A, b[i], np.zeros((ny, nx), complex), oracle_M(kind, sens[i], mask[i], mu, lam, gam, k),
+                              tol=1e-3, maxit=500)
+                assert abs(res[i][0] - ref.iters) <= 1, (mu, lam, gam, kind, res[i][0], ref.iters)
+        for i in range(nb):
+            assert counts["circulant"][i] < counts["none"][i]
+            assert abs(counts["jacobi"][i] - counts["none"][i]) <= 1
+        plan.close()
+
+
+def test_split_bregman_512_variable_density(torch, sbm):
+    # 512x512 (three-stage transforms), R = 6 variable-density lines with 32 centre lines,
+    # TV + 4-level Haar, fixed schedule against the oracle
+    wl = synth.Workload("512x512 Nc6 R6 vd TV+Haar4", 512, 512, 6, 6.0, 32, "variable", 1.0, 0.05, 0.05, 4, 3, 1,
+                        1e-3, 100, 0, seed=synth.SEED_BASE + 3)
+    xg, refs, _ = run_sb_both(torch, sbm, wl, 1, wl.seed, tau=0.02, fixed=6)
+    assert rel(xg[0], refs[0].x) <= IMG_TOL
+
+
+def test_split_bregman_five_haar_levels(torch, sbm):
+    # the deepest Haar tree the 32 x 32 update tiles hold (5 levels), active shrinkage
+    wl = synth.Workload("64x64 Nc4 TV+Haar5", 64, 64, 4, 4.0, 8, "uniform", 1.0, 0.05, 0.05, 5, 4, 1,
+                        1e-3, 100, 0, seed=29)
+    xg, refs, _ = run_sb_both(torch, sbm, wl, 2, wl.seed, tau=0.02, fixed=10)
+    for b in range(2):
+        assert rel(xg[b], refs[b].x) <= IMG_TOL
