@@ -65,6 +65,16 @@ typedef struct {
                                host thread, so that one group's work fills the GPU while another
                                waits on its convergence test; 0 = automatic (nbatch / 8, at most
                                4, at least 1); clamped to [1, nbatch] */
+    int precond_passes;     /* schedule of the circulant M^{-1} inside PCG: 1 = one launch per
+                               iteration, each slice on one thread-block cluster that exchanges
+                               the 2D spectrum through distributed shared memory (needs
+                               nx * ny <= 65536 and nx, ny <= 256, else SB_ERR_UNSUPPORTED at
+                               create); 3 = three launches (DFT along x, DFT along y with k^{-1}
+                               and its inverse, inverse DFT along x) through an HBM buffer;
+                               0 = automatic (3: on a 64-slice 256 x 256 batch the cluster
+                               launch took 151 us against 92 us for the three passes, as too
+                               few 8-CTA clusters are resident at once).  Both give the same
+                               iterates up to rounding order. */
 } sb_plan_desc;
 
 typedef struct sb_plan_s* sb_plan;
@@ -180,7 +190,9 @@ typedef enum {
     SB_KCLASS_SB_UPDATE = 5,     /* shrink, Bregman updates, Haar analysis / synthesis */
     SB_KCLASS_VEC = 6,           /* preconditioner-free CG vector updates */
     SB_KCLASS_OTHER = 7,         /* set-up: k construction, mask analysis, y transform, RSS */
-    SB_KCLASS_COUNT = 8
+    SB_KCLASS_PRECOND_FUSED = 8, /* whole M^{-1} step in one cluster launch per slice: r, x, p
+                                    updates, 2D DFT, k^{-1}, inverse 2D DFT, r^H z */
+    SB_KCLASS_COUNT = 9
 } sb_kernel_class;
 
 /* Event timer (instrumentation).  With bit c of class_mask set, the plan records a CUDA event

@@ -74,6 +74,17 @@ cudaError_t launch_row_inv(const Dims& d, int mode, const float2* t, float2* out
 // CG with a diagonal preconditioner z = w r (w == nullptr: w = 1, plain CG; else w = 1 / diag(A),
 // Jacobi): mode 0 (init): p = z, rho = r^H z; mode 1 (step, after q = A p): r -= alpha q,
 // ||r||^2 test, beta = r^H z / rho; mode 2 (step): x += alpha p, p = z + beta p.
+// The whole circulant M^{-1} step of PCG in one cluster launch per slice (k_precond_fused.cu):
+// mode 0 (init): p = z = M^{-1} r, rho = r^H z; mode 1 (step, after q = A p): r -= alpha q,
+// ||r||^2 test (converged: x += alpha p, done), z = M^{-1} r, beta, x += alpha p, p = z + beta p.
+// nx, ny in {32, 64, 128, 256}.
+bool precond_fused_shape_ok(const Dims& d);
+// clusters of the fused kernel that fit on the device at once (0: cannot run)
+int precond_fused_clusters(const Dims& d);
+cudaError_t launch_precond_fused(const Dims& d, int mode, float2* x, float2* r, float2* p, const float2* q,
+                                 const float* invk, const float2* tw_x, const float2* tw_y, SliceState* st,
+                                 double tol2, cudaStream_t s);
+
 cudaError_t launch_vec_plain(const Dims& d, int mode, float2* x, float2* r, float2* p,
                              const float2* q, const float* w, SliceState* st, double tol2, Red red,
                              cudaStream_t s);

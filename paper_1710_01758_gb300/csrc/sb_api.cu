@@ -66,6 +66,7 @@ struct sb_plan_s {
     size_t n = 0;  // pixels per slice
     const float2* sens = nullptr;
     bool have_coils = false, have_mask = false;
+    bool fused_precond = false;  // circulant M^{-1} as one cluster launch per PCG iteration
     std::string err;
 
     float2* tw_x = nullptr;
@@ -289,7 +290,11 @@ sb_status pcg_run(Exec& ex, const sb_pcg_opts& o, float2* x_full, sb_pcg_result*
     const float* maskw = at(pl->maskw, ex, (size_t)d.ny);
 
     SB_LAUNCH(ex, SB_KCLASS_VEC, 1, launch_zero_rhs_slices(d, x, ex.st, s));
-    if (circ) {
+    const bool fused = circ && pl->fused_precond;
+    if (fused) {
+        SB_LAUNCH(ex, SB_KCLASS_PRECOND_FUSED, 1,
+                  launch_precond_fused(d, 0, x, r, p, nullptr, invk, pl->tw_x, pl->tw_y, ex.st, tol2, s));
+    } else if (circ) {
         SB_LAUNCH(ex, SB_KCLASS_PRECOND_ROW_FWD, 1, launch_row_fwd(d, 0, r, nullptr, tb, pl->tw_x, ex.st, tol2, red, s));
         SB_LAUNCH(ex, SB_KCLASS_PRECOND_COL, 1, launch_col_precond(d, tb, invk, pl->tw_y, ex.st, 1, red, s));
         SB_LAUNCH(ex, SB_KCLASS_PRECOND_ROW_INV, 1, launch_row_inv(d, 1, tb, nullptr, x, p, pl->tw_x, ex.st, red, s));
@@ -303,7 +308,10 @@ sb_status pcg_run(Exec& ex, const sb_pcg_opts& o, float2* x_full, sb_pcg_result*
         for (int i = 0; i < g; ++i) {
             SB_LAUNCH(ex, SB_KCLASS_APPLY_A, 1,
                       launch_apply_A(d, ex.smap_sw, p, q, maskw, pl->tw_y, mu, lam, gam, ex.st, red, s));
-            if (circ) {
+            if (fused) {
+                SB_LAUNCH(ex, SB_KCLASS_PRECOND_FUSED, 1,
+                          launch_precond_fused(d, 1, x, r, p, q, invk, pl->tw_x, pl->tw_y, ex.st, tol2, s));
+            } else if (circ) {
                 SB_LAUNCH(ex, SB_KCLASS_PRECOND_ROW_FWD, 1, launch_row_fwd(d, 1, r, q, tb, pl->tw_x, ex.st, tol2, red, s));
                 SB_LAUNCH(ex, SB_KCLASS_PRECOND_COL, 1, launch_col_precond(d, tb, invk, pl->tw_y, ex.st, 0, red, s));
                 SB_LAUNCH(ex, SB_KCLASS_PRECOND_ROW_INV, 1, launch_row_inv(d, 2, tb, nullptr, x, p, pl->tw_x, ex.st, red, s));
@@ -494,13 +502,21 @@ sb_status sb_plan_create(const sb_plan_desc* desc, void* cuda_stream, sb_plan* o
     *out = nullptr;
     const sb_plan_desc& d = *desc;
     if (d.ndim != 2 || (d.nz != 1 && d.nz != 0) || d.ncoils < 1 || d.nbatch < 1 || !(d.mu > 0.0) ||
-        !(d.lambda >= 0.0) || !(d.gamma >= 0.0) || d.wavelet_levels < 0 || d.groups < 0)
+        !(d.lambda >= 0.0) || !(d.gamma >= 0.0) || d.wavelet_levels < 0 || d.groups < 0 ||
+        (d.precond_passes != 0 && d.precond_passes != 1 && d.precond_passes != 3))
         return SB_ERR_INVALID_ARG;
     if (!supported_n(d.nx) || !supported_n(d.ny) || d.wavelet_levels > 5 || d.prec != SB_PREC_FP32)
         return SB_ERR_UNSUPPORTED;
+    // the fused preconditioner (opt-in) needs a slice on one cluster that fits the device
+    bool fused = false;
+    if (d.precond_passes == 1) {
+        fused = precond_fused_clusters(Dims{d.nx, d.ny, d.ncoils, d.nbatch}) > 0;
+        if (!fused) return SB_ERR_UNSUPPORTED;
+    }
     sb_plan pl = new (std::nothrow) sb_plan_s();
     if (!pl) return SB_ERR_INVALID_ARG;
     pl->d = d;
+    pl->fused_precond = fused;
     pl->d.nz = 1;
     pl->stream = static_cast<cudaStream_t>(cuda_stream);
     pl->dims = Dims{d.nx, d.ny, d.ncoils, d.nbatch};

@@ -37,7 +37,7 @@ class sb_plan_desc(ctypes.Structure):
     _fields_ = [("ndim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
                 ("ncoils", ctypes.c_int), ("nbatch", ctypes.c_int), ("mu", ctypes.c_double),
                 ("lambda_", ctypes.c_double), ("gamma", ctypes.c_double), ("wavelet_levels", ctypes.c_int),
-                ("prec", ctypes.c_int), ("groups", ctypes.c_int)]
+                ("prec", ctypes.c_int), ("groups", ctypes.c_int), ("precond_passes", ctypes.c_int)]
 
 
 class sb_pcg_opts(ctypes.Structure):
@@ -85,9 +85,10 @@ SB_KCLASS_RHS = 4
 SB_KCLASS_SB_UPDATE = 5
 SB_KCLASS_VEC = 6
 SB_KCLASS_OTHER = 7
-SB_KCLASS_COUNT = 8
+SB_KCLASS_PRECOND_FUSED = 8
+SB_KCLASS_COUNT = 9
 KCLASS_NAMES = ["apply_A", "precond_row_fwd", "precond_col", "precond_row_inv", "rhs", "sb_update", "vec",
-                "other"]
+                "other", "precond_fused"]
 
 
 def load(path: str = LIB_PATH) -> ctypes.CDLL:
@@ -126,8 +127,9 @@ def _check(status: int, plan=None, allow=()):
     return status
 
 
-def plan_desc(nx, ny, ncoils, nbatch, mu, lam, gam, wavelet_levels, prec=SB_PREC_FP32, groups=0) -> sb_plan_desc:
-    return sb_plan_desc(2, nx, ny, 1, ncoils, nbatch, mu, lam, gam, wavelet_levels, prec, groups)
+def plan_desc(nx, ny, ncoils, nbatch, mu, lam, gam, wavelet_levels, prec=SB_PREC_FP32, groups=0,
+              precond_passes=0) -> sb_plan_desc:
+    return sb_plan_desc(2, nx, ny, 1, ncoils, nbatch, mu, lam, gam, wavelet_levels, prec, groups, precond_passes)
 
 
 def sb_plan_create(desc: sb_plan_desc, stream: int = 0) -> int:
@@ -205,14 +207,16 @@ def sb_plan_get_timing(plan: int, kernel_class: int):
 class Plan:
     """Owns an sb_plan and the device tensors it borrows (torch CUDA tensors)."""
 
-    def __init__(self, nx, ny, ncoils, nbatch, mu, lam, gam, wavelet_levels, stream=None, groups=0):
+    def __init__(self, nx, ny, ncoils, nbatch, mu, lam, gam, wavelet_levels, stream=None, groups=0,
+                 precond_passes=0):
         import torch
         self.torch = torch
         self.nbatch = nbatch
         self.shape = (nbatch, ny, nx)
         s = stream if stream is not None else torch.cuda.current_stream()
         self.stream = s
-        self.handle = sb_plan_create(plan_desc(nx, ny, ncoils, nbatch, mu, lam, gam, wavelet_levels, groups=groups),
+        self.handle = sb_plan_create(plan_desc(nx, ny, ncoils, nbatch, mu, lam, gam, wavelet_levels, groups=groups,
+                                                       precond_passes=precond_passes),
                                      s.cuda_stream)
         self._sens = None
 

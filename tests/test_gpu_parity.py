@@ -54,9 +54,9 @@ def problem(nx, ny, nc, nb, seed, accel=4.0, n_centre=4):
     return sens, mask, rng
 
 
-def make_plan(sbm, torch, sens, mask, mu, lam, gam, levels=0):
+def make_plan(sbm, torch, sens, mask, mu, lam, gam, levels=0, passes=0):
     nb, nc, ny, nx = sens.shape
-    plan = sbm.Plan(nx, ny, nc, nb, mu, lam, gam, levels)
+    plan = sbm.Plan(nx, ny, nc, nb, mu, lam, gam, levels, precond_passes=passes)
     s_dev = to_dev(torch, sens)
     plan.set_coils(s_dev)
     plan.set_mask(torch.from_numpy(mask).cuda())
@@ -255,6 +255,12 @@ def test_unsupported_inputs(torch, sbm):
     with pytest.raises(sbm.SbError) as ei:  # Haar blocks larger than the update tiles
         sbm.Plan(64, 64, 2, 1, 1.0, 0.1, 0.1, 6)
     assert ei.value.status == sbm.SB_ERR_UNSUPPORTED
+    with pytest.raises(sbm.SbError) as ei:  # a 512 x 512 slice does not fit one cluster
+        sbm.Plan(512, 512, 2, 1, 1.0, 0.1, 0.1, 0, precond_passes=1)
+    assert ei.value.status == sbm.SB_ERR_UNSUPPORTED
+    with pytest.raises(sbm.SbError) as ei:
+        sbm.Plan(64, 64, 2, 1, 1.0, 0.1, 0.1, 0, precond_passes=2)
+    assert ei.value.status == sbm.SB_ERR_INVALID_ARG
     nx = ny = 32
     sens, mask, rng = problem(nx, ny, 2, 1, seed=1)
     plan = sbm.Plan(nx, ny, 2, 1, 1.0, 0.1, 0.1, 0)
@@ -316,3 +322,33 @@ def test_split_bregman_five_haar_levels(torch, sbm):
     xg, refs, _ = run_sb_both(torch, sbm, wl, 2, wl.seed, tau=0.02, fixed=10)
     for b in range(2):
         assert rel(xg[b], refs[b].x) <= IMG_TOL
+
+
+@pytest.mark.parametrize("nx,ny,nc,nb", [(256, 256, 6, 3), (128, 256, 3, 2), (256, 64, 2, 2), (32, 32, 2, 2),
+                                         (128, 128, 4, 2)])
+@pytest.mark.parametrize("passes", [1, 3])
+def test_pcg_precond_schedules(torch, sbm, nx, ny, nc, nb, passes):
+    # the circulant M^{-1} inside PCG as one cluster launch (1) or three HBM passes (3): both
+    # against the oracle, for a fixed count and to the tolerance
+    sens, mask, rng = problem(nx, ny, nc, nb, seed=nx + 3 * ny + nc, n_centre=8)
+    mu, lam, gam = 1.0, 0.05, 0.05
+    plan = make_plan(sbm, torch, sens, mask, mu, lam, gam, passes=passes)
+    b = synth.random_complex((nb, ny, nx), rng)
+    x0 = synth.random_complex((nb, ny, nx), rng) * 0.1
+    xd = to_dev(torch, x0)
+    st, res = plan.pcg_solve(to_dev(torch, b), xd, fixed_iters=9)
+    assert st == sbm.SB_OK and all(r[0] == 9 for r in res)
+    xt = to_dev(torch, x0)
+    st, rest = plan.pcg_solve(to_dev(torch, b), xt, tol=1e-4, maxit=200)
+    assert st == sbm.SB_OK
+    xg, xtg = xd.cpu().numpy(), xt.cpu().numpy()
+    for i in range(nb):
+        A = lambda v: operators.apply_A(v, sens[i], mask[i], mu, lam, gam, 2)  # noqa: E731
+        k = precond.k_diag(sens[i], mask[i], mu, lam, gam, 2)
+        M = lambda v: precond.apply_precond(v, k, 2)  # noqa: E731
+        ref = pcg.pcg(A, b[i], x0[i], M, fixed_iters=9)
+        assert rel(xg[i], ref.x) <= IMG_TOL
+        reft = pcg.pcg(A, b[i], x0[i], M, tol=1e-4, maxit=200)
+        assert abs(rest[i][0] - reft.iters) <= 1, (rest[i], reft.iters)
+        assert rest[i][1] <= 1e-4 and rest[i][2]
+        assert rel(xtg[i], reft.x) <= 1e-3
