@@ -72,9 +72,8 @@ typedef struct {
                                create); 3 = three launches (DFT along x, DFT along y with k^{-1}
                                and its inverse, inverse DFT along x) through an HBM buffer;
                                0 = automatic (3: on a 64-slice 256 x 256 batch the cluster
-                               launch took 151 us against 92 us for the three passes, as too
-                               few 8-CTA clusters are resident at once).  Both give the same
-                               iterates up to rounding order. */
+                               launch took 151 us against 92 us for the three passes).  Both
+                               give the same iterates up to rounding order. */
 } sb_plan_desc;
 
 typedef struct sb_plan_s* sb_plan;

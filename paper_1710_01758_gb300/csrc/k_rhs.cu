@@ -10,8 +10,9 @@
 // computes e = bd' - B(R F S x), so bd' = (e + bd + bd1) / 2 exactly, without a second
 // inverse transform per coil.  Then b = mu bd' + g, r = mu e + g - lambda D^H D x - gamma x,
 // with ||b||^2, ||r||^2 and the initial convergence test in the last CTA of the slice.  The
-// coil tile S_c and the compact rows of yt and yt1 arrive by TMA into a two-stage
-// shared-memory pipeline (coil c + 1 in flight while coil c is transformed).
+// coil tile S_c and the compact rows of yt and yt1 arrive by TMA into a shared-memory stage
+// (the load of coil c + 1 is issued as soon as coil c has left the stage; the second CTA on
+// the SM computes meanwhile).
 #include "common.cuh"
 #include "kernels.h"
 #include "tma.cuh"
@@ -26,12 +27,14 @@ struct ColIdx {
     __device__ __forceinline__ int operator()(int pos) const { return pos * TX + col; }
 };
 
-// pipeline stages: two up to ny = 256, one at ny = 512 (shared memory)
+// one pipeline stage: ~95 KB of shared memory at ny = 256 lets two CTAs share an SM, which
+// hides the coil-tile loads better than a second stage at one CTA per SM (measured: 125 us
+// against 173 us per 16-slice launch inside the benchmark)
 template <int NY>
-constexpr int kRhsStages = NY <= 256 ? 2 : 1;
+constexpr int kRhsStages = 1;
 
 template <int NY, bool ADDBACK>
-__global__ void __launch_bounds__(TX * NY / 16, 1)
+__global__ void __launch_bounds__(TX * NY / 16, NY <= 256 ? 2 : 1)
 k_rhs(const __grid_constant__ CUtensorMap smap, const __grid_constant__ CUtensorMap ymap,
       const __grid_constant__ CUtensorMap y1map, SbFields f, int nx, int nc, const float2* __restrict__ xin,
       float2* __restrict__ r, const float2* __restrict__ tw_g, float mu, float lam, float gam, SliceState* st,
@@ -189,7 +192,7 @@ cudaError_t rhs_n(const Dims& d, const CUtensorMap& smap, const CUtensorMap& yma
 }  // namespace
 
 size_t rhs_smem_bytes(int ny, int ms) {
-    const size_t nst = ny <= 256 ? 2 : 1;
+    const size_t nst = 1;
     return (nst * (size_t)(ny + 2 * ms) * TX + (size_t)ny * TX + 3 * (size_t)ny) * sizeof(float2) +
            ny * sizeof(int) + 64 * sizeof(double);
 }
