@@ -24,7 +24,8 @@
  *  - The mask must be constant along the readout (x) axis: Cartesian phase-encode line masks,
  *    the sampling of the paper's Methods ("Undersampling", random lines).  Other masks are
  *    rejected with SB_ERR_UNSUPPORTED.
- *  - Supported sizes: ndim = 2; nx, ny in {32, 64, 128, 256, 512}; ncoils >= 1; nbatch >= 1;
+ *  - Supported sizes: ndim = 2; nx, ny in {32, 64, 128, 192, 224, 256, 320, 384, 512}
+ *    (powers of two and 16 x {12, 14, 20, 24}, mixed-radix transforms); ncoils >= 1; nbatch >= 1;
  *    wavelet_levels in [0, 5] (Haar blocks stay inside the 32 x 32 update tiles).
  */
 #ifndef SB_H

@@ -238,11 +238,149 @@ __device__ __forceinline__ void fft_3stage_bar(float2 (&v)[16], int t, float2* b
     }
 }
 
-// Size dispatch: two stages up to N = 256, three for N = 512.
+// ------------------------------------------------------------------ lengths 16 x {12, 14, 20, 24}
+// cos and sin of 2 pi m / R for the odd radices (values of the functions, to float precision)
+template <int R> __host__ __device__ constexpr float cos_r(int m);
+template <int R> __host__ __device__ constexpr float sin_r(int m);
+template <> __host__ __device__ constexpr float cos_r<3>(int m) { return m % 3 == 0 ? 1.f : -0.5f; }
+template <> __host__ __device__ constexpr float sin_r<3>(int m) {
+    return m % 3 == 0 ? 0.f : (m % 3 == 1 ? 0.86602540378443865f : -0.86602540378443865f);
+}
+template <> __host__ __device__ constexpr float cos_r<5>(int m) {
+    switch (m % 5) {
+        case 0: return 1.f; case 1: case 4: return 0.30901699437494742f; default: return -0.80901699437494742f;
+    }
+}
+template <> __host__ __device__ constexpr float sin_r<5>(int m) {
+    switch (m % 5) {
+        case 0: return 0.f; case 1: return 0.95105651629515357f; case 2: return 0.58778525229247313f;
+        case 3: return -0.58778525229247313f; default: return -0.95105651629515357f;
+    }
+}
+template <> __host__ __device__ constexpr float cos_r<7>(int m) {
+    switch (m % 7) {
+        case 0: return 1.f; case 1: case 6: return 0.62348980185873353f;
+        case 2: case 5: return -0.22252093395631440f; default: return -0.90096886790241913f;
+    }
+}
+template <> __host__ __device__ constexpr float sin_r<7>(int m) {
+    switch (m % 7) {
+        case 0: return 0.f; case 1: return 0.78183148246802981f; case 2: return 0.97492791218182361f;
+        case 3: return 0.43388373911755812f; case 4: return -0.43388373911755812f;
+        case 5: return -0.97492791218182361f; default: return -0.78183148246802981f;
+    }
+}
+
+// Odd-length DFT from the definition, folding x_j and x_{R-j}: with s_j = x_j + x_{R-j},
+// d_j = x_j - x_{R-j}, A_k = x_0 + sum_j cos(2 pi j k / R) s_j and B_k = sum_j sin(..) d_j,
+// X_k = A_k - i B_k and X_{R-k} = A_k + i B_k (forward; signs swapped for INV).
+template <int R, bool INV> __device__ __forceinline__ void dft_odd(float2 (&a)[R]) {
+    constexpr int H = (R - 1) / 2;
+    float2 sj[H], dj[H];
+#pragma unroll
+    for (int j = 1; j <= H; ++j) {
+        sj[j - 1] = cadd(a[j], a[R - j]);
+        dj[j - 1] = csub(a[j], a[R - j]);
+    }
+    const float2 x0 = a[0];
+    float2 s0 = x0;
+#pragma unroll
+    for (int j = 0; j < H; ++j) s0 = cadd(s0, sj[j]);
+    a[0] = s0;
+#pragma unroll
+    for (int k = 1; k <= H; ++k) {
+        float2 A = x0, B = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int j = 1; j <= H; ++j) {
+            const float c = cos_r<R>(j * k), sn = sin_r<R>(j * k);
+            A = make_float2(fmaf(c, sj[j - 1].x, A.x), fmaf(c, sj[j - 1].y, A.y));
+            B = make_float2(fmaf(sn, dj[j - 1].x, B.x), fmaf(sn, dj[j - 1].y, B.y));
+        }
+        const float2 mib = make_float2(B.y, -B.x);  // -i B
+        a[k] = INV ? csub(A, mib) : cadd(A, mib);
+        a[R - k] = INV ? cadd(A, mib) : csub(A, mib);
+    }
+}
+
+template <int R, bool INV> __device__ __forceinline__ void dft_any(float2 (&a)[R]) {
+    if constexpr (R % 2 == 1) dft_odd<R, INV>(a);
+    else dftR<R, INV>(a);
+}
+
+// radices after the first radix-16 stage
+template <int N> struct GenericPlan;
+template <> struct GenericPlan<192> { static constexpr int R2 = 4, R3 = 3; };
+template <> struct GenericPlan<224> { static constexpr int R2 = 2, R3 = 7; };
+template <> struct GenericPlan<320> { static constexpr int R2 = 4, R3 = 5; };
+template <> struct GenericPlan<384> { static constexpr int R2 = 8, R3 = 3; };
+
+// One in-place Stockham stage of radix R and span NS on the shared-memory transform: butterfly
+// j (of N / R, spread over the T threads, the last ones idle where T does not divide N / R)
+// reads x[j + (N / R) r], applies W_{NS R}^{(j mod NS) r} = tw[(j mod NS) r N / (NS R)] with
+// tw[m] = W_N^m, and writes y[(j / NS) NS R + j mod NS + NS r].  All reads finish (bar) before
+// the writes, and the writes (bar) before the next stage.
+template <int N, int R, int NS, int T, bool INV, class Idx, class Bar>
+__device__ __forceinline__ void stockham_stage(float2* buf, Idx idx, const float2* tw, int t, Bar bar) {
+    constexpr int NB = N / R;
+    constexpr int PER = (NB + T - 1) / T;
+    float2 a[PER][R];
+#pragma unroll
+    for (int m = 0; m < PER; ++m) {
+        const int j = t + T * m;
+        if (PER * T == NB || j < NB) {
+            const int k = j % NS;
+#pragma unroll
+            for (int r = 0; r < R; ++r) a[m][r] = buf[idx(j + NB * r)];
+#pragma unroll
+            for (int r = 1; r < R; ++r) {
+                float2 w = tw[k * r * (N / (NS * R))];
+                if (INV) w.y = -w.y;
+                a[m][r] = cmul(a[m][r], w);
+            }
+            dft_any<R, INV>(a[m]);
+        }
+    }
+    bar();
+#pragma unroll
+    for (int m = 0; m < PER; ++m) {
+        const int j = t + T * m;
+        if (PER * T == NB || j < NB) {
+            const int base = (j / NS) * NS * R + j % NS;
+#pragma unroll
+            for (int r = 0; r < R; ++r) buf[idx(base + NS * r)] = a[m][r];
+        }
+    }
+    bar();
+}
+
+// N = 16 x {12, 14, 20, 24}: the same register layout as the power-of-two transforms (thread t
+// of T = N / 16 holds x[t + T e] in and X[t + T e] out); radix 16 on the registers, then the
+// two stages of GenericPlan<N> in shared memory (tw[m] = W_N^m, m < N).
+template <int N, bool INV, class Idx, class Bar>
+__device__ __forceinline__ void fft_generic_bar(float2 (&v)[16], int t, float2* buf, Idx idx, const float2* tw,
+                                                Bar bar) {
+    constexpr int T = N / 16;
+    constexpr int R2 = GenericPlan<N>::R2, R3 = GenericPlan<N>::R3;
+    static_assert(16 * R2 * R3 == N, "plan covers N");
+    dft16<INV>(v);
+#pragma unroll
+    for (int r = 0; r < 16; ++r) buf[idx(16 * t + r)] = v[r];
+    bar();
+    stockham_stage<N, R2, 16, T, INV>(buf, idx, tw, t, bar);
+    stockham_stage<N, R3, 16 * R2, T, INV>(buf, idx, tw, t, bar);
+#pragma unroll
+    for (int e = 0; e < 16; ++e) v[e] = buf[idx(t + T * e)];
+}
+
+__host__ __device__ constexpr bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+// Size dispatch: two stages for powers of two up to 256, three for 512, the generic
+// mixed-radix transform for 192, 224, 320 and 384.
 template <int N, bool INV, class Idx, class Bar>
 __device__ __forceinline__ void fft_bar(float2 (&v)[16], int t, float2* buf, Idx idx, const float2* tw, Bar bar) {
-    if constexpr (N <= 256) fft_2stage_bar<N, INV>(v, t, buf, idx, tw, bar);
-    else fft_3stage_bar<N, INV>(v, t, buf, idx, tw, bar);
+    if constexpr (is_pow2(N) && N <= 256) fft_2stage_bar<N, INV>(v, t, buf, idx, tw, bar);
+    else if constexpr (N == 512) fft_3stage_bar<N, INV>(v, t, buf, idx, tw, bar);
+    else fft_generic_bar<N, INV>(v, t, buf, idx, tw, bar);
 }
 
 struct CtaBar {

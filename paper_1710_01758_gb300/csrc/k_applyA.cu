@@ -12,8 +12,10 @@
 //    two-stage ring; a "full" mbarrier per stage completes on the bytes, an "empty" mbarrier
 //    (one arrival per warp) tells the producing thread when the stage may be refilled.
 //  * Each column transform belongs to ny / 16 threads of one exchange group (64 threads for
-//    ny <= 256, 128 at ny = 512); a group owns CPG columns, exchanges data only through its private shared-memory region, and
-//    synchronises with a named barrier of its own: no CTA-wide barrier inside the coil loop.
+//    ny <= 256, 128 at ny = 512, whole warps of whole columns for ny = 16 x {12, 14, 20, 24});
+//    a group owns CPG columns, exchanges data only through its private shared-memory region,
+//    and synchronises with a named barrier of its own: no CTA-wide barrier inside the coil
+//    loop (one group per CTA at ny = 224).
 //  * 8-byte shared-memory accesses are served per half-warp, so each half-warp holds 8
 //    consecutive rows of 2 adjacent columns: the TMA swizzle then spreads the tile reads over
 //    16 distinct bank pairs, and so does the exchange region, stored column by column with one
@@ -62,7 +64,7 @@ struct TileRows {
 
 // rows of one TMA box (the box extent is limited to 256 per dimension)
 template <int NY>
-constexpr int kBoxRows = NY < 256 ? NY : 256;
+constexpr int kBoxRows = coil_box_rows(NY);
 
 // issue the TMA loads of coil tile (slice b, coil c) into `dst`, completing on `bar`
 template <int NY>
@@ -74,6 +76,12 @@ __device__ __forceinline__ void load_coil_tile(float2* dst, const CUtensorMap* m
         tma_load_2d(dst + r0 * TX, map, 2 * x0, (b * nc + c) * NY + r0, bar);
 }
 
+__host__ __device__ constexpr int lcm32(int t) {
+    int m = 32;
+    while (m % t != 0) m += 32;
+    return m;
+}
+
 template <int NY, bool PCG>
 __global__ void __launch_bounds__(TX * NY / 16, NY <= 256 ? 2 : 1)
 k_apply_A(const __grid_constant__ CUtensorMap smap, const float2* __restrict__ p, float2* __restrict__ q,
@@ -81,8 +89,10 @@ k_apply_A(const __grid_constant__ CUtensorMap smap, const float2* __restrict__ p
           float gam, SliceState* st, Red red) {
     constexpr int T = NY / 16;            // threads per column transform
     constexpr int NT = TX * T;            // threads per CTA
-    // threads per exchange group: 4 columns (a warp = 8 rows x 4 columns needs T / 8 warps)
-    constexpr int GT = NT < 64 ? NT : (4 * T > 64 ? 4 * T : 64);
+    // threads per exchange group: 4 columns when T is a multiple of 8 (a warp = 8 rows x 4
+    // columns needs T / 8 warps), else the smallest whole number of warps that holds whole
+    // columns (lcm(T, 32): 96 threads for T = 12, 224 for 14, 160 for 20)
+    constexpr int GT = NT < 64 ? NT : (T % 8 == 0 ? (4 * T > 64 ? 4 * T : 64) : lcm32(T));
     constexpr int CPG = GT / T;           // columns per group
     constexpr int NW = NT / 32;           // warps per CTA
     const int b = blockIdx.y;
@@ -245,6 +255,10 @@ cudaError_t launch_apply_A(const Dims& d, const CUtensorMap& smap, const float2*
         case 128: return apply_A_n<128>(d, smap, p, q, maskw, tw_y, mu, lam, gam, st, red, s);
         case 256: return apply_A_n<256>(d, smap, p, q, maskw, tw_y, mu, lam, gam, st, red, s);
         case 512: return apply_A_n<512>(d, smap, p, q, maskw, tw_y, mu, lam, gam, st, red, s);
+        case 192: return apply_A_n<192>(d, smap, p, q, maskw, tw_y, mu, lam, gam, st, red, s);
+        case 224: return apply_A_n<224>(d, smap, p, q, maskw, tw_y, mu, lam, gam, st, red, s);
+        case 320: return apply_A_n<320>(d, smap, p, q, maskw, tw_y, mu, lam, gam, st, red, s);
+        case 384: return apply_A_n<384>(d, smap, p, q, maskw, tw_y, mu, lam, gam, st, red, s);
         default: return cudaErrorInvalidValue;
     }
 }

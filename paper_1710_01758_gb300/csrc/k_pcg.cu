@@ -415,6 +415,10 @@ cudaError_t launch_row_fwd(const Dims& d, int mode, float2* r, const float2* q, 
         case 128: return CALL(128);
         case 256: return CALL(256);
         case 512: return CALL(512);
+        case 192: return CALL(192);
+        case 224: return CALL(224);
+        case 320: return CALL(320);
+        case 384: return CALL(384);
         default: return cudaErrorInvalidValue;
     }
 #undef CALL
@@ -429,6 +433,10 @@ cudaError_t launch_col_precond(const Dims& d, float2* t, const float* invk, cons
         case 128: return CALL(128);
         case 256: return CALL(256);
         case 512: return CALL(512);
+        case 192: return CALL(192);
+        case 224: return CALL(224);
+        case 320: return CALL(320);
+        case 384: return CALL(384);
         default: return cudaErrorInvalidValue;
     }
 #undef CALL
@@ -443,6 +451,10 @@ cudaError_t launch_row_inv(const Dims& d, int mode, const float2* t, float2* out
         case 128: return CALL(128);
         case 256: return CALL(256);
         case 512: return CALL(512);
+        case 192: return CALL(192);
+        case 224: return CALL(224);
+        case 320: return CALL(320);
+        case 384: return CALL(384);
         default: return cudaErrorInvalidValue;
     }
 #undef CALL

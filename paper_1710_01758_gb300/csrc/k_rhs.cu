@@ -42,7 +42,7 @@ k_rhs(const __grid_constant__ CUtensorMap smap, const __grid_constant__ CUtensor
     constexpr int T = NY / 16;
     constexpr int NT = TX * T;
     constexpr int NST = kRhsStages<NY>;
-    constexpr int SBOX = NY < 256 ? NY : 256;  // rows per TMA box of a coil tile
+    constexpr int SBOX = coil_box_rows(NY);  // rows per TMA box of a coil tile
     const int b = blockIdx.y;
     const int ms = f.ms;  // <= 256: one box of compact rows
     const uint32_t sbytes = NY * TX * sizeof(float2);
@@ -209,6 +209,10 @@ cudaError_t launch_rhs(const Dims& d, const CUtensorMap& smap, const CUtensorMap
         case 128: CALL(128)
         case 256: CALL(256)
         case 512: CALL(512)
+        case 192: CALL(192)
+        case 224: CALL(224)
+        case 320: CALL(320)
+        case 384: CALL(384)
         default: return cudaErrorInvalidValue;
     }
 #undef CALL

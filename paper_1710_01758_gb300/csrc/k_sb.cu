@@ -145,6 +145,10 @@ cudaError_t launch_ytilde(const Dims& d, const float2* y, const int* lines, int 
         case 128: CALL(128)
         case 256: CALL(256)
         case 512: CALL(512)
+        case 192: CALL(192)
+        case 224: CALL(224)
+        case 320: CALL(320)
+        case 384: CALL(384)
         default: return cudaErrorInvalidValue;
     }
 #undef CALL
@@ -170,6 +174,10 @@ cudaError_t launch_rss(const Dims& d, const SbFields& f, float2* x, int write_x,
         case 128: CALL(128)
         case 256: CALL(256)
         case 512: CALL(512)
+        case 192: CALL(192)
+        case 224: CALL(224)
+        case 320: CALL(320)
+        case 384: CALL(384)
         default: return cudaErrorInvalidValue;
     }
 #undef CALL

@@ -210,6 +210,10 @@ cudaError_t launch_fft_rows(int nx, int ny, int nimg, float2* data, const float2
         case 128: return fft_rows_n<128>(ny, nimg, data, tw_x, inv, s);
         case 256: return fft_rows_n<256>(ny, nimg, data, tw_x, inv, s);
         case 512: return fft_rows_n<512>(ny, nimg, data, tw_x, inv, s);
+        case 192: return fft_rows_n<192>(ny, nimg, data, tw_x, inv, s);
+        case 224: return fft_rows_n<224>(ny, nimg, data, tw_x, inv, s);
+        case 320: return fft_rows_n<320>(ny, nimg, data, tw_x, inv, s);
+        case 384: return fft_rows_n<384>(ny, nimg, data, tw_x, inv, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -221,6 +225,10 @@ cudaError_t launch_fft_cols(int nx, int ny, int nimg, float2* data, const float2
         case 128: return fft_cols_n<128>(nx, nimg, data, tw_y, inv, s);
         case 256: return fft_cols_n<256>(nx, nimg, data, tw_y, inv, s);
         case 512: return fft_cols_n<512>(nx, nimg, data, tw_y, inv, s);
+        case 192: return fft_cols_n<192>(nx, nimg, data, tw_y, inv, s);
+        case 224: return fft_cols_n<224>(nx, nimg, data, tw_y, inv, s);
+        case 320: return fft_cols_n<320>(nx, nimg, data, tw_y, inv, s);
+        case 384: return fft_cols_n<384>(nx, nimg, data, tw_y, inv, s);
         default: return cudaErrorInvalidValue;
     }
 }

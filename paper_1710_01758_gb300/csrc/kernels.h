@@ -31,6 +31,9 @@ struct SliceState {
     int iters;      // A applications since the initial residual
 };
 
+// rows of one TMA box of a coil tile (boxes span at most 256 rows and must tile ny)
+__host__ __device__ constexpr int coil_box_rows(int ny) { return ny <= 256 ? ny : (ny % 256 == 0 ? 256 : ny / 2); }
+
 struct Dims {
     int nx, ny, nc, nb;
 };

@@ -30,7 +30,9 @@ std::atomic<uint64_t> g_launches{0};
 // PCG iterations enqueued between two reads of the per-slice state
 constexpr int kPollEvery = 4;
 
-bool supported_n(int n) { return n == 32 || n == 64 || n == 128 || n == 256 || n == 512; }
+bool supported_n(int n) {
+    return n == 32 || n == 64 || n == 128 || n == 256 || n == 512 || n == 192 || n == 224 || n == 320 || n == 384;
+}
 
 struct Pending {
     int cls;
@@ -208,13 +210,18 @@ void dfree(void* p) {
 // Twiddle tables of the register-resident transforms (common.cuh), computed in double:
 // n <= 256: tw[r * 16 + j] = exp(-2 pi i r j / n), r < n/16, j < 16 (the second stage);
 // n = 512: tw[r * 16 + k] = exp(-2 pi i r k / 256) (second stage), tw[256 + k] =
-// exp(-2 pi i k / 512), k < 256 (third stage).
+// exp(-2 pi i k / 512), k < 256 (third stage);
+// n = 192, 224, 320, 384 (mixed radix): tw[m] = exp(-2 pi i m / n), m < n.
 std::vector<float2> twiddles(int n) {
     std::vector<float2> t(n);
     auto w = [](double num, double den) {
         const double a = -2.0 * M_PI * num / den;
         return make_float2((float)std::cos(a), (float)std::sin(a));
     };
+    if ((n & (n - 1)) != 0) {
+        for (int m = 0; m < n; ++m) t[m] = w(m, n);
+        return t;
+    }
     const int m = n <= 256 ? n : 256;
     for (int r = 0; r < m / 16; ++r)
         for (int j = 0; j < 16; ++j) t[r * 16 + j] = w((double)r * j, m);
@@ -622,7 +629,7 @@ sb_status sb_set_coils(sb_plan pl, const void* d_sens) {
     auto enc = [&](Exec& ex) {
         const float2* base = static_cast<const float2*>(d_sens) + (size_t)ex.b0 * per;
         const size_t rows = (size_t)ex.d.nb * d.nc * d.ny;
-        const int box = std::min(d.ny, 256);  // a TMA box spans at most 256 rows
+        const int box = coil_box_rows(d.ny);  // a TMA box spans at most 256 rows
         return encode_rows(&ex.smap, base, d.nx, rows, box) && encode_rows(&ex.smap_sw, base, d.nx, rows, box, true);
     };
     bool ok = enc(pl->whole);

@@ -64,7 +64,9 @@ def make_plan(sbm, torch, sens, mask, mu, lam, gam, levels=0, passes=0):
 
 
 SHAPES = [(32, 64, 3, 2), (64, 32, 2, 3), (128, 128, 4, 1), (256, 256, 12, 1), (256, 128, 5, 2),
-          (512, 512, 32, 1), (512, 128, 3, 2)]
+          (512, 512, 32, 1), (512, 128, 3, 2),
+          # mixed-radix lengths 16 x {12, 14, 20, 24}
+          (192, 192, 8, 2), (256, 224, 12, 1), (320, 320, 16, 1), (384, 320, 32, 1), (224, 384, 3, 1)]
 
 
 @pytest.mark.parametrize("nx,ny,nc,nb", SHAPES)
@@ -352,3 +354,13 @@ def test_pcg_precond_schedules(torch, sbm, nx, ny, nc, nb, passes):
         assert abs(rest[i][0] - reft.iters) <= 1, (rest[i], reft.iters)
         assert rest[i][1] <= 1e-4 and rest[i][2]
         assert rel(xtg[i], reft.x) <= 1e-3
+
+
+def test_split_bregman_mixed_radix_sizes(torch, sbm):
+    # 224 x 192 (x by y): radix-16 x 2 x 7 along x, 16 x 4 x 3 along y; TV + 4-level Haar with
+    # active shrinkage, R = 3 lines
+    wl = synth.Workload("192x224 Nc8 R3 TV+Haar4", 192, 224, 8, 3.0, 16, "uniform", 1.0, 0.05, 0.05, 4, 4, 1,
+                        1e-3, 100, 0, seed=4242)
+    xg, refs, _ = run_sb_both(torch, sbm, wl, 2, wl.seed, tau=0.02, fixed=8)
+    for b in range(2):
+        assert rel(xg[b], refs[b].x) <= IMG_TOL
