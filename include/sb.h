@@ -154,6 +154,17 @@ typedef struct {
 sb_status sb_split_bregman(sb_plan plan, const void* d_y, void* d_x, const sb_sb_opts* opts,
                            sb_pcg_result* h_last);
 
+/* sb_split_bregman on several plans at once: a batch of slices that differ in size, coil count
+ * or weights is split by the caller into one plan per geometry, and this call reconstructs all
+ * of them concurrently (plan i from its own host thread on its own stream, so plans whose
+ * streams differ overlap on the GPU).  For plan i: d_y[i], d_x[i], opts[i] and h_last[i] (may be
+ * NULL) mean what they mean for sb_split_bregman.  The same plan may not appear twice
+ * (SB_ERR_INVALID_ARG).  Synchronises every plan's stream; returns the first non-OK status in
+ * plan order (every plan still runs to completion).  No counterpart in the paper: it batches the
+ * independent slice reconstructions of the Methods. */
+sb_status sb_split_bregman_many(const sb_plan* plans, int nplans, const void* const* d_y, void* const* d_x,
+                                const sb_sb_opts* opts, sb_pcg_result* const* h_last);
+
 /* d_z = F^H diag(d_k)^{-1} F d_r, like sb_apply_precond, but without a plan and without any
  * device allocation, for callers that cannot call cudaMalloc when they apply the
  * preconditioner (fixed memory budgets after start-up, plugins handed only pre-allocated

@@ -841,6 +841,37 @@ sb_status sb_split_bregman(sb_plan pl, const void* d_y, void* d_x, const sb_sb_o
     return st;
 }
 
+sb_status sb_split_bregman_many(const sb_plan* plans, int nplans, const void* const* d_y, void* const* d_x,
+                                const sb_sb_opts* opts, sb_pcg_result* const* h_last) {
+    if (!plans || nplans < 1 || !d_y || !d_x || !opts) return SB_ERR_INVALID_ARG;
+    for (int i = 0; i < nplans; ++i) {
+        if (!plans[i]) return SB_ERR_INVALID_ARG;
+        for (int k = 0; k < i; ++k)
+            if (plans[k] == plans[i]) return fail(plans[i], SB_ERR_INVALID_ARG, "a plan appears twice");
+    }
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return SB_ERR_CUDA;
+    std::vector<sb_status> st(nplans, SB_OK);
+    auto run = [&](int i) {
+        st[i] = sb_split_bregman(plans[i], d_y[i], d_x[i], &opts[i], h_last ? h_last[i] : nullptr);
+    };
+    std::vector<std::thread> th;
+    th.reserve(nplans - 1);
+    for (int i = 1; i < nplans; ++i)
+        th.emplace_back([&, i] {
+            if (cudaSetDevice(dev) != cudaSuccess) {
+                st[i] = fail(plans[i], SB_ERR_CUDA, "cudaSetDevice in a worker thread");
+                return;
+            }
+            run(i);
+        });
+    run(0);
+    for (auto& t : th) t.join();
+    for (int i = 0; i < nplans; ++i)
+        if (st[i] != SB_OK) return st[i];
+    return SB_OK;
+}
+
 sb_status sb_plan_set_timing(sb_plan pl, unsigned class_mask) {
     if (!pl) return SB_ERR_INVALID_ARG;
     SB_CK(pl, pl->stream ? cudaStreamSynchronize(pl->stream) : cudaDeviceSynchronize());

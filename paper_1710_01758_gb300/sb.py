@@ -71,6 +71,9 @@ SIGNATURES = [
     ("sb_plan_last_error", ctypes.c_char_p, [_P]),
     ("sb_kernel_launches", ctypes.c_uint64, []),
     ("sb_apply_precond_noalloc", ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P]),
+    ("sb_split_bregman_many", ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(_P),
+                                             ctypes.POINTER(_P), ctypes.POINTER(sb_sb_opts),
+                                             ctypes.POINTER(ctypes.POINTER(sb_pcg_result))]),
     ("sb_plan_set_timing", ctypes.c_int, [_P, ctypes.c_uint]),
     ("sb_plan_get_timing", ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_uint64),
                                           ctypes.POINTER(ctypes.c_double)]),
@@ -187,6 +190,26 @@ def sb_split_bregman(plan: int, d_y: int, d_x: int, n_outer: int, n_inner: int, 
     return st, it, [(r.iters, r.rel_resid, bool(r.converged)) for r in last]
 
 
+def sb_split_bregman_many(plans, d_ys, d_xs, nbatches, n_outer: int, n_inner: int, pcg: sb_pcg_opts,
+                          tau_tv: float = 0.0, tau_w: float = 0.0, init_rss: bool = True,
+                          allow=(SB_ERR_NOT_CONVERGED,)):
+    """Concurrent sb_split_bregman over several plans.  Returns (status, [iters per plan],
+    [last results per plan]) with the per-plan layouts of sb_split_bregman."""
+    n = len(plans)
+    nsolve = n_outer * n_inner
+    iters = [(ctypes.c_int * (nb * nsolve))() for nb in nbatches]
+    opts = (sb_sb_opts * n)(*[sb_sb_opts(n_outer, n_inner, pcg, tau_tv, tau_w, 1 if init_rss else 0,
+                                         ctypes.cast(it, ctypes.POINTER(ctypes.c_int))) for it in iters])
+    lasts = [(sb_pcg_result * nb)() for nb in nbatches]
+    last_p = (ctypes.POINTER(sb_pcg_result) * n)(*[ctypes.cast(l, ctypes.POINTER(sb_pcg_result)) for l in lasts])
+    st = _lib.sb_split_bregman_many((_P * n)(*plans), n, (_P * n)(*d_ys), (_P * n)(*d_xs), opts, last_p)
+    if st != SB_OK and st not in allow:
+        msgs = "; ".join(_lib.sb_plan_last_error(_P(p)).decode() for p in plans)
+        raise SbError(st, msgs)
+    its = [[[it[b * nsolve + i] for i in range(nsolve)] for b in range(nb)] for it, nb in zip(iters, nbatches)]
+    return st, its, [[(r.iters, r.rel_resid, bool(r.converged)) for r in l] for l in lasts]
+
+
 def sb_apply_precond_noalloc(d_r: int, d_k: int, d_z: int, nx: int, ny: int, nbatch: int, stream: int = 0) -> None:
     """Plan-free, allocation-free M^{-1} r (see include/sb.h)."""
     _check(_lib.sb_apply_precond_noalloc(_P(d_r), _P(d_k), _P(d_z), nx, ny, nbatch, _P(stream)))
@@ -270,3 +293,11 @@ class Plan:
     def split_bregman(self, y, x, n_outer, n_inner=1, tau_tv=0.0, tau_w=0.0, init_rss=True, **pcg_kw):
         return sb_split_bregman(self.handle, self._c64(y), self._c64(x), n_outer, n_inner, pcg_opts(**pcg_kw),
                                 self.nbatch, tau_tv, tau_w, init_rss)
+
+
+def split_bregman_many(plans, ys, xs, n_outer, n_inner=1, tau_tv=0.0, tau_w=0.0, init_rss=True, **pcg_kw):
+    """sb_split_bregman_many over Plan objects (one per geometry) and their y / x tensors.  Give
+    each plan its own CUDA stream so that the reconstructions overlap on the GPU."""
+    return sb_split_bregman_many([p.handle for p in plans], [p._c64(y) for p, y in zip(plans, ys)],
+                                 [p._c64(x) for p, x in zip(plans, xs)], [p.nbatch for p in plans], n_outer,
+                                 n_inner, pcg_opts(**pcg_kw), tau_tv, tau_w, init_rss)

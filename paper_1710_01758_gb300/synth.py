@@ -159,6 +159,38 @@ METRIC_256 = Workload("256x256 Nc12 R4 TV+Haar4 20SB PCG-tol1e-3", 256, 256, 12,
                       1.0, 0.05, 0.05, 4, 20, 1, 1e-3, 200, 0, seed=SEED_BASE + 2)
 
 
+# 512x512, 32 coils, R=6 variable-density lines + 32 centre lines, TV + 4-level Haar, 20 SB.
+LARGE_512 = Workload("512x512 Nc32 R6vd TV+Haar4 20SB PCG-tol1e-3", 512, 512, 32, 6.0, 32, "variable",
+                     1.0, 0.05, 0.05, 4, 20, 1, 1e-3, 200, 0, seed=SEED_BASE + 3)
+
+# The uneven batch: per slice a seeded choice of image size, coil count and acceleration.
+# Sizes are (ny, nx): 192 x 192, 256 x 224 (x by y), 320 x 320 and 384 x 320 (x by y).
+UNEVEN_SIZES = ((192, 192), (224, 256), (320, 320), (320, 384))
+UNEVEN_COILS = (8, 12, 16, 32)
+UNEVEN_ACCEL = (3.0, 4.0, 6.0)
+UNEVEN_SEED = SEED_BASE + 4
+
+
+def uneven_workloads(n: int = 64, seed: int = UNEVEN_SEED) -> list[Workload]:
+    """Workloads of the ``n`` slices of the uneven batch: size, coils and R drawn per slice
+    (uniform over UNEVEN_SIZES x UNEVEN_COILS x UNEVEN_ACCEL), 16 centre lines, uniform line
+    density, TV + 4-level Haar and the weights and schedule of METRIC_256."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n):
+        ny, nx = UNEVEN_SIZES[int(rng.integers(len(UNEVEN_SIZES)))]
+        nc = UNEVEN_COILS[int(rng.integers(len(UNEVEN_COILS)))]
+        accel = UNEVEN_ACCEL[int(rng.integers(len(UNEVEN_ACCEL)))]
+        out.append(Workload(f"{nx}x{ny} Nc{nc} R{accel:g} TV+Haar4", ny, nx, nc, accel, 16, "uniform",
+                            1.0, 0.05, 0.05, 4, 20, 1, 1e-3, 200, 0, seed=seed))
+    return out
+
+
+def uneven_slice(wls: list[Workload], i: int) -> "Slice":
+    """Slice i of the uneven batch (seed = batch seed * 1000 + i)."""
+    return make_slice(wls[i], wls[i].seed * 1000 + i)
+
+
 @dataclasses.dataclass
 class Slice:
     x_true: np.ndarray    # complex128 [ny, nx]
