@@ -15,6 +15,12 @@ the dominant kernel's achieved HBM bandwidth against the measured peak; the imag
 the FP64 oracle.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload 256|128|512|uneven64]
+
+The default workload is the one above; --workload selects further measurement lines: 512 x 128
+slices of 128x128 x 4 coils (TV only, 10 Split Bregman x 20 fixed PCG iterations), 8 slices of
+512x512 x 32 coils (R = 6 variable-density lines), or 64 uneven slices (sizes 192x192 to 384x320,
+8-32 coils, R = 3/4/6) solved as one plan per geometry, concurrently.
 
 Multi-GPU (torchrun): each rank reconstructs its own batch (weak scaling, no collective on the
 data path); rank 0 prints one JSON line with the max-over-ranks time.
@@ -36,12 +42,15 @@ if ROOT not in sys.path:
 
 METRIC = "PCG iters/s and recon/s at 256²×12 coils; HBM GB/s vs peak; err vs FP64"
 UNIT = "PCG iter/s"
-DEFAULT_BATCH = 64
 HBM_FALLBACK_GBS = 6800.0
-# DRAM bytes (read + write) of one k_apply_A launch over the full 64-slice batch: the ncu capture
-# of profiles/k_apply_A_256x256x12_b32.md (32 slices: 227.49 MB read + 9.21 MB written) scaled by
-# the slices processed.  Set to None whenever the kernel changes until it is captured again.
-TRAFFIC_K1 = 2 * (227.49e6 + 9.21e6)
+# DRAM bytes (read + write) of one k_apply_A launch over the full 64-slice 256x256x12 batch: the
+# ncu capture of profiles/k_apply_A_256x256x12_b32.md (32 slices: 228.29 MB read + 9.14 MB
+# written) scaled by the slices processed.  Set to None whenever the kernel changes until it is
+# captured again.
+TRAFFIC_K1 = 2 * (228.29e6 + 9.14e6)
+# workloads: name -> (synth workload attribute, default batch).  The default is the headline
+# configuration; the others are further measurement lines (batches sized above L2).
+WORKLOADS = {"256": ("METRIC_256", 64), "128": ("SMALL_128", 512), "512": ("LARGE_512", 8)}
 
 
 def log(*a):
@@ -54,7 +63,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--batch", type=int, default=DEFAULT_BATCH)
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["uneven64"], default="256",
+                    help="256: 256x256x12 (default); 128: 128x128x4; 512: 512x512x32; uneven64: 64 slices "
+                         "of mixed size / coils / R, one plan per geometry, solved concurrently")
+    ap.add_argument("--batch", type=int, default=0, help="slices per step (0 = the workload's default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--groups", type=int, default=0, help="concurrent slice groups (0 = library default)")
@@ -147,7 +159,8 @@ def oracle_recon(wl, s, n_outer=None):
     from oracle import split_bregman as sbo
     t0 = time.perf_counter()
     r = sbo.split_bregman(s.y, s.sens, s.mask, wl.mu, wl.lam, wl.gam, wl.wavelet_levels, 2,
-                          wl.n_outer if n_outer is None else n_outer, wl.n_inner, wl.pcg_tol, wl.pcg_maxit)
+                          wl.n_outer if n_outer is None else n_outer, wl.n_inner, wl.pcg_tol, wl.pcg_maxit,
+                          wl.pcg_fixed_iters)
     return r.x, int(sum(r.iters)), time.perf_counter() - t0
 
 
@@ -219,8 +232,13 @@ def run_ours(args):
     build_mod.build()
     from paper_1710_01758_gb300 import sb, synth
 
-    wl = synth.METRIC_256
-    B = args.batch
+    if args.workload == "uneven64":
+        return run_uneven(args, torch, sb, synth, world, rank, local, dist)
+    attr, default_b = WORKLOADS[args.workload]
+    wl = getattr(synth, attr)
+    B = args.batch or default_b
+    pcg_kw = ({"fixed_iters": wl.pcg_fixed_iters} if wl.pcg_fixed_iters > 0
+              else {"tol": wl.pcg_tol, "maxit": wl.pcg_maxit})
     t0 = time.perf_counter()
     slices, sens_h, mask_h, y_h = make_inputs(wl, B, rank_seed(wl.seed, rank))
     log(f"[bench] rank {rank}: generated {B} slices in {time.perf_counter() - t0:.1f}s")
@@ -236,7 +254,7 @@ def run_ours(args):
     def step(ys=d_y, ss=d_sens, ms=d_mask, xx=x):
         plan.set_coils(ss)
         plan.set_mask(ms)
-        st, iters, _ = plan.split_bregman(ys, xx, wl.n_outer, wl.n_inner, tol=wl.pcg_tol, maxit=wl.pcg_maxit)
+        st, iters, _ = plan.split_bregman(ys, xx, wl.n_outer, wl.n_inner, **pcg_kw)
         if st != sb.SB_OK:
             raise RuntimeError(f"split_bregman: {sb.status_string(st)}")
         return int(sum(sum(i) for i in iters)), iters
@@ -308,8 +326,8 @@ def run_ours(args):
         sub.set_coils(d_sens[:nsub].contiguous())
         sub.set_mask(d_mask[:nsub].contiguous())
         xs = torch.zeros((nsub, wl.ny, wl.nx), dtype=torch.complex64, device=dev)
-        _, it_plain, _ = sub.split_bregman(d_y[:nsub].contiguous(), xs, wl.n_outer, wl.n_inner, tol=wl.pcg_tol,
-                                           maxit=wl.pcg_maxit, precond=sb.SB_PRECOND_NONE)
+        _, it_plain, _ = sub.split_bregman(d_y[:nsub].contiguous(), xs, wl.n_outer, wl.n_inner,
+                                           precond=sb.SB_PRECOND_NONE, **pcg_kw)
         sub.close()
         it_pre = iters_last[:nsub]
         extra["pcg_iters_per_solve"] = {
@@ -364,7 +382,8 @@ def run_ours(args):
                 "pcg_iters_per_step": total_all / args.steps,
                 "roofline": {"bound": "hbm", "kernel": "k_apply_A (q = A p)",
                              "achieved": achieved, "peak": peak, "unit": "GB/s",
-                             "frac": (achieved / peak) if achieved else None, "traffic": TRAFFIC_K1,
+                             "frac": (achieved / peak) if achieved else None,
+                             "traffic": TRAFFIC_K1 if (args.workload == "256" and B == 64) else None,
                              "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
                              else "fallback",
                              "timing": f"timed alone: {k1_alone_n} launches over the {B}-slice batch, "
@@ -378,6 +397,100 @@ def run_ours(args):
                 "kernel_time_breakdown": breakdown,
                 "gpu_launches": int(launches),
                 "clocks": clocks, "e2e": e2e}
+        line.update(extra)
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def run_uneven(args, torch, sb, synth, world, rank, local, dist):
+    """64 slices of mixed size, coil count and R: one plan per geometry, each on its own stream,
+    reconstructed concurrently by sb_split_bregman_many.  A step = k construction of every plan
+    (sb_set_mask) + the concurrent reconstructions."""
+    import collections
+    import numpy as np
+    wls = synth.uneven_workloads(seed=rank_seed(synth.UNEVEN_SEED, rank))
+    groups = collections.defaultdict(list)
+    for i, w in enumerate(wls):
+        groups[(w.nx, w.ny, w.ncoils)].append(i)
+    dev = torch.device("cuda", local)
+    t0 = time.perf_counter()
+    plans, ys, xs, sens, masks, members = [], [], [], [], [], []
+    for (nx, ny, nc), ids in sorted(groups.items()):
+        sl = [synth.uneven_slice(wls, i) for i in ids]
+        w = wls[ids[0]]
+        sens.append(torch.from_numpy(np.stack([s.sens for s in sl]).astype(np.complex64)).to(dev))
+        masks.append(torch.from_numpy(np.stack([s.mask for s in sl])).to(dev))
+        ys.append(torch.from_numpy(np.stack([s.y for s in sl]).astype(np.complex64)).to(dev))
+        xs.append(torch.zeros((len(ids), ny, nx), dtype=torch.complex64, device=dev))
+        plans.append(sb.Plan(nx, ny, nc, len(ids), w.mu, w.lam, w.gam, w.wavelet_levels, stream=torch.cuda.Stream(dev)))
+        members.append((ids, sl))
+    torch.cuda.synchronize()
+    log(f"[bench] rank {rank}: generated {len(wls)} uneven slices ({len(plans)} geometries) in "
+        f"{time.perf_counter() - t0:.1f}s")
+    w0 = wls[0]
+
+    def step():
+        for p, s_, m_ in zip(plans, sens, masks):
+            p.set_coils(s_)
+            p.set_mask(m_)
+        st, iters, _ = sb.split_bregman_many(plans, ys, xs, w0.n_outer, w0.n_inner, tol=w0.pcg_tol,
+                                             maxit=w0.pcg_maxit)
+        if st != sb.SB_OK:
+            raise RuntimeError(f"split_bregman_many: {sb.status_string(st)}")
+        return int(sum(sum(sum(r) for r in it) for it in iters))
+
+    for _ in range(args.warmup):
+        step()
+    sampler = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    launches0 = sb.kernel_launches()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev0.record(torch.cuda.current_stream(dev))
+    torch.cuda.synchronize()
+    total = 0
+    for _ in range(args.steps):
+        total += step()
+    ends = []
+    for p in plans:
+        e = torch.cuda.Event(enable_timing=True)
+        e.record(p.stream)
+        ends.append(e)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    launches = sb.kernel_launches() - launches0
+    elapsed = max(ev0.elapsed_time(e) for e in ends) / 1e3
+    total_all, elapsed_max = total, elapsed
+    if dist:
+        elapsed_max, total_all = reduce_over_ranks(dist, dev, elapsed, total)
+    extra = {}
+    if rank == 0 and not args.no_cpu_baseline:
+        ids, sl = members[0]
+        x_or, it_or, t_or = oracle_recon(wls[ids[0]], sl[0])
+        extra["err_vs_fp64"] = float(np.linalg.norm(xs[0][0].cpu().numpy() - x_or) / np.linalg.norm(x_or))
+        extra["err_slice"] = wls[ids[0]].name
+        extra["cpu_baseline"] = {"value": it_or / t_or, "unit": UNIT, "cores": host_threads(), "kind": "oracle",
+                                 "sample": f"one {wls[ids[0]].name} slice, full Split Bregman, FP64 numpy"}
+    for p in plans:
+        p.close()
+    if rank == 0:
+        sizes = collections.Counter(f"{w.nx}x{w.ny}" for w in wls)
+        line = {"metric": METRIC, "value": total_all / elapsed_max, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * elapsed_max / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "fp32",
+                "scalars": "fp64", "data": "synthetic",
+                "config": {"workload": f"{len(wls)} uneven slices ({len(plans)} geometries)",
+                           "sizes": dict(sizes), "coils": sorted({w.ncoils for w in wls}),
+                           "accel": sorted({w.accel for w in wls}), "haar_levels": w0.wavelet_levels,
+                           "n_outer": w0.n_outer, "pcg_tol": w0.pcg_tol, "precond": "circulant",
+                           "l2": "inputs larger than L2", "parallelism": f"{world} ranks x independent batches"},
+                "recon_per_s": args.steps * len(wls) * world / elapsed_max,
+                "pcg_iters_per_step": total_all / args.steps, "roofline": None,
+                "gpu_launches": int(launches), "clocks": clocks, "e2e": None}
         line.update(extra)
         print(json.dumps(line), flush=True)
     if dist:
