@@ -110,14 +110,17 @@ __global__ void k_mul_conj(float2* __restrict__ R, const float2* __restrict__ G,
 
 // k = mu kc + lam kd + gam (first pass) and its per-slice maximum (non-negative floats compare
 // as integers)
-__global__ void k_form_k(const float2* __restrict__ kc_raw, int nx, int ny, float mu, float lam, float gam,
+// (volumes: k_d = 6 - 2 cos - 2 cos - 2 cos; with nz = 1 the z term vanishes and this is the 2D
+// formula)
+__global__ void k_form_k(const float2* __restrict__ kc_raw, int nx, int ny, int nz, float mu, float lam, float gam,
                          float inv_n, float* __restrict__ k, unsigned* __restrict__ kmax) {
     const int b = blockIdx.y;
-    const int n = nx * ny;
+    const int n = nx * ny * nz;
     float local = 0.f;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const int kx = i % nx, ky = i / nx;
-        const float kd = 4.f - 2.f * cospif(2.f * kx / nx) - 2.f * cospif(2.f * ky / ny);
+        const int kx = i % nx, ky = (i / nx) % ny, kz = i / (nx * ny);
+        const float kd = 6.f - 2.f * cospif(2.f * kx / nx) - 2.f * cospif(2.f * ky / ny) -
+                         2.f * cospif(2.f * kz / nz);
         const float kc = kc_raw[(size_t)b * n + i].x * inv_n;
         const float v = fmaf(mu, kc, fmaf(lam, kd, gam));
         k[(size_t)b * n + i] = v;
@@ -138,10 +141,11 @@ __global__ void k_clamp_invert(float* __restrict__ k, float* __restrict__ invk, 
     }
 }
 
-// Jacobi: w = 1 / diag(A), diag(A)_j = mu (nnz(r)/N) sum_c |S_c[j]|^2 + 4 lam + gam
-// ((S^H F^H R F S)_jj = |s_j|^2 (F^H R F)_jj = |s_j|^2 nnz(r)/N; each D_a^H D_a adds 2)
+// Jacobi: w = 1 / diag(A), diag(A)_j = mu (nnz(r)/N) sum_c |S_c[j]|^2 + 2 ndim lam + gam
+// ((S^H F^H R F S)_jj = |s_j|^2 (F^H R F)_jj = |s_j|^2 nnz(r)/N; each D_a^H D_a adds 2).
+// `ny` here counts the readout lines of one slice or volume (ny nz for a volume).
 __global__ void k_jacobi_diag(const float2* __restrict__ sens, const float* __restrict__ maskw, int n, int ny, int nc,
-                              float mu, float lam, float gam, float* __restrict__ w) {
+                              float mu, float lam, float gam, float tvd, float* __restrict__ w) {
     const int b = blockIdx.y;
     __shared__ float frac_s;
     if (threadIdx.x < 32) {
@@ -156,7 +160,7 @@ __global__ void k_jacobi_diag(const float2* __restrict__ sens, const float* __re
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         float p = 0.f;
         for (int c = 0; c < nc; ++c) p += cabs2(sens[((size_t)b * nc + c) * n + i]);
-        w[(size_t)b * n + i] = 1.f / fmaf(mu * frac, p, 4.f * lam + gam);
+        w[(size_t)b * n + i] = 1.f / fmaf(mu * frac, p, tvd * lam + gam);
     }
 }
 
@@ -252,20 +256,21 @@ cudaError_t launch_mul_conj(const Dims& d, float2* R, const float2* G, cudaStrea
     return cudaGetLastError();
 }
 
-cudaError_t launch_jacobi_diag(const Dims& d, const float2* sens, const float* maskw, float mu, float lam, float gam,
-                               float* w, cudaStream_t s) {
-    const int n = d.nx * d.ny;
-    k_jacobi_diag<<<dim3(elem_blocks(n), d.nb), 256, 0, s>>>(sens, maskw, n, d.ny, d.nc, mu, lam, gam, w);
+cudaError_t launch_jacobi_diag(const Dims& d, int nz, const float2* sens, const float* maskw, float mu, float lam,
+                               float gam, float* w, cudaStream_t s) {
+    const int n = d.nx * d.ny * nz;
+    k_jacobi_diag<<<dim3(elem_blocks(n), d.nb), 256, 0, s>>>(sens, maskw, n, d.ny * nz, d.nc, mu, lam, gam,
+                                                             nz > 1 ? 6.f : 4.f, w);
     return cudaGetLastError();
 }
 
-cudaError_t launch_finish_k(const Dims& d, const float2* kc_raw, float mu, float lam, float gam, float* k,
+cudaError_t launch_finish_k(const Dims& d, int nz, const float2* kc_raw, float mu, float lam, float gam, float* k,
                             float* invk, unsigned* kmax, cudaStream_t s) {
-    const int n = d.nx * d.ny;
+    const int n = d.nx * d.ny * nz;
     cudaError_t e = cudaMemsetAsync(kmax, 0, sizeof(unsigned) * d.nb, s);
     if (e != cudaSuccess) return e;
     const dim3 grid(elem_blocks(n), d.nb);
-    k_form_k<<<grid, 256, 0, s>>>(kc_raw, d.nx, d.ny, mu, lam, gam, 1.f / n, k, kmax);
+    k_form_k<<<grid, 256, 0, s>>>(kc_raw, d.nx, d.ny, nz, mu, lam, gam, 1.f / n, k, kmax);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_clamp_invert<<<grid, 256, 0, s>>>(k, invk, n, kmax);
     return cudaGetLastError();

@@ -92,7 +92,7 @@ cudaError_t launch_vec_plain(const Dims& d, int mode, float2* x, float2* r, floa
                              const float2* q, const float* w, SliceState* st, double tol2, Red red,
                              cudaStream_t s);
 // w = 1 / (mu nnz(r)/N sum_c |S_c|^2 + 4 lambda + gamma): the inverse diagonal of A (Jacobi).
-cudaError_t launch_jacobi_diag(const Dims& d, const float2* sens, const float* maskw, float mu, float lam,
+cudaError_t launch_jacobi_diag(const Dims& d, int nz, const float2* sens, const float* maskw, float mu, float lam,
                                float gam, float* w, cudaStream_t s);
 
 // r = b - q, ||b||^2, ||r||^2, initial convergence test and state.
@@ -121,8 +121,8 @@ cudaError_t launch_mask_to_complex(const Dims& d, const uint8_t* mask, float2* o
 cudaError_t launch_mul_conj(const Dims& d, float2* R, const float2* G, cudaStream_t s);
 // k = mu Re(kc)/N + lam k_d + gam, clamped; invk = 1 / (k N).
 // kmax: nb words of scratch.
-cudaError_t launch_finish_k(const Dims& d, const float2* kc_unscaled, float mu, float lam,
-                            float gam, float* k, float* invk, unsigned* kmax, cudaStream_t s);
+cudaError_t launch_finish_k(const Dims& d, int nz, const float2* kc_unscaled, float mu, float lam, float gam,
+                            float* k, float* invk, unsigned* kmax, cudaStream_t s);
 
 // ------------------------------------------------------------------ Split Bregman (k_sb.cu)
 struct SbFields {
@@ -136,6 +136,8 @@ struct SbFields {
     const float2* by;
     float2* bx_new;       // ... after it (written; the caller swaps the two buffers)
     float2* by_new;
+    const float2* bz;     // volumes: b_z before / after (nullptr in 2D)
+    float2* bz_new;
     float2* bw;           // wavelet Bregman variable, tile-local Mallat layout, in place
     float2* g;            // lam Dx^H(dx-bx) + lam Dy^H(dy-by) + gam W^H(dw-bw)
     float2* bd;           // [nb][N]: data term of b for the current y^[j]: sum_c S_c^H F^H R y_c^[j]
@@ -162,5 +164,26 @@ size_t rhs_smem_bytes(int ny, int ms);
 // Shrink + Bregman updates (steps 6-11) and the next g.
 cudaError_t launch_sb_update(const Dims& d, const SbFields& f, const float2* x, int levels,
                              float lam, float gam, float tau_tv, float tau_w, cudaStream_t s);
+
+// ---- volumes (k_vol.cu): Dims are per plane (nx, ny, nc, nb volumes), nz planes each
+// DFT along y of every plane (nplanes = nb * nz); st (optional) filters by volume.
+cudaError_t launch_col_dft(int nx, int ny, int nplanes, int nz, float2* data, const float2* tw_y, bool inv,
+                           const SliceState* st, cudaStream_t s);
+// U[b][c] = DFT_y(S_c v) per plane.
+cudaError_t launch_g3_fwd_y(const Dims& d, int nz, const float2* sens, const float2* v, float2* U, const float2* tw_y,
+                            const SliceState* st, cudaStream_t s);
+// DFT_z, mask operation (mode 0: A; 1: right-hand side with the outer update if addback;
+// 2: back-projection of yt1), IDFT_z.
+cudaError_t launch_g3_z(const Dims& d, int nz, int mode, int addback, float2* U, const int* slot, float2* yt,
+                        const float2* yt1, int ms, const float2* tw_z, const SliceState* st, cudaStream_t s);
+// IDFT_y, coil combine and the epilogue of the mode (0: q = A p, flag = PCG; 1: right-hand side,
+// flag = addback; 2: bd1, bd and the RSS start if write_x).
+cudaError_t launch_g3_inv_y(const Dims& d, int nz, int mode, int flag, const float2* U, const SbFields& f,
+                            const float2* vin, float2* out, int write_x, const float2* tw_y, float mu, float lam,
+                            float gam, SliceState* st, double tol2, Red red, cudaStream_t s);
+// Steps 6-11 of Algorithm 1 on 16^3 tiles (levels <= 4).
+cudaError_t launch_sb_update3(const Dims& d, int nz, const SbFields& f, const float2* x, int levels, float lam,
+                              float gam, float tau_tv, float tau_w, cudaStream_t s);
+
 
 }  // namespace sb

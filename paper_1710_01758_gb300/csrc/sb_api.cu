@@ -69,6 +69,11 @@ struct sb_plan_s {
     const float2* sens = nullptr;
     bool have_coils = false, have_mask = false;
     bool fused_precond = false;  // circulant M^{-1} as one cluster launch per PCG iteration
+    // volumes: dims is the rows view {nx, ny nz, Nc, nb}; the planes are ny_plane x nx, nz of them
+    int nz = 1, ny_plane = 0;
+    size_t maxparts = kMaxParts;  // per-slice capacity of the cross-CTA partial sums
+    float2* tw_z = nullptr;
+    float2* bz[2] = {nullptr, nullptr};
     std::string err;
 
     float2* tw_x = nullptr;
@@ -268,13 +273,59 @@ void bind_exec(sb_plan pl, Exec& ex, int b0, int nb, cudaStream_t s) {
     ex.s = s;
     ex.st = pl->st + b0;
     ex.h_st = pl->h_st + b0;
-    ex.red = Red{pl->part + (size_t)b0 * kMaxParts * 2, pl->counter + b0, pl->derr};
+    ex.red = Red{pl->part + (size_t)b0 * pl->maxparts * 2, pl->counter + b0, pl->derr};
 }
 
 // pointer to slice b0 of an array whose slices hold `per` elements
 template <class T>
 T* at(T* base, const Exec& ex, size_t per) {
     return base + (size_t)ex.b0 * per;
+}
+
+// ---- volumes (nz > 1): the data term as three passes through the coil scratch (k_vol.cu)
+Dims plane_dims(const Exec& ex) { return Dims{ex.d.nx, ex.pl->ny_plane, ex.d.nc, ex.d.nb}; }
+
+// out = A v on the context's volumes; pcg: PCG mode (inactive volumes skipped, p^H q, alpha)
+sb_status vol_apply_A(Exec& ex, const float2* v, float2* out, bool pcg) {
+    sb_plan pl = ex.pl;
+    const Dims dp = plane_dims(ex);
+    const size_t n = pl->n;
+    float2* U = at(pl->spec, ex, (size_t)dp.nc * n);
+    const float2* sens = at(pl->sens, ex, (size_t)dp.nc * n);
+    const SliceState* stf = pcg ? ex.st : nullptr;
+    SbFields f{};
+    f.sens = sens;
+    const float mu = (float)pl->d.mu, lam = (float)pl->d.lambda, gam = (float)pl->d.gamma;
+    SB_LAUNCH(ex, SB_KCLASS_APPLY_A, 1, launch_g3_fwd_y(dp, pl->nz, sens, v, U, pl->tw_y, stf, ex.s));
+    SB_LAUNCH(ex, SB_KCLASS_APPLY_A, 1,
+              launch_g3_z(dp, pl->nz, 0, 0, U, at(pl->slot, ex, (size_t)ex.d.ny), nullptr, nullptr, pl->ms,
+                          pl->tw_z, stf, ex.s));
+    SB_LAUNCH(ex, SB_KCLASS_APPLY_A, 1,
+              launch_g3_inv_y(dp, pl->nz, 0, pcg ? 1 : 0, U, f, v, out, 0, pl->tw_y, mu, lam, gam, ex.st, 0.0, ex.red,
+                              ex.s));
+    return SB_OK;
+}
+
+// M^{-1} = F^H diag(k)^{-1} F on volumes: DFT along x (rows), y (per plane), z with 1/(kN) and
+// r^H z, then the inverses.  phase 0: out = M^{-1} r; 1: CG start (p = z, rho); 2: CG step
+// (r -= alpha q and the stop test first; x += alpha p, p = z + beta p after).
+sb_status vol_precond(Exec& ex, int phase, float2* r, const float2* q, float2* x, float2* p, float2* out,
+                      double tol2) {
+    sb_plan pl = ex.pl;
+    const Dims& d = ex.d;  // rows view
+    const int nyp = pl->ny_plane, nz = pl->nz;
+    const Dims dz{d.nx * nyp, nz, d.nc, d.nb};  // z columns
+    SliceState* st = phase ? ex.st : nullptr;
+    float2* tb = at(pl->tb, ex, pl->n);
+    const float* invk = at(pl->invk, ex, pl->n);
+    SB_LAUNCH(ex, SB_KCLASS_PRECOND_ROW_FWD, 1,
+              launch_row_fwd(d, phase == 2 ? 1 : 0, r, q, tb, pl->tw_x, st, tol2, ex.red, ex.s));
+    SB_LAUNCH(ex, SB_KCLASS_PRECOND_COL, 1, launch_col_dft(d.nx, nyp, d.nb * nz, nz, tb, pl->tw_y, false, st, ex.s));
+    SB_LAUNCH(ex, SB_KCLASS_PRECOND_COL, 1,
+              launch_col_precond(dz, tb, invk, pl->tw_z, st, phase == 1 ? 1 : 0, ex.red, ex.s));
+    SB_LAUNCH(ex, SB_KCLASS_PRECOND_COL, 1, launch_col_dft(d.nx, nyp, d.nb * nz, nz, tb, pl->tw_y, true, st, ex.s));
+    SB_LAUNCH(ex, SB_KCLASS_PRECOND_ROW_INV, 1, launch_row_inv(d, phase, tb, out, x, p, pl->tw_x, st, ex.red, ex.s));
+    return SB_OK;
 }
 
 // Sequence CG on the context's slices from the state left by launch_resid_init / launch_rhs
@@ -298,7 +349,10 @@ sb_status pcg_run(Exec& ex, const sb_pcg_opts& o, float2* x_full, sb_pcg_result*
 
     SB_LAUNCH(ex, SB_KCLASS_VEC, 1, launch_zero_rhs_slices(d, x, ex.st, s));
     const bool fused = circ && pl->fused_precond;
-    if (fused) {
+    const bool vol = pl->nz > 1;
+    if (circ && vol) {
+        if (sb_status e = vol_precond(ex, 1, r, nullptr, x, p, nullptr, tol2)) return e;
+    } else if (fused) {
         SB_LAUNCH(ex, SB_KCLASS_PRECOND_FUSED, 1,
                   launch_precond_fused(d, 0, x, r, p, nullptr, invk, pl->tw_x, pl->tw_y, ex.st, tol2, s));
     } else if (circ) {
@@ -313,9 +367,15 @@ sb_status pcg_run(Exec& ex, const sb_pcg_opts& o, float2* x_full, sb_pcg_result*
     while (it < nit) {
         const int g = std::min(kPollEvery, nit - it);
         for (int i = 0; i < g; ++i) {
-            SB_LAUNCH(ex, SB_KCLASS_APPLY_A, 1,
-                      launch_apply_A(d, ex.smap_sw, p, q, maskw, pl->tw_y, mu, lam, gam, ex.st, red, s));
-            if (fused) {
+            if (vol) {
+                if (sb_status e = vol_apply_A(ex, p, q, true)) return e;
+            } else {
+                SB_LAUNCH(ex, SB_KCLASS_APPLY_A, 1,
+                          launch_apply_A(d, ex.smap_sw, p, q, maskw, pl->tw_y, mu, lam, gam, ex.st, red, s));
+            }
+            if (circ && vol) {
+                if (sb_status e = vol_precond(ex, 2, r, q, x, p, nullptr, tol2)) return e;
+            } else if (fused) {
                 SB_LAUNCH(ex, SB_KCLASS_PRECOND_FUSED, 1,
                           launch_precond_fused(d, 1, x, r, p, q, invk, pl->tw_x, pl->tw_y, ex.st, tol2, s));
             } else if (circ) {
@@ -435,6 +495,8 @@ sb_status sb_run(Exec& ex, const sb_sb_opts& o, const float2* y_full, float2* x_
     int cur = 0;
     SB_XCK(ex, cudaMemsetAsync(at(pl->bx[0], ex, n), 0, sizeof(float2) * nb * n, s));
     SB_XCK(ex, cudaMemsetAsync(at(pl->by[0], ex, n), 0, sizeof(float2) * nb * n, s));
+    const bool vol = pl->nz > 1;
+    if (vol) SB_XCK(ex, cudaMemsetAsync(at(pl->bz[0], ex, n), 0, sizeof(float2) * nb * n, s));
     SB_XCK(ex, cudaMemsetAsync(at(pl->bw, ex, n), 0, sizeof(float2) * nb * n, s));
     SB_XCK(ex, cudaMemsetAsync(at(pl->g, ex, n), 0, sizeof(float2) * nb * n, s));
     auto fields = [&]() {
@@ -449,13 +511,26 @@ sb_status sb_run(Exec& ex, const sb_sb_opts& o, const float2* y_full, float2* x_
         f.by = at(pl->by[cur], ex, n);
         f.bx_new = at(pl->bx[cur ^ 1], ex, n);
         f.by_new = at(pl->by[cur ^ 1], ex, n);
+        f.bz = vol ? at(pl->bz[cur], ex, n) : nullptr;
+        f.bz_new = vol ? at(pl->bz[cur ^ 1], ex, n) : nullptr;
         f.bw = at(pl->bw, ex, n);
         f.g = at(pl->g, ex, n);
         f.bd = at(pl->bd, ex, n);
         f.bd1 = at(pl->bd1, ex, n);
         return f;
     };
-    SB_LAUNCH(ex, SB_KCLASS_OTHER, 1, launch_rss(d, fields(), x, o.init_rss ? 1 : 0, pl->tw_y, s));
+    const Dims dp = plane_dims(ex);
+    float2* U = at(pl->spec, ex, (size_t)d.nc * n);
+    if (vol) {
+        SbFields f0 = fields();
+        SB_LAUNCH(ex, SB_KCLASS_OTHER, 1,
+                  launch_g3_z(dp, pl->nz, 2, 0, U, f0.slot, f0.yt, f0.yt1, (int)ms, pl->tw_z, nullptr, s));
+        SB_LAUNCH(ex, SB_KCLASS_OTHER, 1,
+                  launch_g3_inv_y(dp, pl->nz, 2, 0, U, f0, nullptr, x, o.init_rss ? 1 : 0, pl->tw_y, mu, lam, gam,
+                                  ex.st, 0.0, ex.red, s));
+    } else {
+        SB_LAUNCH(ex, SB_KCLASS_OTHER, 1, launch_rss(d, fields(), x, o.init_rss ? 1 : 0, pl->tw_y, s));
+    }
 
     sb_status first_err = SB_OK;
     int solve = 0;
@@ -463,15 +538,30 @@ sb_status sb_run(Exec& ex, const sb_sb_opts& o, const float2* y_full, float2* x_
     for (int j = 0; j < o.n_outer; ++j) {
         for (int k = 0; k < o.n_inner; ++k, ++solve) {
             const int addback = (j > 0 && k == 0);
-            SB_LAUNCH(ex, SB_KCLASS_RHS, 1,
-                      launch_rhs(d, ex.smap, ex.ymap, ex.y1map, fields(), addback, x, r, pl->tw_y, mu, lam, gam, ex.st,
-                                 tol2, ex.red, s));
+            if (vol) {
+                SbFields f1 = fields();
+                SB_LAUNCH(ex, SB_KCLASS_RHS, 1, launch_g3_fwd_y(dp, pl->nz, f1.sens, x, U, pl->tw_y, nullptr, s));
+                SB_LAUNCH(ex, SB_KCLASS_RHS, 1,
+                          launch_g3_z(dp, pl->nz, 1, addback, U, f1.slot, f1.yt, f1.yt1, (int)ms, pl->tw_z, nullptr, s));
+                SB_LAUNCH(ex, SB_KCLASS_RHS, 1,
+                          launch_g3_inv_y(dp, pl->nz, 1, addback, U, f1, x, r, 0, pl->tw_y, mu, lam, gam, ex.st, tol2,
+                                          ex.red, s));
+            } else {
+                SB_LAUNCH(ex, SB_KCLASS_RHS, 1,
+                          launch_rhs(d, ex.smap, ex.ymap, ex.y1map, fields(), addback, x, r, pl->tw_y, mu, lam, gam,
+                                     ex.st, tol2, ex.red, s));
+            }
             sb_status ps = pcg_run(ex, o.pcg, x_full, h_last, iters + solve, nsolve);
             if (ps == SB_ERR_TIMEOUT || ps == SB_ERR_CUDA) return ps;
             if (ps != SB_OK && first_err == SB_OK) first_err = ps;
             const bool last = (j == o.n_outer - 1) && (k == o.n_inner - 1);
             if (!last) {
-                SB_LAUNCH(ex, SB_KCLASS_SB_UPDATE, 1, launch_sb_update(d, fields(), x, levels, lam, gam, tau_tv, tau_w, s));
+                if (vol)
+                    SB_LAUNCH(ex, SB_KCLASS_SB_UPDATE, 1,
+                              launch_sb_update3(dp, pl->nz, fields(), x, levels, lam, gam, tau_tv, tau_w, s));
+                else
+                    SB_LAUNCH(ex, SB_KCLASS_SB_UPDATE, 1,
+                              launch_sb_update(d, fields(), x, levels, lam, gam, tau_tv, tau_w, s));
                 if (lam != 0.f) cur ^= 1;
             }
         }
@@ -508,12 +598,16 @@ sb_status sb_plan_create(const sb_plan_desc* desc, void* cuda_stream, sb_plan* o
     if (!desc || !out) return SB_ERR_INVALID_ARG;
     *out = nullptr;
     const sb_plan_desc& d = *desc;
-    if (d.ndim != 2 || (d.nz != 1 && d.nz != 0) || d.ncoils < 1 || d.nbatch < 1 || !(d.mu > 0.0) ||
+    const bool vol = d.ndim == 3;
+    if ((d.ndim != 2 && d.ndim != 3) || (!vol && d.nz != 1 && d.nz != 0) || d.ncoils < 1 || d.nbatch < 1 ||
+        !(d.mu > 0.0) ||
         !(d.lambda >= 0.0) || !(d.gamma >= 0.0) || d.wavelet_levels < 0 || d.groups < 0 ||
         (d.precond_passes != 0 && d.precond_passes != 1 && d.precond_passes != 3))
         return SB_ERR_INVALID_ARG;
-    if (!supported_n(d.nx) || !supported_n(d.ny) || d.wavelet_levels > 5 || d.prec != SB_PREC_FP32)
+    if (!supported_n(d.nx) || !supported_n(d.ny) || d.wavelet_levels > (vol ? 4 : 5) || d.prec != SB_PREC_FP32 ||
+        (vol && (!supported_n(d.nz) || d.precond_passes == 1)))
         return SB_ERR_UNSUPPORTED;
+    const int nz = vol ? d.nz : 1;
     // the fused preconditioner (opt-in) needs a slice on one cluster that fits the device
     bool fused = false;
     if (d.precond_passes == 1) {
@@ -524,10 +618,16 @@ sb_status sb_plan_create(const sb_plan_desc* desc, void* cuda_stream, sb_plan* o
     if (!pl) return SB_ERR_INVALID_ARG;
     pl->d = d;
     pl->fused_precond = fused;
-    pl->d.nz = 1;
+    pl->d.nz = nz;
+    pl->nz = nz;
+    pl->ny_plane = d.ny;
     pl->stream = static_cast<cudaStream_t>(cuda_stream);
-    pl->dims = Dims{d.nx, d.ny, d.ncoils, d.nbatch};
-    pl->n = (size_t)d.nx * d.ny;
+    pl->dims = Dims{d.nx, d.ny * nz, d.ncoils, d.nbatch};
+    pl->n = (size_t)d.nx * d.ny * nz;
+    // CTAs per slice of the widest cross-CTA reduction: rows / 16, column tiles x planes, and
+    // the z-columns of a volume (ny nx / 16)
+    pl->maxparts = std::max<size_t>({(size_t)kMaxParts, (size_t)d.ny * nz / 16, (size_t)d.nx / 16 * nz,
+                                     vol ? (size_t)d.ny * d.nx / 16 : (size_t)0});
     const size_t nb = d.nbatch, n = pl->n;
     cudaError_t e = cudaGetDevice(&pl->device);
     auto bail = [&](const char* what) {
@@ -541,8 +641,9 @@ sb_status sb_plan_create(const sb_plan_desc* desc, void* cuda_stream, sb_plan* o
     if ((e = dalloc(&(ptr), (count))) != cudaSuccess) return bail("cudaMalloc " #ptr);
     ALLOC(pl->tw_x, d.nx);
     ALLOC(pl->tw_y, d.ny);
-    ALLOC(pl->maskw, nb * d.ny);
-    ALLOC(pl->slot, nb * d.ny);
+    ALLOC(pl->tw_z, nz);
+    ALLOC(pl->maskw, nb * d.ny * nz);
+    ALLOC(pl->slot, nb * d.ny * nz);
     ALLOC(pl->k, nb * n);
     ALLOC(pl->invk, nb * n);
     ALLOC(pl->r, nb * n);
@@ -550,17 +651,19 @@ sb_status sb_plan_create(const sb_plan_desc* desc, void* cuda_stream, sb_plan* o
     ALLOC(pl->q, nb * n);
     ALLOC(pl->tb, nb * n);
     ALLOC(pl->st, nb);
-    ALLOC(pl->part, nb * kMaxParts * 2);
+    ALLOC(pl->part, nb * pl->maxparts * 2);
     ALLOC(pl->counter, nb);
     ALLOC(pl->kmax, nb);
     ALLOC(pl->derr, 1);
 #undef ALLOC
     if ((e = cudaMallocHost(reinterpret_cast<void**>(&pl->h_st), sizeof(SliceState) * nb)) != cudaSuccess)
         return bail("cudaMallocHost");
-    const std::vector<float2> tx = twiddles(d.nx), ty = twiddles(d.ny);
+    const std::vector<float2> tx = twiddles(d.nx), ty = twiddles(d.ny), tz = twiddles(nz > 1 ? nz : 32);
     if ((e = cudaMemcpy(pl->tw_x, tx.data(), sizeof(float2) * d.nx, cudaMemcpyHostToDevice)) != cudaSuccess)
         return bail("cudaMemcpy twiddles");
     if ((e = cudaMemcpy(pl->tw_y, ty.data(), sizeof(float2) * d.ny, cudaMemcpyHostToDevice)) != cudaSuccess)
+        return bail("cudaMemcpy twiddles");
+    if ((e = cudaMemcpy(pl->tw_z, tz.data(), sizeof(float2) * nz, cudaMemcpyHostToDevice)) != cudaSuccess)
         return bail("cudaMemcpy twiddles");
     if ((e = cudaMemset(pl->counter, 0, sizeof(unsigned) * nb)) != cudaSuccess) return bail("cudaMemset");
     if ((e = cudaMemset(pl->derr, 0, sizeof(unsigned))) != cudaSuccess) return bail("cudaMemset");
@@ -598,7 +701,8 @@ sb_status sb_plan_destroy(sb_plan pl) {
                     (void*)pl->bx[0], (void*)pl->bx[1], (void*)pl->by[0], (void*)pl->by[1], (void*)pl->bw,
                     (void*)pl->g, (void*)pl->bd, (void*)pl->bd1, (void*)pl->yt, (void*)pl->yt1, (void*)pl->st,
                     (void*)pl->part, (void*)pl->counter, (void*)pl->kmax, (void*)pl->derr, (void*)pl->spec,
-                    (void*)pl->gb, (void*)pl->rb, (void*)pl->line_val, (void*)pl->line_uni, (void*)pl->jw})
+                    (void*)pl->gb, (void*)pl->rb, (void*)pl->line_val, (void*)pl->line_uni, (void*)pl->jw,
+                    (void*)pl->tw_z, (void*)pl->bz[0], (void*)pl->bz[1]})
         dfree(p);
     if (pl->h_st) cudaFreeHost(pl->h_st);
     auto release = [](Exec& ex) {
@@ -632,8 +736,11 @@ sb_status sb_set_coils(sb_plan pl, const void* d_sens) {
         const int box = coil_box_rows(d.ny);  // a TMA box spans at most 256 rows
         return encode_rows(&ex.smap, base, d.nx, rows, box) && encode_rows(&ex.smap_sw, base, d.nx, rows, box, true);
     };
-    bool ok = enc(pl->whole);
-    for (Exec& ex : pl->groups) ok = ok && enc(ex);
+    bool ok = true;
+    if (pl->nz == 1) {  // the TMA coil-tile maps serve the 2D kernels only
+        ok = enc(pl->whole);
+        for (Exec& ex : pl->groups) ok = ok && enc(ex);
+    }
     if (!ok) return fail(pl, SB_ERR_CUDA, "cuTensorMapEncodeTiled failed for the sensitivities");
     pl->sens = static_cast<const float2*>(d_sens);
     pl->have_coils = true;
@@ -702,24 +809,29 @@ sb_status sb_set_mask(sb_plan pl, const uint8_t* d_mask) {
     float2 *spec = pl->spec, *gb = pl->gb, *rb = pl->rb;
     const int nimg_c = d.nb * d.nc;
     SB_CK(pl, cudaMemcpyAsync(spec, pl->sens, sizeof(float2) * nb * d.nc * n, cudaMemcpyDeviceToDevice, s));
+    // unnormalised 2D / 3D DFT of nimg images: rows (x), per-plane columns (y), z columns
+    const int nyp = pl->ny_plane, nz = pl->nz;
+    const Dims dp{d.nx, nyp, d.nc, d.nb};  // plane dims
+    auto fft_nd = [&](float2* data, int nimg, bool inv) -> sb_status {
+        SB_LAUNCH(ex, SB_KCLASS_OTHER, 1, launch_fft_rows(d.nx, d.ny, nimg, data, pl->tw_x, inv, s));
+        SB_LAUNCH(ex, SB_KCLASS_OTHER, 1, launch_fft_cols(d.nx, nyp, nimg * nz, data, pl->tw_y, inv, s));
+        if (nz > 1) SB_LAUNCH(ex, SB_KCLASS_OTHER, 1, launch_fft_cols(d.nx * nyp, nz, nimg, data, pl->tw_z, inv, s));
+        return SB_OK;
+    };
     auto build_k = [&]() -> sb_status {
-        SB_LAUNCH(ex, SB_KCLASS_OTHER, 1, launch_fft_rows(d.nx, d.ny, nimg_c, spec, pl->tw_x, false, s));
-        SB_LAUNCH(ex, SB_KCLASS_OTHER, 1, launch_fft_cols(d.nx, d.ny, nimg_c, spec, pl->tw_y, false, s));
+        if (sb_status e2 = fft_nd(spec, nimg_c, false)) return e2;
         SB_LAUNCH(ex, SB_KCLASS_OTHER, 1, launch_coil_power(d, spec, gb, s));
         SB_LAUNCH(ex, SB_KCLASS_OTHER, 1, launch_mask_to_complex(d, d_mask, rb, s));
-        SB_LAUNCH(ex, SB_KCLASS_OTHER, 1, launch_fft_rows(d.nx, d.ny, d.nb, gb, pl->tw_x, false, s));
-        SB_LAUNCH(ex, SB_KCLASS_OTHER, 1, launch_fft_cols(d.nx, d.ny, d.nb, gb, pl->tw_y, false, s));
-        SB_LAUNCH(ex, SB_KCLASS_OTHER, 1, launch_fft_rows(d.nx, d.ny, d.nb, rb, pl->tw_x, false, s));
-        SB_LAUNCH(ex, SB_KCLASS_OTHER, 1, launch_fft_cols(d.nx, d.ny, d.nb, rb, pl->tw_y, false, s));
+        if (sb_status e2 = fft_nd(gb, d.nb, false)) return e2;
+        if (sb_status e2 = fft_nd(rb, d.nb, false)) return e2;
         SB_LAUNCH(ex, SB_KCLASS_OTHER, 1, launch_mul_conj(d, rb, gb, s));
-        SB_LAUNCH(ex, SB_KCLASS_OTHER, 1, launch_fft_rows(d.nx, d.ny, d.nb, rb, pl->tw_x, true, s));
-        SB_LAUNCH(ex, SB_KCLASS_OTHER, 1, launch_fft_cols(d.nx, d.ny, d.nb, rb, pl->tw_y, true, s));
+        if (sb_status e2 = fft_nd(rb, d.nb, true)) return e2;
         SB_LAUNCH(ex, SB_KCLASS_OTHER, 2,
-                  launch_finish_k(d, rb, (float)pl->d.mu, (float)pl->d.lambda, (float)pl->d.gamma, pl->k, pl->invk,
-                                  pl->kmax, s));
+                  launch_finish_k(dp, nz, rb, (float)pl->d.mu, (float)pl->d.lambda, (float)pl->d.gamma, pl->k,
+                                  pl->invk, pl->kmax, s));
         SB_LAUNCH(ex, SB_KCLASS_OTHER, 1,
-                  launch_jacobi_diag(d, pl->sens, pl->maskw, (float)pl->d.mu, (float)pl->d.lambda, (float)pl->d.gamma,
-                                     pl->jw, s));
+                  launch_jacobi_diag(dp, nz, pl->sens, pl->maskw, (float)pl->d.mu, (float)pl->d.lambda,
+                                     (float)pl->d.gamma, pl->jw, s));
         return SB_OK;
     };
     if ((st = build_k()) != SB_OK) return fail(pl, st, ex.err);
@@ -739,13 +851,17 @@ sb_status sb_set_mask(sb_plan pl, const uint8_t* d_mask) {
     const size_t yrow = (size_t)d.nc * ms * d.nx;
     auto enc = [&](Exec& e2) {
         const size_t rows = (size_t)e2.d.nb * d.nc * ms;
-        if (ms > 256) return true;  // no compact-row maps: sb_split_bregman refuses this mask
+        if (ms > 256 || pl->nz > 1) return true;  // no compact-row maps (2D RHS kernel only)
         return encode_rows(&e2.ymap, pl->yt + e2.b0 * yrow, d.nx, rows, ms) &&
                encode_rows(&e2.y1map, pl->yt1 + e2.b0 * yrow, d.nx, rows, ms);
     };
     bool ok = enc(pl->whole);
     for (Exec& e2 : pl->groups) ok = ok && enc(e2);
     if (!ok) return fail(pl, SB_ERR_CUDA, "cuTensorMapEncodeTiled failed for the k-space rows");
+    if (pl->nz > 1 && !pl->bz[0]) {
+        SB_CK(pl, dalloc(&pl->bz[0], nb * n));
+        SB_CK(pl, dalloc(&pl->bz[1], nb * n));
+    }
     if (!pl->g) {
         SB_CK(pl, dalloc(&pl->bx[0], nb * n));
         SB_CK(pl, dalloc(&pl->bx[1], nb * n));
@@ -772,6 +888,7 @@ sb_status sb_apply_A(sb_plan pl, const void* d_x, void* d_y) {
     if (!d_x || !d_y || d_x == d_y) return fail(pl, SB_ERR_INVALID_ARG, "need distinct non-null x and y");
     Exec& ex = pl->whole;
     auto go = [&]() -> sb_status {
+        if (pl->nz > 1) return vol_apply_A(ex, static_cast<const float2*>(d_x), static_cast<float2*>(d_y), false);
         SB_LAUNCH(ex, SB_KCLASS_APPLY_A, 1,
                   launch_apply_A(pl->dims, ex.smap_sw, static_cast<const float2*>(d_x), static_cast<float2*>(d_y),
                                  pl->maskw, pl->tw_y, (float)pl->d.mu, (float)pl->d.lambda, (float)pl->d.gamma,
@@ -788,6 +905,9 @@ sb_status sb_apply_precond(sb_plan pl, const void* d_r, void* d_z) {
     Exec& ex = pl->whole;
     const Dims& d = pl->dims;
     auto go = [&]() -> sb_status {
+        if (pl->nz > 1)
+            return vol_precond(ex, 0, const_cast<float2*>(static_cast<const float2*>(d_r)), nullptr, nullptr, nullptr,
+                               static_cast<float2*>(d_z), 0.0);
         SB_LAUNCH(ex, SB_KCLASS_PRECOND_ROW_FWD, 1,
                   launch_row_fwd(d, 0, const_cast<float2*>(static_cast<const float2*>(d_r)), nullptr, pl->tb, pl->tw_x,
                                  nullptr, 0.0, ex.red, pl->stream));
@@ -813,9 +933,13 @@ sb_status sb_pcg_solve(sb_plan pl, const void* d_b, void* d_x, const sb_pcg_opts
         const size_t n = pl->n;
         float2* x = at(x_full, ex, n);
         float2* q = at(pl->q, ex, n);
-        SB_LAUNCH(ex, SB_KCLASS_APPLY_A, 1,
-                  launch_apply_A(ex.d, ex.smap_sw, x, q, at(pl->maskw, ex, (size_t)ex.d.ny), pl->tw_y, (float)pl->d.mu,
-                                 (float)pl->d.lambda, (float)pl->d.gamma, nullptr, ex.red, ex.s));
+        if (pl->nz > 1) {
+            if (sb_status e = vol_apply_A(ex, x, q, false)) return e;
+        } else {
+            SB_LAUNCH(ex, SB_KCLASS_APPLY_A, 1,
+                      launch_apply_A(ex.d, ex.smap_sw, x, q, at(pl->maskw, ex, (size_t)ex.d.ny), pl->tw_y,
+                                     (float)pl->d.mu, (float)pl->d.lambda, (float)pl->d.gamma, nullptr, ex.red, ex.s));
+        }
         SB_LAUNCH(ex, SB_KCLASS_VEC, 1,
                   launch_resid_init(ex.d, at(b_full, ex, n), q, at(pl->r, ex, n), ex.st, tol2, ex.red, ex.s));
         return pcg_run(ex, *o, x_full, h_results, nullptr, 0);
@@ -827,7 +951,7 @@ sb_status sb_split_bregman(sb_plan pl, const void* d_y, void* d_x, const sb_sb_o
     if (!o || !d_y || !d_x) return fail(pl, SB_ERR_INVALID_ARG, "null argument");
     if (o->n_outer < 1 || o->n_inner < 1) return fail(pl, SB_ERR_INVALID_ARG, "n_outer and n_inner must be >= 1");
     if (sb_status s = check_opts(pl, &o->pcg)) return s;
-    if (pl->ms > 256 || rhs_smem_bytes(pl->dims.ny, pl->ms) > 227 * 1024)
+    if (pl->nz == 1 && (pl->ms > 256 || rhs_smem_bytes(pl->dims.ny, pl->ms) > 227 * 1024))
         return fail(pl, SB_ERR_UNSUPPORTED, "too many sampled lines for the shared-memory pipeline of this size");
     const int nsolve = o->n_outer * o->n_inner;
     std::vector<int> iters((size_t)pl->dims.nb * nsolve, 0);

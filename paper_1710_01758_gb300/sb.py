@@ -131,8 +131,10 @@ def _check(status: int, plan=None, allow=()):
 
 
 def plan_desc(nx, ny, ncoils, nbatch, mu, lam, gam, wavelet_levels, prec=SB_PREC_FP32, groups=0,
-              precond_passes=0) -> sb_plan_desc:
-    return sb_plan_desc(2, nx, ny, 1, ncoils, nbatch, mu, lam, gam, wavelet_levels, prec, groups, precond_passes)
+              precond_passes=0, nz=1) -> sb_plan_desc:
+    """nz > 1 describes volumes (ndim = 3) of nz planes."""
+    return sb_plan_desc(3 if nz > 1 else 2, nx, ny, nz, ncoils, nbatch, mu, lam, gam, wavelet_levels, prec, groups,
+                        precond_passes)
 
 
 def sb_plan_create(desc: sb_plan_desc, stream: int = 0) -> int:
@@ -231,15 +233,15 @@ class Plan:
     """Owns an sb_plan and the device tensors it borrows (torch CUDA tensors)."""
 
     def __init__(self, nx, ny, ncoils, nbatch, mu, lam, gam, wavelet_levels, stream=None, groups=0,
-                 precond_passes=0):
+                 precond_passes=0, nz=1):
         import torch
         self.torch = torch
         self.nbatch = nbatch
-        self.shape = (nbatch, ny, nx)
+        self.shape = (nbatch, nz, ny, nx) if nz > 1 else (nbatch, ny, nx)
         s = stream if stream is not None else torch.cuda.current_stream()
         self.stream = s
         self.handle = sb_plan_create(plan_desc(nx, ny, ncoils, nbatch, mu, lam, gam, wavelet_levels, groups=groups,
-                                                       precond_passes=precond_passes),
+                                                       precond_passes=precond_passes, nz=nz),
                                      s.cuda_stream)
         self._sens = None
 

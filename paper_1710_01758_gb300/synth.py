@@ -23,7 +23,7 @@ import math
 
 import numpy as np
 
-# Seeds of the two 2D workloads: seed = SEED_BASE + workload number.
+# Seeds of the workloads: seed = SEED_BASE + workload number.
 SEED_BASE = 1710017580
 
 
@@ -126,6 +126,107 @@ def acquire(x: np.ndarray, sens: np.ndarray, mask: np.ndarray, sigma: float,
     k = np.fft.fft2(coil_imgs, norm="ortho")
     noise = sigma * (rng.standard_normal(k.shape) + 1j * rng.standard_normal(k.shape))
     return (k + noise) * mask[None].astype(np.float64)
+
+
+def _grid3(nz: int, ny: int, nx: int):
+    """Voxel-centre coordinates in [-1, 1) along x, y and z, shaped [nz, ny, nx]."""
+    xs = -1.0 + 2.0 * np.arange(nx) / nx
+    ys = -1.0 + 2.0 * np.arange(ny) / ny
+    zs = -1.0 + 2.0 * np.arange(nz) / nz
+    Z, Y, X = np.meshgrid(zs, ys, xs, indexing="ij")
+    return X, Y, Z
+
+
+def ellipsoid_phantom(nz: int, ny: int, nx: int, rng: np.random.Generator, n_ellipsoids: int = 12) -> np.ndarray:
+    """3D counterpart of ``ellipse_phantom``: ellipsoids painted in order with U[0, 1] intensities
+    (centres U[-0.7, 0.7]^3, semi-axes U[0.05, 0.5]^3, orientation from three angles U[0, pi)),
+    background 0, times the smooth phase exp(i*pi*(a*x + b*y + c*z)), a, b, c ~ U[-0.5, 0.5]."""
+    X, Y, Z = _grid3(nz, ny, nx)
+    img = np.zeros((nz, ny, nx), np.float64)
+    for _ in range(n_ellipsoids):
+        c = rng.uniform(-0.7, 0.7, 3)
+        ax = rng.uniform(0.05, 0.5, 3)
+        a1, a2, a3 = rng.uniform(0.0, math.pi, 3)
+        val = rng.uniform(0.0, 1.0)
+        rz = np.array([[math.cos(a1), -math.sin(a1), 0], [math.sin(a1), math.cos(a1), 0], [0, 0, 1]])
+        ry = np.array([[math.cos(a2), 0, math.sin(a2)], [0, 1, 0], [-math.sin(a2), 0, math.cos(a2)]])
+        rx = np.array([[1, 0, 0], [0, math.cos(a3), -math.sin(a3)], [0, math.sin(a3), math.cos(a3)]])
+        rot = rz @ ry @ rx
+        d = np.stack([X - c[0], Y - c[1], Z - c[2]], axis=-1) @ rot
+        img[np.sum((d / ax) ** 2, axis=-1) <= 1.0] = val
+    pa, pb, pc = rng.uniform(-0.5, 0.5, 3)
+    return img * np.exp(1j * math.pi * (pa * X + pb * Y + pc * Z))
+
+
+def coil_maps_3d(nz: int, ny: int, nx: int, nc: int, rng: np.random.Generator) -> np.ndarray:
+    """Smooth 3D coil sensitivities ``[nc, nz, ny, nx]``: coils alternate between two rings of
+    radius 1.2 at z = -0.5 and z = +0.5, coil c at angle 2*pi*c/nc + theta_0, with the profile
+    and phase of ``coil_maps``; normalised pointwise to sum_c |S_c|^2 = 1."""
+    X, Y, Z = _grid3(nz, ny, nx)
+    theta0 = rng.uniform(0.0, 2.0 * math.pi / nc)
+    maps = np.empty((nc, nz, ny, nx), np.complex128)
+    for c in range(nc):
+        th = 2.0 * math.pi * c / nc + theta0
+        xc, yc, zc = 1.2 * math.cos(th), 1.2 * math.sin(th), (-0.5 if c % 2 == 0 else 0.5)
+        prof = np.exp(-((X - xc) ** 2 + (Y - yc) ** 2 + (Z - zc) ** 2) / (2.0 * 0.6 ** 2))
+        maps[c] = prof * np.exp(1j * th)
+    maps /= np.sqrt(np.sum(np.abs(maps) ** 2, axis=0, keepdims=True))
+    return maps
+
+
+def readout_mask_3d(nz: int, ny: int, nx: int, accel: float, centre: int, rng: np.random.Generator) -> np.ndarray:
+    """3D Cartesian mask with the readout (x) fully sampled: round(ny*nz/accel) (k_y, k_z) lines,
+    a ``centre`` x ``centre`` block around the origin always, the rest drawn without replacement
+    with probability proportional to (1 - r/r_max)^2 (variable density); DFT order, [nz, ny, nx]."""
+    return np.repeat(random_mask(nz, ny, accel, centre, rng)[:, :, None], nx, axis=2)
+
+
+def acquire_nd(x: np.ndarray, sens: np.ndarray, mask: np.ndarray, sigma: float,
+               rng: np.random.Generator) -> np.ndarray:
+    """``acquire`` for images of any dimension (unitary DFT over all image axes)."""
+    axes = tuple(range(1, sens.ndim))
+    k = np.fft.fftn(sens * x[None], axes=axes, norm="ortho")
+    noise = sigma * (rng.standard_normal(k.shape) + 1j * rng.standard_normal(k.shape))
+    return (k + noise) * mask[None].astype(np.float64)
+
+
+@dataclasses.dataclass
+class Volume:
+    """A 3D PI+CS reconstruction workload (readout along x fully sampled)."""
+    name: str
+    nz: int
+    ny: int
+    nx: int
+    ncoils: int
+    accel: float
+    centre: int
+    mu: float
+    lam: float
+    gam: float
+    wavelet_levels: int
+    n_outer: int
+    n_inner: int
+    pcg_tol: float
+    pcg_maxit: int
+    pcg_fixed_iters: int
+    sigma: float = 1e-3
+    seed: int = SEED_BASE + 5
+
+
+# 256 x 256 x 128 volume, 16 coils, (k_y, k_z) lines at R = 8 with a 24 x 24 centre, TV + 4-level
+# Haar, 20 SB iterations, PCG to 1e-3.
+VOLUME_256 = Volume("256x256x128 Nc16 R8 TV+Haar4 20SB PCG-tol1e-3", 128, 256, 256, 16, 8.0, 24,
+                    1.0, 0.05, 0.05, 4, 20, 1, 1e-3, 200, 0)
+
+
+def make_volume(v: Volume, seed: int | None = None) -> "Slice":
+    """One seeded volume of ``v`` (arrays [nz, ny, nx] / [Nc, nz, ny, nx])."""
+    rng = np.random.default_rng(v.seed if seed is None else seed)
+    x = ellipsoid_phantom(v.nz, v.ny, v.nx, rng)
+    s = coil_maps_3d(v.nz, v.ny, v.nx, v.ncoils, rng)
+    m = readout_mask_3d(v.nz, v.ny, v.nx, v.accel, v.centre, rng)
+    y = acquire_nd(x, s, m, v.sigma, rng)
+    return Slice(x, s, m, y)
 
 
 @dataclasses.dataclass
