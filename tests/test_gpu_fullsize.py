@@ -50,3 +50,34 @@ def test_benchmark_batch_sampled_slices():
         err = float(np.linalg.norm(xg[i] - ref.x) / np.linalg.norm(ref.x))
         assert err <= 1e-3, (i, err, diffs)
     plan.close()
+
+
+def test_volume_full_size_operators():
+    """The 256 x 256 x 128 volume with 16 coils and (k_y, k_z) lines at R = 8 (24 x 24 centre):
+    one application of A and of M^{-1}, and k, against the FP64 oracle over the whole volume."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from oracle import operators, precond
+    from paper_1710_01758_gb300 import sb
+
+    v = synth.VOLUME_256
+    rng = np.random.default_rng(v.seed)
+    sens = synth.coil_maps_3d(v.nz, v.ny, v.nx, v.ncoils, rng)
+    mask = synth.readout_mask_3d(v.nz, v.ny, v.nx, v.accel, v.centre, rng)
+    x = synth.random_complex((v.nz, v.ny, v.nx), rng)
+    plan = sb.Plan(v.nx, v.ny, v.ncoils, 1, v.mu, v.lam, v.gam, v.wavelet_levels, nz=v.nz)
+    d_sens = torch.from_numpy(sens[None].astype(np.complex64)).cuda()
+    plan.set_coils(d_sens)
+    plan.set_mask(torch.from_numpy(mask[None]).cuda())
+    q = plan.apply_A(torch.from_numpy(x[None].astype(np.complex64)).cuda()).cpu().numpy()[0]
+    z = plan.apply_precond(torch.from_numpy(x[None].astype(np.complex64)).cuda()).cpu().numpy()[0]
+    kg = plan.k().cpu().numpy()[0]
+    plan.close()
+    del d_sens
+    ref = operators.apply_A(x, sens, mask, v.mu, v.lam, v.gam, 3)
+    assert np.linalg.norm(q - ref) / np.linalg.norm(ref) <= 1e-5
+    kref = precond.k_diag(sens, mask, v.mu, v.lam, v.gam, 3)
+    assert np.max(np.abs(kg - kref)) <= 1e-5 * np.max(kref)
+    zref = precond.apply_precond(x, kref, 3)
+    assert np.linalg.norm(z - zref) / np.linalg.norm(zref) <= 1e-5
