@@ -16,6 +16,11 @@
 //                 MODE 1: the Split Bregman right-hand side and initial residual (as in 2D)
 //                 MODE 2: bd1 = bd = acc and, optionally, x = sqrt(sum_c |u_c|^2) (step 1)
 //
+// The same passes serve 2D slices with an arbitrary mask (nz = 1): k_g2_x replaces k_g3_z with
+// the transform along x and a per-point mask in (k_y, k_x), the k-space data kept whole
+// ([nb][Nc][ny][nx], no hybrid space); the 7-point stencil of k_g3_inv_y reduces to the 5-point
+// one when nz = 1 (both z neighbours are the plane itself).
+//
 // k_col_dft is a plain per-plane DFT along y (the y passes of the 3D preconditioner and of the
 // 3D k construction); k_sb_update3 is steps 6-11 of Algorithm 1 on 16^3 tiles (anisotropic TV
 // in x, y, z and the 3D Haar transform in place, levels <= 4).
@@ -138,6 +143,65 @@ k_g3_z(float2* __restrict__ U, const int* __restrict__ slot, float2* __restrict_
     fft<NZ, true>(u, t, buf1, idx, tw);
 #pragma unroll
     for (int e = 0; e < 16; ++e) U[base + (size_t)(t + T * e) * zs] = u[e];
+}
+
+// ---------------------------------------------------------------------- pass B (along x, 2D)
+template <int N>
+struct RowIdx {
+    int row;
+    __device__ __forceinline__ int operator()(int pos) const { return row * (N + N / 16) + pos + (pos >> 4); }
+};
+constexpr int RY2 = 16;  // rows per CTA
+
+template <int NX, int MODE, bool ADDBACK>
+__global__ void __launch_bounds__(RY2 * NX / 16)
+k_g2_x(float2* __restrict__ U, const uint8_t* __restrict__ mask, float2* __restrict__ yt,
+       const float2* __restrict__ yt1, int ny, int nc, const float2* __restrict__ tw_g, const SliceState* st) {
+    constexpr int T = NX / 16;
+    constexpr int NT = RY2 * T;
+    const int bc = blockIdx.y, b = bc / nc;
+    if (st && st[b].state != ST_ACTIVE) return;
+    extern __shared__ __align__(128) unsigned char smem[];
+    float2* buf0 = reinterpret_cast<float2*>(smem);
+    float2* buf1 = buf0 + RY2 * (NX + NX / 16);
+    float2* tw = buf1 + RY2 * (NX + NX / 16);
+    const int tid = threadIdx.x, t = tid % T, row = tid / T;
+    const int ky = blockIdx.x * RY2 + row;
+    for (int i = tid; i < NX; i += NT) tw[i] = tw_g[i];
+    const size_t base = ((size_t)bc * ny + ky) * NX;
+    const uint8_t* m = mask + ((size_t)b * ny + ky) * NX;
+    const RowIdx<NX> idx{row};
+    float2 u[16];
+    if constexpr (MODE != 2) {
+#pragma unroll
+        for (int e = 0; e < 16; ++e) u[e] = U[base + t + T * e];
+    }
+    __syncthreads();
+    if constexpr (MODE != 2) fft<NX, false>(u, t, buf0, idx, tw);
+    const float nn = (float)NX * (float)ny;
+    const float isq = rsqrtf(nn);
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+        const int kx = t + T * e;
+        if (!m[kx]) {
+            u[e] = make_float2(0.f, 0.f);
+        } else if constexpr (MODE == 0) {
+            u[e] = cscale(u[e], 1.f / nn);
+        } else if constexpr (MODE == 1) {
+            const float2 tt = cscale(u[e], isq);
+            float2 yv = yt[base + kx];
+            if (ADDBACK) {
+                yv = csub(cadd(yv, yt1[base + kx]), tt);
+                yt[base + kx] = yv;
+            }
+            u[e] = cscale(csub(yv, tt), isq);
+        } else {
+            u[e] = cscale(yt1[base + kx], isq);
+        }
+    }
+    fft<NX, true>(u, t, buf1, idx, tw);
+#pragma unroll
+    for (int e = 0; e < 16; ++e) U[base + t + T * e] = u[e];
 }
 
 // ---------------------------------------------------------------------- pass C
@@ -506,6 +570,16 @@ cudaError_t inv_y_n(const Dims& d, int nz, const float2* U, const SbFields& f, c
     return cudaGetLastError();
 }
 
+template <int NX, int MODE, bool AB>
+cudaError_t x_n(const Dims& d, float2* U, const uint8_t* mask, float2* yt, const float2* yt1, const float2* tw,
+                const SliceState* st, cudaStream_t s) {
+    const size_t sm = (2 * RY2 * (NX + NX / 16) + NX) * sizeof(float2);
+    cudaError_t e = prep(k_g2_x<NX, MODE, AB>, sm);
+    if (e != cudaSuccess) return e;
+    k_g2_x<NX, MODE, AB><<<dim3(d.ny / RY2, d.nb * d.nc), RY2 * NX / 16, sm, s>>>(U, mask, yt, yt1, d.ny, d.nc, tw, st);
+    return cudaGetLastError();
+}
+
 #define VOL_SIZES(X) X(32) X(64) X(128) X(192) X(224) X(256) X(320) X(384) X(512)
 
 }  // namespace
@@ -541,6 +615,21 @@ cudaError_t launch_g3_z(const Dims& d, int nz, int mode, int addback, float2* U,
         if (mode == 2) return z_n<N, 2, false>(d, U, slot, yt, yt1, ms, tw_z, st, s); \
         return addback ? z_n<N, 1, true>(d, U, slot, yt, yt1, ms, tw_z, st, s)         \
                        : z_n<N, 1, false>(d, U, slot, yt, yt1, ms, tw_z, st, s);
+        VOL_SIZES(C_)
+#undef C_
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_g2_x(const Dims& d, int mode, int addback, float2* U, const uint8_t* mask, float2* yt,
+                        const float2* yt1, const float2* tw_x, const SliceState* st, cudaStream_t s) {
+    switch (d.nx) {
+#define C_(N)                                                                   \
+    case N:                                                                     \
+        if (mode == 0) return x_n<N, 0, false>(d, U, mask, yt, yt1, tw_x, st, s); \
+        if (mode == 2) return x_n<N, 2, false>(d, U, mask, yt, yt1, tw_x, st, s); \
+        return addback ? x_n<N, 1, true>(d, U, mask, yt, yt1, tw_x, st, s)         \
+                       : x_n<N, 1, false>(d, U, mask, yt, yt1, tw_x, st, s);
         VOL_SIZES(C_)
 #undef C_
         default: return cudaErrorInvalidValue;

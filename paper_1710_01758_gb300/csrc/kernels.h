@@ -176,6 +176,10 @@ cudaError_t launch_g3_fwd_y(const Dims& d, int nz, const float2* sens, const flo
 // 2: back-projection of yt1), IDFT_z.
 cudaError_t launch_g3_z(const Dims& d, int nz, int mode, int addback, float2* U, const int* slot, float2* yt,
                         const float2* yt1, int ms, const float2* tw_z, const SliceState* st, cudaStream_t s);
+// 2D slices with an arbitrary mask (the x pass between the y passes, nz = 1): DFT_x, the
+// per-point mask operation of `mode` (as launch_g3_z, on whole k-space rows), IDFT_x.
+cudaError_t launch_g2_x(const Dims& d, int mode, int addback, float2* U, const uint8_t* mask, float2* yt,
+                        const float2* yt1, const float2* tw_x, const SliceState* st, cudaStream_t s);
 // IDFT_y, coil combine and the epilogue of the mode (0: q = A p, flag = PCG; 1: right-hand side,
 // flag = addback; 2: bd1, bd and the RSS start if write_x).
 cudaError_t launch_g3_inv_y(const Dims& d, int nz, int mode, int flag, const float2* U, const SbFields& f,

@@ -74,6 +74,11 @@ struct sb_plan_s {
     size_t maxparts = kMaxParts;  // per-slice capacity of the cross-CTA partial sums
     float2* tw_z = nullptr;
     float2* bz[2] = {nullptr, nullptr};
+    // 2D slices whose mask varies along x (the paper's random 2D sampling): the data term runs
+    // as the three passes of the volumes with a per-point mask (copied here)
+    bool general = false;
+    uint8_t* mask8 = nullptr;
+    bool passes() const { return nz > 1 || general; }
     std::string err;
 
     float2* tw_x = nullptr;
@@ -282,7 +287,8 @@ T* at(T* base, const Exec& ex, size_t per) {
     return base + (size_t)ex.b0 * per;
 }
 
-// ---- volumes (nz > 1): the data term as three passes through the coil scratch (k_vol.cu)
+// ---- volumes (nz > 1) and 2D arbitrary masks: the data term as three passes through the coil
+// scratch (k_vol.cu)
 Dims plane_dims(const Exec& ex) { return Dims{ex.d.nx, ex.pl->ny_plane, ex.d.nc, ex.d.nb}; }
 
 // out = A v on the context's volumes; pcg: PCG mode (inactive volumes skipped, p^H q, alpha)
@@ -297,9 +303,13 @@ sb_status vol_apply_A(Exec& ex, const float2* v, float2* out, bool pcg) {
     f.sens = sens;
     const float mu = (float)pl->d.mu, lam = (float)pl->d.lambda, gam = (float)pl->d.gamma;
     SB_LAUNCH(ex, SB_KCLASS_APPLY_A, 1, launch_g3_fwd_y(dp, pl->nz, sens, v, U, pl->tw_y, stf, ex.s));
-    SB_LAUNCH(ex, SB_KCLASS_APPLY_A, 1,
-              launch_g3_z(dp, pl->nz, 0, 0, U, at(pl->slot, ex, (size_t)ex.d.ny), nullptr, nullptr, pl->ms,
-                          pl->tw_z, stf, ex.s));
+    if (pl->general)
+        SB_LAUNCH(ex, SB_KCLASS_APPLY_A, 1,
+                  launch_g2_x(dp, 0, 0, U, at(pl->mask8, ex, n), nullptr, nullptr, pl->tw_x, stf, ex.s));
+    else
+        SB_LAUNCH(ex, SB_KCLASS_APPLY_A, 1,
+                  launch_g3_z(dp, pl->nz, 0, 0, U, at(pl->slot, ex, (size_t)ex.d.ny), nullptr, nullptr, pl->ms,
+                              pl->tw_z, stf, ex.s));
     SB_LAUNCH(ex, SB_KCLASS_APPLY_A, 1,
               launch_g3_inv_y(dp, pl->nz, 0, pcg ? 1 : 0, U, f, v, out, 0, pl->tw_y, mu, lam, gam, ex.st, 0.0, ex.red,
                               ex.s));
@@ -349,7 +359,7 @@ sb_status pcg_run(Exec& ex, const sb_pcg_opts& o, float2* x_full, sb_pcg_result*
 
     SB_LAUNCH(ex, SB_KCLASS_VEC, 1, launch_zero_rhs_slices(d, x, ex.st, s));
     const bool fused = circ && pl->fused_precond;
-    const bool vol = pl->nz > 1;
+    const bool vol = pl->nz > 1, passes = pl->passes();
     if (circ && vol) {
         if (sb_status e = vol_precond(ex, 1, r, nullptr, x, p, nullptr, tol2)) return e;
     } else if (fused) {
@@ -367,7 +377,7 @@ sb_status pcg_run(Exec& ex, const sb_pcg_opts& o, float2* x_full, sb_pcg_result*
     while (it < nit) {
         const int g = std::min(kPollEvery, nit - it);
         for (int i = 0; i < g; ++i) {
-            if (vol) {
+            if (passes) {
                 if (sb_status e = vol_apply_A(ex, p, q, true)) return e;
             } else {
                 SB_LAUNCH(ex, SB_KCLASS_APPLY_A, 1,
@@ -487,9 +497,13 @@ sb_status sb_run(Exec& ex, const sb_sb_opts& o, const float2* y_full, float2* x_
     const int nsolve = o.n_outer * o.n_inner;
     const size_t yrow = (size_t)d.nc * ms * d.nx;  // yt elements per slice
 
-    SB_LAUNCH(ex, SB_KCLASS_OTHER, 1,
-              launch_ytilde(d, at(y_full, ex, (size_t)d.nc * n), at(pl->lines, ex, ms), (int)ms, at(pl->yt1, ex, yrow),
-                            pl->tw_x, s));
+    if (pl->general)  // whole k-space rows: the data themselves
+        SB_XCK(ex, cudaMemcpyAsync(at(pl->yt1, ex, yrow), at(y_full, ex, (size_t)d.nc * n), sizeof(float2) * nb * yrow,
+                                   cudaMemcpyDeviceToDevice, s));
+    else
+        SB_LAUNCH(ex, SB_KCLASS_OTHER, 1,
+                  launch_ytilde(d, at(y_full, ex, (size_t)d.nc * n), at(pl->lines, ex, ms), (int)ms,
+                                at(pl->yt1, ex, yrow), pl->tw_x, s));
     SB_XCK(ex, cudaMemcpyAsync(at(pl->yt, ex, yrow), at(pl->yt1, ex, yrow), sizeof(float2) * nb * yrow,
                                cudaMemcpyDeviceToDevice, s));
     int cur = 0;
@@ -521,10 +535,15 @@ sb_status sb_run(Exec& ex, const sb_sb_opts& o, const float2* y_full, float2* x_
     };
     const Dims dp = plane_dims(ex);
     float2* U = at(pl->spec, ex, (size_t)d.nc * n);
-    if (vol) {
+    const bool passes = pl->passes();
+    const uint8_t* mask8 = pl->general ? at(pl->mask8, ex, n) : nullptr;
+    if (passes) {
         SbFields f0 = fields();
-        SB_LAUNCH(ex, SB_KCLASS_OTHER, 1,
-                  launch_g3_z(dp, pl->nz, 2, 0, U, f0.slot, f0.yt, f0.yt1, (int)ms, pl->tw_z, nullptr, s));
+        if (pl->general)
+            SB_LAUNCH(ex, SB_KCLASS_OTHER, 1, launch_g2_x(dp, 2, 0, U, mask8, f0.yt, f0.yt1, pl->tw_x, nullptr, s));
+        else
+            SB_LAUNCH(ex, SB_KCLASS_OTHER, 1,
+                      launch_g3_z(dp, pl->nz, 2, 0, U, f0.slot, f0.yt, f0.yt1, (int)ms, pl->tw_z, nullptr, s));
         SB_LAUNCH(ex, SB_KCLASS_OTHER, 1,
                   launch_g3_inv_y(dp, pl->nz, 2, 0, U, f0, nullptr, x, o.init_rss ? 1 : 0, pl->tw_y, mu, lam, gam,
                                   ex.st, 0.0, ex.red, s));
@@ -538,11 +557,16 @@ sb_status sb_run(Exec& ex, const sb_sb_opts& o, const float2* y_full, float2* x_
     for (int j = 0; j < o.n_outer; ++j) {
         for (int k = 0; k < o.n_inner; ++k, ++solve) {
             const int addback = (j > 0 && k == 0);
-            if (vol) {
+            if (passes) {
                 SbFields f1 = fields();
                 SB_LAUNCH(ex, SB_KCLASS_RHS, 1, launch_g3_fwd_y(dp, pl->nz, f1.sens, x, U, pl->tw_y, nullptr, s));
-                SB_LAUNCH(ex, SB_KCLASS_RHS, 1,
-                          launch_g3_z(dp, pl->nz, 1, addback, U, f1.slot, f1.yt, f1.yt1, (int)ms, pl->tw_z, nullptr, s));
+                if (pl->general)
+                    SB_LAUNCH(ex, SB_KCLASS_RHS, 1,
+                              launch_g2_x(dp, 1, addback, U, mask8, f1.yt, f1.yt1, pl->tw_x, nullptr, s));
+                else
+                    SB_LAUNCH(ex, SB_KCLASS_RHS, 1,
+                              launch_g3_z(dp, pl->nz, 1, addback, U, f1.slot, f1.yt, f1.yt1, (int)ms, pl->tw_z, nullptr,
+                                          s));
                 SB_LAUNCH(ex, SB_KCLASS_RHS, 1,
                           launch_g3_inv_y(dp, pl->nz, 1, addback, U, f1, x, r, 0, pl->tw_y, mu, lam, gam, ex.st, tol2,
                                           ex.red, s));
@@ -702,7 +726,7 @@ sb_status sb_plan_destroy(sb_plan pl) {
                     (void*)pl->g, (void*)pl->bd, (void*)pl->bd1, (void*)pl->yt, (void*)pl->yt1, (void*)pl->st,
                     (void*)pl->part, (void*)pl->counter, (void*)pl->kmax, (void*)pl->derr, (void*)pl->spec,
                     (void*)pl->gb, (void*)pl->rb, (void*)pl->line_val, (void*)pl->line_uni, (void*)pl->jw,
-                    (void*)pl->tw_z, (void*)pl->bz[0], (void*)pl->bz[1]})
+                    (void*)pl->tw_z, (void*)pl->bz[0], (void*)pl->bz[1], (void*)pl->mask8})
         dfree(p);
     if (pl->h_st) cudaFreeHost(pl->h_st);
     auto release = [](Exec& ex) {
@@ -776,23 +800,45 @@ sb_status sb_set_mask(sb_plan pl, const uint8_t* d_mask) {
     SB_CK(pl, cudaMemcpyAsync(hv.data(), lv, sizeof(int) * hv.size(), cudaMemcpyDeviceToHost, s));
     SB_CK(pl, cudaMemcpyAsync(hu.data(), lu, sizeof(int) * hu.size(), cudaMemcpyDeviceToHost, s));
     SB_CK(pl, cudaStreamSynchronize(s));
-    for (size_t i = 0; i < hu.size(); ++i)
-        if (!hu[i]) return fail(pl, SB_ERR_UNSUPPORTED, "mask varies along the readout (x) axis");
+    bool lines_only = true;
+    for (size_t i = 0; i < hu.size(); ++i) lines_only = lines_only && hu[i];
+    if (!lines_only && pl->nz > 1)
+        return fail(pl, SB_ERR_UNSUPPORTED, "a volume mask must be constant along the readout (x) axis");
+    pl->general = !lines_only;
     int ms = 1;
-    for (size_t b = 0; b < nb; ++b) {
-        int c = 0;
-        for (int y = 0; y < d.ny; ++y) c += hv[b * d.ny + y] != 0;
-        ms = std::max(ms, c);
-    }
     std::vector<float> hw(nb * d.ny);
-    std::vector<int> hs(nb * d.ny), hl(nb * ms, -1);
-    for (size_t b = 0; b < nb; ++b) {
-        int c = 0;
-        for (int y = 0; y < d.ny; ++y) {
-            const bool on = hv[b * d.ny + y] != 0;
-            hw[b * d.ny + y] = on ? 1.0f / d.ny : 0.0f;
-            hs[b * d.ny + y] = on ? c : -1;
-            if (on) hl[b * ms + c++] = y;
+    std::vector<int> hs(nb * d.ny), hl;
+    if (pl->general) {
+        // every row is a k-space row of the data; hw = sampled fraction contributed by the row
+        std::vector<uint8_t> hm(nb * n);
+        SB_CK(pl, cudaMemcpy(hm.data(), d_mask, nb * n, cudaMemcpyDeviceToHost));
+        ms = d.ny;
+        hl.assign(nb * ms, 0);
+        for (size_t b = 0; b < nb; ++b)
+            for (int y = 0; y < d.ny; ++y) {
+                int c = 0;
+                for (int xx = 0; xx < d.nx; ++xx) c += hm[(b * d.ny + y) * d.nx + xx] != 0;
+                hw[b * d.ny + y] = (float)c / (float)n;
+                hs[b * d.ny + y] = y;
+                hl[b * ms + y] = y;
+            }
+        if (!pl->mask8) SB_CK(pl, dalloc(&pl->mask8, nb * n));
+        SB_CK(pl, cudaMemcpyAsync(pl->mask8, d_mask, nb * n, cudaMemcpyDeviceToDevice, s));
+    } else {
+        for (size_t b = 0; b < nb; ++b) {
+            int c = 0;
+            for (int y = 0; y < d.ny; ++y) c += hv[b * d.ny + y] != 0;
+            ms = std::max(ms, c);
+        }
+        hl.assign(nb * ms, -1);
+        for (size_t b = 0; b < nb; ++b) {
+            int c = 0;
+            for (int y = 0; y < d.ny; ++y) {
+                const bool on = hv[b * d.ny + y] != 0;
+                hw[b * d.ny + y] = on ? 1.0f / d.ny : 0.0f;
+                hs[b * d.ny + y] = on ? c : -1;
+                if (on) hl[b * ms + c++] = y;
+            }
         }
     }
     if (ms != pl->ms) {
@@ -851,7 +897,7 @@ sb_status sb_set_mask(sb_plan pl, const uint8_t* d_mask) {
     const size_t yrow = (size_t)d.nc * ms * d.nx;
     auto enc = [&](Exec& e2) {
         const size_t rows = (size_t)e2.d.nb * d.nc * ms;
-        if (ms > 256 || pl->nz > 1) return true;  // no compact-row maps (2D RHS kernel only)
+        if (ms > 256 || pl->passes()) return true;  // no compact-row maps (2D line RHS kernel only)
         return encode_rows(&e2.ymap, pl->yt + e2.b0 * yrow, d.nx, rows, ms) &&
                encode_rows(&e2.y1map, pl->yt1 + e2.b0 * yrow, d.nx, rows, ms);
     };
@@ -888,7 +934,7 @@ sb_status sb_apply_A(sb_plan pl, const void* d_x, void* d_y) {
     if (!d_x || !d_y || d_x == d_y) return fail(pl, SB_ERR_INVALID_ARG, "need distinct non-null x and y");
     Exec& ex = pl->whole;
     auto go = [&]() -> sb_status {
-        if (pl->nz > 1) return vol_apply_A(ex, static_cast<const float2*>(d_x), static_cast<float2*>(d_y), false);
+        if (pl->passes()) return vol_apply_A(ex, static_cast<const float2*>(d_x), static_cast<float2*>(d_y), false);
         SB_LAUNCH(ex, SB_KCLASS_APPLY_A, 1,
                   launch_apply_A(pl->dims, ex.smap_sw, static_cast<const float2*>(d_x), static_cast<float2*>(d_y),
                                  pl->maskw, pl->tw_y, (float)pl->d.mu, (float)pl->d.lambda, (float)pl->d.gamma,
@@ -933,7 +979,7 @@ sb_status sb_pcg_solve(sb_plan pl, const void* d_b, void* d_x, const sb_pcg_opts
         const size_t n = pl->n;
         float2* x = at(x_full, ex, n);
         float2* q = at(pl->q, ex, n);
-        if (pl->nz > 1) {
+        if (pl->passes()) {
             if (sb_status e = vol_apply_A(ex, x, q, false)) return e;
         } else {
             SB_LAUNCH(ex, SB_KCLASS_APPLY_A, 1,
@@ -951,7 +997,7 @@ sb_status sb_split_bregman(sb_plan pl, const void* d_y, void* d_x, const sb_sb_o
     if (!o || !d_y || !d_x) return fail(pl, SB_ERR_INVALID_ARG, "null argument");
     if (o->n_outer < 1 || o->n_inner < 1) return fail(pl, SB_ERR_INVALID_ARG, "n_outer and n_inner must be >= 1");
     if (sb_status s = check_opts(pl, &o->pcg)) return s;
-    if (pl->nz == 1 && (pl->ms > 256 || rhs_smem_bytes(pl->dims.ny, pl->ms) > 227 * 1024))
+    if (!pl->passes() && (pl->ms > 256 || rhs_smem_bytes(pl->dims.ny, pl->ms) > 227 * 1024))
         return fail(pl, SB_ERR_UNSUPPORTED, "too many sampled lines for the shared-memory pipeline of this size");
     const int nsolve = o->n_outer * o->n_inner;
     std::vector<int> iters((size_t)pl->dims.nb * nsolve, 0);

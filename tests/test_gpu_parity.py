@@ -267,11 +267,6 @@ def test_unsupported_inputs(torch, sbm):
     sens, mask, rng = problem(nx, ny, 2, 1, seed=1)
     plan = sbm.Plan(nx, ny, 2, 1, 1.0, 0.1, 0.1, 0)
     plan.set_coils(to_dev(torch, sens))
-    bad = mask.copy()
-    bad[0, 0, 5] ^= 1                       # breaks the line structure
-    with pytest.raises(sbm.SbError) as ei:
-        plan.set_mask(torch.from_numpy(bad).cuda())
-    assert ei.value.status == sbm.SB_ERR_UNSUPPORTED
     with pytest.raises(sbm.SbError) as ei:  # k was not built: operators refuse
         plan.apply_A(to_dev(torch, np.zeros((1, ny, nx), complex)))
     assert ei.value.status == sbm.SB_ERR_NOT_READY
@@ -364,3 +359,74 @@ def test_split_bregman_mixed_radix_sizes(torch, sbm):
     xg, refs, _ = run_sb_both(torch, sbm, wl, 2, wl.seed, tau=0.02, fixed=8)
     for b in range(2):
         assert rel(xg[b], refs[b].x) <= IMG_TOL
+
+
+def random_mask_problem(nx, ny, nc, nb, seed, accel=3.0, centre=8):
+    rng = np.random.default_rng(seed)
+    sens = np.stack([synth.coil_maps(ny, nx, nc, rng) for _ in range(nb)])
+    mask = np.stack([synth.random_mask(ny, nx, accel, centre, rng) for _ in range(nb)])
+    return sens, mask, rng
+
+
+@pytest.mark.parametrize("nx,ny,nc,nb", [(64, 64, 4, 2), (128, 64, 3, 1), (192, 224, 6, 1), (256, 256, 8, 1)])
+def test_random_mask_operators(torch, sbm, nx, ny, nc, nb):
+    # the paper's second sampling scheme: points drawn at random in (k_y, k_x)
+    sens, mask, rng = random_mask_problem(nx, ny, nc, nb, seed=nx + 5 * ny + nc)
+    mu, lam, gam = 1.0, 0.05, 0.05
+    plan = make_plan(sbm, torch, sens, mask, mu, lam, gam)
+    x = synth.random_complex((nb, ny, nx), rng)
+    q = plan.apply_A(to_dev(torch, x)).cpu().numpy()
+    kg = plan.k().cpu().numpy()
+    z = plan.apply_precond(to_dev(torch, x)).cpu().numpy()
+    for b in range(nb):
+        assert rel(q[b], operators.apply_A(x[b], sens[b], mask[b], mu, lam, gam, 2)) <= OP_TOL
+        kref = precond.k_diag(sens[b], mask[b], mu, lam, gam, 2)
+        assert np.max(np.abs(kg[b] - kref)) <= OP_TOL * np.max(kref)
+        assert rel(z[b], precond.apply_precond(x[b], kref, 2)) <= OP_TOL
+
+
+@pytest.mark.parametrize("kind", ["circulant", "jacobi"])
+def test_random_mask_pcg_and_mixed_batch(torch, sbm, kind):
+    # slice 0 random points, slice 1 Cartesian lines: one plan in the general mode
+    nx = ny = 64
+    rng = np.random.default_rng(8)
+    sens = np.stack([synth.coil_maps(ny, nx, 4, rng) for _ in range(2)])
+    mask = np.stack([synth.random_mask(ny, nx, 3.0, 8, rng), synth.line_mask(ny, nx, 4.0, 8, rng)])
+    mu, lam, gam = 1.0, 0.05, 0.05
+    plan = make_plan(sbm, torch, sens, mask, mu, lam, gam)
+    b = synth.random_complex((2, ny, nx), rng)
+    pc = sbm.SB_PRECOND_CIRCULANT if kind == "circulant" else sbm.SB_PRECOND_JACOBI
+    xd = torch.zeros((2, ny, nx), dtype=torch.complex64, device="cuda")
+    st, res = plan.pcg_solve(to_dev(torch, b), xd, tol=1e-4, maxit=300, precond=pc)
+    assert st == sbm.SB_OK
+    for i in range(2):
+        A = lambda v: operators.apply_A(v, sens[i], mask[i], mu, lam, gam, 2)  # noqa: E731
+        k = precond.k_diag(sens[i], mask[i], mu, lam, gam, 2)
+        M = oracle_M(kind, sens[i], mask[i], mu, lam, gam, k)
+        ref = pcg.pcg(A, b[i], np.zeros((ny, nx), complex), M, tol=1e-4, maxit=300)
+        assert abs(res[i][0] - ref.iters) <= 1, (res[i], ref.iters)
+        assert rel(xd[i].cpu().numpy(), ref.x) <= 1e-3
+
+
+@pytest.mark.parametrize("tau", [0.0, 0.02])
+def test_random_mask_split_bregman(torch, sbm, tau):
+    nx, ny, nc, nb = 64, 64, 4, 2
+    rng = np.random.default_rng(1234)
+    mu, lam, gam, levels = 1.0, 0.05, 0.05, 3
+    sl = []
+    for _ in range(nb):
+        xt = synth.ellipse_phantom(ny, nx, rng)
+        s_ = synth.coil_maps(ny, nx, nc, rng)
+        m_ = synth.random_mask(ny, nx, 3.0, 8, rng)
+        sl.append((s_, m_, synth.acquire(xt, s_, m_, 1e-3, rng)))
+    sens = np.stack([a for a, _, _ in sl])
+    mask = np.stack([m for _, m, _ in sl])
+    y = np.stack([c for _, _, c in sl])
+    plan = make_plan(sbm, torch, sens, mask, mu, lam, gam, levels)
+    xd = torch.zeros((nb, ny, nx), dtype=torch.complex64, device="cuda")
+    st, _, _ = plan.split_bregman(to_dev(torch, y), xd, 4, tau_tv=tau, tau_w=tau, fixed_iters=8)
+    assert st == sbm.SB_OK
+    for i in range(nb):
+        ref = sb_oracle.split_bregman(y[i], sens[i], mask[i], mu, lam, gam, levels, 2, 4, 1, 1e-3, 100, 8,
+                                      "circulant", tau if tau > 0 else None, tau if tau > 0 else None)
+        assert rel(xd[i].cpu().numpy(), ref.x) <= IMG_TOL

@@ -149,3 +149,15 @@ def test_volume_unsupported(torch, sbm):
         with pytest.raises(sbm.SbError) as ei:
             sbm.sb_plan_create(desc, 0)
         assert ei.value.status == sbm.SB_ERR_UNSUPPORTED
+
+
+def test_volume_mask_must_be_lines(torch, sbm):
+    sens, mask, _ = volume_problem(32, 32, 32, 2, 1, seed=3)
+    bad = mask.copy()
+    bad[0, 0, 0, 5] ^= 1  # varies along x
+    plan = sbm.Plan(32, 32, 2, 1, 1.0, 0.1, 0.1, 0, nz=32)
+    plan.set_coils(dev(torch, sens))
+    with pytest.raises(sbm.SbError) as ei:
+        plan.set_mask(torch.from_numpy(np.ascontiguousarray(bad)).cuda())
+    assert ei.value.status == sbm.SB_ERR_UNSUPPORTED
+    plan.close()
