@@ -260,6 +260,10 @@ METRIC_256 = Workload("256x256 Nc12 R4 TV+Haar4 20SB PCG-tol1e-3", 256, 256, 12,
                       1.0, 0.05, 0.05, 4, 20, 1, 1e-3, 200, 0, seed=SEED_BASE + 2)
 
 
+# 256x256, 12 coils, random 2D variable-density points at R=4 with a 24 x 24 centre, TV + 4-level
+# Haar, 20 SB, PCG to 1e-3 (the paper's second sampling scheme).
+RANDOM_256 = Workload("256x256 Nc12 R4 random-2D TV+Haar4 20SB PCG-tol1e-3", 256, 256, 12, 4.0, 24, "random",
+                      1.0, 0.05, 0.05, 4, 20, 1, 1e-3, 200, 0, seed=SEED_BASE + 6)
 # 512x512, 32 coils, R=6 variable-density lines + 32 centre lines, TV + 4-level Haar, 20 SB.
 LARGE_512 = Workload("512x512 Nc32 R6vd TV+Haar4 20SB PCG-tol1e-3", 512, 512, 32, 6.0, 32, "variable",
                      1.0, 0.05, 0.05, 4, 20, 1, 1e-3, 200, 0, seed=SEED_BASE + 3)
@@ -305,7 +309,10 @@ def make_slice(wl: Workload, seed: int | None = None) -> Slice:
     rng = np.random.default_rng(wl.seed if seed is None else seed)
     x = ellipse_phantom(wl.ny, wl.nx, rng)
     s = coil_maps(wl.ny, wl.nx, wl.ncoils, rng)
-    m = line_mask(wl.ny, wl.nx, wl.accel, wl.n_centre, rng, wl.density)
+    if wl.density == "random":  # random 2D points with an n_centre x n_centre centre block
+        m = random_mask(wl.ny, wl.nx, wl.accel, wl.n_centre, rng)
+    else:
+        m = line_mask(wl.ny, wl.nx, wl.accel, wl.n_centre, rng, wl.density)
     y = acquire(x, s, m, wl.sigma, rng)
     return Slice(x, s, m, y)
 
