@@ -15,7 +15,9 @@
 //    ny <= 256, 128 at ny = 512, whole warps of whole columns for ny = 16 x {12, 14, 20, 24});
 //    a group owns CPG columns, exchanges data only through its private shared-memory region,
 //    and synchronises with a named barrier of its own: no CTA-wide barrier inside the coil
-//    loop (one group per CTA at ny = 224).
+//    loop (one group per CTA at ny = 224).  At ny = 256 a warp holds two whole columns (16 rows
+//    x 2 columns; each half-warp 8 rows x 2 columns), and at ny = 128 four, so there the
+//    exchanges are ordered by __syncwarp alone.
 //  * 8-byte shared-memory accesses are served per half-warp, so each half-warp holds 8
 //    consecutive rows of 2 adjacent columns: the TMA swizzle then spreads the tile reads over
 //    16 distinct bank pairs, and so does the exchange region, stored column by column with one
@@ -110,22 +112,33 @@ k_apply_A(const __grid_constant__ CUtensorMap smap, const float2* __restrict__ p
 
     const int tid = threadIdx.x, lane = tid & 31;
     const int grp = tid / GT, gl = tid % GT;
-    int t, cl;
-    if constexpr (T % 8 == 0) {  // a warp = 8 rows x 4 columns; a half-warp = 8 rows x 2 columns
+    // T = 16 and T = 8: every column transform lies within one warp, so the exchanges need only
+    // __syncwarp; otherwise a named barrier per exchange group
+    constexpr bool kWarpLocal = (T == 16 || T == 8);
+    int t, cl, col;
+    if constexpr (T == 16) {  // a warp = 16 rows x 2 columns, a half-warp = 8 rows x 2 columns
+        t = (lane & 7) + 8 * (lane >> 4);
+        cl = (lane >> 3) & 1;
+        col = 2 * (tid >> 5) + cl;
+    } else if constexpr (T % 8 == 0) {  // a warp = 8 rows x 4 columns; a half-warp = 8 rows x 2 columns
         const int wg = gl >> 5;
         t = (lane & 7) + 8 * (wg % (T / 8));
         cl = (lane >> 3) + 4 * (wg / (T / 8));
+        col = grp * CPG + cl;
     } else {
         t = gl / CPG;
         cl = gl % CPG;
+        col = grp * CPG + cl;
     }
-    const int col = grp * CPG + cl;
     const int x0 = blockIdx.x * TX, x = x0 + col;
     const ExIdx<NY> idx{col * ExIdx<NY>::kStride};
     float2* ex = xbuf;
     const TileRows<T> rows(t, col);
     const int bar_id = 1 + grp;
-    auto gbar = [bar_id]() { named_bar(bar_id, GT); };
+    auto gbar = [bar_id]() {
+        if constexpr (kWarpLocal) __syncwarp();
+        else named_bar(bar_id, GT);
+    };
 
     if (tid == 0) {
         for (int s = 0; s < 2; ++s) {
