@@ -45,8 +45,9 @@ class SbResult:
 
 def split_bregman(y, sens, mask, mu, lam, gam, levels, ndim, n_outer, n_inner=1,
                   pcg_tol=1e-3, pcg_maxit=1000, fixed_iters=0, precond_kind="circulant",
-                  tau_tv=None, tau_w=None, x0=None) -> SbResult:
-    """Algorithm 1.  ``precond_kind``: 'circulant' (Eq. precon), 'jacobi' or 'none'."""
+                  tau_tv=None, tau_w=None, x0=None, wavelet="haar") -> SbResult:
+    """Algorithm 1.  ``precond_kind``: 'circulant' (Eq. precon), 'jacobi' or 'none'; ``wavelet``:
+    'haar' or 'daub4' (the paper's)."""
     y = np.asarray(y, np.complex128)
     sens = np.asarray(sens, np.complex128)
     mask = np.asarray(mask)
@@ -81,7 +82,7 @@ def split_bregman(y, sens, mask, mu, lam, gam, levels, ndim, n_outer, n_inner=1,
     iters, resid = [], []
     for _j in range(n_outer):                                   # step 2
         for _k in range(n_inner):                               # step 3
-            b = operators.rhs(yj, sens, mask, mu, lam, gam, d, bb, d_w, b_w, levels, ndim)  # 4
+            b = operators.rhs(yj, sens, mask, mu, lam, gam, d, bb, d_w, b_w, levels, ndim, wavelet)  # 4
             res = pcg.pcg(apply_A, b, x, apply_M, pcg_tol, pcg_maxit, fixed_iters)          # 5
             x = res.x
             iters.append(res.iters)
@@ -91,7 +92,7 @@ def split_bregman(y, sens, mask, mu, lam, gam, levels, ndim, n_outer, n_inner=1,
                 d = [shrink(g + bv, tau_tv) for g, bv in zip(dx, bb)]                        # 6-7
                 bb = [bv + g - dv for bv, g, dv in zip(bb, dx, d)]                           # 9-10
             if gam != 0.0:
-                wx = operators.haar(x, levels, ndim)
+                wx = operators.wavelet(x, levels, ndim, wavelet)
                 d_w = shrink(wx + b_w, tau_w)                                                # 8
                 b_w = b_w + wx - d_w                                                         # 11
         yj = yj + y1 - operators.encode(x, sens, mask, ndim)                                 # 12-14
