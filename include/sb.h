@@ -75,6 +75,11 @@ typedef struct {
                                0 = automatic (3: on a 64-slice 256 x 256 batch the cluster
                                launch took 151 us against 92 us for the three passes).  Both
                                give the same iterates up to rounding order. */
+    int wavelet;            /* W of steps 4, 8 and 11: 0 = orthonormal Haar (in place, 32 x 32
+                               tiles), 1 = periodic Daubechies-4, the wavelet of the paper's
+                               experiments (Methods, "Reconstruction"); 2D only, nx, ny <= 512,
+                               and the coarsest band at least 4 wide, else SB_ERR_UNSUPPORTED.
+                               A and k do not depend on W (W^H W = I). */
 } sb_plan_desc;
 
 typedef struct sb_plan_s* sb_plan;

@@ -185,6 +185,11 @@ cudaError_t launch_g2_x(const Dims& d, int mode, int addback, float2* U, const u
 cudaError_t launch_g3_inv_y(const Dims& d, int nz, int mode, int flag, const float2* U, const SbFields& f,
                             const float2* vin, float2* out, int write_x, const float2* tw_y, float mu, float lam,
                             float gam, SliceState* st, double tol2, Red red, cudaStream_t s);
+// Daubechies-4 steps 8 and 11 (k_wave.cu): w = W x (levels >= 1, Mallat layout), shrink and
+// Bregman update of bw, w = W^H (d_w - b_w), g += gam w.  w: [nb][ny][nx] scratch.
+cudaError_t launch_d4_update(const Dims& d, const float2* x, float2* w, float2* bw, float2* g, int levels, float gam,
+                             float tau_w, cudaStream_t s);
+int d4_update_launches(int levels);
 // Steps 6-11 of Algorithm 1 on 16^3 tiles (levels <= 4).
 cudaError_t launch_sb_update3(const Dims& d, int nz, const SbFields& f, const float2* x, int levels, float lam,
                               float gam, float tau_tv, float tau_w, cudaStream_t s);

@@ -78,6 +78,7 @@ struct sb_plan_s {
     // as the three passes of the volumes with a per-point mask (copied here)
     bool general = false;
     uint8_t* mask8 = nullptr;
+    float2* wb = nullptr;  // Daubechies-4 coefficient scratch [nb][ny][nx]
     bool passes() const { return nz > 1 || general; }
     std::string err;
 
@@ -583,7 +584,14 @@ sb_status sb_run(Exec& ex, const sb_sb_opts& o, const float2* y_full, float2* x_
                 if (vol)
                     SB_LAUNCH(ex, SB_KCLASS_SB_UPDATE, 1,
                               launch_sb_update3(dp, pl->nz, fields(), x, levels, lam, gam, tau_tv, tau_w, s));
-                else
+                else if (pl->d.wavelet == 1 && levels > 0 && gam != 0.f) {
+                    // TV part here (g = lam D^H u), the Daubechies-4 part adds gam W^H u_w
+                    SbFields f2 = fields();
+                    SB_LAUNCH(ex, SB_KCLASS_SB_UPDATE, 1,
+                              launch_sb_update(d, f2, x, levels, lam, 0.f, tau_tv, tau_w, s));
+                    SB_LAUNCH(ex, SB_KCLASS_SB_UPDATE, d4_update_launches(levels),
+                              launch_d4_update(d, x, at(pl->wb, ex, n), f2.bw, f2.g, levels, gam, tau_w, s));
+                } else
                     SB_LAUNCH(ex, SB_KCLASS_SB_UPDATE, 1,
                               launch_sb_update(d, fields(), x, levels, lam, gam, tau_tv, tau_w, s));
                 if (lam != 0.f) cur ^= 1;
@@ -626,10 +634,14 @@ sb_status sb_plan_create(const sb_plan_desc* desc, void* cuda_stream, sb_plan* o
     if ((d.ndim != 2 && d.ndim != 3) || (!vol && d.nz != 1 && d.nz != 0) || d.ncoils < 1 || d.nbatch < 1 ||
         !(d.mu > 0.0) ||
         !(d.lambda >= 0.0) || !(d.gamma >= 0.0) || d.wavelet_levels < 0 || d.groups < 0 ||
-        (d.precond_passes != 0 && d.precond_passes != 1 && d.precond_passes != 3))
+        (d.precond_passes != 0 && d.precond_passes != 1 && d.precond_passes != 3) ||
+        (d.wavelet != 0 && d.wavelet != 1))
         return SB_ERR_INVALID_ARG;
     if (!supported_n(d.nx) || !supported_n(d.ny) || d.wavelet_levels > (vol ? 4 : 5) || d.prec != SB_PREC_FP32 ||
         (vol && (!supported_n(d.nz) || d.precond_passes == 1)))
+        return SB_ERR_UNSUPPORTED;
+    if (d.wavelet == 1 && d.wavelet_levels > 0 &&
+        (vol || (d.nx >> (d.wavelet_levels - 1)) < 4 || (d.ny >> (d.wavelet_levels - 1)) < 4))
         return SB_ERR_UNSUPPORTED;
     const int nz = vol ? d.nz : 1;
     // the fused preconditioner (opt-in) needs a slice on one cluster that fits the device
@@ -726,7 +738,7 @@ sb_status sb_plan_destroy(sb_plan pl) {
                     (void*)pl->g, (void*)pl->bd, (void*)pl->bd1, (void*)pl->yt, (void*)pl->yt1, (void*)pl->st,
                     (void*)pl->part, (void*)pl->counter, (void*)pl->kmax, (void*)pl->derr, (void*)pl->spec,
                     (void*)pl->gb, (void*)pl->rb, (void*)pl->line_val, (void*)pl->line_uni, (void*)pl->jw,
-                    (void*)pl->tw_z, (void*)pl->bz[0], (void*)pl->bz[1], (void*)pl->mask8})
+                    (void*)pl->tw_z, (void*)pl->bz[0], (void*)pl->bz[1], (void*)pl->mask8, (void*)pl->wb})
         dfree(p);
     if (pl->h_st) cudaFreeHost(pl->h_st);
     auto release = [](Exec& ex) {
@@ -904,6 +916,7 @@ sb_status sb_set_mask(sb_plan pl, const uint8_t* d_mask) {
     bool ok = enc(pl->whole);
     for (Exec& e2 : pl->groups) ok = ok && enc(e2);
     if (!ok) return fail(pl, SB_ERR_CUDA, "cuTensorMapEncodeTiled failed for the k-space rows");
+    if (pl->d.wavelet == 1 && !pl->wb) SB_CK(pl, dalloc(&pl->wb, nb * n));
     if (pl->nz > 1 && !pl->bz[0]) {
         SB_CK(pl, dalloc(&pl->bz[0], nb * n));
         SB_CK(pl, dalloc(&pl->bz[1], nb * n));

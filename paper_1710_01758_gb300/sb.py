@@ -31,13 +31,17 @@ SB_PREC_SPLIT_FP16 = 2
 SB_PRECOND_NONE = 0
 SB_PRECOND_CIRCULANT = 1
 SB_PRECOND_JACOBI = 2
+# wavelet kinds (sb_plan_desc.wavelet)
+SB_WAVELET_HAAR = 0
+SB_WAVELET_DAUB4 = 1
 
 
 class sb_plan_desc(ctypes.Structure):
     _fields_ = [("ndim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
                 ("ncoils", ctypes.c_int), ("nbatch", ctypes.c_int), ("mu", ctypes.c_double),
                 ("lambda_", ctypes.c_double), ("gamma", ctypes.c_double), ("wavelet_levels", ctypes.c_int),
-                ("prec", ctypes.c_int), ("groups", ctypes.c_int), ("precond_passes", ctypes.c_int)]
+                ("prec", ctypes.c_int), ("groups", ctypes.c_int), ("precond_passes", ctypes.c_int),
+                ("wavelet", ctypes.c_int)]
 
 
 class sb_pcg_opts(ctypes.Structure):
@@ -131,10 +135,11 @@ def _check(status: int, plan=None, allow=()):
 
 
 def plan_desc(nx, ny, ncoils, nbatch, mu, lam, gam, wavelet_levels, prec=SB_PREC_FP32, groups=0,
-              precond_passes=0, nz=1) -> sb_plan_desc:
-    """nz > 1 describes volumes (ndim = 3) of nz planes."""
+              precond_passes=0, nz=1, wavelet=0) -> sb_plan_desc:
+    """nz > 1 describes volumes (ndim = 3) of nz planes; wavelet: SB_WAVELET_HAAR or
+    SB_WAVELET_DAUB4."""
     return sb_plan_desc(3 if nz > 1 else 2, nx, ny, nz, ncoils, nbatch, mu, lam, gam, wavelet_levels, prec, groups,
-                        precond_passes)
+                        precond_passes, wavelet)
 
 
 def sb_plan_create(desc: sb_plan_desc, stream: int = 0) -> int:
@@ -233,7 +238,7 @@ class Plan:
     """Owns an sb_plan and the device tensors it borrows (torch CUDA tensors)."""
 
     def __init__(self, nx, ny, ncoils, nbatch, mu, lam, gam, wavelet_levels, stream=None, groups=0,
-                 precond_passes=0, nz=1):
+                 precond_passes=0, nz=1, wavelet=0):
         import torch
         self.torch = torch
         self.nbatch = nbatch
@@ -241,7 +246,7 @@ class Plan:
         s = stream if stream is not None else torch.cuda.current_stream()
         self.stream = s
         self.handle = sb_plan_create(plan_desc(nx, ny, ncoils, nbatch, mu, lam, gam, wavelet_levels, groups=groups,
-                                                       precond_passes=precond_passes, nz=nz),
+                                                       precond_passes=precond_passes, nz=nz, wavelet=wavelet),
                                      s.cuda_stream)
         self._sens = None
 

@@ -430,3 +430,40 @@ def test_random_mask_split_bregman(torch, sbm, tau):
         ref = sb_oracle.split_bregman(y[i], sens[i], mask[i], mu, lam, gam, levels, 2, 4, 1, 1e-3, 100, 8,
                                       "circulant", tau if tau > 0 else None, tau if tau > 0 else None)
         assert rel(xd[i].cpu().numpy(), ref.x) <= IMG_TOL
+
+
+@pytest.mark.parametrize("nx,ny,levels,tau,density", [(64, 64, 3, 0.02, "uniform"), (128, 64, 1, 0.02, "uniform"),
+                                                      (64, 64, 4, 0.0, "uniform"), (512, 256, 4, 0.02, "uniform"),
+                                                      (64, 64, 2, 0.02, "random")])
+def test_split_bregman_daubechies4(torch, sbm, nx, ny, levels, tau, density):
+    # the paper's wavelet: W = periodic Daubechies-4 in steps 4, 8 and 11
+    wl = synth.Workload("D4", ny, nx, 4, 4.0, 8, density, 1.0, 0.05, 0.05, levels, 4, 1, 1e-3, 100, 0, seed=606)
+    nb = 2
+    slices = [synth.make_slice(wl, wl.seed * 1000 + i) for i in range(nb)]
+    sens = np.stack([s.sens for s in slices])
+    mask = np.stack([s.mask for s in slices])
+    y = np.stack([s.y for s in slices])
+    plan = sbm.Plan(nx, ny, 4, nb, wl.mu, wl.lam, wl.gam, levels, wavelet=sbm.SB_WAVELET_DAUB4)
+    plan.set_coils(to_dev(torch, sens))
+    plan.set_mask(torch.from_numpy(mask).cuda())
+    xd = torch.zeros((nb, ny, nx), dtype=torch.complex64, device="cuda")
+    st, _, _ = plan.split_bregman(to_dev(torch, y), xd, wl.n_outer, tau_tv=tau, tau_w=tau, fixed_iters=8)
+    assert st == sbm.SB_OK
+    for i, s in enumerate(slices):
+        ref = sb_oracle.split_bregman(s.y, s.sens, s.mask, wl.mu, wl.lam, wl.gam, levels, 2, wl.n_outer, 1, 1e-3, 100,
+                                      8, "circulant", tau if tau > 0 else None, tau if tau > 0 else None,
+                                      wavelet="daub4")
+        assert rel(xd[i].cpu().numpy(), ref.x) <= IMG_TOL
+    plan.close()
+
+
+def test_daubechies4_unsupported(torch, sbm):
+    with pytest.raises(sbm.SbError) as ei:  # coarsest band 2 wide
+        sbm.Plan(32, 32, 2, 1, 1.0, 0.1, 0.1, 5, wavelet=sbm.SB_WAVELET_DAUB4)
+    assert ei.value.status == sbm.SB_ERR_UNSUPPORTED
+    with pytest.raises(sbm.SbError) as ei:  # volumes use Haar
+        sbm.Plan(32, 32, 2, 1, 1.0, 0.1, 0.1, 2, nz=32, wavelet=sbm.SB_WAVELET_DAUB4)
+    assert ei.value.status == sbm.SB_ERR_UNSUPPORTED
+    with pytest.raises(sbm.SbError) as ei:
+        sbm.Plan(32, 32, 2, 1, 1.0, 0.1, 0.1, 2, wavelet=7)
+    assert ei.value.status == sbm.SB_ERR_INVALID_ARG
