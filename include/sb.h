@@ -186,6 +186,27 @@ sb_status sb_split_bregman_many(const sb_plan* plans, int nplans, const void* co
 sb_status sb_apply_precond_noalloc(const void* d_r, const float* d_k, void* d_z, int nx, int ny,
                                    int nbatch, void* cuda_stream);
 
+/* Coil compression (Methods, "Coil Compression"): for every slice of a batch, the nv x nc
+ * compression matrix A from the principal components of its coil data, then the virtual coil
+ * data d_y_out = A d_y and maps d_sens_out = A d_sens (the paper drops the least dominant virtual
+ * coils to shorten the reconstruction; the preconditioner's effect is unchanged).
+ *   d_y, d_sens:          complex64 [nbatch][nc][npix] on the device (npix = nx ny (nz)).
+ *   d_y_out, d_sens_out:  complex64 [nbatch][nv][npix] on the device, distinct from the inputs.
+ *   h_matrix (optional):  host complex64 [nbatch][nv][nc], the matrices used (row v = the
+ *                         conjugate of the v-th eigenvector of C = sum y y^H, eigenvalues
+ *                         descending; a row is defined up to a unit phase).
+ *   h_eig (optional):     host double [nbatch][nc], the eigenvalues of C, descending.
+ *   1 <= nv <= nc <= 32.  C is summed in FP32 over 128-sample chunks and in FP64 across them;
+ * the eigen-decomposition is a cyclic complex Jacobi in FP64 on the host.  Allocates device
+ * scratch, synchronises cuda_stream; SB_ERR_INVALID_ARG / SB_ERR_CUDA on failure. */
+sb_status sb_coil_compress(const void* d_y, const void* d_sens, size_t npix, int nc, int nbatch, int nv,
+                           void* d_y_out, void* d_sens_out, void* h_matrix, double* h_eig, void* cuda_stream);
+
+/* The host step of sb_coil_compress alone (no device work): the compression matrix of one
+ * Hermitian covariance.  cov: interleaved complex double [nc][nc] row-major; mat_out:
+ * interleaved complex double [nv][nc]; eig_out (may be NULL): double [nc], descending. */
+sb_status sb_coil_compression_matrix(const double* cov, int nc, int nv, double* mat_out, double* eig_out);
+
 /* Human-readable name of a status code (static string). */
 const char* sb_status_string(sb_status status);
 

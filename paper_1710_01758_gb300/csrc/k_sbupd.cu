@@ -22,7 +22,6 @@ namespace sb {
 namespace {
 
 constexpr int ST = 32;  // tile edge
-constexpr float kH = 0.70710678118654752f;
 
 __device__ __forceinline__ float2 shrink(float2 z, float t) {
     const float m = sqrtf(cabs2(z));

@@ -78,6 +78,10 @@ SIGNATURES = [
     ("sb_split_bregman_many", ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(_P),
                                              ctypes.POINTER(_P), ctypes.POINTER(sb_sb_opts),
                                              ctypes.POINTER(ctypes.POINTER(sb_pcg_result))]),
+    ("sb_coil_compress", ctypes.c_int, [_P, _P, ctypes.c_size_t, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P,
+                                        _P, ctypes.POINTER(ctypes.c_double), _P]),
+    ("sb_coil_compression_matrix", ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.c_int,
+                                                  ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     ("sb_plan_set_timing", ctypes.c_int, [_P, ctypes.c_uint]),
     ("sb_plan_get_timing", ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_uint64),
                                           ctypes.POINTER(ctypes.c_double)]),
@@ -215,6 +219,38 @@ def sb_split_bregman_many(plans, d_ys, d_xs, nbatches, n_outer: int, n_inner: in
         raise SbError(st, msgs)
     its = [[[it[b * nsolve + i] for i in range(nsolve)] for b in range(nb)] for it, nb in zip(iters, nbatches)]
     return st, its, [[(r.iters, r.rel_resid, bool(r.converged)) for r in l] for l in lasts]
+
+
+def coil_compression_matrix(cov, nv):
+    """Host-only: (matrix [nv][nc] complex128, eigenvalues [nc] descending) of a Hermitian
+    covariance ``cov`` (numpy complex128 [nc][nc])."""
+    import numpy as np
+    nc = cov.shape[0]
+    c = np.ascontiguousarray(cov, np.complex128)
+    mat = np.zeros((nv, nc), np.complex128)
+    eig = np.zeros(nc, np.float64)
+    dp = ctypes.POINTER(ctypes.c_double)
+    _check(_lib.sb_coil_compression_matrix(c.ctypes.data_as(dp), nc, nv, mat.ctypes.data_as(dp),
+                                           eig.ctypes.data_as(dp)))
+    return mat, eig
+
+
+def coil_compress(y, sens, nv, stream=None):
+    """sb_coil_compress on torch CUDA tensors y, sens [nb][nc][...]; returns (y_v, sens_v, matrices
+    [nb][nv][nc] complex64 numpy, eigenvalues [nb][nc])."""
+    import numpy as np
+    import torch
+    nb, nc = y.shape[0], y.shape[1]
+    npix = y[0, 0].numel()
+    yo = torch.empty((nb, nv) + tuple(y.shape[2:]), dtype=y.dtype, device=y.device)
+    so = torch.empty((nb, nv) + tuple(sens.shape[2:]), dtype=sens.dtype, device=sens.device)
+    mat = np.zeros((nb, nv, nc), np.complex64)
+    eig = np.zeros((nb, nc), np.float64)
+    s = stream if stream is not None else torch.cuda.current_stream()
+    _check(_lib.sb_coil_compress(_P(y.data_ptr()), _P(sens.data_ptr()), npix, nc, nb, nv, _P(yo.data_ptr()),
+                                 _P(so.data_ptr()), _P(mat.ctypes.data), eig.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                 _P(s.cuda_stream)))
+    return yo, so, mat, eig
 
 
 def sb_apply_precond_noalloc(d_r: int, d_k: int, d_z: int, nx: int, ny: int, nbatch: int, stream: int = 0) -> None:

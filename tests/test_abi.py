@@ -47,3 +47,24 @@ def test_status_strings_without_gpu(libpath):
     from paper_1710_01758_gb300 import sb
     assert sb.status_string(sb.SB_ERR_UNSUPPORTED) == "SB_ERR_UNSUPPORTED"
     assert sb.status_string(sb.SB_OK) == "SB_OK"
+
+
+def test_coil_compression_matrix_host_step():
+    # the host eigen-step of sb_coil_compress needs no GPU: compare with numpy's eigh
+    import numpy as np
+    from paper_1710_01758_gb300 import sb
+    rng = np.random.default_rng(3)
+    for nc, nv in [(1, 1), (4, 2), (12, 6), (32, 16), (8, 8)]:
+        Y = rng.standard_normal((nc, 500)) + 1j * rng.standard_normal((nc, 500))
+        Y[: max(1, nc // 3)] *= 3.0  # distinct dominant directions
+        C = Y @ Y.conj().T
+        mat, eig = sb.coil_compression_matrix(C, nv)
+        s, V = np.linalg.eigh(C)
+        order = np.argsort(s)[::-1]
+        np.testing.assert_allclose(eig, s[order], rtol=1e-10, atol=1e-9 * s.max())
+        np.testing.assert_allclose(mat @ mat.conj().T, np.eye(nv), atol=1e-10)
+        P = mat.conj().T @ mat
+        Vk = V[:, order[:nv]]
+        np.testing.assert_allclose(P, Vk @ Vk.conj().T, atol=1e-9)
+        # rows are eigenvectors: mat C = diag(eig) mat
+        np.testing.assert_allclose(mat @ C, eig[:nv, None] * mat, atol=1e-8 * s.max())

@@ -467,3 +467,42 @@ def test_daubechies4_unsupported(torch, sbm):
     with pytest.raises(sbm.SbError) as ei:
         sbm.Plan(32, 32, 2, 1, 1.0, 0.1, 0.1, 2, wavelet=7)
     assert ei.value.status == sbm.SB_ERR_INVALID_ARG
+
+
+def test_coil_compression(torch, sbm):
+    # Methods, "Coil Compression": 12 coils to 6 virtual coils, then Split Bregman on the virtual
+    # coils; compared with the oracle's compression through phase-invariant quantities
+    from oracle import coil_compression as cc
+    wl = synth.Workload("cc 64x64 Nc12", 64, 64, 12, 4.0, 8, "uniform", 1.0, 0.05, 0.05, 2, 3, 1, 1e-3, 100, 0,
+                        seed=77)
+    nb, nv = 2, 6
+    slices = [synth.make_slice(wl, wl.seed * 1000 + i) for i in range(nb)]
+    y = np.stack([s.y for s in slices])
+    sens = np.stack([s.sens for s in slices])
+    mask = np.stack([s.mask for s in slices])
+    yv, sv, mat, eig = sbm.coil_compress(to_dev(torch, y), to_dev(torch, sens), nv)
+    yv_h, sv_h = yv.cpu().numpy(), sv.cpu().numpy()
+    refs = []
+    for b in range(nb):
+        A_o, s_o = cc.compression_matrix(y[b], nv)
+        np.testing.assert_allclose(eig[b], s_o, rtol=1e-4, atol=1e-6 * s_o[0])
+        gap = s_o[nv - 1] - s_o[nv]
+        P_g = mat[b].astype(np.complex128).conj().T @ mat[b].astype(np.complex128)
+        assert np.abs(P_g - A_o.conj().T @ A_o).max() <= 1e-5 + 1e-5 * s_o[0] / gap
+        yo, so = cc.compress(y[b], sens[b], A_o)
+        refs.append((yo, so))
+        bp_g = operators.encode_adj(yv_h[b], sv_h[b], mask[b], 2)
+        bp_o = operators.encode_adj(yo, so, mask[b], 2)
+        assert rel(bp_g, bp_o) <= 1e-4
+    plan = sbm.Plan(wl.nx, wl.ny, nv, nb, wl.mu, wl.lam, wl.gam, wl.wavelet_levels)
+    plan.set_coils(sv)
+    plan.set_mask(torch.from_numpy(mask).cuda())
+    xd = torch.zeros((nb, wl.ny, wl.nx), dtype=torch.complex64, device="cuda")
+    st, _, _ = plan.split_bregman(yv, xd, wl.n_outer, tau_tv=0.02, tau_w=0.02, fixed_iters=8)
+    assert st == sbm.SB_OK
+    for b in range(nb):
+        yo, so = refs[b]
+        ref = sb_oracle.split_bregman(yo, so, mask[b], wl.mu, wl.lam, wl.gam, wl.wavelet_levels, 2, wl.n_outer, 1,
+                                      1e-3, 100, 8, "circulant", 0.02, 0.02)
+        assert rel(xd[b].cpu().numpy(), ref.x) <= IMG_TOL
+    plan.close()
