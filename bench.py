@@ -73,6 +73,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--groups", type=int, default=0, help="concurrent slice groups (0 = library default)")
+    ap.add_argument("--wavelet", choices=["haar", "daub4"], default="haar",
+                    help="W of Algorithm 1 (daub4: the paper's Daubechies-4; 2D workloads)")
+    ap.add_argument("--compress", type=int, default=0,
+                    help="coil compression to this many virtual coils inside every step (0 = off)")
     return ap.parse_args()
 
 
@@ -157,13 +161,18 @@ def make_inputs(wl, nbatch, seed):
     return slices, sens, mask, y
 
 
-def oracle_recon(wl, s, n_outer=None):
-    """The FP64 oracle on one slice; returns (x, total PCG iterations, seconds)."""
-    from oracle import split_bregman as sbo
+def oracle_recon(wl, s, n_outer=None, wavelet="haar", nv=0):
+    """The FP64 oracle on one slice (coil-compressed to nv virtual coils by the oracle's own
+    compression if 0 < nv < Nc); returns (x, total PCG iterations, seconds)."""
+    from oracle import coil_compression as cc, split_bregman as sbo
     t0 = time.perf_counter()
-    r = sbo.split_bregman(s.y, s.sens, s.mask, wl.mu, wl.lam, wl.gam, wl.wavelet_levels, 2,
+    y, sens = s.y, s.sens
+    if 0 < nv < sens.shape[0]:
+        A, _ = cc.compression_matrix(y, nv)
+        y, sens = cc.compress(y, sens, A)
+    r = sbo.split_bregman(y, sens, s.mask, wl.mu, wl.lam, wl.gam, wl.wavelet_levels, 2,
                           wl.n_outer if n_outer is None else n_outer, wl.n_inner, wl.pcg_tol, wl.pcg_maxit,
-                          wl.pcg_fixed_iters)
+                          wl.pcg_fixed_iters, wavelet=wavelet)
     return r.x, int(sum(r.iters)), time.perf_counter() - t0
 
 
@@ -253,10 +262,14 @@ def run_ours(args):
     d_y = torch.from_numpy(y_h).to(dev)
     x = torch.zeros((B, wl.ny, wl.nx), dtype=torch.complex64, device=dev)
     stream = torch.cuda.current_stream(dev)
-    plan = sb.Plan(wl.nx, wl.ny, wl.ncoils, B, wl.mu, wl.lam, wl.gam, wl.wavelet_levels, stream=stream,
-                   groups=args.groups)
+    wav = sb.SB_WAVELET_DAUB4 if args.wavelet == "daub4" else sb.SB_WAVELET_HAAR
+    ncv = args.compress if 0 < args.compress < wl.ncoils else wl.ncoils
+    plan = sb.Plan(wl.nx, wl.ny, ncv, B, wl.mu, wl.lam, wl.gam, wl.wavelet_levels, stream=stream,
+                   groups=args.groups, wavelet=wav)
 
     def step(ys=d_y, ss=d_sens, ms=d_mask, xx=x):
+        if ncv < wl.ncoils:  # coil compression (Methods, "Coil Compression") is part of the step
+            ys, ss, _, _ = sb.coil_compress(ys, ss, ncv, stream)
         plan.set_coils(ss)
         plan.set_mask(ms)
         st, iters, _ = plan.split_bregman(ys, xx, wl.n_outer, wl.n_inner, **pcg_kw)
@@ -301,7 +314,7 @@ def run_ours(args):
     # scratch written and read three times, p twice, q once
     n = wl.nx * wl.ny
     general = wl.density == "random"
-    bytes_per_slice_iter = ((48 * wl.ncoils + 24) if general else (2 + wl.ncoils) * 8) * n
+    bytes_per_slice_iter = ((48 * ncv + 24) if general else (2 + ncv) * 8) * n
     a_label = "q = A p: k_g3_fwd_y + k_g2_x + k_g3_inv_y" if general else "k_apply_A (q = A p)"
     k1_launches, k1_ms = timing["apply_A"]
     k1_bytes = total_iters * bytes_per_slice_iter
@@ -325,14 +338,15 @@ def run_ours(args):
     # whole PCG iteration (q = A p, the three preconditioner passes, vector updates) bytes
     pcg_classes = ["apply_A", "precond_row_fwd", "precond_col", "precond_row_inv"]
     pcg_ms = sum(timing[k][1] for k in pcg_classes)
-    bytes_pcg_iter = (2 + wl.ncoils) * 8 * n + 4 * 8 * n + (2 * 8 + 4) * n + 5 * 8 * n
+    bytes_pcg_iter = (2 + ncv) * 8 * n + 4 * 8 * n + (2 * 8 + 4) * n + 5 * 8 * n
 
     # untimed diagnostics (rank 0): preconditioned vs plain CG iteration counts on a sub-batch,
     # image error vs the FP64 oracle, the oracle's own throughput
     extra = {}
-    if rank == 0:
+    if rank == 0 and ncv == wl.ncoils:
         nsub = min(8, B)
-        sub = sb.Plan(wl.nx, wl.ny, wl.ncoils, nsub, wl.mu, wl.lam, wl.gam, wl.wavelet_levels, stream=stream)
+        sub = sb.Plan(wl.nx, wl.ny, wl.ncoils, nsub, wl.mu, wl.lam, wl.gam, wl.wavelet_levels, stream=stream,
+                      wavelet=wav)
         sub.set_coils(d_sens[:nsub].contiguous())
         sub.set_mask(d_mask[:nsub].contiguous())
         xs = torch.zeros((nsub, wl.ny, wl.nx), dtype=torch.complex64, device=dev)
@@ -346,8 +360,9 @@ def run_ours(args):
             "first_solve": [round(float(np.mean([i[0] for i in it_plain])), 2),
                             round(float(np.mean([i[0] for i in it_pre])), 2)],
             "slices": nsub}
+    if rank == 0:
         if not args.no_cpu_baseline:
-            x_or, it_or, t_or = oracle_recon(wl, slices[0])
+            x_or, it_or, t_or = oracle_recon(wl, slices[0], wavelet=args.wavelet, nv=ncv)
             xg = x[0].cpu().numpy()
             extra["err_vs_fp64"] = float(np.linalg.norm(xg - x_or) / np.linalg.norm(x_or))
             extra["cpu_baseline"] = {"value": it_or / t_or, "unit": UNIT, "cores": host_threads(), "kind": "oracle",
@@ -387,7 +402,8 @@ def run_ours(args):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": 1e3 * elapsed_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "fp32", "scalars": "fp64", "data": "synthetic",
-                "config": workload_config(wl, B, {"parallelism": f"{world} ranks x independent batches"}),
+                "config": workload_config(wl, B, {"parallelism": f"{world} ranks x independent batches",
+                                                  "wavelet": args.wavelet, "virtual_coils": ncv}),
                 "recon_per_s": recon_per_s,
                 "pcg_iters_per_step": total_all / args.steps,
                 "roofline": {"bound": "hbm", "kernel": a_label,
@@ -559,7 +575,6 @@ def run_volume(args, torch, sb, synth, world, rank, local, dist):
     all_ms = sum(t[1] for t in timing.values())
     breakdown = {k: {"launches": t[0], "ms": round(t[1], 3), "share": round(t[1] / all_ms, 4) if all_ms else None}
                  for k, t in timing.items() if t[0]}
-    # data-term passes: bytes per voxel and coil of the three passes (S and U traffic)
     plan.close()
     if rank == 0:
         line = {"metric": METRIC, "value": total_all / elapsed_max, "unit": UNIT, "n_gpus": world,

@@ -2,7 +2,7 @@
 // sensitivity maps are mapped onto virtual coils by a compression matrix built from the
 // principal components of the coil data, and only the nv most dominant virtual coils are kept.
 //
-//   C = sum over all samples of y y^H         (Nc x Nc, Hermitian)  k_coil_cov + host sum
+//   C = sum over all samples of y y^H         (Nc x Nc, Hermitian)  k_coil_cov, k_coil_cov_reduce
 //   C = V diag(s) V^H, s descending           cyclic complex Jacobi on the host, FP64
 //   A = V[:, :nv]^H                           (nv x Nc)
 //   y_v = A y,  S_v = A S                     k_coil_project
@@ -53,6 +53,21 @@ k_coil_cov(const float2* __restrict__ y, size_t npts, int nc, int nchunks, doubl
         }
         part[((size_t)b * nchunks + chunk) * npairs + pr] = make_double2(re, im);
     }
+}
+
+// cov[b][pair] = sum over chunks, in chunk order (FP64, deterministic)
+__global__ void k_coil_cov_reduce(const double2* __restrict__ part, int nchunks, int npairs, int nb,
+                                  double2* __restrict__ cov) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nb * npairs) return;
+    const int b = i / npairs, pr = i % npairs;
+    double re = 0.0, im = 0.0;
+    for (int ch = 0; ch < nchunks; ++ch) {
+        const double2 v = part[((size_t)b * nchunks + ch) * npairs + pr];
+        re += v.x;
+        im += v.y;
+    }
+    cov[i] = make_double2(re, im);
 }
 
 // out[b][v][i] = sum_c A[b][v][c] in[b][c][i]
@@ -175,30 +190,32 @@ sb_status sb_coil_compress(const void* d_y, const void* d_sens, size_t npix, int
     double2* part = nullptr;
     float2* dmat = nullptr;
     const size_t nparts = (size_t)nbatch * nchunks * npairs;
-    if (cudaMalloc(&part, nparts * sizeof(double2)) != cudaSuccess) return SB_ERR_CUDA;
+    const size_t ncov = (size_t)nbatch * npairs;
+    // partial sums, then the per-slice sums behind them in the same allocation
+    if (cudaMalloc(&part, (nparts + ncov) * sizeof(double2)) != cudaSuccess) return SB_ERR_CUDA;
+    double2* dcov = part + nparts;
     if (cudaMalloc(&dmat, (size_t)nbatch * nv * nc * sizeof(float2)) != cudaSuccess) {
         cudaFree(part);
         return SB_ERR_CUDA;
     }
     sb_status st = SB_OK;
-    std::vector<double2> hp(nparts);
+    std::vector<double2> hp(ncov);
     std::vector<float2> hm((size_t)nbatch * nv * nc);
     do {
         k_coil_cov<<<dim3(nchunks, nbatch), 256, 0, s>>>(static_cast<const float2*>(d_y), npix, nc, nchunks, part);
+        k_coil_cov_reduce<<<(unsigned)((ncov + 255) / 256), 256, 0, s>>>(part, nchunks, npairs, nbatch, dcov);
         if (cudaGetLastError() != cudaSuccess ||
-            cudaMemcpyAsync(hp.data(), part, nparts * sizeof(double2), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaMemcpyAsync(hp.data(), dcov, ncov * sizeof(double2), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
             cudaStreamSynchronize(s) != cudaSuccess) {
             st = SB_ERR_CUDA;
             break;
         }
         for (int b = 0; b < nbatch; ++b) {
             std::vector<cd> cov((size_t)nc * nc, cd(0.0, 0.0));
-            for (int ch = 0; ch < nchunks; ++ch) {  // fixed summation order
-                const double2* pp = hp.data() + ((size_t)b * nchunks + ch) * npairs;
-                int pr = 0;
-                for (int c = 0; c < nc; ++c)
-                    for (int d = c; d < nc; ++d, ++pr) cov[(size_t)c * nc + d] += cd(pp[pr].x, pp[pr].y);
-            }
+            const double2* pp = hp.data() + (size_t)b * npairs;
+            int pr = 0;
+            for (int c = 0; c < nc; ++c)
+                for (int d = c; d < nc; ++d, ++pr) cov[(size_t)c * nc + d] = cd(pp[pr].x, pp[pr].y);
             for (int c = 0; c < nc; ++c)
                 for (int d = 0; d < c; ++d) cov[(size_t)c * nc + d] = std::conj(cov[(size_t)d * nc + c]);
             std::vector<cd> mat;

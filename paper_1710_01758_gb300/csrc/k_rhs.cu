@@ -182,7 +182,10 @@ cudaError_t rhs_n(const Dims& d, const CUtensorMap& smap, const CUtensorMap& yma
                   const SbFields& f, const float2* x, float2* r, const float2* tw, float mu, float lam, float gam,
                   SliceState* st, double tol2, Red red, cudaStream_t s) {
     const size_t sm = rhs_smem_bytes(NY, f.ms);
-    cudaError_t e = cudaFuncSetAttribute(k_rhs<NY, AB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    // the limit is shared by all host threads (concurrent plans differ in ms): set it to the size
+    // of the largest ms the library accepts (256), never to this launch's own size
+    cudaError_t e = cudaFuncSetAttribute(k_rhs<NY, AB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)rhs_smem_bytes(NY, 256));
     if (e != cudaSuccess) return e;
     k_rhs<NY, AB><<<dim3(d.nx / TX, d.nb), TX * NY / 16, sm, s>>>(smap, ymap, y1map, f, d.nx, d.nc, x, r, tw, mu,
                                                                    lam, gam, st, tol2, red);

@@ -112,6 +112,11 @@ __global__ void k_add_scaled(float2* __restrict__ g, const float2* __restrict__ 
     }
 }
 
+// The dynamic shared-memory limit of a kernel is one setting shared by every host thread, so it
+// is always set to the largest size any launch needs (16 columns x 512 rows): a smaller,
+// per-launch value could be lowered by another thread between its set and its launch.
+constexpr int kColsSmemMax = 16 * 512 * (int)sizeof(float2);
+
 unsigned blocks_for(size_t n) {
     const size_t b = (n + 255) / 256;
     return (unsigned)(b < 8192 ? b : 8192);
@@ -131,7 +136,8 @@ cudaError_t launch_d4_update(const Dims& d, const float2* x, float2* w, float2* 
         k_d4_rows<false><<<dim3(by, d.nb), 256, 0, s>>>(l == 0 ? x : w, w, d.nx, d.ny, bx);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         const size_t sm = (size_t)16 * by * sizeof(float2);
-        if ((e = cudaFuncSetAttribute(k_d4_cols<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)) != cudaSuccess)
+        if ((e = cudaFuncSetAttribute(k_d4_cols<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kColsSmemMax)) !=
+            cudaSuccess)
             return e;
         k_d4_cols<false><<<dim3((bx + 15) / 16, d.nb), 256, sm, s>>>(w, d.nx, d.ny, bx, by);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -142,7 +148,8 @@ cudaError_t launch_d4_update(const Dims& d, const float2* x, float2* w, float2* 
     for (int l = levels - 1; l >= 0; --l) {
         const int bx = d.nx >> l, by = d.ny >> l;
         const size_t sm = (size_t)16 * by * sizeof(float2);
-        if ((e = cudaFuncSetAttribute(k_d4_cols<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)) != cudaSuccess)
+        if ((e = cudaFuncSetAttribute(k_d4_cols<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kColsSmemMax)) !=
+            cudaSuccess)
             return e;
         k_d4_cols<true><<<dim3((bx + 15) / 16, d.nb), 256, sm, s>>>(w, d.nx, d.ny, bx, by);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
