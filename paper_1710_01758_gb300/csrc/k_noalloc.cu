@@ -89,7 +89,7 @@ template <int NY>
 cudaError_t col_k_n(int nx, int nb, float2* t, const float* k, const float2* tw, cudaStream_t s) {
     const size_t sm = (2 * NY * TX + NY) * sizeof(float2);
     if (sm > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_col_precond_k<NY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaError_t e = set_smem_limit(k_col_precond_k<NY>, (int)sm);
         if (e != cudaSuccess) return e;
     }
     k_col_precond_k<NY><<<dim3(nx / TX, nb), TX * NY / 16, sm, s>>>(t, k, tw, nx);

@@ -336,7 +336,7 @@ k_zero_rhs(float2* __restrict__ x, int n, const SliceState* st) {
 // ------------------------------------------------------------------------------ launch helpers
 template <class K>
 cudaError_t prepare(K kernel, size_t smem) {
-    if (smem > 48 * 1024) return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (smem > 48 * 1024) return set_smem_limit(kernel, (int)smem);
     return cudaSuccess;
 }
 

@@ -229,7 +229,7 @@ cudaError_t fused_n(const Dims& d, float2* x, float2* r, float2* p, const float2
                     int* clusters) {
     using F = Fused<NX, NY>;
     auto kern = k_precond_fused<NX, NY, MODE>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)F::smem);
+    cudaError_t e = set_smem_limit(kern, (int)F::smem);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(F::C, d.nb);

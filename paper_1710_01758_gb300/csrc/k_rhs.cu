@@ -184,8 +184,7 @@ cudaError_t rhs_n(const Dims& d, const CUtensorMap& smap, const CUtensorMap& yma
     const size_t sm = rhs_smem_bytes(NY, f.ms);
     // the limit is shared by all host threads (concurrent plans differ in ms): set it to the size
     // of the largest ms the library accepts (256), never to this launch's own size
-    cudaError_t e = cudaFuncSetAttribute(k_rhs<NY, AB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)rhs_smem_bytes(NY, 256));
+    cudaError_t e = set_smem_limit(k_rhs<NY, AB>, (int)rhs_smem_bytes(NY, 256));
     if (e != cudaSuccess) return e;
     k_rhs<NY, AB><<<dim3(d.nx / TX, d.nb), TX * NY / 16, sm, s>>>(smap, ymap, y1map, f, d.nx, d.nc, x, r, tw, mu,
                                                                    lam, gam, st, tol2, red);

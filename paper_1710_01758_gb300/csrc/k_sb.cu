@@ -133,7 +133,7 @@ cudaError_t launch_ytilde(const Dims& d, const float2* y, const int* lines, int 
     {                                                                                                         \
         const size_t sm = smem_row<N>();                                                                      \
         if (sm > 48 * 1024 &&                                                                                 \
-            (e = cudaFuncSetAttribute(k_ytilde<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)) != \
+            (e = set_smem_limit(k_ytilde<N>, (int)sm)) != \
                 cudaSuccess)                                                                                  \
             return e;                                                                                         \
         k_ytilde<N><<<grid, RY * N / 16, sm, s>>>(y, lines, d.ny, d.nc, ms, nrows, yt1, tw_x);                \
@@ -162,7 +162,7 @@ cudaError_t launch_rss(const Dims& d, const SbFields& f, float2* x, int write_x,
     {                                                                                                      \
         const size_t sm = (2 * N * TX + N) * sizeof(float2) + N * sizeof(int);                             \
         if (sm > 48 * 1024 &&                                                                              \
-            (e = cudaFuncSetAttribute(k_rss<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)) != \
+            (e = set_smem_limit(k_rss<N>, (int)sm)) != \
                 cudaSuccess)                                                                               \
             return e;                                                                                      \
         k_rss<N><<<grid, TX * N / 16, sm, s>>>(f, d.nx, d.nc, x, write_x, tw_y);                           \

@@ -171,10 +171,10 @@ cudaError_t fft_rows_n(int ny, int nimg, float2* data, const float2* tw, bool in
     const size_t sm = (RY * (NX + NX / 16) + NX) * sizeof(float2);
     cudaError_t e;
     if (inv) {
-        if (sm > 48 * 1024 && (e = cudaFuncSetAttribute(k_fft_rows<NX, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)) != cudaSuccess) return e;
+        if (sm > 48 * 1024 && (e = set_smem_limit(k_fft_rows<NX, true>, (int)sm)) != cudaSuccess) return e;
         k_fft_rows<NX, true><<<grid, block, sm, s>>>(data, rows, tw);
     } else {
-        if (sm > 48 * 1024 && (e = cudaFuncSetAttribute(k_fft_rows<NX, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)) != cudaSuccess) return e;
+        if (sm > 48 * 1024 && (e = set_smem_limit(k_fft_rows<NX, false>, (int)sm)) != cudaSuccess) return e;
         k_fft_rows<NX, false><<<grid, block, sm, s>>>(data, rows, tw);
     }
     return cudaGetLastError();
@@ -186,10 +186,10 @@ cudaError_t fft_cols_n(int nx, int nimg, float2* data, const float2* tw, bool in
     const size_t sm = (NY * TX + NY) * sizeof(float2);
     cudaError_t e;
     if (inv) {
-        if (sm > 48 * 1024 && (e = cudaFuncSetAttribute(k_fft_cols<NY, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)) != cudaSuccess) return e;
+        if (sm > 48 * 1024 && (e = set_smem_limit(k_fft_cols<NY, true>, (int)sm)) != cudaSuccess) return e;
         k_fft_cols<NY, true><<<grid, block, sm, s>>>(data, nx, tw);
     } else {
-        if (sm > 48 * 1024 && (e = cudaFuncSetAttribute(k_fft_cols<NY, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)) != cudaSuccess) return e;
+        if (sm > 48 * 1024 && (e = set_smem_limit(k_fft_cols<NY, false>, (int)sm)) != cudaSuccess) return e;
         k_fft_cols<NY, false><<<grid, block, sm, s>>>(data, nx, tw);
     }
     return cudaGetLastError();

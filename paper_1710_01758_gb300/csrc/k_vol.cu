@@ -523,7 +523,7 @@ k_sb_update3(SbFields f, int nx, int ny, int nz, const float2* __restrict__ x, i
 // ---------------------------------------------------------------------- launch helpers
 template <class K>
 cudaError_t prep(K kernel, size_t smem) {
-    if (smem > 48 * 1024) return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (smem > 48 * 1024) return set_smem_limit(kernel, (int)smem);
     return cudaSuccess;
 }
 

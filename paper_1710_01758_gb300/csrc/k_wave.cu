@@ -136,7 +136,7 @@ cudaError_t launch_d4_update(const Dims& d, const float2* x, float2* w, float2* 
         k_d4_rows<false><<<dim3(by, d.nb), 256, 0, s>>>(l == 0 ? x : w, w, d.nx, d.ny, bx);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         const size_t sm = (size_t)16 * by * sizeof(float2);
-        if ((e = cudaFuncSetAttribute(k_d4_cols<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kColsSmemMax)) !=
+        if ((e = set_smem_limit(k_d4_cols<false>, kColsSmemMax)) !=
             cudaSuccess)
             return e;
         k_d4_cols<false><<<dim3((bx + 15) / 16, d.nb), 256, sm, s>>>(w, d.nx, d.ny, bx, by);
@@ -148,7 +148,7 @@ cudaError_t launch_d4_update(const Dims& d, const float2* x, float2* w, float2* 
     for (int l = levels - 1; l >= 0; --l) {
         const int bx = d.nx >> l, by = d.ny >> l;
         const size_t sm = (size_t)16 * by * sizeof(float2);
-        if ((e = cudaFuncSetAttribute(k_d4_cols<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kColsSmemMax)) !=
+        if ((e = set_smem_limit(k_d4_cols<true>, kColsSmemMax)) !=
             cudaSuccess)
             return e;
         k_d4_cols<true><<<dim3((bx + 15) / 16, d.nb), 256, sm, s>>>(w, d.nx, d.ny, bx, by);

@@ -34,6 +34,15 @@ struct SliceState {
 // rows of one TMA box of a coil tile (boxes span at most 256 rows and must tile ny)
 __host__ __device__ constexpr int coil_box_rows(int ny) { return ny <= 256 ? ny : (ny % 256 == 0 ? 256 : ny / 2); }
 
+// Raise a kernel's dynamic shared-memory limit to `bytes`, once per (kernel, device): the
+// attribute is one setting shared by all host threads, and a driver call before every launch
+// costs more than the launch itself when several host threads drive slice groups.
+cudaError_t set_smem_limit(const void* kernel, int bytes);
+template <class F>
+cudaError_t set_smem_limit(F* kernel, int bytes) {
+    return set_smem_limit(reinterpret_cast<const void*>(kernel), bytes);
+}
+
 struct Dims {
     int nx, ny, nc, nb;
 };

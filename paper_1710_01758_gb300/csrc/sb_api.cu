@@ -14,6 +14,8 @@
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <set>
+#include <tuple>
 #include <string>
 #include <thread>
 #include <vector>
@@ -23,12 +25,36 @@
 
 using namespace sb;
 
+namespace sb {
+cudaError_t set_smem_limit(const void* kernel, int bytes) {
+    static std::mutex mu;
+    static std::set<std::tuple<const void*, int, int>> done;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const auto key = std::make_tuple(kernel, dev, bytes);
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if (done.count(key)) return cudaSuccess;
+    }
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) {
+        std::lock_guard<std::mutex> lock(mu);
+        done.insert(key);
+    }
+    return e;
+}
+}  // namespace sb
+
 namespace {
 
 std::atomic<uint64_t> g_launches{0};
 
 // PCG iterations enqueued between two reads of the per-slice state
-constexpr int kPollEvery = 4;
+#ifndef SB_POLL_EVERY
+#define SB_POLL_EVERY 4
+#endif
+constexpr int kPollEvery = SB_POLL_EVERY;
 
 bool supported_n(int n) {
     return n == 32 || n == 64 || n == 128 || n == 256 || n == 512 || n == 192 || n == 224 || n == 320 || n == 384;
