@@ -244,12 +244,12 @@ cudaError_t apply_A_n(const Dims& d, const CUtensorMap& smap, const float2* p, f
     const size_t sm = smem_apply_A<NY>();
     cudaError_t e;
     if (st) {
-        if ((e = cudaFuncSetAttribute(k_apply_A<NY, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)) !=
+        if ((e = set_smem_limit(k_apply_A<NY, true>, (int)sm)) !=
             cudaSuccess)
             return e;
         k_apply_A<NY, true><<<grid, block, sm, s>>>(smap, p, q, maskw, tw, d.nx, d.nc, mu, lam, gam, st, red);
     } else {
-        if ((e = cudaFuncSetAttribute(k_apply_A<NY, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)) !=
+        if ((e = set_smem_limit(k_apply_A<NY, false>, (int)sm)) !=
             cudaSuccess)
             return e;
         k_apply_A<NY, false><<<grid, block, sm, s>>>(smap, p, q, maskw, tw, d.nx, d.nc, mu, lam, gam, st, red);
