@@ -197,8 +197,10 @@ sb_status sb_apply_precond_noalloc(const void* d_r, const float* d_k, void* d_z,
  *                         descending; a row is defined up to a unit phase).
  *   h_eig (optional):     host double [nbatch][nc], the eigenvalues of C, descending.
  *   1 <= nv <= nc <= 32.  C is summed in FP32 over 128-sample chunks and in FP64 across them;
- * the eigen-decomposition is a cyclic complex Jacobi in FP64 on the host.  Allocates device
- * scratch, synchronises cuda_stream; SB_ERR_INVALID_ARG / SB_ERR_CUDA on failure. */
+ * the eigen-decomposition is a cyclic complex Jacobi in FP64 on the host.  Keeps one device
+ * scratch block per device, grown on demand and kept until the process exits (calls on one
+ * device are serialised on it); synchronises cuda_stream; SB_ERR_INVALID_ARG / SB_ERR_CUDA on
+ * failure. */
 sb_status sb_coil_compress(const void* d_y, const void* d_sens, size_t npix, int nc, int nbatch, int nv,
                            void* d_y_out, void* d_sens_out, void* h_matrix, double* h_eig, void* cuda_stream);
 

@@ -12,6 +12,8 @@
 #include <algorithm>
 #include <cmath>
 #include <complex>
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -79,18 +81,46 @@ k_coil_project(const float2* __restrict__ in, float2* __restrict__ out, const fl
     for (int k = threadIdx.x; k < nv * nc; k += blockDim.x) a[k] = A[(size_t)b * nv * nc + k];
     __syncthreads();
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < npts; i += (size_t)gridDim.x * blockDim.x) {
-        float2 v[kMaxCoils];
-#pragma unroll 4
-        for (int c = 0; c < nc; ++c) v[c] = in[((size_t)b * nc + c) * npts + i];
+        float2 v[kMaxCoils];  // fixed trip counts keep v in registers
+#pragma unroll
+        for (int c = 0; c < kMaxCoils; ++c)
+            v[c] = c < nc ? in[((size_t)b * nc + c) * npts + i] : make_float2(0.f, 0.f);
         for (int o = 0; o < nv; ++o) {
             float2 acc = make_float2(0.f, 0.f);
-            for (int c = 0; c < nc; ++c) acc = cadd(acc, cmul(a[o * nc + c], v[c]));
+#pragma unroll
+            for (int c = 0; c < kMaxCoils; ++c)
+                if (c < nc) acc = cadd(acc, cmul(a[o * nc + c], v[c]));
             out[((size_t)b * nv + o) * npts + i] = acc;
         }
     }
 }
 
 using cd = std::complex<double>;
+
+// device scratch of sb_coil_compress, kept per device and grown on demand (a cudaFree per call
+// would synchronise the device); the mutex also serialises concurrent calls on one device
+struct Scratch {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+};
+std::mutex g_scratch_mu;
+std::map<int, Scratch> g_scratch;
+
+cudaError_t scratch_get(size_t bytes, void** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    Scratch& s = g_scratch[dev];
+    if (s.bytes < bytes) {
+        if (s.ptr) cudaFree(s.ptr);
+        s.ptr = nullptr;
+        s.bytes = 0;
+        if ((e = cudaMalloc(&s.ptr, bytes)) != cudaSuccess) return e;
+        s.bytes = bytes;
+    }
+    *out = s.ptr;
+    return cudaSuccess;
+}
 
 // Eigen-decomposition of a Hermitian n x n matrix (row-major) by cyclic Jacobi rotations.  Each
 // rotation zeroes a[p][q]: with a[p][q] = |b| e^{i phi}, D = diag(1, e^{-i phi}) makes the 2 x 2
@@ -187,17 +217,17 @@ sb_status sb_coil_compress(const void* d_y, const void* d_sens, size_t npix, int
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     const int nchunks = (int)((npix + kChunk - 1) / kChunk);
     const int npairs = nc * (nc + 1) / 2;
-    double2* part = nullptr;
-    float2* dmat = nullptr;
     const size_t nparts = (size_t)nbatch * nchunks * npairs;
     const size_t ncov = (size_t)nbatch * npairs;
-    // partial sums, then the per-slice sums behind them in the same allocation
-    if (cudaMalloc(&part, (nparts + ncov) * sizeof(double2)) != cudaSuccess) return SB_ERR_CUDA;
-    double2* dcov = part + nparts;
-    if (cudaMalloc(&dmat, (size_t)nbatch * nv * nc * sizeof(float2)) != cudaSuccess) {
-        cudaFree(part);
+    // partial sums, the per-slice sums and the compression matrices in one scratch block
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    void* base = nullptr;
+    if (scratch_get((nparts + ncov) * sizeof(double2) + (size_t)nbatch * nv * nc * sizeof(float2), &base) !=
+        cudaSuccess)
         return SB_ERR_CUDA;
-    }
+    double2* part = static_cast<double2*>(base);
+    double2* dcov = part + nparts;
+    float2* dmat = reinterpret_cast<float2*>(dcov + ncov);
     sb_status st = SB_OK;
     std::vector<double2> hp(ncov);
     std::vector<float2> hm((size_t)nbatch * nv * nc);
@@ -238,8 +268,6 @@ sb_status sb_coil_compress(const void* d_y, const void* d_sens, size_t npix, int
                                                               static_cast<float2*>(d_sens_out), dmat, npix, nc, nv);
         if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) st = SB_ERR_CUDA;
     } while (false);
-    cudaFree(part);
-    cudaFree(dmat);
     return st;
 }
 
