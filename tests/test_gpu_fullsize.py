@@ -81,3 +81,87 @@ def test_volume_full_size_operators():
     assert np.max(np.abs(kg - kref)) <= 1e-5 * np.max(kref)
     zref = precond.apply_precond(x, kref, 3)
     assert np.linalg.norm(z - zref) / np.linalg.norm(zref) <= 1e-5
+
+
+def _oracle_recon(wl, s):
+    return sb_oracle.split_bregman(s.y, s.sens, s.mask, wl.mu, wl.lam, wl.gam, wl.wavelet_levels, 2, wl.n_outer,
+                                   wl.n_inner, wl.pcg_tol, wl.pcg_maxit)
+
+
+def test_large_512_batch_sampled_slice():
+    """512 x 512, 32 coils, R = 6 variable-density lines (the bench's --workload 512: 8 slices in
+    one call): slice 5 recomputed by the oracle; iterations within one per solve, image within
+    the PCG tolerance."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1710_01758_gb300 import sb
+
+    wl = synth.LARGE_512
+    B = 8
+    slices = synth.make_batch(wl, B, wl.seed)
+    sens = torch.from_numpy(np.stack([s.sens for s in slices])).to(torch.complex64).cuda()
+    mask = torch.from_numpy(np.stack([s.mask for s in slices])).cuda()
+    y = torch.from_numpy(np.stack([s.y for s in slices])).to(torch.complex64).cuda()
+    x = torch.zeros((B, wl.ny, wl.nx), dtype=torch.complex64, device="cuda")
+    plan = sb.Plan(wl.nx, wl.ny, wl.ncoils, B, wl.mu, wl.lam, wl.gam, wl.wavelet_levels)
+    plan.set_coils(sens)
+    plan.set_mask(mask)
+    st, iters, last = plan.split_bregman(y, x, wl.n_outer, wl.n_inner, tol=wl.pcg_tol, maxit=wl.pcg_maxit)
+    assert st == sb.SB_OK
+    xg = x.cpu().numpy()
+    assert np.isfinite(xg).all() and all(r[2] for r in last)
+    ref = _oracle_recon(wl, slices[5])
+    assert all(abs(a - b) <= 1 for a, b in zip(iters[5], ref.iters)), (iters[5], ref.iters)
+    assert np.linalg.norm(xg[5] - ref.x) / np.linalg.norm(ref.x) <= 1e-3
+    plan.close()
+
+
+def test_uneven_batch_full_size_sampled_slices():
+    """The 64-slice uneven batch (the bench's --workload uneven64): all geometries reconstructed
+    concurrently with sb_split_bregman_many; one slice of each image size recomputed by the
+    oracle, iterations within one per solve, images within the PCG tolerance."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import collections
+    from paper_1710_01758_gb300 import sb
+
+    wls = synth.uneven_workloads()
+    groups = collections.defaultdict(list)
+    for i, w in enumerate(wls):
+        groups[(w.nx, w.ny, w.ncoils)].append(i)
+    plans, ys, xs, keep, members = [], [], [], [], []
+    for (nx, ny, nc), ids in sorted(groups.items()):
+        sl = [synth.uneven_slice(wls, i) for i in ids]
+        w = wls[ids[0]]
+        s_ = torch.from_numpy(np.stack([s.sens for s in sl])).to(torch.complex64).cuda()
+        m_ = torch.from_numpy(np.stack([s.mask for s in sl])).cuda()
+        ys.append(torch.from_numpy(np.stack([s.y for s in sl])).to(torch.complex64).cuda())
+        xs.append(torch.zeros((len(ids), ny, nx), dtype=torch.complex64, device="cuda"))
+        torch.cuda.synchronize()
+        p = sb.Plan(nx, ny, nc, len(ids), w.mu, w.lam, w.gam, w.wavelet_levels, stream=torch.cuda.Stream())
+        p.set_coils(s_)
+        p.set_mask(m_)
+        keep.append(s_)
+        plans.append(p)
+        members.append((ids, sl))
+    torch.cuda.synchronize()
+    w0 = wls[0]
+    st, iters, last = sb.split_bregman_many(plans, ys, xs, w0.n_outer, w0.n_inner, tol=w0.pcg_tol,
+                                            maxit=w0.pcg_maxit)
+    assert st == sb.SB_OK
+    seen = set()
+    for (ids, sl), x, it, la in zip(members, xs, iters, last):
+        xg = x.cpu().numpy()
+        assert np.isfinite(xg).all() and all(r[2] for r in la)
+        w = wls[ids[0]]
+        if (w.nx, w.ny) in seen:
+            continue
+        seen.add((w.nx, w.ny))
+        ref = _oracle_recon(w, sl[0])
+        assert all(abs(a - b) <= 1 for a, b in zip(it[0], ref.iters)), (w.name, it[0], ref.iters)
+        assert np.linalg.norm(xg[0] - ref.x) / np.linalg.norm(ref.x) <= 1e-3, w.name
+    assert len(seen) == 4
+    for p in plans:
+        p.close()
