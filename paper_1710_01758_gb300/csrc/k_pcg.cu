@@ -177,9 +177,16 @@ k_row_inv(const float2* __restrict__ tb, float2* __restrict__ out, float2* __res
         return;
     }
     for (int i = tid; i < NX; i += NT) tw[i] = tw_g[i];
-    float2 v[16];
+    float2 v[16], pp[MODE == 2 ? 16 : 1], xv[MODE == 2 ? 16 : 1];
+    // every load of the pass is issued before the transform: one memory latency per CTA
 #pragma unroll
-    for (int e = 0; e < 16; ++e) v[e] = tb[base + t + T * e];
+    for (int e = 0; e < 16; ++e) {
+        v[e] = tb[base + t + T * e];
+        if constexpr (MODE == 2) {
+            pp[e] = p[base + t + T * e];
+            xv[e] = x[base + t + T * e];
+        }
+    }
     __syncthreads();
     fft<NX, true>(v, t, buf, RowIdx<NX>{row}, tw);
     if constexpr (MODE == 0) {
@@ -193,12 +200,8 @@ k_row_inv(const float2* __restrict__ tb, float2* __restrict__ out, float2* __res
 #pragma unroll
         for (int e = 0; e < 16; ++e) {
             const size_t i = base + t + T * e;
-            const float2 pp = p[i];
-            float2 xv = x[i];
-            xv.x = fmaf(alpha, pp.x, xv.x);
-            xv.y = fmaf(alpha, pp.y, xv.y);
-            x[i] = xv;
-            p[i] = make_float2(fmaf(beta, pp.x, v[e].x), fmaf(beta, pp.y, v[e].y));
+            x[i] = make_float2(fmaf(alpha, pp[e].x, xv[e].x), fmaf(alpha, pp[e].y, xv[e].y));
+            p[i] = make_float2(fmaf(beta, pp[e].x, v[e].x), fmaf(beta, pp[e].y, v[e].y));
         }
     }
 }
