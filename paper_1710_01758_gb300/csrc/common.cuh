@@ -1,5 +1,6 @@
-// Shared device helpers: complex arithmetic, small DFTs, the two-stage Stockham FFT that
-// keeps a transform in registers, and deterministic block / cross-CTA reductions.
+// Shared device helpers: complex arithmetic, small DFTs, the register-resident Stockham FFTs
+// (two stages up to 256 points, three at 512, a radix-16 stage plus two shared-memory stages for
+// 192, 224, 320 and 384 points), and deterministic block / cross-CTA reductions.
 #pragma once
 
 #include <cuda_runtime.h>

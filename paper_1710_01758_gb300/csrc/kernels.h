@@ -55,6 +55,8 @@ struct Red {
     unsigned* err;
 };
 
+// minimum per-slice capacity of Red::part (plans raise it to their widest launch: rows / 16,
+// column tiles x planes, z columns of a volume)
 constexpr int kMaxParts = 1024;
 constexpr int kVecThreads = 256;
 constexpr int kVecPerThread = 8;
