@@ -48,6 +48,9 @@ HBM_FALLBACK_GBS = 6800.0
 # written) scaled by the slices processed.  Set to None whenever the kernel changes until it is
 # captured again.
 TRAFFIC_K1 = 2 * (228.29e6 + 9.14e6)
+# --prec: (sb_precision, dtype label of the JSON line)
+PRECS = {"fp32": (0, "fp32"), "split-bf16": (1, "bf16x2 split, fp32 accumulate (tensor-core DFT stages)"),
+         "split-fp16": (2, "fp16x2 split, fp32 accumulate (tensor-core DFT stages)")}
 # workloads: name -> (synth workload attribute, default batch).  The default is the headline
 # configuration; the others are further measurement lines (batches sized above L2).
 WORKLOADS = {"256": ("METRIC_256", 64), "128": ("SMALL_128", 512), "512": ("LARGE_512", 8),
@@ -73,6 +76,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--groups", type=int, default=0, help="concurrent slice groups (0 = library default)")
+    ap.add_argument("--prec", choices=list(PRECS), default="fp32",
+                    help="fp32, or a split-precision mode: the radix-16 DFT stages of q = A p on the tensor cores "
+                         "with operands split in two bf16 / fp16 terms and FP32 accumulation (ny = 256)")
     ap.add_argument("--wavelet", choices=["haar", "daub4"], default="haar",
                     help="W of Algorithm 1 (daub4: the paper's Daubechies-4; 2D workloads)")
     ap.add_argument("--compress", type=int, default=0,
@@ -264,8 +270,9 @@ def run_ours(args):
     stream = torch.cuda.current_stream(dev)
     wav = sb.SB_WAVELET_DAUB4 if args.wavelet == "daub4" else sb.SB_WAVELET_HAAR
     ncv = args.compress if 0 < args.compress < wl.ncoils else wl.ncoils
+    prec, dtype_label = PRECS[args.prec]
     plan = sb.Plan(wl.nx, wl.ny, ncv, B, wl.mu, wl.lam, wl.gam, wl.wavelet_levels, stream=stream,
-                   groups=args.groups, wavelet=wav)
+                   groups=args.groups, wavelet=wav, prec=prec)
 
     def step(ys=d_y, ss=d_sens, ms=d_mask, xx=x):
         if ncv < wl.ncoils:  # coil compression (Methods, "Coil Compression") is part of the step
@@ -349,7 +356,7 @@ def run_ours(args):
     if rank == 0 and ncv == wl.ncoils:
         nsub = min(8, B)
         sub = sb.Plan(wl.nx, wl.ny, wl.ncoils, nsub, wl.mu, wl.lam, wl.gam, wl.wavelet_levels, stream=stream,
-                      wavelet=wav)
+                      wavelet=wav, prec=prec)
         sub.set_coils(d_sens[:nsub].contiguous())
         sub.set_mask(d_mask[:nsub].contiguous())
         xs = torch.zeros((nsub, wl.ny, wl.nx), dtype=torch.complex64, device=dev)
@@ -421,9 +428,10 @@ def run_ours(args):
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": 1e3 * elapsed_max / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "fp32", "scalars": "fp64", "data": "synthetic",
+                "scaling": "weak", "vs_baseline": None, "dtype": dtype_label, "scalars": "fp64", "data": "synthetic",
                 "config": workload_config(wl, B, {"parallelism": f"{world} ranks x independent batches",
-                                                  "wavelet": args.wavelet, "virtual_coils": ncv}),
+                                                  "wavelet": args.wavelet, "virtual_coils": ncv,
+                                                  "precision": args.prec}),
                 "recon_per_s": recon_per_s,
                 "pcg_iters_per_step": total_all / args.steps,
                 "roofline": {"bound": "hbm", "kernel": a_label,
@@ -440,6 +448,7 @@ def run_ours(args):
                                          "achieved_gbs": achieved_in_step,
                                          "note": "concurrent slice groups overlap; active slices only"}},
                 "pcg_iteration_gbs": (it_breakdown * bytes_pcg_iter / (pcg_ms / 1e3) / 1e9) if pcg_ms else None,
+                "tensor_core": tensor_core_rate(args, wl, B, ncv, k1_alone_us),
                 "kernel_time_breakdown": breakdown,
                 "kernel_time_breakdown_from": "one extra untimed step with CUDA events around every launch",
                 "gpu_launches": int(launches),
@@ -449,6 +458,17 @@ def run_ours(args):
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def tensor_core_rate(args, wl, B, ncv, k1_us):
+    """Split-precision modes: the MMA work of one q = A p over the batch (4 radix-16 stages per
+    coil and 8-column tile, 2 K-steps x 3 split products of 128 x 32 x 16 each) per launch time."""
+    if args.prec == "fp32" or not k1_us:
+        return None
+    flops = B * ncv * (wl.nx // 8) * 4 * 6 * (2 * 128 * 32 * 16)
+    return {"mma_tflops_per_launch": flops / 1e12, "achieved_tflops": flops / (k1_us / 1e6) / 1e12,
+            "note": "kind::f16 tcgen05.mma, M=128 N=32 K=16; the kernel is bound by the stage round trips "
+                    "(TMEM -> registers -> shared memory), not by the tensor pipe"}
 
 
 def run_uneven(args, torch, sb, synth, world, rank, local, dist):

@@ -1,0 +1,369 @@
+// q = A p with the DFT stages of the data term on the tensor cores (the split-precision modes).
+//
+// A = mu sum_c S_c^H F^H R F S_c + lambda D^H D + gamma I (Eq. system; PI+CS paragraph), with a
+// mask constant along the readout axis x, so the data term is a length-256 DFT along y per
+// column, the mask, and the inverse DFT.  Each 256-point transform is factored 16 x 16:
+// y = s + 16 e and k = k1 + 16 k2,
+//   X[k1 + 16 k2] = 1/4 sum_s W_256^{s k1} W_16^{s k2} (1/4 sum_e W_16^{e k1} u[s + 16 e])
+// (unitary overall, 1/4 per stage), and the inverse runs the conjugate steps in reverse order.
+// Each of the four radix-16 stages is one tensor-core product D[128 x 32] = A[128 x 32] B^T with
+// A = 128 sub-vectors of 16 complex values (8 columns x 16 per column) as 32 reals, interleaved
+// (re, im), and B = the real form of the 16-point DFT matrix (32 x 32).  The operands are split
+// in two 16-bit terms, v = v_hi + v_lo (bf16 or fp16), and a stage accumulates
+//   A_hi B_hi + (A_lo 2^L)(B_hi 2^-L) + A_hi B_lo
+// in FP32 in tensor memory (L = 10 for fp16, which keeps the low parts in its normal range;
+// L = 0 for bf16).  For fp16 the p tile of a CTA is first scaled by an exact power of two so
+// that its largest component lies in [1/2, 1).  Between stages the 32 accumulator columns of
+// each lane come back to registers (tcgen05.ld), take the twiddles W_256^{+-s k1} or the mask,
+// and are split and stored as the next stage's A operand; the transposes of the factorisation
+// happen in that store.  Coil tiles arrive by TMA as 8-column boxes with the 64-byte swizzle.
+// The epilogue (periodic 5-point stencil, gamma p, Re(p^H q) and alpha) is that of the FP32
+// kernel.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <cmath>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "tma.cuh"
+#include "umma.cuh"
+
+namespace sb {
+namespace {
+
+constexpr int kTcNY = 256, kTcTX = 8, kTcNT = 128;
+// A operand: 128 rows x (32 hi + 32 lo) 16-bit elements.  K-adjacent core matrices 144 B apart
+// and 8-row groups 1184 B apart: the transposed stores of a warp (16 rows' worth of one element
+// each from 32 threads) then fall on 32 distinct banks.
+constexpr uint32_t kLboA = 144, kSboA = 1184;
+constexpr int kAbytes = 16 * kSboA;
+// B operands: 32 rows x 32 elements, 2048 B each, in the order forward (hi, hi 2^-L, lo),
+// inverse (hi, hi 2^-L, lo).
+constexpr uint32_t kLboB = 128, kSboB = 512, kBmat = 2048;
+constexpr int kBbytes = 6 * kBmat;
+
+__device__ __forceinline__ uint32_t pad1024(const void* p) {
+    const uint32_t a = static_cast<uint32_t>(__cvta_generic_to_shared(p));
+    return ((a + 1023u) & ~1023u) - a;
+}
+
+// 8-column tile (64-byte rows) with the 64-byte TMA swizzle: 16-byte chunk index ^= (row >> 1) & 3
+__device__ __forceinline__ int swz64(int row, int col) {
+    return row * kTcTX + ((((col >> 1) ^ ((row >> 1) & 3)) << 1) | (col & 1));
+}
+
+// byte offset of complex element kc (elements 2 kc, 2 kc + 1) of A-operand row `row`, part 0 (hi)
+// or 1 (lo)
+__device__ __forceinline__ uint32_t a_off(int row, int kc, int part) {
+    const int k = 2 * kc;
+    return (uint32_t)(row >> 3) * kSboA + (uint32_t)(part * 4 + (k >> 3)) * kLboA + (uint32_t)(row & 7) * 16u +
+           (uint32_t)(k & 7) * 2u;
+}
+
+template <bool BF16>
+__device__ __forceinline__ void split_pack(float2 v, float ls, uint32_t& hi, uint32_t& lo) {
+    if constexpr (BF16) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(v.x, v.y);
+        const float2 hf = __bfloat1622float2(h);
+        const __nv_bfloat162 l = __floats2bfloat162_rn((v.x - hf.x) * ls, (v.y - hf.y) * ls);
+        hi = *reinterpret_cast<const uint32_t*>(&h);
+        lo = *reinterpret_cast<const uint32_t*>(&l);
+    } else {
+        const __half2 h = __floats2half2_rn(v.x, v.y);
+        const float2 hf = __half22float2(h);
+        const __half2 l = __floats2half2_rn((v.x - hf.x) * ls, (v.y - hf.y) * ls);
+        hi = *reinterpret_cast<const uint32_t*>(&h);
+        lo = *reinterpret_cast<const uint32_t*>(&l);
+    }
+}
+
+// the thread's own A row: 16 complex values, four 16-byte stores per part
+template <bool BF16>
+__device__ __forceinline__ void write_row(unsigned char* A, int row, const float2 (&v)[16], float ls) {
+#pragma unroll
+    for (int q4 = 0; q4 < 4; ++q4) {
+        uint32_t h[4], l[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) split_pack<BF16>(v[4 * q4 + i], ls, h[i], l[i]);
+        *reinterpret_cast<uint4*>(A + a_off(row, 4 * q4, 0)) = make_uint4(h[0], h[1], h[2], h[3]);
+        *reinterpret_cast<uint4*>(A + a_off(row, 4 * q4, 1)) = make_uint4(l[0], l[1], l[2], l[3]);
+    }
+}
+
+template <bool BF16>
+__device__ __forceinline__ void write_elem(unsigned char* A, int row, int kc, float2 v, float ls) {
+    uint32_t h, l;
+    split_pack<BF16>(v, ls, h, l);
+    *reinterpret_cast<uint32_t*>(A + a_off(row, kc, 0)) = h;
+    *reinterpret_cast<uint32_t*>(A + a_off(row, kc, 1)) = l;
+}
+
+// one radix-16 stage on 128 sub-vectors: 2 K-steps x 3 split products, D overwritten
+__device__ __forceinline__ void issue_stage(uint32_t d_tmem, uint32_t a_s, uint32_t b_s, uint32_t idesc) {
+#pragma unroll
+    for (int st = 0; st < 2; ++st) {
+        const uint64_t ah = umma_desc(a_s + (uint32_t)(2 * st) * kLboA, kLboA, kSboA);
+        const uint64_t al = umma_desc(a_s + (uint32_t)(4 + 2 * st) * kLboA, kLboA, kSboA);
+        const uint64_t bh = umma_desc(b_s + (uint32_t)(2 * st) * kLboB, kLboB, kSboB);
+        const uint64_t bh2 = umma_desc(b_s + kBmat + (uint32_t)(2 * st) * kLboB, kLboB, kSboB);
+        const uint64_t bl = umma_desc(b_s + 2 * kBmat + (uint32_t)(2 * st) * kLboB, kLboB, kSboB);
+        umma_f16(d_tmem, ah, bh, idesc, st > 0 ? 1u : 0u);
+        umma_f16(d_tmem, al, bh2, idesc, 1u);
+        umma_f16(d_tmem, ah, bl, idesc, 1u);
+    }
+}
+
+template <bool BF16, bool PCG>
+__global__ void __launch_bounds__(kTcNT, 3)
+k_apply_A_tc(const __grid_constant__ CUtensorMap smap8, const float2* __restrict__ p, float2* __restrict__ q,
+             const float* __restrict__ maskw, const float2* __restrict__ tw_g, const uint4* __restrict__ bmat,
+             int nx, int nc, float mu, float lam, float gam, SliceState* st, Red red) {
+    constexpr int NY = kTcNY, NT = kTcNT, TX = kTcTX;
+    const int b = blockIdx.y;
+    if (PCG && st[b].state != ST_ACTIVE) return;
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* smem = smem_raw + pad1024(smem_raw);
+    float2* sbuf = reinterpret_cast<float2*>(smem);                // [2][NY * TX] swizzled coil tiles
+    unsigned char* Aop = smem + 2 * NY * TX * sizeof(float2);      // A operand
+    unsigned char* Bop = Aop + kAbytes;                            // six B operands
+    float2* tw = reinterpret_cast<float2*>(Bop + kBbytes);          // W_256^m
+    float2* halo = tw + NY;                                         // [2][NY]: columns x0-1, x0+TX
+    float* mk = reinterpret_cast<float*>(halo + 2 * NY);
+    double* red_s = reinterpret_cast<double*>(mk + NY);
+    __shared__ __align__(8) uint64_t full[2], mma_bar;
+    __shared__ uint32_t tmem_s;
+    __shared__ float wmax[NT / 32];
+    __shared__ int flag;
+
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int j = tid >> 4, s = tid & 15;  // column of the tile, sub-vector index within it
+    const int x0 = blockIdx.x * TX, x = x0 + j;
+    const int rbase = swz64(s, j);        // rows s + 16 e share the swizzle term of s
+    auto S_at = [rbase](const float2* S, int e) { return S[rbase + e * 16 * TX]; };
+    auto load_tile = [&](int c) {
+        uint64_t* bar = &full[c & 1];
+        mbar_arrive_expect_tx(bar, NY * TX * sizeof(float2));
+        tma_load_2d(sbuf + (c & 1) * NY * TX, &smap8, 2 * x0, (b * nc + c) * NY, bar);
+    };
+
+    if (w == 0) tmem_alloc(&tmem_s, 32);
+    if (tid == 0) {
+        mbar_init(&full[0], 1);
+        mbar_init(&full[1], 1);
+        mbar_init(&mma_bar, 1);
+        mbar_init_fence();
+    }
+    for (int i = tid; i < kBbytes / 16; i += NT) reinterpret_cast<uint4*>(Bop)[i] = bmat[i];
+    for (int i = tid; i < NY; i += NT) {
+        tw[i] = tw_g[i];
+        mk[i] = maskw[(size_t)b * NY + i] * (float)NY;  // the line weights carry 1/ny; the stages are unitary
+    }
+    const size_t img = (size_t)b * NY * nx;
+    float2 pv[16], acc[16];
+    float m = 0.f;
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+        pv[e] = p[img + (size_t)(s + 16 * e) * nx + x];
+        acc[e] = make_float2(0.f, 0.f);
+        m = fmaxf(m, fmaxf(fabsf(pv[e].x), fabsf(pv[e].y)));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) wmax[w] = m;
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (tid == 0)
+        for (int c = 0; c < 2 && c < nc; ++c) load_tile(c);
+    m = fmaxf(fmaxf(wmax[0], wmax[1]), fmaxf(wmax[2], wmax[3]));
+    float scale = 1.f, unscale = 1.f;
+    if (!BF16 && m > 0.f && isfinite(m)) {
+        int ex;
+        frexpf(m, &ex);
+        scale = ldexpf(1.f, -ex);
+        unscale = ldexpf(1.f, ex);
+    }
+    const float ls = BF16 ? 1.f : 1024.f;
+    const uint32_t tmem = tmem_s;
+    const uint32_t t_lane = tmem + ((uint32_t)(32 * w) << 16);
+    const uint32_t a_s = smem_addr(Aop), b_s = smem_addr(Bop);
+    constexpr uint32_t idesc = umma_idesc_f16(128, 32, BF16);
+    uint32_t mph = 0;
+    // operands stored -> one thread issues the stage -> everyone waits for its completion
+    auto stage = [&](int dir, int prefetch) {
+        fence_proxy_async();
+        tc_fence_before();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            issue_stage(tmem, a_s, b_s + (uint32_t)dir * 3u * kBmat, idesc);
+            umma_commit(&mma_bar);
+            if (prefetch >= 0) load_tile(prefetch);  // the other stage's tile is no longer read
+        }
+        mbar_wait(&mma_bar, mph, red.err);
+        mph ^= 1u;
+        tc_fence_after();
+    };
+
+    float d[32];
+    for (int c = 0; c < nc; ++c) {
+        const float2* S = sbuf + (c & 1) * NY * TX;
+        mbar_wait(&full[c & 1], (c >> 1) & 1, red.err);
+        float2 u[16];
+        // stage 1: thread (j, s) holds u[s + 16 e], e < 16
+#pragma unroll
+        for (int e = 0; e < 16; ++e) u[e] = cscale(cmul(S_at(S, e), pv[e]), scale);
+        write_row<BF16>(Aop, tid, u, ls);
+        stage(0, (c >= 1 && c + 1 < nc) ? c + 1 : -1);
+        tmem_ld32(t_lane, d);  // T[s][k1], k1 < 16
+        // twiddle W_256^{s k1}; row (j, k1) of stage 2 takes element s
+#pragma unroll
+        for (int k1 = 0; k1 < 16; ++k1)
+            write_elem<BF16>(Aop, 16 * j + k1, s, cmul(make_float2(d[2 * k1], d[2 * k1 + 1]), tw[s * k1]), ls);
+        stage(0, -1);
+        tmem_ld32(t_lane, d);  // thread (j, k1 = s): X[k1 + 16 k2], k2 < 16
+#pragma unroll
+        for (int k2 = 0; k2 < 16; ++k2) u[k2] = cscale(make_float2(d[2 * k2], d[2 * k2 + 1]), mk[s + 16 * k2]);
+        write_row<BF16>(Aop, tid, u, ls);
+        stage(1, -1);
+        tmem_ld32(t_lane, d);  // thread (j, k1 = s): T'[s'][k1], s' < 16
+#pragma unroll
+        for (int s2 = 0; s2 < 16; ++s2)
+            write_elem<BF16>(Aop, 16 * j + s2, s, cmulc(tw[s2 * s], make_float2(d[2 * s2], d[2 * s2 + 1])), ls);
+        stage(1, -1);
+        tmem_ld32(t_lane, d);  // thread (j, s): (F^H R F u)[s + 16 e], scaled
+#pragma unroll
+        for (int e = 0; e < 16; ++e) acc[e] = cfmac(acc[e], S_at(S, e), make_float2(d[2 * e], d[2 * e + 1]));
+    }
+    // periodic 5-point stencil for lambda (D_x^H D_x + D_y^H D_y) p; p tile in stage 0
+    tc_fence_before();
+    __syncthreads();
+    if (w == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem, 32);
+    }
+    float2* pt = sbuf;
+#pragma unroll
+    for (int e = 0; e < 16; ++e) pt[rbase + e * 16 * TX] = pv[e];
+    for (int i = tid; i < NY; i += NT) {
+        halo[i] = p[img + (size_t)i * nx + (x0 == 0 ? nx - 1 : x0 - 1)];
+        halo[NY + i] = p[img + (size_t)i * nx + (x0 + TX == nx ? 0 : x0 + TX)];
+    }
+    __syncthreads();
+    float dot = 0.f;
+    const float mus = mu * unscale;
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+        const int y = s + 16 * e;
+        const float2 up = pt[swz64(y == 0 ? NY - 1 : y - 1, j)];
+        const float2 dn = pt[swz64(y == NY - 1 ? 0 : y + 1, j)];
+        const float2 lf = j > 0 ? pt[swz64(y, j - 1)] : halo[y];
+        const float2 rt = j < TX - 1 ? pt[swz64(y, j + 1)] : halo[NY + y];
+        const float tvx = 4.f * pv[e].x - up.x - dn.x - lf.x - rt.x;
+        const float tvy = 4.f * pv[e].y - up.y - dn.y - lf.y - rt.y;
+        float2 o;
+        o.x = fmaf(mus, acc[e].x, fmaf(lam, tvx, gam * pv[e].x));
+        o.y = fmaf(mus, acc[e].y, fmaf(lam, tvy, gam * pv[e].y));
+        q[img + (size_t)y * nx + x] = o;
+        dot = fmaf(pv[e].x, o.x, fmaf(pv[e].y, o.y, dot));
+    }
+    if constexpr (PCG) {
+        double v[1] = {(double)dot}, tot[1];
+        const int np = gridDim.x;
+        if (last_block_total<1>(v, red.part, np, b * np + blockIdx.x, red.counter + b, tot, red_s, &flag) &&
+            threadIdx.x == 0) {
+            SliceState& S = st[b];
+            const double pq = tot[0];
+            S.pq = pq;
+            if (!isfinite(pq) || !isfinite(S.rho)) {
+                S.state = ST_NONFINITE;
+            } else if (!(pq > 0.0)) {
+                S.state = ST_BREAKDOWN;
+            } else {
+                S.alpha = S.rho / pq;
+                S.iters += 1;
+            }
+        }
+    }
+}
+
+constexpr size_t kSmemApplyATc = 1024 + 2 * kTcNY * kTcTX * sizeof(float2) + kAbytes + kBbytes +
+                                 3 * kTcNY * sizeof(float2) + kTcNY * sizeof(float) + 64 * sizeof(double);
+
+template <bool BF16>
+cudaError_t launch_tc(const Dims& d, const TcOperands& tc, const float2* p, float2* q, const float* maskw,
+                      float mu, float lam, float gam, SliceState* st, Red red, cudaStream_t s) {
+    const dim3 grid(d.nx / kTcTX, d.nb);
+    cudaError_t e;
+    if (st) {
+        if ((e = set_smem_limit(k_apply_A_tc<BF16, true>, (int)kSmemApplyATc)) != cudaSuccess) return e;
+        k_apply_A_tc<BF16, true><<<grid, kTcNT, kSmemApplyATc, s>>>(*tc.smap8, p, q, maskw, tc.tw,
+                                                                    static_cast<const uint4*>(tc.bmat), d.nx, d.nc,
+                                                                    mu, lam, gam, st, red);
+    } else {
+        if ((e = set_smem_limit(k_apply_A_tc<BF16, false>, (int)kSmemApplyATc)) != cudaSuccess) return e;
+        k_apply_A_tc<BF16, false><<<grid, kTcNT, kSmemApplyATc, s>>>(*tc.smap8, p, q, maskw, tc.tw,
+                                                                     static_cast<const uint4*>(tc.bmat), d.nx,
+                                                                     d.nc, mu, lam, gam, st, red);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+bool apply_A_tc_supported(const Dims& d) { return d.ny == kTcNY && d.nx % kTcTX == 0 && d.nx >= kTcTX; }
+
+cudaError_t launch_apply_A_tc(const Dims& d, const TcOperands& tc, const float2* p, float2* q, const float* maskw,
+                              float mu, float lam, float gam, SliceState* st, Red red, cudaStream_t s) {
+    if (!apply_A_tc_supported(d) || !tc.smap8 || !tc.tw || !tc.bmat) return cudaErrorInvalidValue;
+    return tc.bf16 ? launch_tc<true>(d, tc, p, q, maskw, mu, lam, gam, st, red, s)
+                   : launch_tc<false>(d, tc, p, q, maskw, mu, lam, gam, st, red, s);
+}
+
+// B operands of the split stages: the real form of the 1/4-scaled 16-point DFT matrix
+// (forward, then inverse), each as hi, hi * 2^-L and lo, in the core-matrix layout above.
+void build_tc_bmat(bool bf16, uint16_t* img) {
+    for (int i = 0; i < kBbytes / 2; ++i) img[i] = 0;
+    const double L = bf16 ? 1.0 : 1.0 / 1024.0;
+    for (int dir = 0; dir < 2; ++dir) {
+        for (int n = 0; n < 32; ++n) {
+            for (int k = 0; k < 32; ++k) {
+                const int ko = n >> 1, e = k >> 1;
+                const double th = (dir == 0 ? -2.0 : 2.0) * M_PI * (double)((ko * e) % 16) / 16.0;
+                const double wr = std::cos(th) / 4.0, wi = std::sin(th) / 4.0;
+                // out_re = a_re wr - a_im wi, out_im = a_re wi + a_im wr
+                double v;
+                if ((n & 1) == 0) v = (k & 1) == 0 ? wr : -wi;
+                else v = (k & 1) == 0 ? wi : wr;
+                float hi;
+                uint16_t bh, bh2, bl;
+                if (bf16) {
+                    const __nv_bfloat16 h = __float2bfloat16_rn((float)v);
+                    hi = __bfloat162float(h);
+                    const __nv_bfloat16 l = __float2bfloat16_rn((float)(v - (double)hi));
+                    const __nv_bfloat16 h2 = __float2bfloat16_rn((float)((double)hi * L));
+                    bh = *reinterpret_cast<const uint16_t*>(&h);
+                    bh2 = *reinterpret_cast<const uint16_t*>(&h2);
+                    bl = *reinterpret_cast<const uint16_t*>(&l);
+                } else {
+                    const __half h = __float2half_rn((float)v);
+                    hi = __half2float(h);
+                    const __half l = __float2half_rn((float)(v - (double)hi));
+                    const __half h2 = __float2half_rn((float)((double)hi * L));
+                    bh = *reinterpret_cast<const uint16_t*>(&h);
+                    bh2 = *reinterpret_cast<const uint16_t*>(&h2);
+                    bl = *reinterpret_cast<const uint16_t*>(&l);
+                }
+                const size_t off = ((size_t)(n >> 3) * kSboB + (size_t)(k >> 3) * kLboB + (n & 7) * 16 + (k & 7) * 2) / 2;
+                img[(dir * 3 + 0) * (kBmat / 2) + off] = bh;
+                img[(dir * 3 + 1) * (kBmat / 2) + off] = bh2;
+                img[(dir * 3 + 2) * (kBmat / 2) + off] = bl;
+            }
+        }
+    }
+}
+
+size_t tc_bmat_bytes() { return kBbytes; }
+
+}  // namespace sb

@@ -69,6 +69,22 @@ cudaError_t launch_apply_A(const Dims& d, const CUtensorMap& smap, const float2*
                            const float* maskw, const float2* tw_y, float mu, float lam, float gam,
                            SliceState* st, Red red, cudaStream_t s);
 
+// q = A p with the radix-16 DFT stages on the tensor cores, operands split in two bf16 or fp16
+// terms with FP32 accumulation (the split-precision modes; ny = 256, nx a multiple of 8).
+// smap8: the coil maps as 8-column x 256-row boxes with the 64-byte swizzle; tw: W_256^m, m < 256;
+// bmat: tc_bmat_bytes() of DFT-matrix operands from build_tc_bmat (same bf16 flag).
+struct TcOperands {
+    const CUtensorMap* smap8;
+    const float2* tw;
+    const void* bmat;
+    bool bf16;
+};
+bool apply_A_tc_supported(const Dims& d);
+cudaError_t launch_apply_A_tc(const Dims& d, const TcOperands& tc, const float2* p, float2* q, const float* maskw,
+                              float mu, float lam, float gam, SliceState* st, Red red, cudaStream_t s);
+size_t tc_bmat_bytes();
+void build_tc_bmat(bool bf16, uint16_t* img);  // img: tc_bmat_bytes() / 2 entries
+
 // Row pass of M^{-1}: mode 0 = t = F_x(in) (no CG work); mode 1 = PCG update r -= alpha q,
 // ||r||^2, convergence test, t = F_x(r).
 cudaError_t launch_row_fwd(const Dims& d, int mode, float2* r, const float2* q, float2* t,

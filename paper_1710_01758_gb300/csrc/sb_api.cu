@@ -76,6 +76,7 @@ struct Exec {
     bool own_stream = false;
     CUtensorMap smap{}, ymap{}, y1map{};  // TMA maps whose first row belongs to slice b0
     CUtensorMap smap_sw{};                // coil tiles with the 128-byte swizzle (q = A p)
+    CUtensorMap smap_sw64{};              // 8-column coil tiles, 64-byte swizzle (split-precision q = A p)
     SliceState* st = nullptr;             // device state of the range
     SliceState* h_st = nullptr;           // pinned mirror of the range
     Red red{};
@@ -99,6 +100,8 @@ struct sb_plan_s {
     int nz = 1, ny_plane = 0;
     size_t maxparts = kMaxParts;  // per-slice capacity of the cross-CTA partial sums
     float2* tw_z = nullptr;
+    float2* tw_full = nullptr;  // W_256^m, m < 256, and the DFT-matrix operands (split-precision modes)
+    void* bmat = nullptr;
     float2* bz[2] = {nullptr, nullptr};
     // 2D slices whose mask varies along x (the paper's random 2D sampling): the data term runs
     // as the three passes of the volumes with a per-point mask (copied here)
@@ -286,15 +289,16 @@ EncodeTiledFn tensor_map_encoder() {
 }
 
 // float32 view [rows][2 nx] of complex rows starting at base; box = box_rows x one column tile
-bool encode_rows(CUtensorMap* m, const void* base, int nx, size_t rows, int box_rows, bool swizzle = false) {
+bool encode_rows(CUtensorMap* m, const void* base, int nx, size_t rows, int box_rows, bool swizzle = false,
+                 int box_cols = kColTile, CUtensorMapSwizzle sw = CU_TENSOR_MAP_SWIZZLE_128B) {
     auto encode = tensor_map_encoder();
     if (!encode) return false;
     const cuuint64_t gdim[2] = {(cuuint64_t)2 * nx, (cuuint64_t)rows};
     const cuuint64_t gstride[1] = {(cuuint64_t)2 * nx * sizeof(float)};
-    const cuuint32_t box[2] = {(cuuint32_t)2 * kColTile, (cuuint32_t)box_rows};
+    const cuuint32_t box[2] = {(cuuint32_t)2 * box_cols, (cuuint32_t)box_rows};
     const cuuint32_t estride[2] = {1, 1};
     return encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), gdim, gstride, box, estride,
-                  CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle ? sw : CU_TENSOR_MAP_SWIZZLE_NONE,
                   CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -312,6 +316,18 @@ void bind_exec(sb_plan pl, Exec& ex, int b0, int nb, cudaStream_t s) {
 template <class T>
 T* at(T* base, const Exec& ex, size_t per) {
     return base + (size_t)ex.b0 * per;
+}
+
+// q = A p on 2D slices with a line mask: the FP32 kernel, or in the split-precision modes the
+// kernel whose radix-16 DFT stages run on the tensor cores
+cudaError_t apply_A_2d(const sb_plan_s* pl, const Exec& ex, const Dims& d, const float2* p, float2* q,
+                       const float* maskw, SliceState* st, Red red, cudaStream_t s) {
+    const float mu = (float)pl->d.mu, lam = (float)pl->d.lambda, gam = (float)pl->d.gamma;
+    if (pl->d.prec != SB_PREC_FP32) {
+        const TcOperands tc{&ex.smap_sw64, pl->tw_full, pl->bmat, pl->d.prec == SB_PREC_SPLIT_BF16};
+        return launch_apply_A_tc(d, tc, p, q, maskw, mu, lam, gam, st, red, s);
+    }
+    return launch_apply_A(d, ex.smap_sw, p, q, maskw, pl->tw_y, mu, lam, gam, st, red, s);
 }
 
 // ---- volumes (nz > 1) and 2D arbitrary masks: the data term as three passes through the coil
@@ -408,7 +424,7 @@ sb_status pcg_run(Exec& ex, const sb_pcg_opts& o, float2* x_full, sb_pcg_result*
                 if (sb_status e = vol_apply_A(ex, p, q, true)) return e;
             } else {
                 SB_LAUNCH(ex, SB_KCLASS_APPLY_A, 1,
-                          launch_apply_A(d, ex.smap_sw, p, q, maskw, pl->tw_y, mu, lam, gam, ex.st, red, s));
+                          apply_A_2d(pl, ex, d, p, q, maskw, ex.st, red, s));
             }
             if (circ && vol) {
                 if (sb_status e = vol_precond(ex, 2, r, q, x, p, nullptr, tol2)) return e;
@@ -663,8 +679,13 @@ sb_status sb_plan_create(const sb_plan_desc* desc, void* cuda_stream, sb_plan* o
         (d.precond_passes != 0 && d.precond_passes != 1 && d.precond_passes != 3) ||
         (d.wavelet != 0 && d.wavelet != 1))
         return SB_ERR_INVALID_ARG;
-    if (!supported_n(d.nx) || !supported_n(d.ny) || d.wavelet_levels > (vol ? 4 : 5) || d.prec != SB_PREC_FP32 ||
+    if (d.prec != SB_PREC_FP32 && d.prec != SB_PREC_SPLIT_BF16 && d.prec != SB_PREC_SPLIT_FP16)
+        return SB_ERR_INVALID_ARG;
+    if (!supported_n(d.nx) || !supported_n(d.ny) || d.wavelet_levels > (vol ? 4 : 5) ||
         (vol && (!supported_n(d.nz) || d.precond_passes == 1)))
+        return SB_ERR_UNSUPPORTED;
+    // the split-precision modes: tensor-core radix-16 stages of the 256-point column transform
+    if (d.prec != SB_PREC_FP32 && (vol || !apply_A_tc_supported(Dims{d.nx, d.ny, d.ncoils, d.nbatch})))
         return SB_ERR_UNSUPPORTED;
     if (d.wavelet == 1 && d.wavelet_levels > 0 &&
         (vol || (d.nx >> (d.wavelet_levels - 1)) < 4 || (d.ny >> (d.wavelet_levels - 1)) < 4))
@@ -704,6 +725,10 @@ sb_status sb_plan_create(const sb_plan_desc* desc, void* cuda_stream, sb_plan* o
     ALLOC(pl->tw_x, d.nx);
     ALLOC(pl->tw_y, d.ny);
     ALLOC(pl->tw_z, nz);
+    if (d.prec != SB_PREC_FP32) {
+        ALLOC(pl->tw_full, 256);
+        if ((e = cudaMalloc(&pl->bmat, tc_bmat_bytes())) != cudaSuccess) return bail("cudaMalloc");
+    }
     ALLOC(pl->maskw, nb * d.ny * nz);
     ALLOC(pl->slot, nb * d.ny * nz);
     ALLOC(pl->k, nb * n);
@@ -727,6 +752,18 @@ sb_status sb_plan_create(const sb_plan_desc* desc, void* cuda_stream, sb_plan* o
         return bail("cudaMemcpy twiddles");
     if ((e = cudaMemcpy(pl->tw_z, tz.data(), sizeof(float2) * nz, cudaMemcpyHostToDevice)) != cudaSuccess)
         return bail("cudaMemcpy twiddles");
+    if (pl->tw_full) {
+        std::vector<float2> tf(256);
+        for (int m = 0; m < 256; ++m) {
+            const double a = -2.0 * M_PI * m / 256.0;
+            tf[m] = make_float2((float)std::cos(a), (float)std::sin(a));
+        }
+        std::vector<uint16_t> bm(tc_bmat_bytes() / 2);
+        build_tc_bmat(d.prec == SB_PREC_SPLIT_BF16, bm.data());
+        if ((e = cudaMemcpy(pl->tw_full, tf.data(), sizeof(float2) * 256, cudaMemcpyHostToDevice)) != cudaSuccess ||
+            (e = cudaMemcpy(pl->bmat, bm.data(), tc_bmat_bytes(), cudaMemcpyHostToDevice)) != cudaSuccess)
+            return bail("cudaMemcpy twiddles");
+    }
     if ((e = cudaMemset(pl->counter, 0, sizeof(unsigned) * nb)) != cudaSuccess) return bail("cudaMemset");
     if ((e = cudaMemset(pl->derr, 0, sizeof(unsigned))) != cudaSuccess) return bail("cudaMemset");
     if ((e = cudaMemset(pl->st, 0, sizeof(SliceState) * nb)) != cudaSuccess) return bail("cudaMemset");
@@ -764,7 +801,8 @@ sb_status sb_plan_destroy(sb_plan pl) {
                     (void*)pl->g, (void*)pl->bd, (void*)pl->bd1, (void*)pl->yt, (void*)pl->yt1, (void*)pl->st,
                     (void*)pl->part, (void*)pl->counter, (void*)pl->kmax, (void*)pl->derr, (void*)pl->spec,
                     (void*)pl->gb, (void*)pl->rb, (void*)pl->line_val, (void*)pl->line_uni, (void*)pl->jw,
-                    (void*)pl->tw_z, (void*)pl->bz[0], (void*)pl->bz[1], (void*)pl->mask8, (void*)pl->wb})
+                    (void*)pl->tw_z, (void*)pl->bz[0], (void*)pl->bz[1], (void*)pl->mask8, (void*)pl->wb,
+                    (void*)pl->tw_full, pl->bmat})
         dfree(p);
     if (pl->h_st) cudaFreeHost(pl->h_st);
     auto release = [](Exec& ex) {
@@ -796,7 +834,9 @@ sb_status sb_set_coils(sb_plan pl, const void* d_sens) {
         const float2* base = static_cast<const float2*>(d_sens) + (size_t)ex.b0 * per;
         const size_t rows = (size_t)ex.d.nb * d.nc * d.ny;
         const int box = coil_box_rows(d.ny);  // a TMA box spans at most 256 rows
-        return encode_rows(&ex.smap, base, d.nx, rows, box) && encode_rows(&ex.smap_sw, base, d.nx, rows, box, true);
+        return encode_rows(&ex.smap, base, d.nx, rows, box) && encode_rows(&ex.smap_sw, base, d.nx, rows, box, true) &&
+               (pl->d.prec == SB_PREC_FP32 ||
+                encode_rows(&ex.smap_sw64, base, d.nx, rows, 256, true, 8, CU_TENSOR_MAP_SWIZZLE_64B));
     };
     bool ok = true;
     if (pl->nz == 1) {  // the TMA coil-tile maps serve the 2D kernels only
@@ -842,6 +882,8 @@ sb_status sb_set_mask(sb_plan pl, const uint8_t* d_mask) {
     for (size_t i = 0; i < hu.size(); ++i) lines_only = lines_only && hu[i];
     if (!lines_only && pl->nz > 1)
         return fail(pl, SB_ERR_UNSUPPORTED, "a volume mask must be constant along the readout (x) axis");
+    if (!lines_only && pl->d.prec != SB_PREC_FP32)
+        return fail(pl, SB_ERR_UNSUPPORTED, "the split-precision modes need a mask constant along the readout (x) axis");
     pl->general = !lines_only;
     int ms = 1;
     std::vector<float> hw(nb * d.ny);
@@ -975,9 +1017,8 @@ sb_status sb_apply_A(sb_plan pl, const void* d_x, void* d_y) {
     auto go = [&]() -> sb_status {
         if (pl->passes()) return vol_apply_A(ex, static_cast<const float2*>(d_x), static_cast<float2*>(d_y), false);
         SB_LAUNCH(ex, SB_KCLASS_APPLY_A, 1,
-                  launch_apply_A(pl->dims, ex.smap_sw, static_cast<const float2*>(d_x), static_cast<float2*>(d_y),
-                                 pl->maskw, pl->tw_y, (float)pl->d.mu, (float)pl->d.lambda, (float)pl->d.gamma,
-                                 nullptr, ex.red, pl->stream));
+                  apply_A_2d(pl, ex, pl->dims, static_cast<const float2*>(d_x), static_cast<float2*>(d_y),
+                             pl->maskw, nullptr, ex.red, pl->stream));
         return SB_OK;
     };
     sb_status st = go();
@@ -1022,8 +1063,7 @@ sb_status sb_pcg_solve(sb_plan pl, const void* d_b, void* d_x, const sb_pcg_opts
             if (sb_status e = vol_apply_A(ex, x, q, false)) return e;
         } else {
             SB_LAUNCH(ex, SB_KCLASS_APPLY_A, 1,
-                      launch_apply_A(ex.d, ex.smap_sw, x, q, at(pl->maskw, ex, (size_t)ex.d.ny), pl->tw_y,
-                                     (float)pl->d.mu, (float)pl->d.lambda, (float)pl->d.gamma, nullptr, ex.red, ex.s));
+                      apply_A_2d(pl, ex, ex.d, x, q, at(pl->maskw, ex, (size_t)ex.d.ny), nullptr, ex.red, ex.s));
         }
         SB_LAUNCH(ex, SB_KCLASS_VEC, 1,
                   launch_resid_init(ex.d, at(b_full, ex, n), q, at(pl->r, ex, n), ex.st, tol2, ex.red, ex.s));

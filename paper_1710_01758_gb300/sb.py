@@ -274,15 +274,15 @@ class Plan:
     """Owns an sb_plan and the device tensors it borrows (torch CUDA tensors)."""
 
     def __init__(self, nx, ny, ncoils, nbatch, mu, lam, gam, wavelet_levels, stream=None, groups=0,
-                 precond_passes=0, nz=1, wavelet=0):
+                 precond_passes=0, nz=1, wavelet=0, prec=SB_PREC_FP32):
         import torch
         self.torch = torch
         self.nbatch = nbatch
         self.shape = (nbatch, nz, ny, nx) if nz > 1 else (nbatch, ny, nx)
         s = stream if stream is not None else torch.cuda.current_stream()
         self.stream = s
-        self.handle = sb_plan_create(plan_desc(nx, ny, ncoils, nbatch, mu, lam, gam, wavelet_levels, groups=groups,
-                                                       precond_passes=precond_passes, nz=nz, wavelet=wavelet),
+        self.handle = sb_plan_create(plan_desc(nx, ny, ncoils, nbatch, mu, lam, gam, wavelet_levels, prec=prec,
+                                               groups=groups, precond_passes=precond_passes, nz=nz, wavelet=wavelet),
                                      s.cuda_stream)
         self._sens = None
 
