@@ -32,7 +32,7 @@
 namespace sb {
 namespace {
 
-constexpr int kTcNY = 256, kTcTX = 8, kTcNT = 128;
+constexpr int kTcNY = 256, kTcTX = 8, kTcNT = 256;
 // A operand: 128 rows x (32 hi + 32 lo) 16-bit elements.  K-adjacent core matrices 144 B apart
 // and 8-row groups 1184 B apart: the transposed stores of a warp (16 rows' worth of one element
 // each from 32 threads) then fall on 32 distinct banks.
@@ -78,16 +78,16 @@ __device__ __forceinline__ void split_pack(float2 v, float ls, uint32_t& hi, uin
     }
 }
 
-// the thread's own A row: 16 complex values, four 16-byte stores per part
+// half h of the thread's own A row: complex elements 8 h .. 8 h + 7, two 16-byte stores per part
 template <bool BF16>
-__device__ __forceinline__ void write_row(unsigned char* A, int row, const float2 (&v)[16], float ls) {
+__device__ __forceinline__ void write_half_row(unsigned char* A, int row, int h, const float2 (&v)[8], float ls) {
 #pragma unroll
-    for (int q4 = 0; q4 < 4; ++q4) {
-        uint32_t h[4], l[4];
+    for (int q2 = 0; q2 < 2; ++q2) {
+        uint32_t hi[4], lo[4];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) split_pack<BF16>(v[4 * q4 + i], ls, h[i], l[i]);
-        *reinterpret_cast<uint4*>(A + a_off(row, 4 * q4, 0)) = make_uint4(h[0], h[1], h[2], h[3]);
-        *reinterpret_cast<uint4*>(A + a_off(row, 4 * q4, 1)) = make_uint4(l[0], l[1], l[2], l[3]);
+        for (int i = 0; i < 4; ++i) split_pack<BF16>(v[4 * q2 + i], ls, hi[i], lo[i]);
+        *reinterpret_cast<uint4*>(A + a_off(row, 8 * h + 4 * q2, 0)) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+        *reinterpret_cast<uint4*>(A + a_off(row, 8 * h + 4 * q2, 1)) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
     }
 }
 
@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(kTcNT, 3)
 k_apply_A_tc(const __grid_constant__ CUtensorMap smap8, const float2* __restrict__ p, float2* __restrict__ q,
              const float* __restrict__ maskw, const float2* __restrict__ tw_g, const uint4* __restrict__ bmat,
              int nx, int nc, float mu, float lam, float gam, SliceState* st, Red red) {
-    constexpr int NY = kTcNY, NT = kTcNT, TX = kTcTX;
+    constexpr int NY = kTcNY, NT = kTcNT, TX = kTcTX, NW = NT / 32;
     const int b = blockIdx.y;
     if (PCG && st[b].state != ST_ACTIVE) return;
     extern __shared__ unsigned char smem_raw[];
@@ -127,19 +127,22 @@ k_apply_A_tc(const __grid_constant__ CUtensorMap smap8, const float2* __restrict
     float2* sbuf = reinterpret_cast<float2*>(smem);                // [2][NY * TX] swizzled coil tiles
     unsigned char* Aop = smem + 2 * NY * TX * sizeof(float2);      // A operand
     unsigned char* Bop = Aop + kAbytes;                            // six B operands
-    float2* tw = reinterpret_cast<float2*>(Bop + kBbytes);          // W_256^m
+    float2* tw = reinterpret_cast<float2*>(Bop + kBbytes);          // tw[16 a + b] = W_256^{a b}
     float2* halo = tw + NY;                                         // [2][NY]: columns x0-1, x0+TX
     float* mk = reinterpret_cast<float*>(halo + 2 * NY);
     double* red_s = reinterpret_cast<double*>(mk + NY);
     __shared__ __align__(8) uint64_t full[2], mma_bar;
     __shared__ uint32_t tmem_s;
-    __shared__ float wmax[NT / 32];
+    __shared__ float wmax[NW];
     __shared__ int flag;
 
+    // TMEM lane (= A row) r = (j, s) is shared by the threads tid = r (half 0) and r + 128
+    // (half 1; warps w and w + 4 read the same lanes): each owns 8 of the row's 16 complex values
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    const int j = tid >> 4, s = tid & 15;  // column of the tile, sub-vector index within it
+    const int r = tid & 127, h = tid >> 7;
+    const int j = r >> 4, s = r & 15;  // column of the tile, sub-vector index within it
     const int x0 = blockIdx.x * TX, x = x0 + j;
-    const int rbase = swz64(s, j);        // rows s + 16 e share the swizzle term of s
+    const int rbase = swz64(s, j);     // rows s + 16 e share the swizzle term of s
     auto S_at = [rbase](const float2* S, int e) { return S[rbase + e * 16 * TX]; };
     auto load_tile = [&](int c) {
         uint64_t* bar = &full[c & 1];
@@ -156,17 +159,17 @@ k_apply_A_tc(const __grid_constant__ CUtensorMap smap8, const float2* __restrict
     }
     for (int i = tid; i < kBbytes / 16; i += NT) reinterpret_cast<uint4*>(Bop)[i] = bmat[i];
     for (int i = tid; i < NY; i += NT) {
-        tw[i] = tw_g[i];
+        tw[i] = tw_g[(i >> 4) * (i & 15)];
         mk[i] = maskw[(size_t)b * NY + i] * (float)NY;  // the line weights carry 1/ny; the stages are unitary
     }
     const size_t img = (size_t)b * NY * nx;
-    float2 pv[16], acc[16];
+    float2 pv[8], acc[8];
     float m = 0.f;
 #pragma unroll
-    for (int e = 0; e < 16; ++e) {
-        pv[e] = p[img + (size_t)(s + 16 * e) * nx + x];
-        acc[e] = make_float2(0.f, 0.f);
-        m = fmaxf(m, fmaxf(fabsf(pv[e].x), fabsf(pv[e].y)));
+    for (int i = 0; i < 8; ++i) {
+        pv[i] = p[img + (size_t)(s + 16 * (8 * h + i)) * nx + x];
+        acc[i] = make_float2(0.f, 0.f);
+        m = fmaxf(m, fmaxf(fabsf(pv[i].x), fabsf(pv[i].y)));
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
@@ -176,7 +179,9 @@ k_apply_A_tc(const __grid_constant__ CUtensorMap smap8, const float2* __restrict
     tc_fence_after();
     if (tid == 0)
         for (int c = 0; c < 2 && c < nc; ++c) load_tile(c);
-    m = fmaxf(fmaxf(wmax[0], wmax[1]), fmaxf(wmax[2], wmax[3]));
+    m = wmax[0];
+#pragma unroll
+    for (int i = 1; i < NW; ++i) m = fmaxf(m, wmax[i]);
     float scale = 1.f, unscale = 1.f;
     if (!BF16 && m > 0.f && isfinite(m)) {
         int ex;
@@ -186,7 +191,7 @@ k_apply_A_tc(const __grid_constant__ CUtensorMap smap8, const float2* __restrict
     }
     const float ls = BF16 ? 1.f : 1024.f;
     const uint32_t tmem = tmem_s;
-    const uint32_t t_lane = tmem + ((uint32_t)(32 * w) << 16);
+    const uint32_t t_lane = tmem + ((uint32_t)(32 * (w & 3)) << 16) + (uint32_t)(16 * h);
     const uint32_t a_s = smem_addr(Aop), b_s = smem_addr(Bop);
     constexpr uint32_t idesc = umma_idesc_f16(128, 32, BF16);
     uint32_t mph = 0;
@@ -206,35 +211,40 @@ k_apply_A_tc(const __grid_constant__ CUtensorMap smap8, const float2* __restrict
         tc_fence_after();
     };
 
-    float d[32];
+    float d[16];
     for (int c = 0; c < nc; ++c) {
         const float2* S = sbuf + (c & 1) * NY * TX;
         mbar_wait(&full[c & 1], (c >> 1) & 1, red.err);
-        float2 u[16];
-        // stage 1: thread (j, s) holds u[s + 16 e], e < 16
+        float2 u[8];
+        // stage 1: row (j, s) holds u[s + 16 e], e < 16 (this thread: e = 8 h + i)
 #pragma unroll
-        for (int e = 0; e < 16; ++e) u[e] = cscale(cmul(S_at(S, e), pv[e]), scale);
-        write_row<BF16>(Aop, tid, u, ls);
+        for (int i = 0; i < 8; ++i) u[i] = cscale(cmul(S_at(S, 8 * h + i), pv[i]), scale);
+        write_half_row<BF16>(Aop, r, h, u, ls);
         stage(0, (c >= 1 && c + 1 < nc) ? c + 1 : -1);
-        tmem_ld32(t_lane, d);  // T[s][k1], k1 < 16
+        tmem_ld16(t_lane, d);  // T[s][k1], k1 = 8 h + i
         // twiddle W_256^{s k1}; row (j, k1) of stage 2 takes element s
 #pragma unroll
-        for (int k1 = 0; k1 < 16; ++k1)
-            write_elem<BF16>(Aop, 16 * j + k1, s, cmul(make_float2(d[2 * k1], d[2 * k1 + 1]), tw[s * k1]), ls);
+        for (int i = 0; i < 8; ++i) {
+            const int k1 = 8 * h + i;
+            write_elem<BF16>(Aop, 16 * j + k1, s, cmul(make_float2(d[2 * i], d[2 * i + 1]), tw[16 * k1 + s]), ls);
+        }
         stage(0, -1);
-        tmem_ld32(t_lane, d);  // thread (j, k1 = s): X[k1 + 16 k2], k2 < 16
+        tmem_ld16(t_lane, d);  // row (j, k1 = s): X[k1 + 16 k2], k2 = 8 h + i
 #pragma unroll
-        for (int k2 = 0; k2 < 16; ++k2) u[k2] = cscale(make_float2(d[2 * k2], d[2 * k2 + 1]), mk[s + 16 * k2]);
-        write_row<BF16>(Aop, tid, u, ls);
+        for (int i = 0; i < 8; ++i) u[i] = cscale(make_float2(d[2 * i], d[2 * i + 1]), mk[s + 16 * (8 * h + i)]);
+        write_half_row<BF16>(Aop, r, h, u, ls);
         stage(1, -1);
-        tmem_ld32(t_lane, d);  // thread (j, k1 = s): T'[s'][k1], s' < 16
+        tmem_ld16(t_lane, d);  // row (j, k1 = s): T'[s'][k1], s' = 8 h + i
 #pragma unroll
-        for (int s2 = 0; s2 < 16; ++s2)
-            write_elem<BF16>(Aop, 16 * j + s2, s, cmulc(tw[s2 * s], make_float2(d[2 * s2], d[2 * s2 + 1])), ls);
+        for (int i = 0; i < 8; ++i) {
+            const int s2 = 8 * h + i;
+            write_elem<BF16>(Aop, 16 * j + s2, s, cmulc(tw[16 * s2 + s], make_float2(d[2 * i], d[2 * i + 1])), ls);
+        }
         stage(1, -1);
-        tmem_ld32(t_lane, d);  // thread (j, s): (F^H R F u)[s + 16 e], scaled
+        tmem_ld16(t_lane, d);  // row (j, s): (F^H R F u)[s + 16 e], e = 8 h + i, scaled
 #pragma unroll
-        for (int e = 0; e < 16; ++e) acc[e] = cfmac(acc[e], S_at(S, e), make_float2(d[2 * e], d[2 * e + 1]));
+        for (int i = 0; i < 8; ++i)
+            acc[i] = cfmac(acc[i], S_at(S, 8 * h + i), make_float2(d[2 * i], d[2 * i + 1]));
     }
     // periodic 5-point stencil for lambda (D_x^H D_x + D_y^H D_y) p; p tile in stage 0
     tc_fence_before();
@@ -245,7 +255,7 @@ k_apply_A_tc(const __grid_constant__ CUtensorMap smap8, const float2* __restrict
     }
     float2* pt = sbuf;
 #pragma unroll
-    for (int e = 0; e < 16; ++e) pt[rbase + e * 16 * TX] = pv[e];
+    for (int i = 0; i < 8; ++i) pt[rbase + (8 * h + i) * 16 * TX] = pv[i];
     for (int i = tid; i < NY; i += NT) {
         halo[i] = p[img + (size_t)i * nx + (x0 == 0 ? nx - 1 : x0 - 1)];
         halo[NY + i] = p[img + (size_t)i * nx + (x0 + TX == nx ? 0 : x0 + TX)];
@@ -254,19 +264,19 @@ k_apply_A_tc(const __grid_constant__ CUtensorMap smap8, const float2* __restrict
     float dot = 0.f;
     const float mus = mu * unscale;
 #pragma unroll
-    for (int e = 0; e < 16; ++e) {
-        const int y = s + 16 * e;
+    for (int i = 0; i < 8; ++i) {
+        const int y = s + 16 * (8 * h + i);
         const float2 up = pt[swz64(y == 0 ? NY - 1 : y - 1, j)];
         const float2 dn = pt[swz64(y == NY - 1 ? 0 : y + 1, j)];
         const float2 lf = j > 0 ? pt[swz64(y, j - 1)] : halo[y];
         const float2 rt = j < TX - 1 ? pt[swz64(y, j + 1)] : halo[NY + y];
-        const float tvx = 4.f * pv[e].x - up.x - dn.x - lf.x - rt.x;
-        const float tvy = 4.f * pv[e].y - up.y - dn.y - lf.y - rt.y;
+        const float tvx = 4.f * pv[i].x - up.x - dn.x - lf.x - rt.x;
+        const float tvy = 4.f * pv[i].y - up.y - dn.y - lf.y - rt.y;
         float2 o;
-        o.x = fmaf(mus, acc[e].x, fmaf(lam, tvx, gam * pv[e].x));
-        o.y = fmaf(mus, acc[e].y, fmaf(lam, tvy, gam * pv[e].y));
+        o.x = fmaf(mus, acc[i].x, fmaf(lam, tvx, gam * pv[i].x));
+        o.y = fmaf(mus, acc[i].y, fmaf(lam, tvy, gam * pv[i].y));
         q[img + (size_t)y * nx + x] = o;
-        dot = fmaf(pv[e].x, o.x, fmaf(pv[e].y, o.y, dot));
+        dot = fmaf(pv[i].x, o.x, fmaf(pv[i].y, o.y, dot));
     }
     if constexpr (PCG) {
         double v[1] = {(double)dot}, tot[1];
