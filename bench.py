@@ -75,6 +75,7 @@ def parse():
     ap.add_argument("--batch", type=int, default=0, help="slices per step (0 = the workload's default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-loop", action="store_true", help="uneven64: skip the per-slice loop comparison")
     ap.add_argument("--groups", type=int, default=0, help="concurrent slice groups (0 = library default)")
     ap.add_argument("--prec", choices=list(PRECS), default="fp32",
                     help="fp32, or a split-precision mode: the radix-16 DFT stages of q = A p on the tensor cores "
@@ -471,6 +472,49 @@ def tensor_core_rate(args, wl, B, ncv, k1_us):
                     "(TMEM -> registers -> shared memory), not by the tensor pipe"}
 
 
+def per_slice_loop(torch, sb, dev, groups, members, sens, masks, ys, wls, batched_recon_per_s):
+    """The uneven batch reconstructed one slice at a time with the same library (one 1-slice plan
+    per geometry, coils and mask set per slice as in the batched step), timed once after a warm-up
+    slice per geometry: the per-slice loop that batching is compared against."""
+    stream = torch.cuda.current_stream(dev)
+    loop = []
+    for (nx, ny, nc), ids in sorted(groups.items()):
+        w = wls[ids[0]]
+        loop.append(sb.Plan(nx, ny, nc, 1, w.mu, w.lam, w.gam, w.wavelet_levels, stream=stream))
+    w0 = wls[0]
+    xs1 = [torch.zeros((1, p.shape[1], p.shape[2]), dtype=torch.complex64, device=dev) for p in loop]
+
+    def one(k, i):
+        p = loop[k]
+        p.set_coils(sens[k][i:i + 1])
+        p.set_mask(masks[k][i:i + 1])
+        xs1[k].zero_()
+        st, iters, _ = p.split_bregman(ys[k][i:i + 1], xs1[k], w0.n_outer, w0.n_inner, tol=w0.pcg_tol,
+                                       maxit=w0.pcg_maxit)
+        if st != sb.SB_OK:
+            raise RuntimeError(f"split_bregman: {sb.status_string(st)}")
+        return int(sum(sum(r) for r in iters))
+
+    for k in range(len(loop)):
+        one(k, 0)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    n = iters = 0
+    for k, (ids, _) in enumerate(members):
+        for i in range(len(ids)):
+            iters += one(k, i)
+            n += 1
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3
+    for p in loop:
+        p.close()
+    return {"recon_per_s": n / t, "pcg_iters_per_s": iters / t, "slices": n,
+            "batched_over_loop": batched_recon_per_s / (n / t),
+            "how": "one slice at a time through sb_split_bregman (1-slice plan per geometry), CUDA events"}
+
+
 def run_uneven(args, torch, sb, synth, world, rank, local, dist):
     """64 slices of mixed size, coil count and R: one plan per geometry, each on its own stream,
     reconstructed concurrently by sb_split_bregman_many.  A step = k construction of every plan
@@ -535,6 +579,9 @@ def run_uneven(args, torch, sb, synth, world, rank, local, dist):
     if dist:
         elapsed_max, total_all = reduce_over_ranks(dist, dev, elapsed, total)
     extra = {}
+    if rank == 0 and not args.no_loop:
+        extra["per_slice_loop"] = per_slice_loop(torch, sb, dev, groups, members, sens, masks, ys, wls,
+                                                 batched_recon_per_s=args.steps * len(wls) / elapsed)
     if rank == 0 and not args.no_cpu_baseline:
         ids, sl = members[0]
         x_or, it_or, t_or = oracle_recon(wls[ids[0]], sl[0])

@@ -219,6 +219,17 @@ const char* sb_plan_last_error(sb_plan plan);
  * kernel node they run).  Instrumentation for benchmarks. */
 uint64_t sb_kernel_launches(void);
 
+/* CUDA graphs for the PCG loop (default on).  PCG polls the slices' convergence state every
+ * few iterations; with graphs enabled, each such block of iterations (q = A p and the
+ * preconditioner step, Algorithm 1 step 5 / the Complexity section's PCG) is captured once per
+ * execution context (slice group) on the context's stream and replayed while its parameters
+ * (the x buffer, tolerance, preconditioner, schedule and block length) repeat.  Capture starts
+ * with the context's second block and is skipped while the event timer below is on and on the
+ * legacy or per-thread default stream (which cannot be captured).  Results
+ * are bitwise identical either way.  enable: 0 = direct launches, 1 = graphs.  Synchronises the
+ * plan's stream; SB_ERR_INVALID_ARG for a null plan. */
+sb_status sb_set_graphs(sb_plan plan, int enable);
+
 /* Kernel classes for the event timer below. */
 typedef enum {
     SB_KCLASS_APPLY_A = 0,       /* q = A p (data term by DFTs along y, TV stencil, gamma p) */

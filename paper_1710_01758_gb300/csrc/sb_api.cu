@@ -49,6 +49,7 @@ cudaError_t set_smem_limit(const void* kernel, int bytes) {
 namespace {
 
 std::atomic<uint64_t> g_launches{0};
+thread_local uint64_t t_launches = 0;  // this host thread's launches (sizes a graph capture)
 
 // PCG iterations enqueued between two reads of the per-slice state
 #ifndef SB_POLL_EVERY
@@ -68,6 +69,17 @@ struct Pending {
 }  // namespace
 
 // A contiguous range of slices [b0, b0 + d.nb) driven on one stream.
+// A captured block of PCG iterations (CUDA graph), replayed while its parameters hold
+struct PcgGraph {
+    const void* sens;  // the coil maps (TMA descriptors) are captured by value
+    bool general;      // line-mask or general data-term path
+    const void* x;
+    double tol2;
+    int precond, fixed, iters;
+    cudaGraphExec_t exec;
+    uint64_t launches;  // kernels per replay
+};
+
 struct Exec {
     sb_plan pl = nullptr;
     int b0 = 0;
@@ -85,6 +97,8 @@ struct Exec {
     std::vector<Pending> pending;
     std::vector<cudaEvent_t> ev_pool;
     cudaEvent_t join = nullptr;
+    std::vector<PcgGraph> graphs;  // captured PCG iteration blocks of this context
+    bool primed = false;           // one block ran uncaptured (kernel attributes are set)
 };
 
 struct sb_plan_s {
@@ -96,6 +110,7 @@ struct sb_plan_s {
     const float2* sens = nullptr;
     bool have_coils = false, have_mask = false;
     bool fused_precond = false;  // circulant M^{-1} as one cluster launch per PCG iteration
+    bool graphs = true;          // PCG iteration blocks replayed as CUDA graphs
     // volumes: dims is the rows view {nx, ny nz, Nc, nb}; the planes are ny_plane x nx, nz of them
     int nz = 1, ny_plane = 0;
     size_t maxparts = kMaxParts;  // per-slice capacity of the cross-CTA partial sums
@@ -236,6 +251,7 @@ void timer_harvest(Exec& ex) {
         if (e_ != cudaSuccess) return xfail((ex), SB_ERR_CUDA, cuda_msg(#call, e_)); \
         timer_end((ex), (cls), ta_);                                               \
         g_launches.fetch_add((nk), std::memory_order_relaxed);                     \
+        t_launches += (nk);                                                        \
     } while (0)
 
 template <class T>
@@ -416,30 +432,85 @@ sb_status pcg_run(Exec& ex, const sb_pcg_opts& o, float2* x_full, sb_pcg_result*
         SB_LAUNCH(ex, SB_KCLASS_VEC, 1, launch_vec_plain(d, 0, x, r, p, nullptr, w, ex.st, tol2, red, s));
     }
     const int nit = fixed ? o.fixed_iters : o.maxit;
+    // one PCG iteration: q = A p (with p^H q and alpha), then M^{-1} (r update, stop test, z,
+    // rho, beta, x and p updates); slices that are not active skip every kernel
+    auto body = [&]() -> sb_status {
+        if (passes) {
+            if (sb_status e = vol_apply_A(ex, p, q, true)) return e;
+        } else {
+            SB_LAUNCH(ex, SB_KCLASS_APPLY_A, 1,
+                      apply_A_2d(pl, ex, d, p, q, maskw, ex.st, red, s));
+        }
+        if (circ && vol) {
+            if (sb_status e = vol_precond(ex, 2, r, q, x, p, nullptr, tol2)) return e;
+        } else if (fused) {
+            SB_LAUNCH(ex, SB_KCLASS_PRECOND_FUSED, 1,
+                      launch_precond_fused(d, 1, x, r, p, q, invk, pl->tw_x, pl->tw_y, ex.st, tol2, s));
+        } else if (circ) {
+            SB_LAUNCH(ex, SB_KCLASS_PRECOND_ROW_FWD, 1, launch_row_fwd(d, 1, r, q, tb, pl->tw_x, ex.st, tol2, red, s));
+            SB_LAUNCH(ex, SB_KCLASS_PRECOND_COL, 1, launch_col_precond(d, tb, invk, pl->tw_y, ex.st, 0, red, s));
+            SB_LAUNCH(ex, SB_KCLASS_PRECOND_ROW_INV, 1, launch_row_inv(d, 2, tb, nullptr, x, p, pl->tw_x, ex.st, red, s));
+        } else {
+            SB_LAUNCH(ex, SB_KCLASS_VEC, 1, launch_vec_plain(d, 1, x, r, p, q, w, ex.st, tol2, red, s));
+            SB_LAUNCH(ex, SB_KCLASS_VEC, 1, launch_vec_plain(d, 2, x, r, p, q, w, ex.st, tol2, red, s));
+        }
+        return SB_OK;
+    };
+    // g iterations between two polls: replayed from a CUDA graph captured on this context's
+    // stream once its parameters (x, tol, preconditioner, schedule, g) repeat; direct launches
+    // while the per-kernel timer is on and for the context's first block (which also sets the
+    // kernels' shared-memory attributes outside any capture)
+    auto block = [&](int g) -> sb_status {
+        // the legacy and per-thread default streams cannot be captured: direct launches there
+        const bool use_graph = pl->graphs && pl->tmask == 0 && s != nullptr && s != cudaStreamLegacy &&
+                               s != cudaStreamPerThread;
+        PcgGraph* hit = nullptr;
+        if (use_graph)
+            for (auto& pg : ex.graphs)
+                if (pg.sens == pl->sens && pg.general == pl->general && pg.x == x && pg.tol2 == tol2 && pg.precond == (int)o.precond && pg.fixed == (int)fixed &&
+                    pg.iters == g)
+                    hit = &pg;
+        if (!hit && (!use_graph || !ex.primed)) {
+            for (int i = 0; i < g; ++i)
+                if (sb_status e = body()) return e;
+            ex.primed = true;
+            return SB_OK;
+        }
+        if (!hit) {
+            cudaError_t ce = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+            if (ce != cudaSuccess) return xfail(ex, SB_ERR_CUDA, cuda_msg("cudaStreamBeginCapture", ce));
+            const uint64_t l0 = t_launches;
+            sb_status st = SB_OK;
+            for (int i = 0; i < g && st == SB_OK; ++i) st = body();
+            cudaGraph_t graph = nullptr;
+            ce = cudaStreamEndCapture(s, &graph);
+            const uint64_t nk = t_launches - l0;
+            t_launches = l0;
+            g_launches.fetch_sub(nk);  // captured, not launched
+            if (st != SB_OK || ce != cudaSuccess) {
+                if (graph) cudaGraphDestroy(graph);
+                return st != SB_OK ? st : xfail(ex, SB_ERR_CUDA, cuda_msg("cudaStreamEndCapture", ce));
+            }
+            cudaGraphExec_t exec = nullptr;
+            ce = cudaGraphInstantiate(&exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (ce != cudaSuccess) return xfail(ex, SB_ERR_CUDA, cuda_msg("cudaGraphInstantiate", ce));
+            if (ex.graphs.size() >= 8) {  // a bounded cache: drop the oldest
+                cudaGraphExecDestroy(ex.graphs.front().exec);
+                ex.graphs.erase(ex.graphs.begin());
+            }
+            ex.graphs.push_back(PcgGraph{pl->sens, pl->general, x, tol2, (int)o.precond, (int)fixed, g, exec, nk});
+            hit = &ex.graphs.back();
+        }
+        const cudaError_t ce = cudaGraphLaunch(hit->exec, s);
+        if (ce != cudaSuccess) return xfail(ex, SB_ERR_CUDA, cuda_msg("cudaGraphLaunch", ce));
+        g_launches.fetch_add(hit->launches, std::memory_order_relaxed);
+        return SB_OK;
+    };
     int it = 0;
     while (it < nit) {
         const int g = std::min(kPollEvery, nit - it);
-        for (int i = 0; i < g; ++i) {
-            if (passes) {
-                if (sb_status e = vol_apply_A(ex, p, q, true)) return e;
-            } else {
-                SB_LAUNCH(ex, SB_KCLASS_APPLY_A, 1,
-                          apply_A_2d(pl, ex, d, p, q, maskw, ex.st, red, s));
-            }
-            if (circ && vol) {
-                if (sb_status e = vol_precond(ex, 2, r, q, x, p, nullptr, tol2)) return e;
-            } else if (fused) {
-                SB_LAUNCH(ex, SB_KCLASS_PRECOND_FUSED, 1,
-                          launch_precond_fused(d, 1, x, r, p, q, invk, pl->tw_x, pl->tw_y, ex.st, tol2, s));
-            } else if (circ) {
-                SB_LAUNCH(ex, SB_KCLASS_PRECOND_ROW_FWD, 1, launch_row_fwd(d, 1, r, q, tb, pl->tw_x, ex.st, tol2, red, s));
-                SB_LAUNCH(ex, SB_KCLASS_PRECOND_COL, 1, launch_col_precond(d, tb, invk, pl->tw_y, ex.st, 0, red, s));
-                SB_LAUNCH(ex, SB_KCLASS_PRECOND_ROW_INV, 1, launch_row_inv(d, 2, tb, nullptr, x, p, pl->tw_x, ex.st, red, s));
-            } else {
-                SB_LAUNCH(ex, SB_KCLASS_VEC, 1, launch_vec_plain(d, 1, x, r, p, q, w, ex.st, tol2, red, s));
-                SB_LAUNCH(ex, SB_KCLASS_VEC, 1, launch_vec_plain(d, 2, x, r, p, q, w, ex.st, tol2, red, s));
-            }
-        }
+        if (sb_status e = block(g)) return e;
         it += g;
         if (!fixed || it >= nit) {
             SB_XCK(ex, cudaMemcpyAsync(ex.h_st, ex.st, sizeof(SliceState) * d.nb, cudaMemcpyDeviceToHost, s));
@@ -812,6 +883,7 @@ sb_status sb_plan_destroy(sb_plan pl) {
         }
         for (cudaEvent_t e : ex.ev_pool) cudaEventDestroy(e);
         if (ex.join) cudaEventDestroy(ex.join);
+        for (const auto& g : ex.graphs) cudaGraphExecDestroy(g.exec);
         if (ex.own_stream) {
             cudaStreamSynchronize(ex.s);
             cudaStreamDestroy(ex.s);
@@ -822,6 +894,18 @@ sb_status sb_plan_destroy(sb_plan pl) {
     if (pl->fork) cudaEventDestroy(pl->fork);
     delete pl;
     return SB_OK;
+}
+
+// retire every captured PCG graph of the plan (after the plan's work on them has finished)
+void drop_graphs(sb_plan pl) {
+    auto drop = [](Exec& ex) {
+        if (ex.graphs.empty()) return;
+        cudaStreamSynchronize(ex.s);
+        for (const auto& g : ex.graphs) cudaGraphExecDestroy(g.exec);
+        ex.graphs.clear();
+    };
+    drop(pl->whole);
+    for (Exec& ex : pl->groups) drop(ex);
 }
 
 sb_status sb_set_coils(sb_plan pl, const void* d_sens) {
@@ -1118,6 +1202,14 @@ sb_status sb_split_bregman_many(const sb_plan* plans, int nplans, const void* co
     for (auto& t : th) t.join();
     for (int i = 0; i < nplans; ++i)
         if (st[i] != SB_OK) return st[i];
+    return SB_OK;
+}
+
+sb_status sb_set_graphs(sb_plan pl, int enable) {
+    if (!pl) return SB_ERR_INVALID_ARG;
+    SB_CK(pl, pl->stream ? cudaStreamSynchronize(pl->stream) : cudaDeviceSynchronize());
+    pl->graphs = enable != 0;
+    drop_graphs(pl);
     return SB_OK;
 }
 

@@ -83,6 +83,7 @@ SIGNATURES = [
     ("sb_coil_compression_matrix", ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.c_int,
                                                   ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     ("sb_plan_set_timing", ctypes.c_int, [_P, ctypes.c_uint]),
+    ("sb_set_graphs", ctypes.c_int, [_P, ctypes.c_int]),
     ("sb_plan_get_timing", ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_uint64),
                                           ctypes.POINTER(ctypes.c_double)]),
 ]
@@ -326,6 +327,10 @@ class Plan:
 
     def pcg_solve(self, b, x, **kw):
         return sb_pcg_solve(self.handle, self._c64(b), self._c64(x), pcg_opts(**kw), self.nbatch)
+
+    def set_graphs(self, enable: bool):
+        """Replay the PCG iteration blocks from CUDA graphs (default) or launch directly."""
+        _check(_lib.sb_set_graphs(_P(self.handle), 1 if enable else 0), self.handle)
 
     def set_timing(self, class_mask: int):
         sb_plan_set_timing(self.handle, class_mask)

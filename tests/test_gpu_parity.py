@@ -250,6 +250,53 @@ def test_concurrent_groups_are_bitwise_identical(torch, sbm):
         assert all(abs(a - b) <= 1 for a, b in zip(out[1][1][i], ref.iters))
 
 
+@pytest.mark.parametrize("prec,groups", [(0, 3), (2, 3), (0, 1)])
+def test_graph_replay_is_bitwise_identical(torch, sbm, prec, groups):
+    """PCG iteration blocks replayed from CUDA graphs give exactly the direct launches' results
+    (tolerance-stopped and fixed schedules, three concurrent slice groups, repeated calls that
+    reuse the captured graphs, and a second coil buffer whose maps need their own capture)."""
+    wl = synth.Workload("256x256 Nc4 TV+Haar graphs", 256, 256, 4, 4.0, 16, "uniform", 1.0, 0.05, 0.05, 3, 4, 1,
+                        1e-3, 100, 0, seed=6)
+    nb = 5
+    slices = [synth.make_slice(wl, 88 * 1000 + i) for i in range(nb)]
+    sens = to_dev(torch, np.stack([s.sens for s in slices]))
+    mask = torch.from_numpy(np.stack([s.mask for s in slices])).cuda()
+    y = to_dev(torch, np.stack([s.y for s in slices]))
+    out = []
+    for graphs in (False, True):
+        # one group runs on the plan's stream: a stream of its own (the default stream is never captured)
+        stream = torch.cuda.Stream() if groups == 1 else None
+        torch.cuda.synchronize()
+        plan = sbm.Plan(wl.nx, wl.ny, wl.ncoils, nb, wl.mu, wl.lam, wl.gam, wl.wavelet_levels, groups=groups,
+                        prec=prec, stream=stream)
+        plan.set_graphs(graphs)
+        plan.set_coils(sens)
+        plan.set_mask(mask)
+        runs = []
+        for rep, kw in enumerate([{"tol": wl.pcg_tol, "maxit": wl.pcg_maxit}, {"fixed_iters": 6},
+                                  {"tol": wl.pcg_tol, "maxit": wl.pcg_maxit}]):
+            x = torch.zeros((nb, wl.ny, wl.nx), dtype=torch.complex64, device="cuda")
+            torch.cuda.synchronize()
+            st, iters, _ = plan.split_bregman(y, x, wl.n_outer, **kw)
+            assert st == sbm.SB_OK
+            runs.append((x.cpu().numpy(), iters))
+        sens2 = sens.clone()  # same coils at another address, then back to the first buffer
+        for sd in (sens2, sens):
+            plan.set_coils(sd)
+            plan.set_mask(mask)
+            x = torch.zeros((nb, wl.ny, wl.nx), dtype=torch.complex64, device="cuda")
+            torch.cuda.synchronize()
+            st, iters, _ = plan.split_bregman(y, x, wl.n_outer, tol=wl.pcg_tol, maxit=wl.pcg_maxit)
+            assert st == sbm.SB_OK
+            runs.append((x.cpu().numpy(), iters))
+        out.append(runs)
+        plan.close()
+    for (xa, ia), (xb, ib) in zip(out[0], out[1]):
+        assert np.array_equal(xa, xb) and ia == ib
+    for k in (2, 3, 4):
+        assert np.array_equal(out[1][0][0], out[1][k][0])
+
+
 def test_unsupported_inputs(torch, sbm):
     with pytest.raises(sbm.SbError) as ei:
         sbm.Plan(48, 64, 2, 1, 1.0, 0.1, 0.1, 0)
