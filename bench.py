@@ -76,6 +76,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-loop", action="store_true", help="uneven64: skip the per-slice loop comparison")
+    ap.add_argument("--autotune", action="store_true",
+                    help="choose slice groups, the preconditioner's column tile and the poll interval with the "
+                         "library's autotuner (timed before the measured region, cached per geometry)")
     ap.add_argument("--groups", type=int, default=0, help="concurrent slice groups (0 = library default)")
     ap.add_argument("--prec", choices=list(PRECS), default="fp32",
                     help="fp32, or a split-precision mode: the radix-16 DFT stages of q = A p on the tensor cores "
@@ -272,8 +275,27 @@ def run_ours(args):
     wav = sb.SB_WAVELET_DAUB4 if args.wavelet == "daub4" else sb.SB_WAVELET_HAAR
     ncv = args.compress if 0 < args.compress < wl.ncoils else wl.ncoils
     prec, dtype_label = PRECS[args.prec]
+    tuned = None
+    groups = args.groups
+    if args.autotune and ncv == wl.ncoils:
+        from paper_1710_01758_gb300 import autotune
+
+        def make(g):
+            p = sb.Plan(wl.nx, wl.ny, ncv, B, wl.mu, wl.lam, wl.gam, wl.wavelet_levels, stream=stream, groups=g,
+                        wavelet=wav, prec=prec)
+            p.set_coils(d_sens)
+            p.set_mask(d_mask)
+            return p
+
+        t0 = time.perf_counter()
+        tuned = autotune.tune(make, wl.nx, wl.ny, ncv, B, prec)
+        tuned["tuning_s"] = round(time.perf_counter() - t0, 2)
+        log(f"[bench] autotune: {tuned}")
+        groups = tuned["groups"]
     plan = sb.Plan(wl.nx, wl.ny, ncv, B, wl.mu, wl.lam, wl.gam, wl.wavelet_levels, stream=stream,
-                   groups=args.groups, wavelet=wav, prec=prec)
+                   groups=groups, wavelet=wav, prec=prec)
+    if tuned:
+        plan.set_tuning(col_tile=tuned["col_tile"], poll_every=tuned["poll_every"])
 
     def step(ys=d_y, ss=d_sens, ms=d_mask, xx=x):
         if ncv < wl.ncoils:  # coil compression (Methods, "Coil Compression") is part of the step
@@ -432,7 +454,7 @@ def run_ours(args):
                 "scaling": "weak", "vs_baseline": None, "dtype": dtype_label, "scalars": "fp64", "data": "synthetic",
                 "config": workload_config(wl, B, {"parallelism": f"{world} ranks x independent batches",
                                                   "wavelet": args.wavelet, "virtual_coils": ncv,
-                                                  "precision": args.prec}),
+                                                  "precision": args.prec, "autotune": tuned}),
                 "recon_per_s": recon_per_s,
                 "pcg_iters_per_step": total_all / args.steps,
                 "roofline": {"bound": "hbm", "kernel": a_label,
@@ -528,6 +550,7 @@ def run_uneven(args, torch, sb, synth, world, rank, local, dist):
     dev = torch.device("cuda", local)
     t0 = time.perf_counter()
     plans, ys, xs, sens, masks, members = [], [], [], [], [], []
+    tuned_all = {}
     for (nx, ny, nc), ids in sorted(groups.items()):
         sl = [synth.uneven_slice(wls, i) for i in ids]
         w = wls[ids[0]]
@@ -535,7 +558,25 @@ def run_uneven(args, torch, sb, synth, world, rank, local, dist):
         masks.append(torch.from_numpy(np.stack([s.mask for s in sl])).to(dev))
         ys.append(torch.from_numpy(np.stack([s.y for s in sl]).astype(np.complex64)).to(dev))
         xs.append(torch.zeros((len(ids), ny, nx), dtype=torch.complex64, device=dev))
-        plans.append(sb.Plan(nx, ny, nc, len(ids), w.mu, w.lam, w.gam, w.wavelet_levels, stream=torch.cuda.Stream(dev)))
+        pstream = torch.cuda.Stream(dev)
+        g, tuning = 0, None
+        if args.autotune:
+            from paper_1710_01758_gb300 import autotune
+
+            def make(gg, nx=nx, ny=ny, nc=nc, ids=ids, w=w, k=len(sens) - 1):
+                p = sb.Plan(nx, ny, nc, len(ids), w.mu, w.lam, w.gam, w.wavelet_levels, stream=pstream, groups=gg)
+                p.set_coils(sens[k])
+                p.set_mask(masks[k])
+                return p
+
+            torch.cuda.synchronize()
+            tuning = autotune.tune(make, nx, ny, nc, len(ids))
+            g = tuning["groups"]
+            tuned_all[f"{nx}x{ny}x{nc}"] = {k: tuning[k] for k in ("groups", "col_tile", "poll_every")}
+        plan = sb.Plan(nx, ny, nc, len(ids), w.mu, w.lam, w.gam, w.wavelet_levels, stream=pstream, groups=g)
+        if tuning:
+            plan.set_tuning(col_tile=tuning["col_tile"], poll_every=tuning["poll_every"])
+        plans.append(plan)
         members.append((ids, sl))
     torch.cuda.synchronize()
     log(f"[bench] rank {rank}: generated {len(wls)} uneven slices ({len(plans)} geometries) in "
@@ -601,7 +642,8 @@ def run_uneven(args, torch, sb, synth, world, rank, local, dist):
                            "sizes": dict(sizes), "coils": sorted({w.ncoils for w in wls}),
                            "accel": sorted({w.accel for w in wls}), "haar_levels": w0.wavelet_levels,
                            "n_outer": w0.n_outer, "pcg_tol": w0.pcg_tol, "precond": "circulant",
-                           "l2": "inputs larger than L2", "parallelism": f"{world} ranks x independent batches"},
+                           "l2": "inputs larger than L2", "parallelism": f"{world} ranks x independent batches",
+                           "autotune": tuned_all or None},
                 "recon_per_s": args.steps * len(wls) * world / elapsed_max,
                 "pcg_iters_per_step": total_all / args.steps, "roofline": None,
                 "gpu_launches": int(launches), "clocks": clocks, "e2e": None}

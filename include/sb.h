@@ -219,6 +219,22 @@ const char* sb_plan_last_error(sb_plan plan);
  * kernel node they run).  Instrumentation for benchmarks. */
 uint64_t sb_kernel_launches(void);
 
+/* Tuning of a plan's launch configuration (results are unchanged up to the summation order of
+ * the FP64 partial sums).  col_tile: columns per CTA of the preconditioner's column pass (the
+ * length-ny DFTs of M^{-1} = F^H diag(k)^{-1} F, Eq. precon): 8, 16 (default) or 32.  poll_every:
+ * PCG iterations between two polls of the slices' convergence state, which is also the length
+ * of a captured graph block (default 4, 1..64).  A zero field keeps the current value.  The
+ * library's autotuner (paper_1710_01758_gb300.autotune) times the choices per geometry and
+ * caches the fastest.  SB_ERR_UNSUPPORTED when col_tile does not divide nx or does not fit the
+ * column pass (at most 1024 threads, 160 KB of exchange buffers); SB_ERR_INVALID_ARG for other
+ * out-of-range values.  Synchronises the plan's stream. */
+typedef struct {
+    int col_tile;
+    int poll_every;
+} sb_tuning;
+sb_status sb_set_tuning(sb_plan plan, const sb_tuning* tuning);
+sb_status sb_get_tuning(sb_plan plan, sb_tuning* tuning);
+
 /* CUDA graphs for the PCG loop (default on).  PCG polls the slices' convergence state every
  * few iterations; with graphs enabled, each such block of iterations (q = A p and the
  * preconditioner step, Algorithm 1 step 5 / the Complexity section's PCG) is captured once per

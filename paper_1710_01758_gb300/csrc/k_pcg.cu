@@ -15,12 +15,12 @@
 namespace sb {
 namespace {
 
-constexpr int TX = kColTile;  // columns per CTA in column kernels
 constexpr int RY = 16;  // rows per CTA in row kernels
 
+template <int CT>
 struct ColIdx {
     int col;
-    __device__ __forceinline__ int operator()(int pos) const { return pos * TX + col; }
+    __device__ __forceinline__ int operator()(int pos) const { return pos * CT + col; }
 };
 template <int N>
 struct RowIdx {
@@ -86,36 +86,41 @@ k_row_fwd(float2* __restrict__ r, const float2* __restrict__ q, float2* __restri
 }
 
 // ------------------------------------------------------------------------------ column pass
-template <int NY, bool PCG>
-__global__ void __launch_bounds__(TX * NY / 16)
+// CT columns per CTA (8, 16 or 32: a tuning choice); the 1/(kN) weights are loaded with the data,
+// before the forward transform, so their latency overlaps it.
+template <int NY, bool PCG, int CT>
+__global__ void __launch_bounds__(CT * NY / 16)
 k_col_precond(float2* __restrict__ tb, const float* __restrict__ invk, const float2* __restrict__ tw_g,
               int nx, SliceState* st, int init, Red red) {
     constexpr int T = NY / 16;
-    constexpr int NT = TX * T;
+    constexpr int NT = CT * T;
     const int b = blockIdx.y;
     if (PCG && st[b].state != ST_ACTIVE) return;
     extern __shared__ __align__(128) unsigned char smem[];
     float2* buf0 = reinterpret_cast<float2*>(smem);
-    float2* buf1 = buf0 + NY * TX;
-    float2* tw = buf1 + NY * TX;
+    float2* buf1 = buf0 + NY * CT;
+    float2* tw = buf1 + NY * CT;
     double* red_s = reinterpret_cast<double*>(tw + NY);
     __shared__ int flag;
-    const int tid = threadIdx.x, col = tid % TX, t = tid / TX;
-    const int x = blockIdx.x * TX + col;
+    const int tid = threadIdx.x, col = tid % CT, t = tid / CT;
+    const int x = blockIdx.x * CT + col;
     for (int i = tid; i < NY; i += NT) tw[i] = tw_g[i];
     const size_t img = (size_t)b * NY * nx;
     float2 v[16];
+    float wk[16];
 #pragma unroll
-    for (int e = 0; e < 16; ++e) v[e] = tb[img + (size_t)(t + T * e) * nx + x];
+    for (int e = 0; e < 16; ++e) {
+        v[e] = tb[img + (size_t)(t + T * e) * nx + x];
+        wk[e] = __ldg(invk + img + (size_t)(t + T * e) * nx + x);
+    }
     __syncthreads();
-    const ColIdx idx{col};
+    const ColIdx<CT> idx{col};
     fft<NY, false>(v, t, buf0, idx, tw);
     float rz = 0.f;
 #pragma unroll
     for (int e = 0; e < 16; ++e) {
-        const float w = __ldg(invk + img + (size_t)(t + T * e) * nx + x);
-        rz = fmaf(cabs2(v[e]), w, rz);
-        v[e] = cscale(v[e], w);
+        rz = fmaf(cabs2(v[e]), wk[e], rz);
+        v[e] = cscale(v[e], wk[e]);
     }
     fft<NY, true>(v, t, buf1, idx, tw);
 #pragma unroll
@@ -343,8 +348,8 @@ cudaError_t prepare(K kernel, size_t smem) {
     return cudaSuccess;
 }
 
-template <int NY>
-size_t smem_col() { return (2 * NY * TX + NY) * sizeof(float2) + 64 * sizeof(double); }
+template <int NY, int CT>
+size_t smem_col() { return (2 * NY * CT + NY) * sizeof(float2) + 64 * sizeof(double); }
 template <int NX>
 size_t smem_row() { return (RY * (NX + NX / 16) + NX) * sizeof(float2) + 64 * sizeof(double); }
 
@@ -364,20 +369,33 @@ cudaError_t row_fwd_n(const Dims& d, int mode, float2* r, const float2* q, float
     return cudaGetLastError();
 }
 
-template <int NY>
-cudaError_t col_precond_n(const Dims& d, float2* t, const float* invk, const float2* tw, SliceState* st,
-                          int init, Red red, cudaStream_t s) {
-    const dim3 grid(d.nx / TX, d.nb), block(TX * NY / 16);
-    const size_t sm = smem_col<NY>();
+template <int NY, int CT>
+cudaError_t col_precond_ct(const Dims& d, float2* t, const float* invk, const float2* tw, SliceState* st,
+                           int init, Red red, cudaStream_t s) {
+    const dim3 grid(d.nx / CT, d.nb), block(CT * NY / 16);
+    const size_t sm = smem_col<NY, CT>();
     cudaError_t e;
     if (st) {
-        if ((e = prepare(k_col_precond<NY, true>, sm)) != cudaSuccess) return e;
-        k_col_precond<NY, true><<<grid, block, sm, s>>>(t, invk, tw, d.nx, st, init, red);
+        if ((e = prepare(k_col_precond<NY, true, CT>, sm)) != cudaSuccess) return e;
+        k_col_precond<NY, true, CT><<<grid, block, sm, s>>>(t, invk, tw, d.nx, st, init, red);
     } else {
-        if ((e = prepare(k_col_precond<NY, false>, sm)) != cudaSuccess) return e;
-        k_col_precond<NY, false><<<grid, block, sm, s>>>(t, invk, tw, d.nx, st, init, red);
+        if ((e = prepare(k_col_precond<NY, false, CT>, sm)) != cudaSuccess) return e;
+        k_col_precond<NY, false, CT><<<grid, block, sm, s>>>(t, invk, tw, d.nx, st, init, red);
     }
     return cudaGetLastError();
+}
+
+template <int NY>
+cudaError_t col_precond_n(const Dims& d, float2* t, const float* invk, const float2* tw, SliceState* st,
+                          int init, Red red, cudaStream_t s, int ct) {
+    if (!col_tile_ok(NY, d.nx, ct)) return cudaErrorInvalidValue;
+    if (ct == 8) return col_precond_ct<NY, 8>(d, t, invk, tw, st, init, red, s);
+    if (ct == 32) {
+        if constexpr (NY * 32 / 16 <= 1024 && 2 * NY * 32 * 8 <= 160 * 1024)
+            return col_precond_ct<NY, 32>(d, t, invk, tw, st, init, red, s);
+        return cudaErrorInvalidValue;
+    }
+    return col_precond_ct<NY, 16>(d, t, invk, tw, st, init, red, s);
 }
 
 template <int NX>
@@ -427,9 +445,16 @@ cudaError_t launch_row_fwd(const Dims& d, int mode, float2* r, const float2* q, 
 #undef CALL
 }
 
+bool col_tile_ok(int ny, int nx, int ct) {
+    if (ct != 8 && ct != 16 && ct != 32) return false;
+    if (nx % ct != 0) return false;
+    // one thread per 16 values: ct * ny / 16 threads and 2 ny ct complex values of shared memory
+    return ct * ny / 16 <= 1024 && 2 * (size_t)ny * ct * 8 <= 160 * 1024;
+}
+
 cudaError_t launch_col_precond(const Dims& d, float2* t, const float* invk, const float2* tw_y, SliceState* st,
-                               int init, Red red, cudaStream_t s) {
-#define CALL(N) col_precond_n<N>(d, t, invk, tw_y, st, init, red, s)
+                               int init, Red red, cudaStream_t s, int ct) {
+#define CALL(N) col_precond_n<N>(d, t, invk, tw_y, st, init, red, s, ct)
     switch (d.ny) {
         case 32: return CALL(32);
         case 64: return CALL(64);

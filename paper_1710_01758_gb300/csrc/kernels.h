@@ -93,8 +93,12 @@ cudaError_t launch_row_fwd(const Dims& d, int mode, float2* r, const float2* q, 
 // Column pass of M^{-1}: t <- F_y^H diag(invk) F_y t (in place); with st != nullptr also
 // rho_new = sum |F t|^2 invk and (init = 0) beta = rho_new / rho, rho = rho_new or
 // (init = 1) rho = rho_new.
+// ct: columns per CTA of the column pass (8, 16 or 32; a tuning choice, see col_tile_ok)
 cudaError_t launch_col_precond(const Dims& d, float2* t, const float* invk, const float2* tw_y,
-                               SliceState* st, int init, Red red, cudaStream_t s);
+                               SliceState* st, int init, Red red, cudaStream_t s, int ct = kColTile);
+// whether `ct` columns per CTA fit the column pass at (ny, nx): 8 | 16 | 32 dividing nx, at most
+// 1024 threads and 160 KB of exchange buffers
+bool col_tile_ok(int ny, int nx, int ct);
 
 // Row pass back: z = F_x^H t; mode 0: out = z; mode 1 (PCG init): p = z;
 // mode 2 (PCG step): x += alpha p, p = z + beta p (FINISHING slices: x += alpha p, -> DONE).

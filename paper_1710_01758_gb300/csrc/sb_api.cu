@@ -111,6 +111,8 @@ struct sb_plan_s {
     bool have_coils = false, have_mask = false;
     bool fused_precond = false;  // circulant M^{-1} as one cluster launch per PCG iteration
     bool graphs = true;          // PCG iteration blocks replayed as CUDA graphs
+    int col_tile = kColTile;     // columns per CTA of the preconditioner's column pass (tuning)
+    int poll_every = kPollEvery; // PCG iterations between convergence polls (tuning)
     // volumes: dims is the rows view {nx, ny nz, Nc, nb}; the planes are ny_plane x nx, nz of them
     int nz = 1, ny_plane = 0;
     size_t maxparts = kMaxParts;  // per-slice capacity of the cross-CTA partial sums
@@ -426,7 +428,7 @@ sb_status pcg_run(Exec& ex, const sb_pcg_opts& o, float2* x_full, sb_pcg_result*
                   launch_precond_fused(d, 0, x, r, p, nullptr, invk, pl->tw_x, pl->tw_y, ex.st, tol2, s));
     } else if (circ) {
         SB_LAUNCH(ex, SB_KCLASS_PRECOND_ROW_FWD, 1, launch_row_fwd(d, 0, r, nullptr, tb, pl->tw_x, ex.st, tol2, red, s));
-        SB_LAUNCH(ex, SB_KCLASS_PRECOND_COL, 1, launch_col_precond(d, tb, invk, pl->tw_y, ex.st, 1, red, s));
+        SB_LAUNCH(ex, SB_KCLASS_PRECOND_COL, 1, launch_col_precond(d, tb, invk, pl->tw_y, ex.st, 1, red, s, pl->col_tile));
         SB_LAUNCH(ex, SB_KCLASS_PRECOND_ROW_INV, 1, launch_row_inv(d, 1, tb, nullptr, x, p, pl->tw_x, ex.st, red, s));
     } else {
         SB_LAUNCH(ex, SB_KCLASS_VEC, 1, launch_vec_plain(d, 0, x, r, p, nullptr, w, ex.st, tol2, red, s));
@@ -448,7 +450,7 @@ sb_status pcg_run(Exec& ex, const sb_pcg_opts& o, float2* x_full, sb_pcg_result*
                       launch_precond_fused(d, 1, x, r, p, q, invk, pl->tw_x, pl->tw_y, ex.st, tol2, s));
         } else if (circ) {
             SB_LAUNCH(ex, SB_KCLASS_PRECOND_ROW_FWD, 1, launch_row_fwd(d, 1, r, q, tb, pl->tw_x, ex.st, tol2, red, s));
-            SB_LAUNCH(ex, SB_KCLASS_PRECOND_COL, 1, launch_col_precond(d, tb, invk, pl->tw_y, ex.st, 0, red, s));
+            SB_LAUNCH(ex, SB_KCLASS_PRECOND_COL, 1, launch_col_precond(d, tb, invk, pl->tw_y, ex.st, 0, red, s, pl->col_tile));
             SB_LAUNCH(ex, SB_KCLASS_PRECOND_ROW_INV, 1, launch_row_inv(d, 2, tb, nullptr, x, p, pl->tw_x, ex.st, red, s));
         } else {
             SB_LAUNCH(ex, SB_KCLASS_VEC, 1, launch_vec_plain(d, 1, x, r, p, q, w, ex.st, tol2, red, s));
@@ -509,7 +511,7 @@ sb_status pcg_run(Exec& ex, const sb_pcg_opts& o, float2* x_full, sb_pcg_result*
     };
     int it = 0;
     while (it < nit) {
-        const int g = std::min(kPollEvery, nit - it);
+        const int g = std::min(pl->poll_every, nit - it);
         if (sb_status e = block(g)) return e;
         it += g;
         if (!fixed || it >= nit) {
@@ -1122,7 +1124,8 @@ sb_status sb_apply_precond(sb_plan pl, const void* d_r, void* d_z) {
                   launch_row_fwd(d, 0, const_cast<float2*>(static_cast<const float2*>(d_r)), nullptr, pl->tb, pl->tw_x,
                                  nullptr, 0.0, ex.red, pl->stream));
         SB_LAUNCH(ex, SB_KCLASS_PRECOND_COL, 1,
-                  launch_col_precond(d, pl->tb, pl->invk, pl->tw_y, nullptr, 0, ex.red, pl->stream));
+                  launch_col_precond(d, pl->tb, pl->invk, pl->tw_y, nullptr, 0, ex.red, pl->stream,
+                                     pl->col_tile));
         SB_LAUNCH(ex, SB_KCLASS_PRECOND_ROW_INV, 1,
                   launch_row_inv(d, 0, pl->tb, static_cast<float2*>(d_z), nullptr, nullptr, pl->tw_x, nullptr, ex.red,
                                  pl->stream));
@@ -1202,6 +1205,25 @@ sb_status sb_split_bregman_many(const sb_plan* plans, int nplans, const void* co
     for (auto& t : th) t.join();
     for (int i = 0; i < nplans; ++i)
         if (st[i] != SB_OK) return st[i];
+    return SB_OK;
+}
+
+sb_status sb_set_tuning(sb_plan pl, const sb_tuning* t) {
+    if (!pl || !t) return SB_ERR_INVALID_ARG;
+    if (t->col_tile != 0 && !col_tile_ok(pl->ny_plane, pl->dims.nx, t->col_tile))
+        return fail(pl, SB_ERR_UNSUPPORTED, "col_tile must be 8, 16 or 32, divide nx and fit the column pass");
+    if (t->poll_every < 0 || t->poll_every > 64) return fail(pl, SB_ERR_INVALID_ARG, "poll_every must be 0..64");
+    SB_CK(pl, pl->stream ? cudaStreamSynchronize(pl->stream) : cudaDeviceSynchronize());
+    if (t->col_tile) pl->col_tile = t->col_tile;
+    if (t->poll_every) pl->poll_every = t->poll_every;
+    drop_graphs(pl);
+    return SB_OK;
+}
+
+sb_status sb_get_tuning(sb_plan pl, sb_tuning* t) {
+    if (!pl || !t) return SB_ERR_INVALID_ARG;
+    t->col_tile = pl->col_tile;
+    t->poll_every = pl->poll_every;
     return SB_OK;
 }
 

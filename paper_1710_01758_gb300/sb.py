@@ -44,6 +44,10 @@ class sb_plan_desc(ctypes.Structure):
                 ("wavelet", ctypes.c_int)]
 
 
+class sb_tuning(ctypes.Structure):
+    _fields_ = [("col_tile", ctypes.c_int), ("poll_every", ctypes.c_int)]
+
+
 class sb_pcg_opts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("maxit", ctypes.c_int), ("fixed_iters", ctypes.c_int),
                 ("precond", ctypes.c_int)]
@@ -84,6 +88,8 @@ SIGNATURES = [
                                                   ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     ("sb_plan_set_timing", ctypes.c_int, [_P, ctypes.c_uint]),
     ("sb_set_graphs", ctypes.c_int, [_P, ctypes.c_int]),
+    ("sb_set_tuning", ctypes.c_int, [_P, _P]),
+    ("sb_get_tuning", ctypes.c_int, [_P, _P]),
     ("sb_plan_get_timing", ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_uint64),
                                           ctypes.POINTER(ctypes.c_double)]),
 ]
@@ -327,6 +333,17 @@ class Plan:
 
     def pcg_solve(self, b, x, **kw):
         return sb_pcg_solve(self.handle, self._c64(b), self._c64(x), pcg_opts(**kw), self.nbatch)
+
+    def set_tuning(self, col_tile: int = 0, poll_every: int = 0):
+        """Columns per CTA of the preconditioner's column pass (8, 16, 32) and PCG iterations per
+        convergence poll; 0 keeps the current value."""
+        t = sb_tuning(col_tile, poll_every)
+        _check(_lib.sb_set_tuning(_P(self.handle), ctypes.byref(t)), self.handle)
+
+    def tuning(self) -> dict:
+        t = sb_tuning(0, 0)
+        _check(_lib.sb_get_tuning(_P(self.handle), ctypes.byref(t)), self.handle)
+        return {"col_tile": t.col_tile, "poll_every": t.poll_every}
 
     def set_graphs(self, enable: bool):
         """Replay the PCG iteration blocks from CUDA graphs (default) or launch directly."""
