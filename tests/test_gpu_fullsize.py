@@ -52,6 +52,39 @@ def test_benchmark_batch_sampled_slices():
     plan.close()
 
 
+@pytest.mark.parametrize("prec,tol", [(2, 1e-3), (1, 2e-3)])
+def test_benchmark_batch_split_precision_sampled_slice(prec, tol):
+    """The same 64-slice batch in the split-precision modes (bench.py --prec split-fp16 /
+    split-bf16): tensor-core DFT stages in every q = A p.  Slice 21 recomputed by the FP64
+    oracle: iterations within one per solve, image within the PCG tolerance (split-fp16) or twice
+    it (split-bf16, whose operator error is ~1e-5 relative)."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1710_01758_gb300 import sb
+
+    wl = synth.METRIC_256
+    B = 64
+    slices = synth.make_batch(wl, B, wl.seed)
+    sens = torch.from_numpy(np.stack([s.sens for s in slices])).to(torch.complex64).cuda()
+    mask = torch.from_numpy(np.stack([s.mask for s in slices])).cuda()
+    y = torch.from_numpy(np.stack([s.y for s in slices])).to(torch.complex64).cuda()
+    x = torch.zeros((B, wl.ny, wl.nx), dtype=torch.complex64, device="cuda")
+    plan = sb.Plan(wl.nx, wl.ny, wl.ncoils, B, wl.mu, wl.lam, wl.gam, wl.wavelet_levels, prec=prec)
+    plan.set_coils(sens)
+    plan.set_mask(mask)
+    st, iters, last = plan.split_bregman(y, x, wl.n_outer, wl.n_inner, tol=wl.pcg_tol, maxit=wl.pcg_maxit)
+    assert st == sb.SB_OK
+    xg = x.cpu().numpy()
+    assert np.all(np.isfinite(xg)) and all(r[2] for r in last)
+    i = 21
+    ref = _oracle_recon(wl, slices[i])
+    assert all(abs(a - b) <= 1 for a, b in zip(iters[i], ref.iters)), (iters[i], ref.iters)
+    err = float(np.linalg.norm(xg[i] - ref.x) / np.linalg.norm(ref.x))
+    assert err <= tol, err
+    plan.close()
+
+
 def test_volume_full_size_operators():
     """The 256 x 256 x 128 volume with 16 coils and (k_y, k_z) lines at R = 8 (24 x 24 centre):
     one application of A and of M^{-1}, and k, against the FP64 oracle over the whole volume."""
