@@ -155,7 +155,9 @@ typedef struct {
  * A x = b by PCG warm-started from x (step 5), shrinks and updates the Bregman variables
  * (steps 6-11); each outer iteration adds the data residual back (steps 12-14).
  * h_last (host, may be NULL) receives the last solve's result per slice.  Synchronises.
- * Returns the first non-OK PCG status met (the reconstruction still completes). */
+ * d_x must be 16-byte aligned (SB_ERR_INVALID_ARG otherwise; the update kernels move pixel
+ * pairs as 16-byte words).  Returns the first non-OK PCG status met (the reconstruction still
+ * completes). */
 sb_status sb_split_bregman(sb_plan plan, const void* d_y, void* d_x, const sb_sb_opts* opts,
                            sb_pcg_result* h_last);
 

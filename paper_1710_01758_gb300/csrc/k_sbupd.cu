@@ -41,6 +41,29 @@ __device__ __forceinline__ void haar2x2(float2& a, float2& b, float2& c, float2&
 // inverse of haar2x2 (the matrix is symmetric and orthogonal: it is its own inverse)
 __device__ __forceinline__ void ihaar2x2(float2& a, float2& b, float2& c, float2& d) { haar2x2(a, b, c, d); }
 
+__device__ __forceinline__ float4 pack2(float2 a, float2 b) { return make_float4(a.x, a.y, b.x, b.y); }
+__device__ __forceinline__ float2 lo2(float4 v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.z, v.w); }
+
+// TV step at tile position (ly, lx) in [0, ST]^2 from the old b_x, b_y values there: returns the
+// new b values and leaves u = d - b in ux / uy
+__device__ __forceinline__ void tv_point(float2 (&xs)[ST + 2][ST + 2], float2 (&ux)[ST + 1][ST + 1],
+                                         float2 (&uy)[ST + 1][ST + 1], int ly, int lx, float2 bxv, float2 byv,
+                                         float tau_tv, float2& bxn, float2& byn) {
+    const float2 xc = xs[ly + 1][lx + 1];
+    const float2 dxv = csub(xc, xs[ly + 1][lx]);  // D_x x
+    const float2 dyv = csub(xc, xs[ly][lx + 1]);  // D_y x
+    const float2 dx = shrink(cadd(dxv, bxv), tau_tv);
+    const float2 dy = shrink(cadd(dyv, byv), tau_tv);
+    bxn = csub(cadd(bxv, dxv), dx);
+    byn = csub(cadd(byv, dyv), dy);
+    ux[ly][lx] = csub(dx, bxn);
+    uy[ly][lx] = csub(dy, byn);
+}
+
+// Memory access: each thread's 2 x 2 group of the tile interior is two 16-byte row pairs (x0 + c0
+// even, nx even, buffers 16-byte aligned), read and written with float4; only the one-pixel
+// periodic halo (132 positions of x, 65 of b_x / b_y) uses wrapped scalar indices.
 __global__ void __launch_bounds__(256)
 k_sb_update(SbFields f, int nx, int ny, const float2* __restrict__ x, int levels, float lam, float gam,
             float tau_tv, float tau_w) {
@@ -52,35 +75,52 @@ k_sb_update(SbFields f, int nx, int ny, const float2* __restrict__ x, int levels
     const int y0 = blockIdx.y * ST, x0 = blockIdx.x * ST;
     const int tid = threadIdx.x;
     const size_t img = (size_t)b * ny * nx;
-    for (int i = tid; i < (ST + 2) * (ST + 2); i += 256) {
-        const int ly = i / (ST + 2), lx = i % (ST + 2);
+    const int gi = tid / 16, gj = tid % 16;     // 2x2 group: rows 2gi, 2gi+1; cols 2gj, 2gj+1
+    const int r0 = 2 * gi, c0 = 2 * gj;
+    const size_t p00 = img + (size_t)(y0 + r0) * nx + x0 + c0;
+    const size_t p10 = p00 + nx;
+    {
+        const float4 xa = __ldg(reinterpret_cast<const float4*>(x + p00));
+        const float4 xb = __ldg(reinterpret_cast<const float4*>(x + p10));
+        xs[r0 + 1][c0 + 1] = lo2(xa);
+        xs[r0 + 1][c0 + 2] = hi2(xa);
+        xs[r0 + 2][c0 + 1] = lo2(xb);
+        xs[r0 + 2][c0 + 2] = hi2(xb);
+    }
+    if (tid < 4 * (ST + 1)) {  // the ring of the 34 x 34 tile: rows 0 and 33, columns 0 and 33
+        int ly, lx;
+        if (tid < ST + 2) { ly = 0; lx = tid; }
+        else if (tid < 2 * (ST + 2)) { ly = ST + 1; lx = tid - (ST + 2); }
+        else if (tid < 2 * (ST + 2) + ST) { lx = 0; ly = tid - 2 * (ST + 2) + 1; }
+        else { lx = ST + 1; ly = tid - 2 * (ST + 2) - ST + 1; }
         const int gy = (y0 - 1 + ly + ny) % ny, gx = (x0 - 1 + lx + nx) % nx;
         xs[ly][lx] = x[img + (size_t)gy * nx + gx];
     }
     __syncthreads();
-    const int gi = tid / 16, gj = tid % 16;     // 2x2 group: rows 2gi, 2gi+1; cols 2gj, 2gj+1
-    const int r0 = 2 * gi, c0 = 2 * gj;
     float2 g4[4] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
 
     if (lam != 0.f) {
-        for (int i = tid; i < (ST + 1) * (ST + 1); i += 256) {
-            const int ly = i / (ST + 1), lx = i % (ST + 1);
-            const int gy = (y0 + ly) % ny, gx = (x0 + lx) % nx;
-            const size_t gidx = img + (size_t)gy * nx + gx;
-            const float2 xc = xs[ly + 1][lx + 1];
-            const float2 dxv = csub(xc, xs[ly + 1][lx]);  // D_x x
-            const float2 dyv = csub(xc, xs[ly][lx + 1]);  // D_y x
-            const float2 bxv = f.bx[gidx], byv = f.by[gidx];
-            const float2 dx = shrink(cadd(dxv, bxv), tau_tv);
-            const float2 dy = shrink(cadd(dyv, byv), tau_tv);
-            const float2 bxn = csub(cadd(bxv, dxv), dx);
-            const float2 byn = csub(cadd(byv, dyv), dy);
-            ux[ly][lx] = csub(dx, bxn);
-            uy[ly][lx] = csub(dy, byn);
-            if (ly < ST && lx < ST) {
-                f.bx_new[gidx] = bxn;
-                f.by_new[gidx] = byn;
-            }
+        {  // the thread's 2 x 2 group of the interior
+            const float4 bxa = reinterpret_cast<const float4*>(f.bx + p00)[0];
+            const float4 bxb = reinterpret_cast<const float4*>(f.bx + p10)[0];
+            const float4 bya = reinterpret_cast<const float4*>(f.by + p00)[0];
+            const float4 byb = reinterpret_cast<const float4*>(f.by + p10)[0];
+            float2 nx0, ny0, nx1, ny1, nx2, ny2, nx3, ny3;
+            tv_point(xs, ux, uy, r0, c0, lo2(bxa), lo2(bya), tau_tv, nx0, ny0);
+            tv_point(xs, ux, uy, r0, c0 + 1, hi2(bxa), hi2(bya), tau_tv, nx1, ny1);
+            tv_point(xs, ux, uy, r0 + 1, c0, lo2(bxb), lo2(byb), tau_tv, nx2, ny2);
+            tv_point(xs, ux, uy, r0 + 1, c0 + 1, hi2(bxb), hi2(byb), tau_tv, nx3, ny3);
+            reinterpret_cast<float4*>(f.bx_new + p00)[0] = pack2(nx0, nx1);
+            reinterpret_cast<float4*>(f.bx_new + p10)[0] = pack2(nx2, nx3);
+            reinterpret_cast<float4*>(f.by_new + p00)[0] = pack2(ny0, ny1);
+            reinterpret_cast<float4*>(f.by_new + p10)[0] = pack2(ny2, ny3);
+        }
+        if (tid < 2 * ST + 1) {  // the +1 halo: row ST (columns 0..ST) and column ST (rows 0..ST-1)
+            const int ly = tid <= ST ? ST : tid - (ST + 1);
+            const int lx = tid <= ST ? tid : ST;
+            const size_t gidx = img + (size_t)((y0 + ly) % ny) * nx + (x0 + lx) % nx;
+            float2 bxn, byn;
+            tv_point(xs, ux, uy, ly, lx, f.bx[gidx], f.by[gidx], tau_tv, bxn, byn);
         }
         __syncthreads();
 #pragma unroll
@@ -94,25 +134,30 @@ k_sb_update(SbFields f, int nx, int ny, const float2* __restrict__ x, int levels
     if (gam != 0.f) {
         // pixel values of the group, then level 1 in registers
         float2 a = xs[r0 + 1][c0 + 1], bq = xs[r0 + 1][c0 + 2], c = xs[r0 + 2][c0 + 1], d = xs[r0 + 2][c0 + 2];
-        const size_t p00 = img + (size_t)(y0 + r0) * nx + x0 + c0;
-        const size_t p10 = p00 + nx;
         if (levels >= 1) haar2x2(a, bq, c, d);
         // shrink + Bregman update of every coefficient this group holds at the finest level
         // (the approximation a is shrunk only when no coarser level follows)
         float2* bw = f.bw;
-        auto update = [&](float2& w, size_t gidx) {
-            const float2 bv = bw[gidx];
+        auto upd = [&](float2& w, float2 bv) {
             const float2 dw = shrink(cadd(w, bv), tau_w);
             const float2 bn = csub(cadd(bv, w), dw);
-            bw[gidx] = bn;
             w = csub(dw, bn);  // u_w = d_w - b_w
+            return bn;
         };
-        update(bq, p00 + 1);
-        update(c, p10);
-        update(d, p10 + 1);
-        if (levels <= 1) {
-            update(a, p00);
-        } else {
+        {
+            // the group's four b_w slots as two row pairs; the slot of a is rewritten unchanged
+            // when a coarser level owns it (that level updates it after the next barrier)
+            const float4 ba = reinterpret_cast<const float4*>(bw + p00)[0];
+            const float4 bb = reinterpret_cast<const float4*>(bw + p10)[0];
+            const float2 n01 = upd(bq, hi2(ba));
+            const float2 n10 = upd(c, lo2(bb));
+            const float2 n11 = upd(d, hi2(bb));
+            const float2 n00 = levels <= 1 ? upd(a, lo2(ba)) : lo2(ba);
+            reinterpret_cast<float4*>(bw + p00)[0] = pack2(n00, n01);
+            reinterpret_cast<float4*>(bw + p10)[0] = pack2(n10, n11);
+        }
+        auto update = [&](float2& w, size_t gidx) { bw[gidx] = upd(w, bw[gidx]); };
+        if (levels > 1) {
             ws[r0][c0] = a;
             __syncthreads();
             for (int l = 1; l < levels; ++l) {  // coarser levels, stride s, in place
@@ -154,9 +199,8 @@ k_sb_update(SbFields f, int nx, int ny, const float2* __restrict__ x, int levels
         g4[2] = cadd(g4[2], cscale(c, gam));
         g4[3] = cadd(g4[3], cscale(d, gam));
     }
-    const size_t p00 = img + (size_t)(y0 + r0) * nx + x0 + c0;
-    reinterpret_cast<float4*>(f.g + p00)[0] = make_float4(g4[0].x, g4[0].y, g4[1].x, g4[1].y);
-    reinterpret_cast<float4*>(f.g + p00 + nx)[0] = make_float4(g4[2].x, g4[2].y, g4[3].x, g4[3].y);
+    reinterpret_cast<float4*>(f.g + p00)[0] = pack2(g4[0], g4[1]);
+    reinterpret_cast<float4*>(f.g + p10)[0] = pack2(g4[2], g4[3]);
 }
 
 }  // namespace

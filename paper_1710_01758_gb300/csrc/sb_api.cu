@@ -1161,6 +1161,8 @@ sb_status sb_pcg_solve(sb_plan pl, const void* d_b, void* d_x, const sb_pcg_opts
 sb_status sb_split_bregman(sb_plan pl, const void* d_y, void* d_x, const sb_sb_opts* o, sb_pcg_result* h_last) {
     if (sb_status s = check_ready(pl)) return s;
     if (!o || !d_y || !d_x) return fail(pl, SB_ERR_INVALID_ARG, "null argument");
+    if (reinterpret_cast<uintptr_t>(d_x) % 16 != 0)
+        return fail(pl, SB_ERR_INVALID_ARG, "the image buffer must be 16-byte aligned");
     if (o->n_outer < 1 || o->n_inner < 1) return fail(pl, SB_ERR_INVALID_ARG, "n_outer and n_inner must be >= 1");
     if (sb_status s = check_opts(pl, &o->pcg)) return s;
     if (!pl->passes() && (pl->ms > 256 || rhs_smem_bytes(pl->dims.ny, pl->ms) > 227 * 1024))

@@ -317,6 +317,13 @@ def test_unsupported_inputs(torch, sbm):
     with pytest.raises(sbm.SbError) as ei:  # k was not built: operators refuse
         plan.apply_A(to_dev(torch, np.zeros((1, ny, nx), complex)))
     assert ei.value.status == sbm.SB_ERR_NOT_READY
+    plan.set_mask(torch.from_numpy(mask).cuda())
+    y = to_dev(torch, np.zeros((1, 2, ny, nx), complex))
+    buf = torch.zeros(ny * nx + 1, dtype=torch.complex64, device="cuda")
+    x_off = buf[1:].view(1, ny, nx)  # 8 bytes past a 16-byte boundary
+    with pytest.raises(sbm.SbError) as ei:
+        plan.split_bregman(y, x_off, 1, 1)
+    assert ei.value.status == sbm.SB_ERR_INVALID_ARG
 
 
 def test_parameter_sets_preconditioner_comparison(torch, sbm):
