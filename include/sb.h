@@ -60,7 +60,13 @@ typedef struct {
     int nbatch;             /* independent slices of this geometry solved together (>= 1) */
     double mu, lambda, gamma;  /* weights of Eq. system; mu > 0, lambda >= 0, gamma >= 0 */
     int wavelet_levels;     /* Haar levels of W used by sb_split_bregman; 0 = identity W */
-    sb_precision prec;      /* SB_PREC_FP32 */
+    sb_precision prec;      /* arithmetic of q = A p (Eq. system): SB_PREC_FP32 (FP32 DFTs), or
+                               SB_PREC_SPLIT_BF16 / SB_PREC_SPLIT_FP16: the DFT stages along y
+                               (256 = 16 x 16 or 512 = 16 x 32) run as tensor-core products on
+                               operands split in two bf16 or fp16 terms, FP32 accumulation; 2D
+                               line masks (a mask varying along x gives SB_ERR_UNSUPPORTED at
+                               sb_set_mask), ny = 256 or 512, nx a multiple of 8, else
+                               SB_ERR_UNSUPPORTED at create.  CG scalars stay FP64 in every mode. */
     int groups;             /* sb_pcg_solve / sb_split_bregman run the batch as this many
                                contiguous slice groups, each on its own stream driven by its own
                                host thread, so that one group's work fills the GPU while another

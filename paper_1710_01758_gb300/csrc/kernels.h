@@ -70,7 +70,7 @@ cudaError_t launch_apply_A(const Dims& d, const CUtensorMap& smap, const float2*
                            SliceState* st, Red red, cudaStream_t s);
 
 // q = A p with the radix-16 DFT stages on the tensor cores, operands split in two bf16 or fp16
-// terms with FP32 accumulation (the split-precision modes; ny = 256, nx a multiple of 8).
+// terms with FP32 accumulation (the split-precision modes; ny = 256 or 512, nx a multiple of 8).
 // smap8: the coil maps as 8-column x 256-row boxes with the 64-byte swizzle; tw: W_256^m, m < 256;
 // bmat: tc_bmat_bytes() of DFT-matrix operands from build_tc_bmat (same bf16 flag).
 struct TcOperands {

@@ -117,7 +117,7 @@ struct sb_plan_s {
     int nz = 1, ny_plane = 0;
     size_t maxparts = kMaxParts;  // per-slice capacity of the cross-CTA partial sums
     float2* tw_z = nullptr;
-    float2* tw_full = nullptr;  // W_256^m, m < 256, and the DFT-matrix operands (split-precision modes)
+    float2* tw_full = nullptr;  // W_ny^m, m < ny, and the DFT-matrix operands (split-precision modes)
     void* bmat = nullptr;
     float2* bz[2] = {nullptr, nullptr};
     // 2D slices whose mask varies along x (the paper's random 2D sampling): the data term runs
@@ -799,7 +799,7 @@ sb_status sb_plan_create(const sb_plan_desc* desc, void* cuda_stream, sb_plan* o
     ALLOC(pl->tw_y, d.ny);
     ALLOC(pl->tw_z, nz);
     if (d.prec != SB_PREC_FP32) {
-        ALLOC(pl->tw_full, 256);
+        ALLOC(pl->tw_full, d.ny);
         if ((e = cudaMalloc(&pl->bmat, tc_bmat_bytes())) != cudaSuccess) return bail("cudaMalloc");
     }
     ALLOC(pl->maskw, nb * d.ny * nz);
@@ -826,14 +826,14 @@ sb_status sb_plan_create(const sb_plan_desc* desc, void* cuda_stream, sb_plan* o
     if ((e = cudaMemcpy(pl->tw_z, tz.data(), sizeof(float2) * nz, cudaMemcpyHostToDevice)) != cudaSuccess)
         return bail("cudaMemcpy twiddles");
     if (pl->tw_full) {
-        std::vector<float2> tf(256);
-        for (int m = 0; m < 256; ++m) {
-            const double a = -2.0 * M_PI * m / 256.0;
+        std::vector<float2> tf(d.ny);
+        for (int m = 0; m < d.ny; ++m) {
+            const double a = -2.0 * M_PI * m / d.ny;
             tf[m] = make_float2((float)std::cos(a), (float)std::sin(a));
         }
         std::vector<uint16_t> bm(tc_bmat_bytes() / 2);
         build_tc_bmat(d.prec == SB_PREC_SPLIT_BF16, bm.data());
-        if ((e = cudaMemcpy(pl->tw_full, tf.data(), sizeof(float2) * 256, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        if ((e = cudaMemcpy(pl->tw_full, tf.data(), sizeof(float2) * d.ny, cudaMemcpyHostToDevice)) != cudaSuccess ||
             (e = cudaMemcpy(pl->bmat, bm.data(), tc_bmat_bytes(), cudaMemcpyHostToDevice)) != cudaSuccess)
             return bail("cudaMemcpy twiddles");
     }

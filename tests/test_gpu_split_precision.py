@@ -1,4 +1,4 @@
-"""GPU parity of the split-precision modes (the radix-16 DFT stages of q = A p on the tensor cores,
+"""GPU parity of the split-precision modes (the radix-16 and radix-32 DFT stages of q = A p on the tensor cores,
 operands split in two bf16 or fp16 terms, FP32 accumulation) against the FP64 oracle.
 
 Stated tolerances, per mode (relative L2):
@@ -58,11 +58,11 @@ def make_plan(sbm, torch, sens, mask, mu, lam, gam, prec, levels=0):
 
 
 @pytest.mark.parametrize("mode", list(MODES))
-@pytest.mark.parametrize("nx,nc,nb", [(256, 12, 2), (64, 3, 3), (8 * 64, 4, 1), (32, 1, 2)])
-def test_split_apply_A(torch, sbm, mode, nx, nc, nb):
+@pytest.mark.parametrize("nx,ny,nc,nb", [(256, 256, 12, 2), (64, 256, 3, 3), (512, 256, 4, 1), (32, 256, 1, 2),
+                                         (512, 512, 6, 1), (64, 512, 3, 2), (192, 512, 2, 1)])
+def test_split_apply_A(torch, sbm, mode, nx, ny, nc, nb):
     prec, op_tol, _ = MODES[mode]
-    ny = 256
-    sens, mask, rng = problem(nx, ny, nc, nb, seed=nx + nc)
+    sens, mask, rng = problem(nx, ny, nc, nb, seed=nx + ny + nc, n_centre=32 if ny == 512 else 24)
     mu, lam, gam = 1.0, 0.05, 0.05
     plan = make_plan(sbm, torch, sens, mask, mu, lam, gam, prec)
     x = synth.random_complex((nb, ny, nx), rng)
@@ -79,11 +79,12 @@ def test_split_apply_A(torch, sbm, mode, nx, nc, nb):
 
 
 @pytest.mark.parametrize("mode", list(MODES))
-def test_split_scale_invariance_and_zero(torch, sbm, mode):
+@pytest.mark.parametrize("ny", [256, 512])
+def test_split_scale_invariance_and_zero(torch, sbm, mode, ny):
     """A is linear: A (2^-70 x) and A (2^60 x) are 2^-70 A x and 2^60 A x to the same tolerance
     (fp16 keeps its range by exact power-of-two scaling of each tile), and A 0 = 0."""
     prec, op_tol, _ = MODES[mode]
-    nx, ny, nc, nb = 64, 256, 4, 2
+    nx, nc, nb = 64, 4, 2
     sens, mask, rng = problem(nx, ny, nc, nb, seed=9)
     mu = 1.0
     plan = make_plan(sbm, torch, sens, mask, mu, 0.0, 0.0, prec)
@@ -98,9 +99,10 @@ def test_split_scale_invariance_and_zero(torch, sbm, mode):
 
 
 @pytest.mark.parametrize("mode", list(MODES))
-def test_split_pcg_fixed_iterations(torch, sbm, mode):
+@pytest.mark.parametrize("nx,ny", [(128, 256), (64, 512)])
+def test_split_pcg_fixed_iterations(torch, sbm, mode, nx, ny):
     prec, _, img_tol = MODES[mode]
-    nx, ny, nc, nb = 128, 256, 6, 2
+    nc, nb = 6, 2
     sens, mask, rng = problem(nx, ny, nc, nb, seed=41)
     mu, lam, gam = 1.0, 0.05, 0.05
     plan = make_plan(sbm, torch, sens, mask, mu, lam, gam, prec)
@@ -151,9 +153,10 @@ def test_split_tolerance_run_matches_fp32_iteration_counts(torch, sbm):
 
 
 def test_split_unsupported(torch, sbm):
-    with pytest.raises(sbm.SbError) as ei:  # the tensor-core stages factor 256 = 16 x 16 only
-        sbm.Plan(128, 128, 2, 1, 1.0, 0.1, 0.1, 0, prec=sbm.SB_PREC_SPLIT_BF16)
-    assert ei.value.status == sbm.SB_ERR_UNSUPPORTED
+    for nx, ny in [(128, 128), (384, 384), (256, 320), (32, 192)]:  # the stages factor 256 and 512 only
+        with pytest.raises(sbm.SbError) as ei:
+            sbm.Plan(nx, ny, 2, 1, 1.0, 0.1, 0.1, 0, prec=sbm.SB_PREC_SPLIT_BF16)
+        assert ei.value.status == sbm.SB_ERR_UNSUPPORTED
     with pytest.raises(sbm.SbError) as ei:
         sbm.Plan(64, 64, 2, 1, 1.0, 0.1, 0.1, 0, nz=64, prec=sbm.SB_PREC_SPLIT_FP16)
     assert ei.value.status == sbm.SB_ERR_UNSUPPORTED
