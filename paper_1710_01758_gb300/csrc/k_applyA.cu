@@ -57,7 +57,7 @@ __host__ __device__ constexpr int lcm32(int t) {
 }
 
 template <int NY, bool PCG>
-__global__ void __launch_bounds__(TX * NY / 16, NY <= 256 ? 2 : 1)
+__global__ void __launch_bounds__(TX * NY / 16, is_pow2(NY) && NY <= 256 ? 2 : 1)
 k_apply_A(const __grid_constant__ CUtensorMap smap, const float2* __restrict__ p, float2* __restrict__ q,
           const float* __restrict__ maskw, const float2* __restrict__ tw_g, int nx, int nc, float mu, float lam,
           float gam, SliceState* st, Red red) {

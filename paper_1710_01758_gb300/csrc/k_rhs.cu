@@ -34,7 +34,7 @@ template <int NY>
 constexpr int kRhsStages = 1;
 
 template <int NY, bool ADDBACK>
-__global__ void __launch_bounds__(TX * NY / 16, NY <= 256 ? 2 : 1)
+__global__ void __launch_bounds__(TX * NY / 16, is_pow2(NY) && NY <= 256 ? 2 : 1)
 k_rhs(const __grid_constant__ CUtensorMap smap, const __grid_constant__ CUtensorMap ymap,
       const __grid_constant__ CUtensorMap y1map, SbFields f, int nx, int nc, const float2* __restrict__ xin,
       float2* __restrict__ r, const float2* __restrict__ tw_g, float mu, float lam, float gam, SliceState* st,
