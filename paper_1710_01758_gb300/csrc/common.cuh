@@ -373,6 +373,55 @@ __device__ __forceinline__ void fft_generic_bar(float2 (&v)[16], int t, float2* 
     for (int e = 0; e < 16; ++e) v[e] = buf[idx(t + T * e)];
 }
 
+// Out-of-place form of the two shared-memory stages (src -> dst, one butterfly at a time, so only
+// R values are live): the callers that can spare a second exchange buffer avoid holding every
+// butterfly's values across the stage barrier.
+template <int N, int R, int NS, int T, bool INV, class Idx>
+__device__ __forceinline__ void stockham_stage_oop(const float2* src, float2* dst, Idx idx, const float2* tw, int t) {
+    constexpr int NB = N / R;
+    constexpr int PER = (NB + T - 1) / T;
+#pragma unroll
+    for (int m = 0; m < PER; ++m) {
+        const int j = t + T * m;
+        if (PER * T == NB || j < NB) {
+            const int k = j % NS;
+            float2 a[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) a[r] = src[idx(j + NB * r)];
+#pragma unroll
+            for (int r = 1; r < R; ++r) {
+                float2 w = tw[k * r * (N / (NS * R))];
+                if (INV) w.y = -w.y;
+                a[r] = cmul(a[r], w);
+            }
+            dft_any<R, INV>(a);
+            const int base = (j / NS) * NS * R + k;
+#pragma unroll
+            for (int r = 0; r < R; ++r) dst[idx(base + NS * r)] = a[r];
+        }
+    }
+}
+
+// fft_generic_bar with the stages out of place through buf2 (same layout as buf): three barriers
+// instead of five; the result and the register layout are those of fft_generic_bar.
+template <int N, bool INV, class Idx, class Bar>
+__device__ __forceinline__ void fft_generic_oop_bar(float2 (&v)[16], int t, float2* buf, float2* buf2, Idx idx,
+                                                    const float2* tw, Bar bar) {
+    constexpr int T = N / 16;
+    constexpr int R2 = GenericPlan<N>::R2, R3 = GenericPlan<N>::R3;
+    static_assert(16 * R2 * R3 == N, "plan covers N");
+    dft16<INV>(v);
+#pragma unroll
+    for (int r = 0; r < 16; ++r) buf[idx(16 * t + r)] = v[r];
+    bar();
+    stockham_stage_oop<N, R2, 16, T, INV>(buf, buf2, idx, tw, t);
+    bar();
+    stockham_stage_oop<N, R3, 16 * R2, T, INV>(buf2, buf, idx, tw, t);
+    bar();
+#pragma unroll
+    for (int e = 0; e < 16; ++e) v[e] = buf[idx(t + T * e)];
+}
+
 __host__ __device__ constexpr bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
 
 // Size dispatch: two stages for powers of two up to 256, three for 512, the generic
@@ -382,6 +431,14 @@ __device__ __forceinline__ void fft_bar(float2 (&v)[16], int t, float2* buf, Idx
     if constexpr (is_pow2(N) && N <= 256) fft_2stage_bar<N, INV>(v, t, buf, idx, tw, bar);
     else if constexpr (N == 512) fft_3stage_bar<N, INV>(v, t, buf, idx, tw, bar);
     else fft_generic_bar<N, INV>(v, t, buf, idx, tw, bar);
+}
+
+// fft_bar, with a second exchange buffer for the mixed-radix sizes (unused by the others)
+template <int N, bool INV, class Idx, class Bar>
+__device__ __forceinline__ void fft_bar2(float2 (&v)[16], int t, float2* buf, float2* buf2, Idx idx, const float2* tw,
+                                         Bar bar) {
+    if constexpr (is_pow2(N)) fft_bar<N, INV>(v, t, buf, idx, tw, bar);
+    else fft_generic_oop_bar<N, INV>(v, t, buf, buf2, idx, tw, bar);
 }
 
 struct CtaBar {

@@ -75,7 +75,10 @@ k_apply_A(const __grid_constant__ CUtensorMap smap, const float2* __restrict__ p
     unsigned char* smem = smem_raw + pad_to_1024(smem_raw);
     float2* sbuf = reinterpret_cast<float2*>(smem);  // [2][NY * TX] swizzled coil tiles
     float2* xbuf = sbuf + 2 * NY * TX;                // [TX][ExIdx::kStride] exchange regions
-    float2* tw = xbuf + ExIdx<NY>::kStride * TX;
+    // mixed-radix sizes: a second set of exchange regions for the out-of-place stages
+    constexpr int kEx2 = is_pow2(NY) ? 0 : ExIdx<NY>::kStride * TX;
+    float2* xbuf2 = xbuf + ExIdx<NY>::kStride * TX;
+    float2* tw = xbuf2 + kEx2;
     float2* halo = tw + NY;                           // [2][NY]: columns x0-1 and x0+TX
     float* mk = reinterpret_cast<float*>(halo + 2 * NY);
     double* red_s = reinterpret_cast<double*>(mk + NY);
@@ -142,11 +145,11 @@ k_apply_A(const __grid_constant__ CUtensorMap smap, const float2* __restrict__ p
         float2 u[16];
 #pragma unroll
         for (int e = 0; e < 16; ++e) u[e] = cmul(S[rows(e)], pv[e]);
-        fft_bar<NY,false>(u, t, ex, idx, tw, gbar);
+        fft_bar2<NY, false>(u, t, ex, xbuf2, idx, tw, gbar);
 #pragma unroll
         for (int e = 0; e < 16; ++e) u[e] = cscale(u[e], mk[t + T * e]);
         gbar();  // the group's forward reads of ex are done
-        fft_bar<NY,true>(u, t, ex, idx, tw, gbar);
+        fft_bar2<NY, true>(u, t, ex, xbuf2, idx, tw, gbar);
 #pragma unroll
         for (int e = 0; e < 16; ++e) acc[e] = cfmac(acc[e], S[rows(e)], u[e]);
         __syncwarp();
@@ -205,7 +208,8 @@ k_apply_A(const __grid_constant__ CUtensorMap smap, const float2* __restrict__ p
 
 template <int NY>
 size_t smem_apply_A() {
-    return 1024 + (2 * (size_t)NY * TX + (size_t)ExIdx<NY>::kStride * TX + 3 * NY) * sizeof(float2) +
+    return 1024 + (2 * (size_t)NY * TX + (is_pow2(NY) ? 1 : 2) * (size_t)ExIdx<NY>::kStride * TX + 3 * NY) *
+                      sizeof(float2) +
            NY * sizeof(float) + 64 * sizeof(double);
 }
 

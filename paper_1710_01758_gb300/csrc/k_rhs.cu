@@ -52,7 +52,8 @@ k_rhs(const __grid_constant__ CUtensorMap smap, const __grid_constant__ CUtensor
     extern __shared__ __align__(128) unsigned char smem[];
     float2* stages = reinterpret_cast<float2*>(smem);  // [NST][S tile | yt rows | yt1 rows]
     float2* xbuf = stages + NST * stage_elems;          // FFT exchange, then the x tile
-    float2* tw = xbuf + NY * TX;
+    float2* xbuf2 = xbuf + NY * TX;                     // mixed-radix sizes: out-of-place stages
+    float2* tw = xbuf2 + (is_pow2(NY) ? 0 : NY * TX);
     float2* halo = tw + NY;
     int* sl = reinterpret_cast<int*>(halo + 2 * NY);
     double* red_s = reinterpret_cast<double*>(sl + NY);
@@ -101,7 +102,7 @@ k_rhs(const __grid_constant__ CUtensorMap smap, const __grid_constant__ CUtensor
         float2 u[16];
 #pragma unroll
         for (int e = 0; e < 16; ++e) u[e] = cmul(S[idx(t + T * e)], xv[e]);
-        fft<NY, false>(u, t, xbuf, idx, tw);
+        fft_bar2<NY, false>(u, t, xbuf, xbuf2, idx, tw, CtaBar{});
         // on sampled lines: tt = R F S x (unitary scale), yv = y^[j] after the outer update,
         // u <- yv - tt; zero elsewhere
 #pragma unroll
@@ -120,7 +121,7 @@ k_rhs(const __grid_constant__ CUtensorMap smap, const __grid_constant__ CUtensor
             }
         }
         __syncthreads();
-        fft<NY, true>(u, t, xbuf, idx, tw);
+        fft_bar2<NY, true>(u, t, xbuf, xbuf2, idx, tw, CtaBar{});
 #pragma unroll
         for (int e = 0; e < 16; ++e) racc[e] = cfmac(racc[e], S[idx(t + T * e)], cscale(u[e], sc));
         __syncthreads();  // this stage's tiles and xbuf are free
@@ -195,7 +196,8 @@ cudaError_t rhs_n(const Dims& d, const CUtensorMap& smap, const CUtensorMap& yma
 
 size_t rhs_smem_bytes(int ny, int ms) {
     const size_t nst = 1;
-    return (nst * (size_t)(ny + 2 * ms) * TX + (size_t)ny * TX + 3 * (size_t)ny) * sizeof(float2) +
+    const size_t xbufs = is_pow2(ny) ? 1 : 2;  // exchange regions (two for the out-of-place mixed-radix stages)
+    return (nst * (size_t)(ny + 2 * ms) * TX + xbufs * (size_t)ny * TX + 3 * (size_t)ny) * sizeof(float2) +
            ny * sizeof(int) + 64 * sizeof(double);
 }
 
