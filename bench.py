@@ -76,6 +76,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-loop", action="store_true", help="uneven64: skip the per-slice loop comparison")
+    ap.add_argument("--no-pcg-iter", action="store_true",
+                    help="skip the standalone PCG-iteration measurement after the timed region")
     ap.add_argument("--autotune", action="store_true",
                     help="choose slice groups, the preconditioner's column tile and the poll interval with the "
                          "library's autotuner (timed before the measured region, cached per geometry)")
@@ -416,7 +418,7 @@ def run_ours(args):
     # written 40 N
     bytes_pcg_iter = (2 + ncv) * 8 * n + 4 * 8 * n + (2 * 8 + 4) * n + 5 * 8 * n
     pcg_iter = None
-    if not general:
+    if not general and not args.no_pcg_iter:
         gen = torch.Generator(device=dev).manual_seed(11)
         bvec = torch.complex(torch.randn(x.shape, device=dev, generator=gen),
                              torch.randn(x.shape, device=dev, generator=gen)).to(torch.complex64)
