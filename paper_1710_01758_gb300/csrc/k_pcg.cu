@@ -22,6 +22,17 @@ struct ColIdx {
     int col;
     __device__ __forceinline__ int operator()(int pos) const { return pos * CT + col; }
 };
+// Barrier of a row transform: a row's T = NX / 16 threads are consecutive, so for power-of-two
+// NX <= 512 they lie within one warp (T divides 32) and its exchanges need only __syncwarp;
+// otherwise (mixed radix, rows straddling warps) the whole CTA synchronises.
+template <int NX>
+struct RowBar {
+    __device__ __forceinline__ void operator()() const {
+        if constexpr (is_pow2(NX) && NX / 16 <= 32) __syncwarp();
+        else __syncthreads();
+    }
+};
+
 template <int N>
 struct RowIdx {
     int row;
@@ -69,7 +80,7 @@ k_row_fwd(float2* __restrict__ r, const float2* __restrict__ q, float2* __restri
         for (int e = 0; e < 16; ++e) v[e] = r[base + t + T * e];
     }
     __syncthreads();
-    fft<NX, false>(v, t, buf, RowIdx<NX>{row}, tw);
+    fft_bar<NX, false>(v, t, buf, RowIdx<NX>{row}, tw, RowBar<NX>{});
 #pragma unroll
     for (int e = 0; e < 16; ++e) tout[base + t + T * e] = v[e];
     if constexpr (MODE == 1) {
@@ -193,7 +204,7 @@ k_row_inv(const float2* __restrict__ tb, float2* __restrict__ out, float2* __res
         }
     }
     __syncthreads();
-    fft<NX, true>(v, t, buf, RowIdx<NX>{row}, tw);
+    fft_bar<NX, true>(v, t, buf, RowIdx<NX>{row}, tw, RowBar<NX>{});
     if constexpr (MODE == 0) {
 #pragma unroll
         for (int e = 0; e < 16; ++e) out[base + t + T * e] = v[e];
