@@ -556,13 +556,20 @@ def run_ours(args):
 
 
 def tensor_core_rate(args, wl, B, ncv, k1_us):
-    """Split-precision modes: the MMA work of one q = A p over the batch (4 radix-16 stages per
-    coil and 8-column tile, 2 K-steps x 3 split products of 128 x 32 x 16 each) per launch time."""
+    """Split-precision modes: the MMA work of one q = A p over the batch per launch time.  Per coil
+    and 8-column tile: ny = 256, four radix-16 stages of 2 K-steps x 3 split products of
+    128 x 32 x 16; ny = 512, two radix-16 stages of two 128-row groups x 2 K-steps x 3 products of
+    128 x 32 x 16 and two radix-32 stages of 4 K-steps x 3 products of 128 x 64 x 16."""
     if args.prec == "fp32" or not k1_us:
         return None
-    flops = B * ncv * (wl.nx // 8) * 4 * 6 * (2 * 128 * 32 * 16)
+    mma = lambda m, n: 2 * m * n * 16  # noqa: E731
+    if wl.ny == 512:
+        per_tile = 2 * (2 * 2 * 3 * mma(128, 32)) + 2 * (4 * 3 * mma(128, 64))
+    else:
+        per_tile = 4 * (2 * 3 * mma(128, 32))
+    flops = B * ncv * (wl.nx // 8) * per_tile
     return {"mma_tflops_per_launch": flops / 1e12, "achieved_tflops": flops / (k1_us / 1e6) / 1e12,
-            "note": "kind::f16 tcgen05.mma, M=128 N=32 K=16; the kernel is bound by the stage round trips "
+            "note": "kind::f16 tcgen05.mma; the kernel is bound by the stage round trips "
                     "(TMEM -> registers -> shared memory), not by the tensor pipe"}
 
 
