@@ -34,7 +34,11 @@ def create(**kw):
     (dict(nx=48), sb.SB_ERR_UNSUPPORTED),            # not a supported transform length
     (dict(ny=1024), sb.SB_ERR_UNSUPPORTED),
     (dict(wavelet_levels=6), sb.SB_ERR_UNSUPPORTED),  # Haar blocks larger than the 32 x 32 tiles
-    (dict(prec=sb.SB_PREC_SPLIT_BF16), sb.SB_ERR_UNSUPPORTED),
+    (dict(prec=sb.SB_PREC_SPLIT_BF16), sb.SB_ERR_UNSUPPORTED),  # tensor-core stages: ny 256 or 512 only
+    (dict(ny=128, prec=sb.SB_PREC_SPLIT_FP16), sb.SB_ERR_UNSUPPORTED),
+    (dict(nx=36, ny=256, prec=sb.SB_PREC_SPLIT_FP16), sb.SB_ERR_UNSUPPORTED),  # nx not a transform length
+    (dict(ny=256, nz=32, prec=sb.SB_PREC_SPLIT_FP16), sb.SB_ERR_UNSUPPORTED),  # volumes stay FP32
+    (dict(prec=7), sb.SB_ERR_INVALID_ARG),
     (dict(nz=16), sb.SB_ERR_UNSUPPORTED),            # volume depth below the shortest transform
     (dict(nz=32, wavelet_levels=5), sb.SB_ERR_UNSUPPORTED),
     (dict(nz=32, wavelet=1), sb.SB_ERR_UNSUPPORTED),  # Daubechies-4 is 2D only
@@ -58,6 +62,10 @@ def test_null_arguments_refused():
     for fn in ("sb_set_coils", "sb_set_mask", "sb_get_k"):
         assert getattr(sb._lib, fn)(None, None) == sb.SB_ERR_INVALID_ARG
     assert sb._lib.sb_apply_A(None, None, None) != sb.SB_OK
+    t = sb.sb_tuning(16, 4)
+    assert sb._lib.sb_set_tuning(None, ctypes.byref(t)) == sb.SB_ERR_INVALID_ARG
+    assert sb._lib.sb_get_tuning(None, ctypes.byref(t)) == sb.SB_ERR_INVALID_ARG
+    assert sb._lib.sb_set_graphs(None, 1) == sb.SB_ERR_INVALID_ARG
     assert sb._lib.sb_split_bregman_many(None, 0, None, None, None, None) == sb.SB_ERR_INVALID_ARG
     # coil compression: nv > nc and more than 32 coils are refused before any device work
     p = ctypes.c_void_p(16)
