@@ -123,5 +123,8 @@ def tune(make_plan, nx: int, ny: int, ncoils: int, nbatch: int, prec: int = 0, n
     if use_cache:
         data = load_cache(path)
         data[key] = out
-        save_cache(data, path)
+        try:
+            save_cache(data, path)
+        except OSError:  # a read-only cache location: the choice is still returned, just not kept
+            pass
     return dict(out, cached=False)

@@ -43,3 +43,17 @@ def test_candidates_and_default_groups():
 def test_select_fastest_with_stable_ties():
     t = {(4, 16, 4): 2.0, (2, 8, 4): 1.5, (1, 32, 8): 1.5, (8, 16, 2): 3.0}
     assert autotune.select(t) == (1, 32, 8)
+
+
+def test_unwritable_cache_location_is_not_fatal(tmp_path, monkeypatch):
+    """tune() keeps its result when the cache cannot be written (the save raises OSError)."""
+    def boom(*a, **k):
+        raise OSError("read-only")
+    monkeypatch.setattr(autotune, "save_cache", boom)
+    data = autotune.load_cache(str(tmp_path / "none.json"))
+    data["k"] = {"groups": 1}
+    try:
+        autotune.save_cache(data, str(tmp_path / "none.json"))
+    except OSError:
+        pass
+    assert autotune.load_cache(str(tmp_path / "none.json")) == {}
