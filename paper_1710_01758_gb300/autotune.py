@@ -121,10 +121,17 @@ def tune(make_plan, nx: int, ny: int, ncoils: int, nbatch: int, prec: int = 0, n
     out = {"groups": g, "col_tile": ct, "poll_every": pe, "ms": timings[(g, ct, pe)],
            "default_ms": timings.get((default_groups(nbatch), 16, 4))}
     if use_cache:
-        data = load_cache(path)
-        data[key] = out
-        try:
-            save_cache(data, path)
-        except OSError:  # a read-only cache location: the choice is still returned, just not kept
-            pass
+        store(key, out, path)
     return dict(out, cached=False)
+
+
+def store(key: str, entry: dict, path: str | None = None) -> bool:
+    """Add one entry to the cache file; False when the location cannot be written (the tuning
+    result is still used, just not kept)."""
+    data = load_cache(path)
+    data[key] = entry
+    try:
+        save_cache(data, path)
+    except OSError:
+        return False
+    return True

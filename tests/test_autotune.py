@@ -45,15 +45,13 @@ def test_select_fastest_with_stable_ties():
     assert autotune.select(t) == (1, 32, 8)
 
 
-def test_unwritable_cache_location_is_not_fatal(tmp_path, monkeypatch):
-    """tune() keeps its result when the cache cannot be written (the save raises OSError)."""
-    def boom(*a, **k):
-        raise OSError("read-only")
-    monkeypatch.setattr(autotune, "save_cache", boom)
-    data = autotune.load_cache(str(tmp_path / "none.json"))
-    data["k"] = {"groups": 1}
-    try:
-        autotune.save_cache(data, str(tmp_path / "none.json"))
-    except OSError:
-        pass
-    assert autotune.load_cache(str(tmp_path / "none.json")) == {}
+def test_store_and_unwritable_location(tmp_path, monkeypatch):
+    path = str(tmp_path / "tune.json")
+    assert autotune.store("a", {"groups": 2}, path) and autotune.store("b", {"groups": 4}, path)
+    assert autotune.load_cache(path) == {"a": {"groups": 2}, "b": {"groups": 4}}
+
+    def readonly(*a, **k):
+        raise OSError("read-only file system")
+    monkeypatch.setattr(autotune, "save_cache", readonly)
+    assert autotune.store("c", {"groups": 1}, path) is False
+    assert "c" not in autotune.load_cache(path)
