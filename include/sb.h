@@ -107,8 +107,10 @@ sb_status sb_set_coils(sb_plan plan, const void* d_sens);
 /* Set the sampling mask r (R = diag(r), Eq. ill0), uint8 [nbatch][ny][nx], nonzero = sampled,
  * DFT order, and build k of Eq. Kdiag by FFTs (Eq. diagonalelements and the k_d paragraph of
  * "Efficient Implementation of the Preconditioner").  Requires sb_set_coils.  d_mask is read
- * during this call only.  Synchronises the stream.  Returns SB_ERR_UNSUPPORTED if some slice's
- * mask varies along x. */
+ * during this call only.  Synchronises the stream.  A 2D mask that varies along x (the paper's
+ * random sampling, Methods, "Undersampling") switches the plan to the general path: the data
+ * term in three passes with a per-point mask.  Returns SB_ERR_UNSUPPORTED for such a mask on a
+ * volume plan or on a split-precision plan. */
 sb_status sb_set_mask(sb_plan plan, const uint8_t* d_mask);
 
 /* Copy k (float32 [nbatch][ny][nx], DFT order, before inversion) into d_k. */
