@@ -54,10 +54,12 @@ typedef enum { SB_PREC_FP32 = 0, SB_PREC_SPLIT_BF16 = 1, SB_PREC_SPLIT_FP16 = 2 
 typedef enum { SB_PRECOND_NONE = 0, SB_PRECOND_CIRCULANT = 1, SB_PRECOND_JACOBI = 2 } sb_precond;
 
 typedef struct {
-    int ndim;               /* 2 */
-    int nx, ny, nz;         /* image size; nz = 1 */
+    int ndim;               /* 2: slices; 3: volumes of nz planes (x the readout; 3D k, 7-point
+                               TV, 3D Haar on 16^3 tiles) */
+    int nx, ny, nz;         /* image size, x fastest; each a supported transform length
+                               (32, 64, 128, 192, 224, 256, 320, 384, 512); nz = 1 (or 0) in 2D */
     int ncoils;             /* N_c */
-    int nbatch;             /* independent slices of this geometry solved together (>= 1) */
+    int nbatch;             /* independent slices (volumes) of this geometry solved together (>= 1) */
     double mu, lambda, gamma;  /* weights of Eq. system; mu > 0, lambda >= 0, gamma >= 0 */
     int wavelet_levels;     /* Haar levels of W used by sb_split_bregman; 0 = identity W */
     sb_precision prec;      /* arithmetic of q = A p (Eq. system): SB_PREC_FP32 (FP32 DFTs), or
