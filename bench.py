@@ -47,7 +47,7 @@ HBM_FALLBACK_GBS = 6800.0
 # ncu capture of profiles/k_apply_A_256x256x12_b32.md (32 slices: 228.29 MB read + 9.14 MB
 # written) scaled by the slices processed.  Set to None whenever the kernel changes until it is
 # captured again.
-TRAFFIC_K1 = 2 * (228.29e6 + 9.14e6)
+TRAFFIC_K1 = 2 * (228.34e6 + 9.01e6)
 # --prec: (sb_precision, dtype label of the JSON line)
 PRECS = {"fp32": (0, "fp32"), "split-bf16": (1, "bf16x2 split, fp32 accumulate (tensor-core DFT stages)"),
          "split-fp16": (2, "fp16x2 split, fp32 accumulate (tensor-core DFT stages)")}
