@@ -1,0 +1,35 @@
+"""Host-side helpers of bench.py on CPU: the tensor-core work per launch for both stage shapes
+(counted by hand from the stage structure), the precision labels, and the workload config that
+the reference arm and our arm share."""
+import types
+
+import bench
+from paper_1710_01758_gb300 import synth
+
+
+def _args(prec):
+    return types.SimpleNamespace(prec=prec)
+
+
+def test_tensor_core_work_per_launch():
+    mma = lambda m, n: 2 * m * n * 16  # flops of one M x N x 16 product  # noqa: E731
+    wl = synth.METRIC_256  # 256 rows: four radix-16 stages x 2 K-steps x 3 split products
+    r = bench.tensor_core_rate(_args("split-fp16"), wl, 64, 12, 100.0)
+    per_tile = 4 * 2 * 3 * mma(128, 32)
+    assert r["mma_tflops_per_launch"] == 64 * 12 * (256 // 8) * per_tile / 1e12
+    assert abs(r["achieved_tflops"] - r["mma_tflops_per_launch"] / 100e-6) < 1e-9
+    wl5 = synth.LARGE_512  # 512 rows: two radix-16 stages of two M groups, two radix-32 of 4 K-steps
+    r5 = bench.tensor_core_rate(_args("split-bf16"), wl5, 8, 32, 50.0)
+    per_tile5 = 2 * (2 * 2 * 3 * mma(128, 32)) + 2 * (4 * 3 * mma(128, 64))
+    assert r5["mma_tflops_per_launch"] == 8 * 32 * (512 // 8) * per_tile5 / 1e12
+    assert bench.tensor_core_rate(_args("fp32"), wl, 64, 12, 100.0) is None
+
+
+def test_precision_labels_and_workload_config():
+    assert bench.PRECS["fp32"][0] == 0 and bench.PRECS["split-bf16"][0] == 1 and bench.PRECS["split-fp16"][0] == 2
+    wl = synth.METRIC_256
+    cfg = bench.workload_config(wl, 64, {"sample": "s"})
+    assert cfg["workload"] == f"64 x [{wl.name}]" and cfg["batch_slices"] == 64 and cfg["sample"] == "s"
+    assert (cfg["nx"], cfg["ny"], cfg["ncoils"]) == (256, 256, 12)
+    # the reference arm reports the same workload string as our arm's default
+    assert bench.WORKLOADS["256"] == ("METRIC_256", 64)
