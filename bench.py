@@ -43,6 +43,8 @@ if ROOT not in sys.path:
 METRIC = "PCG iters/s and recon/s at 256²×12 coils; HBM GB/s vs peak; err vs FP64"
 UNIT = "PCG iter/s"
 HBM_FALLBACK_GBS = 6800.0
+# FP32 CUDA-core peak: 152 SMs x 128 FP32 lanes x 2 flops (FMA) x the SM clock in GHz
+FP32_LANES = 152 * 128
 # DRAM bytes (read + write) of one k_apply_A launch over the full 64-slice 256x256x12 batch: the
 # ncu capture of profiles/k_apply_A_256x256x12_b32.md (32 slices: 228.29 MB read + 9.14 MB
 # written) scaled by the slices processed.  Set to None whenever the kernel changes until it is
@@ -84,7 +86,7 @@ def parse():
     ap.add_argument("--groups", type=int, default=0, help="concurrent slice groups (0 = library default)")
     ap.add_argument("--prec", choices=list(PRECS), default="fp32",
                     help="fp32, or a split-precision mode: the radix-16 DFT stages of q = A p on the tensor cores "
-                         "with operands split in two bf16 / fp16 terms and FP32 accumulation (ny = 256)")
+                         "with operands split in two bf16 / fp16 terms and FP32 accumulation (ny = 256 or 512)")
     ap.add_argument("--wavelet", choices=["haar", "daub4"], default="haar",
                     help="W of Algorithm 1 (daub4: the paper's Daubechies-4; 2D workloads)")
     ap.add_argument("--compress", type=int, default=0,
@@ -539,6 +541,7 @@ def run_ours(args):
                                        f"{B}-slice batch, CUDA events on the plan stream, after the timed region",
                              "algorithmic_bytes_per_launch": B * bytes_per_slice_iter,
                              "mean_launch_us": k1_alone_us,
+                             "alu": alu_side(wl, B, ncv, k1_alone_us, clocks, general),
                              "in_step": {"launches": k1_launches, "mean_launch_us": 1e3 * k1_ms / max(1, k1_launches),
                                          "achieved_gbs": achieved_in_step,
                                          "note": "concurrent slice groups overlap; active slices only"}},
@@ -553,6 +556,22 @@ def run_ours(args):
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def alu_side(wl, B, ncv, k1_us, clocks, general):
+    """The FP32 side of the dominant kernel's roofline (the bound is the larger of the two floors):
+    algorithmic flops per pixel and coil = two length-ny transforms at 5 log2(ny) each, the
+    sensitivity product (6), the mask (2) and the conjugate product accumulated (8); peak =
+    152 SMs x 128 lanes x 2 flops x the median SM clock sampled during the timed region."""
+    if general or not k1_us:
+        return None
+    flops = B * wl.nx * wl.ny * ncv * (2 * 5 * math.log2(wl.ny) + 6 + 2 + 8)
+    ghz = (clocks or {}).get("sm_mhz") or 2070.0
+    peak = FP32_LANES * 2 * ghz / 1e3  # TFLOP/s
+    achieved = flops / (k1_us / 1e6) / 1e12
+    return {"flops_per_launch": flops, "achieved_tflops": achieved, "peak_tflops": peak, "frac": achieved / peak,
+            "floor_us": flops / (peak * 1e12) * 1e6,
+            "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x median sampled SM clock"}
 
 
 def tensor_core_rate(args, wl, B, ncv, k1_us):

@@ -33,3 +33,14 @@ def test_precision_labels_and_workload_config():
     assert (cfg["nx"], cfg["ny"], cfg["ncoils"]) == (256, 256, 12)
     # the reference arm reports the same workload string as our arm's default
     assert bench.WORKLOADS["256"] == ("METRIC_256", 64)
+
+
+def test_alu_side_of_the_roofline():
+    """Two length-256 transforms at 5 log2(256) flops per point, plus 16 flops of products and
+    mask: 96 per pixel and coil; the peak is 152 x 128 x 2 flops per clock."""
+    wl = synth.METRIC_256
+    r = bench.alu_side(wl, 64, 12, 168.0, {"sm_mhz": 2070.0}, general=False)
+    assert r["flops_per_launch"] == 64 * 256 * 256 * 12 * 96
+    assert abs(r["peak_tflops"] - 152 * 128 * 2 * 2.07 / 1e3) < 1e-9
+    assert abs(r["achieved_tflops"] - r["flops_per_launch"] / 168e-6 / 1e12) < 1e-9
+    assert r["floor_us"] < 168.0 and bench.alu_side(wl, 64, 12, 168.0, None, general=True) is None
