@@ -566,7 +566,7 @@ def alu_side(wl, B, ncv, k1_us, clocks, general):
     if general or not k1_us:
         return None
     flops = B * wl.nx * wl.ny * ncv * (2 * 5 * math.log2(wl.ny) + 6 + 2 + 8)
-    ghz = (clocks or {}).get("sm_mhz") or 2070.0
+    ghz = ((clocks or {}).get("sm_mhz") or 2070.0) / 1e3
     peak = FP32_LANES * 2 * ghz / 1e3  # TFLOP/s
     achieved = flops / (k1_us / 1e6) / 1e12
     return {"flops_per_launch": flops, "achieved_tflops": achieved, "peak_tflops": peak, "frac": achieved / peak,
