@@ -43,12 +43,11 @@ if ROOT not in sys.path:
 METRIC = "PCG iters/s and recon/s at 256²×12 coils; HBM GB/s vs peak; err vs FP64"
 UNIT = "PCG iter/s"
 HBM_FALLBACK_GBS = 6800.0
-# FP32 CUDA-core peak: 152 SMs x 128 FP32 lanes x 2 flops (FMA) x the SM clock in GHz
-FP32_LANES = 152 * 128
-# DRAM bytes (read + write) of one k_apply_A launch over the full 64-slice 256x256x12 batch: the
-# ncu capture of profiles/k_apply_A_256x256x12_b32.md (32 slices: 228.29 MB read + 9.14 MB
-# written) scaled by the slices processed.  Set to None whenever the kernel changes until it is
-# captured again.
+# FP32 lanes per SM (the FP32 CUDA-core peak is SMs x lanes x 2 flops (FMA) x the SM clock)
+FP32_LANES_PER_SM = 128
+# DRAM bytes (read + write) of one k_apply_A launch over the full 64-slice 256x256x12 batch: an ncu
+# capture of a 32-slice launch (228.34 MB read + 9.01 MB written) scaled by the slices processed.
+# Set to None whenever the kernel changes until it is captured again.
 TRAFFIC_K1 = 2 * (228.34e6 + 9.01e6)
 # --prec: (sb_precision, dtype label of the JSON line)
 PRECS = {"fp32": (0, "fp32"), "split-bf16": (1, "bf16x2 split, fp32 accumulate (tensor-core DFT stages)"),
@@ -56,7 +55,22 @@ PRECS = {"fp32": (0, "fp32"), "split-bf16": (1, "bf16x2 split, fp32 accumulate (
 # workloads: name -> (synth workload attribute, default batch).  The default is the headline
 # configuration; the others are further measurement lines (batches sized above L2).
 WORKLOADS = {"256": ("METRIC_256", 64), "128": ("SMALL_128", 512), "512": ("LARGE_512", 8),
-             "random256": ("RANDOM_256", 64)}
+             "random256": ("RANDOM_256", 64), "shrink256": ("SHRINK_256", 64),
+             "set1": ("PARAM_256:set1", 64), "set2": ("PARAM_256:set2", 64), "set3": ("PARAM_256:set3", 64)}
+
+
+def workload_of(synth, name):
+    """The synth workload behind a --workload name (``ATTR`` or ``ATTR:key`` of a dict)."""
+    attr = WORKLOADS[name][0]
+    if ":" in attr:
+        a, k = attr.split(":")
+        return getattr(synth, a)[k]
+    return getattr(synth, attr)
+
+
+def sm_count(dev) -> int:
+    import torch
+    return int(torch.cuda.get_device_properties(dev).multi_processor_count)
 
 
 def log(*a):
@@ -73,7 +87,9 @@ def parse():
                     help="256: 256x256x12 (default); 128: 128x128x4; 512: 512x512x32; uneven64: 64 slices "
                          "of mixed size / coils / R, one plan per geometry, solved concurrently; volume: "
                          "256x256x128 x 16 coils, (ky, kz) lines at R 8; random256: 256x256x12 with random "
-                         "2D k-space points")
+                         "2D k-space points; shrink256: the default with shrink thresholds 0.02 (active "
+                         "shrinkage); set1..set3: the paper's weight sets on the default geometry, "
+                         "thresholds 0.02")
     ap.add_argument("--batch", type=int, default=0, help="slices per step (0 = the workload's default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -175,26 +191,32 @@ def make_inputs(wl, nbatch, seed):
     return slices, sens, mask, y
 
 
-def oracle_recon(wl, s, n_outer=None, wavelet="haar", nv=0):
+def oracle_recon(wl, s, n_outer=None, wavelet="haar", nv=0, with_active=False):
     """The FP64 oracle on one slice (coil-compressed to nv virtual coils by the oracle's own
-    compression if 0 < nv < Nc); returns (x, total PCG iterations, seconds)."""
+    compression if 0 < nv < Nc); returns (x, total PCG iterations, seconds) and, with
+    ``with_active``, the mean fraction of non-zero shrink outputs over the solves."""
     from oracle import coil_compression as cc, split_bregman as sbo
     t0 = time.perf_counter()
     y, sens = s.y, s.sens
     if 0 < nv < sens.shape[0]:
         A, _ = cc.compression_matrix(y, nv)
         y, sens = cc.compress(y, sens, A)
+    tau = getattr(wl, "tau", 0.0)
     r = sbo.split_bregman(y, sens, s.mask, wl.mu, wl.lam, wl.gam, wl.wavelet_levels, 2,
                           wl.n_outer if n_outer is None else n_outer, wl.n_inner, wl.pcg_tol, wl.pcg_maxit,
-                          wl.pcg_fixed_iters, wavelet=wavelet)
-    return r.x, int(sum(r.iters)), time.perf_counter() - t0
+                          wl.pcg_fixed_iters, wavelet=wavelet, tau_tv=tau if tau > 0 else None,
+                          tau_w=tau if tau > 0 else None)
+    secs = time.perf_counter() - t0
+    if with_active:
+        return r.x, int(sum(r.iters)), secs, (float(sum(r.shrink_nonzero) / len(r.shrink_nonzero))
+                                              if r.shrink_nonzero else 0.0)
+    return r.x, int(sum(r.iters)), secs
 
 
 def _oracle_worker(job):
     """One slice through the oracle in a spawned worker process (no CUDA in the worker)."""
     wl, s, n_outer, wavelet, nv = job
-    x, it, secs = oracle_recon(wl, s, n_outer, wavelet=wavelet, nv=nv)
-    return x, it, secs
+    return oracle_recon(wl, s, n_outer, wavelet=wavelet, nv=nv, with_active=True)
 
 
 def _oracle_warm(_):
@@ -216,11 +238,13 @@ def oracle_pool(n):
 
 def oracle_parallel(pool, wl, slices, n_outer=None, wavelet="haar", nv=0):
     """The oracle, as it stands, on several slices at once, one per worker process.  Returns (x of
-    the first slice, total PCG iterations, wall seconds, summed per-process seconds, slices)."""
+    the first slice, total PCG iterations, wall seconds, summed per-process seconds, slices, mean
+    fraction of non-zero shrink outputs)."""
     t0 = time.perf_counter()
     res = pool.map(_oracle_worker, [(wl, s, n_outer, wavelet, nv) for s in slices], chunksize=1)
     wall = time.perf_counter() - t0
-    return res[0][0], sum(r[1] for r in res), wall, sum(r[2] for r in res), len(slices)
+    return (res[0][0], sum(r[1] for r in res), wall, sum(r[2] for r in res), len(slices),
+            sum(r[3] for r in res) / len(res))
 
 
 def host_cores():
@@ -241,6 +265,7 @@ def workload_config(wl, nbatch, extra=None):
            "batch_slices": nbatch, "accel": wl.accel, "centre_lines": wl.n_centre, "mu": wl.mu,
            "lambda": wl.lam, "gamma": wl.gam, "haar_levels": wl.wavelet_levels, "n_outer": wl.n_outer,
            "n_inner": wl.n_inner, "pcg_tol": wl.pcg_tol, "precond": "circulant",
+           "shrink_thresholds": (wl.tau if getattr(wl, "tau", 0.0) > 0 else "1/lambda, 1/gamma"),
            "l2": "inputs larger than L2 (coil maps + k-space of the batch)"}
     if extra:
         cfg.update(extra)
@@ -265,7 +290,7 @@ def run_reference(args):
         for _ in range(args.warmup):
             oracle_parallel(pool, wl, slices, n_outer)
         for _ in range(args.steps):
-            _, it, wall, _, _ = oracle_parallel(pool, wl, slices, n_outer)
+            _, it, wall, _, _, _ = oracle_parallel(pool, wl, slices, n_outer)
             iters += it
             secs += wall
     value = iters / secs
@@ -302,8 +327,8 @@ def run_ours(args):
         return run_uneven(args, torch, sb, synth, world, rank, local, dist)
     if args.workload == "volume":
         return run_volume(args, torch, sb, synth, world, rank, local, dist)
-    attr, default_b = WORKLOADS[args.workload]
-    wl = getattr(synth, attr)
+    default_b = WORKLOADS[args.workload][1]
+    wl = workload_of(synth, args.workload)
     B = args.batch or default_b
     pcg_kw = ({"fixed_iters": wl.pcg_fixed_iters} if wl.pcg_fixed_iters > 0
               else {"tol": wl.pcg_tol, "maxit": wl.pcg_maxit})
@@ -346,7 +371,7 @@ def run_ours(args):
             ys, ss, _, _ = sb.coil_compress(ys, ss, ncv, stream)
         plan.set_coils(ss)
         plan.set_mask(ms)
-        st, iters, _ = plan.split_bregman(ys, xx, wl.n_outer, wl.n_inner, **pcg_kw)
+        st, iters, _ = plan.split_bregman(ys, xx, wl.n_outer, wl.n_inner, tau_tv=wl.tau, tau_w=wl.tau, **pcg_kw)
         if st != sb.SB_OK:
             raise RuntimeError(f"split_bregman: {sb.status_string(st)}")
         return int(sum(sum(i) for i in iters)), iters
@@ -354,7 +379,7 @@ def run_ours(args):
     for _ in range(args.warmup):
         step()
     # the timed steps run without the per-kernel-class event timer (two event records around
-    # every launch cost throughput); the class breakdown comes from one extra step afterwards
+    # every launch cost throughput); the split of a step comes from one extra step afterwards
     sampler = ClockSampler(local)
     if dist:
         dist.barrier()
@@ -375,10 +400,36 @@ def run_ours(args):
     if dist:
         dist.barrier()
     elapsed = ev0.elapsed_time(ev1) / 1e3
-    plan.set_timing((1 << sb.SB_KCLASS_COUNT) - 1)
-    it_breakdown, _ = step()
-    timing = {sb.KCLASS_NAMES[c]: plan.timing(c) for c in range(sb.SB_KCLASS_COUNT)}
-    plan.set_timing(0)
+    # where one step's time goes: one extra untimed step of the same batch as ONE slice group
+    # (one stream, so the per-launch event times do not overlap and add up to the step), the
+    # event timer on every kernel class (direct launches: the timer turns graph replay off)
+    split = None
+    if ncv == wl.ncoils:
+        one = sb.Plan(wl.nx, wl.ny, ncv, B, wl.mu, wl.lam, wl.gam, wl.wavelet_levels, stream=stream, groups=1,
+                      wavelet=wav, prec=prec)
+        if tuned:
+            one.set_tuning(col_tile=tuned["col_tile"], poll_every=tuned["poll_every"])
+        one.set_timing((1 << sb.SB_KCLASS_COUNT) - 1)
+        torch.cuda.synchronize()
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        one.set_coils(d_sens)
+        one.set_mask(d_mask)
+        xs1 = torch.zeros_like(x)
+        st1, it1, _ = one.split_bregman(d_y, xs1, wl.n_outer, wl.n_inner, tau_tv=wl.tau, tau_w=wl.tau, **pcg_kw)
+        s1.record(stream)
+        torch.cuda.synchronize()
+        step_ms = s0.elapsed_time(s1)
+        timing1 = {sb.KCLASS_NAMES[c]: one.timing(c) for c in range(sb.SB_KCLASS_COUNT)}
+        one.close()
+        kern_ms = sum(v[1] for v in timing1.values())
+        split = {"step_ms": round(step_ms, 3), "pcg_iterations": int(sum(sum(i) for i in it1)),
+                 "classes": {k: {"launches": v[0], "ms": round(v[1], 3), "share_of_step": round(v[1] / step_ms, 4)}
+                             for k, v in timing1.items() if v[0]},
+                 "host_polls_and_gaps_ms": round(step_ms - kern_ms, 3),
+                 "host_polls_and_gaps_share": round((step_ms - kern_ms) / step_ms, 4),
+                 "how": "one extra untimed step of the same batch as one slice group on one stream, CUDA events "
+                        "around every launch (no graph replay); the shares add up to that step"}
     total_all = total_iters
     elapsed_max = elapsed
     if dist:
@@ -386,20 +437,18 @@ def run_ours(args):
     value = total_all / elapsed_max
     recon_per_s = args.steps * B * world / elapsed_max
 
-    # dominant kernel: q = A p; algorithmic bytes per slice-iteration: line masks (one kernel)
-    # p + S read, q written; arbitrary masks (three passes through the coil scratch) S twice, the
-    # scratch written and read three times, p twice, q once
+    # dominant kernel: q = A p.  Algorithmic bytes per slice and application (the same for every
+    # mask): p and S read, q written, (2 + Nc) 8 N.  The general path (arbitrary masks: three
+    # passes through a coil scratch) moves more, (48 Nc + 24) N: S twice, the scratch written and
+    # read three times, p twice, q once; that is reported beside, as its own figure
     n = wl.nx * wl.ny
     general = wl.density == "random"
-    bytes_per_slice_iter = ((48 * ncv + 24) if general else (2 + ncv) * 8) * n
+    bytes_per_slice_iter = (2 + ncv) * 8 * n
+    impl_bytes_per_slice_iter = ((48 * ncv + 24) if general else (2 + ncv) * 8) * n
     a_label = "q = A p: k_g3_fwd_y + k_g2_x + k_g3_inv_y" if general else "k_apply_A (q = A p)"
-    k1_launches, k1_ms = timing["apply_A"]
-    k1_bytes = it_breakdown * bytes_per_slice_iter
     peak, peak_kind = peaks()
-    # in the step the slice groups run concurrently, so per-launch event times overlap; the
-    # dominant kernel is therefore also timed alone over the whole batch (every slice active),
-    # same kernel and launch configuration, right after the timed region
-    achieved_in_step = (k1_bytes / (k1_ms / 1e3) / 1e9) if k1_ms > 0 else None
+    # the dominant kernel timed alone over the whole batch (every slice active), same kernel and
+    # launch configuration as in the step, right after the timed region
     plan.set_timing(1 << sb.SB_KCLASS_APPLY_A)
     qbuf = torch.empty_like(x)
     n_apply = 20
@@ -409,16 +458,15 @@ def run_ours(args):
     plan.set_timing(0)
     k1_alone_us = 1e3 * k1_alone_ms / n_apply  # per application of A (one or three launches)
     achieved = B * bytes_per_slice_iter / (k1_alone_us / 1e6) / 1e9
-    all_ms = sum(v[1] for v in timing.values())
-    breakdown = {k: {"launches": v[0], "ms": round(v[1], 3), "share": round(v[1] / all_ms, 4) if all_ms else None}
-                 for k, v in timing.items()}
-    # the whole PCG iteration (q = A p and the three preconditioner passes with the CG updates)
-    # timed alone over the batch, as the step runs it (slice groups, graphs): fixed-iteration
-    # solves of 24 and 8 iterations, the difference over 16 iterations (no solve start-up in it).
-    # Algorithmic bytes per slice: q = A p (2 + Nc) 8 N; r -= alpha q and DFT_x: r, q read, r, t
-    # written 32 N; column pass t read and written, 1/(kN) read 20 N; row pass t, x, p read, x, p
-    # written 40 N
-    bytes_pcg_iter = (2 + ncv) * 8 * n + 4 * 8 * n + (2 * 8 + 4) * n + 5 * 8 * n
+    # the whole PCG iteration (q = A p and the preconditioner step with the CG updates) timed alone
+    # over the batch, as the step runs it (slice groups, graphs): fixed-iteration solves of 24 and
+    # 8 iterations, the difference over 16 iterations (no solve start-up in it).  Algorithmic bytes
+    # per slice and iteration with a fused schedule: q = A p reads p and S and writes q,
+    # (16 + 8 Nc) N; M^{-1} reads r, q, 1/k and writes r, z, 36 N; the update reads x, p, z and
+    # writes x, p, 40 N: (92 + 8 Nc) N.  The three-pass M^{-1} built here adds the round trip of its
+    # intermediate t: (108 + 8 Nc) N, reported as implementation bytes
+    bytes_pcg_iter = (92 + 8 * ncv) * n
+    impl_bytes_pcg_iter = (108 + 8 * ncv) * n
     pcg_iter = None
     if not general and not args.no_pcg_iter:
         gen = torch.Generator(device=dev).manual_seed(11)
@@ -439,6 +487,8 @@ def run_ours(args):
         gbs = B * bytes_pcg_iter / (it_us / 1e6) / 1e9
         pcg_iter = {"us": it_us, "achieved_gbs": gbs, "peak": peak, "frac": gbs / peak,
                     "algorithmic_bytes_per_iteration": B * bytes_pcg_iter,
+                    "bytes_rule": "(92 + 8 Nc) N per slice (fused schedule: q = A p, M^{-1}, updates)",
+                    "implementation_bytes_per_iteration": B * impl_bytes_pcg_iter,
                     "how": f"fixed 24- and 8-iteration PCG solves over the {B}-slice batch (slice groups, graphs), "
                            "best of 3 each, difference / 16"}
 
@@ -453,7 +503,7 @@ def run_ours(args):
         sub.set_mask(d_mask[:nsub].contiguous())
         xs = torch.zeros((nsub, wl.ny, wl.nx), dtype=torch.complex64, device=dev)
         _, it_plain, _ = sub.split_bregman(d_y[:nsub].contiguous(), xs, wl.n_outer, wl.n_inner,
-                                           precond=sb.SB_PRECOND_NONE, **pcg_kw)
+                                           tau_tv=wl.tau, tau_w=wl.tau, precond=sb.SB_PRECOND_NONE, **pcg_kw)
         sub.close()
         it_pre = iters_last[:nsub]
         extra["pcg_iters_per_solve"] = {
@@ -461,15 +511,23 @@ def run_ours(args):
             "reduction": round(float(np.sum(it_plain)) / max(1, float(np.sum(it_pre))), 3),
             "first_solve": [round(float(np.mean([i[0] for i in it_plain])), 2),
                             round(float(np.mean([i[0] for i in it_pre])), 2)],
+            "last_solve": [round(float(np.mean([i[-1] for i in it_plain])), 2),
+                           round(float(np.mean([i[-1] for i in it_pre])), 2)],
+            "first_last_order": "[plain CG, circulant]",
+            "paper_context": "paper (MATLAB, in-vivo spine, parameter set 1): 6x fewer iterations in the first "
+                             "and 3.5x in the last Split Bregman iteration, 4.65x overall (Results, Fig. 5a "
+                             "paragraph); context, not a target",
             "slices": nsub}
     if rank == 0:
         if not args.no_cpu_baseline:
             ncpu = max(1, min(host_cores(), B))
             with oracle_pool(ncpu) as pool:
-                x_or, it_or, wall, busy, nproc = oracle_parallel(pool, wl, slices[:ncpu], wavelet=args.wavelet,
-                                                                 nv=ncv)
+                x_or, it_or, wall, busy, nproc, act = oracle_parallel(pool, wl, slices[:ncpu],
+                                                                      wavelet=args.wavelet, nv=ncv)
             xg = x[0].cpu().numpy()
             extra["err_vs_fp64"] = float(np.linalg.norm(xg - x_or) / np.linalg.norm(x_or))
+            extra["shrink_active_frac"] = {"value": act, "how": "FP64 oracle on the sampled slices: mean over the "
+                                           "solves of the fraction of non-zero shrink outputs (steps 6-8)"}
             extra["cpu_baseline"] = {"value": it_or / wall, "unit": UNIT, "cores": nproc, "kind": "oracle",
                                      "sample": f"slices 0..{nproc - 1} of the batch, one per process on {nproc} "
                                                f"host cores, full {wl.n_outer}-iteration Split Bregman, FP64 numpy",
@@ -540,15 +598,14 @@ def run_ours(args):
                              "timing": f"timed alone: {n_apply} applications ({k1_alone_n} launches) over the "
                                        f"{B}-slice batch, CUDA events on the plan stream, after the timed region",
                              "algorithmic_bytes_per_launch": B * bytes_per_slice_iter,
+                             "bytes_rule": "(2 + Nc) 8 N per slice: p and S read, q written",
+                             "implementation_bytes_per_launch": B * impl_bytes_per_slice_iter,
+                             "implementation_over_algorithmic": impl_bytes_per_slice_iter / bytes_per_slice_iter,
                              "mean_launch_us": k1_alone_us,
-                             "alu": alu_side(wl, B, ncv, k1_alone_us, clocks, general),
-                             "in_step": {"launches": k1_launches, "mean_launch_us": 1e3 * k1_ms / max(1, k1_launches),
-                                         "achieved_gbs": achieved_in_step,
-                                         "note": "concurrent slice groups overlap; active slices only"}},
+                             "alu": alu_side(wl, B, ncv, k1_alone_us, clocks, general, sm_count(dev))},
                 "pcg_iteration": pcg_iter,
                 "tensor_core": tensor_core_rate(args, wl, B, ncv, k1_alone_us),
-                "kernel_time_breakdown": breakdown,
-                "kernel_time_breakdown_from": "one extra untimed step with CUDA events around every launch",
+                "step_split": split,
                 "gpu_launches": int(launches),
                 "clocks": clocks, "e2e": e2e}
         line.update(extra)
@@ -558,20 +615,20 @@ def run_ours(args):
     return 0
 
 
-def alu_side(wl, B, ncv, k1_us, clocks, general):
+def alu_side(wl, B, ncv, k1_us, clocks, general, sms):
     """The FP32 side of the dominant kernel's roofline (the bound is the larger of the two floors):
     algorithmic flops per pixel and coil = two length-ny transforms at 5 log2(ny) each, the
     sensitivity product (6), the mask (2) and the conjugate product accumulated (8); peak =
-    152 SMs x 128 lanes x 2 flops x the median SM clock sampled during the timed region."""
+    SMs (queried) x 128 lanes x 2 flops x the median SM clock sampled during the timed region."""
     if general or not k1_us:
         return None
     flops = B * wl.nx * wl.ny * ncv * (2 * 5 * math.log2(wl.ny) + 6 + 2 + 8)
     ghz = ((clocks or {}).get("sm_mhz") or 2070.0) / 1e3
-    peak = FP32_LANES * 2 * ghz / 1e3  # TFLOP/s
+    peak = sms * FP32_LANES_PER_SM * 2 * ghz / 1e3  # TFLOP/s
     achieved = flops / (k1_us / 1e6) / 1e12
     return {"flops_per_launch": flops, "achieved_tflops": achieved, "peak_tflops": peak, "frac": achieved / peak,
             "floor_us": flops / (peak * 1e12) * 1e6,
-            "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x median sampled SM clock"}
+            "peak_kind": f"derived: {sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x median sampled SM clock"}
 
 
 def tensor_core_rate(args, wl, B, ncv, k1_us):
@@ -753,32 +810,35 @@ def run_uneven(args, torch, sb, synth, world, rank, local, dist):
 
 
 def run_volume(args, torch, sb, synth, world, rank, local, dist):
-    """One 256x256x128 volume, 16 coils, (ky, kz) lines at R = 8 with a 24 x 24 centre, TV + 4-level
-    Haar, 20 Split Bregman iterations with PCG to 1e-3.  A step = k construction + reconstruction."""
+    """One 256x256x128 volume, 16 coils, (ky, kz) lines at R = 8 with a 24 x 24 centre, 3D TV +
+    3-level 3D Haar, 15 Split Bregman iterations with PCG to 1e-3.  A step = k construction +
+    reconstruction."""
     import numpy as np
     v = synth.VOLUME_256
     t0 = time.perf_counter()
     s = synth.make_volume(v, rank_seed(v.seed, rank))
     log(f"[bench] rank {rank}: generated the volume in {time.perf_counter() - t0:.1f}s")
     dev = torch.device("cuda", local)
-    d_sens = torch.from_numpy(s.sens[None].astype(np.complex64)).to(dev)
-    d_mask = torch.from_numpy(s.mask[None]).to(dev)
-    d_y = torch.from_numpy(s.y[None].astype(np.complex64)).to(dev)
+    sens_h = np.ascontiguousarray(s.sens[None].astype(np.complex64))
+    mask_h = np.ascontiguousarray(s.mask[None])
+    y_h = np.ascontiguousarray(s.y[None].astype(np.complex64))
+    d_sens = torch.from_numpy(sens_h).to(dev)
+    d_mask = torch.from_numpy(mask_h).to(dev)
+    d_y = torch.from_numpy(y_h).to(dev)
     x = torch.zeros((1, v.nz, v.ny, v.nx), dtype=torch.complex64, device=dev)
     stream = torch.cuda.current_stream(dev)
     plan = sb.Plan(v.nx, v.ny, v.ncoils, 1, v.mu, v.lam, v.gam, v.wavelet_levels, stream=stream, nz=v.nz)
 
-    def step():
-        plan.set_coils(d_sens)
-        plan.set_mask(d_mask)
-        st, iters, _ = plan.split_bregman(d_y, x, v.n_outer, v.n_inner, tol=v.pcg_tol, maxit=v.pcg_maxit)
+    def step(ss=d_sens, ms=d_mask, ys=d_y):
+        plan.set_coils(ss)
+        plan.set_mask(ms)
+        st, iters, _ = plan.split_bregman(ys, x, v.n_outer, v.n_inner, tol=v.pcg_tol, maxit=v.pcg_maxit)
         if st != sb.SB_OK:
             raise RuntimeError(f"split_bregman: {sb.status_string(st)}")
         return int(sum(sum(i) for i in iters))
 
     for _ in range(args.warmup):
         step()
-    plan.set_timing((1 << sb.SB_KCLASS_COUNT) - 1)
     sampler = ClockSampler(local)
     if dist:
         dist.barrier()
@@ -794,15 +854,97 @@ def run_volume(args, torch, sb, synth, world, rank, local, dist):
     torch.cuda.synchronize()
     clocks = sampler.stop()
     launches = sb.kernel_launches() - launches0
-    timing = {sb.KCLASS_NAMES[c]: plan.timing(c) for c in range(sb.SB_KCLASS_COUNT)}
-    plan.set_timing(0)
     elapsed = ev0.elapsed_time(ev1) / 1e3
     total_all, elapsed_max = total, elapsed
     if dist:
         elapsed_max, total_all = reduce_over_ranks(dist, dev, elapsed, total)
-    all_ms = sum(t[1] for t in timing.values())
-    breakdown = {k: {"launches": t[0], "ms": round(t[1], 3), "share": round(t[1] / all_ms, 4) if all_ms else None}
-                 for k, t in timing.items() if t[0]}
+
+    # where a step's time goes: one extra untimed step with the event timer on every class (the
+    # volume is one slice group on one stream, so the class times add up to the step)
+    plan.set_timing((1 << sb.SB_KCLASS_COUNT) - 1)
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
+    it_split = step()
+    s1.record(stream)
+    torch.cuda.synchronize()
+    step_ms = s0.elapsed_time(s1)
+    timing = {sb.KCLASS_NAMES[c]: plan.timing(c) for c in range(sb.SB_KCLASS_COUNT)}
+    plan.set_timing(0)
+    kern_ms = sum(t[1] for t in timing.values())
+    split = {"step_ms": round(step_ms, 3), "pcg_iterations": it_split,
+             "classes": {k: {"launches": t[0], "ms": round(t[1], 3), "share_of_step": round(t[1] / step_ms, 4)}
+                         for k, t in timing.items() if t[0]},
+             "host_polls_and_gaps_ms": round(step_ms - kern_ms, 3),
+             "how": "one extra untimed step, CUDA events around every launch; the shares add up to that step"}
+
+    # q = A p timed alone (three launches: y DFT per coil into the coil scratch, z DFT + mask +
+    # inverse, inverse y DFT + coil combine + TV).  Algorithmic bytes per application: p and S
+    # read, q written, (16 + 8 Nc) N; the three passes move (48 Nc + 24) N
+    n = v.nx * v.ny * v.nz
+    peak, peak_kind = peaks()
+    plan.set_timing(1 << sb.SB_KCLASS_APPLY_A)
+    qbuf = torch.empty_like(x)
+    n_apply = 5
+    for _ in range(n_apply):
+        plan.apply_A(x, qbuf)
+    a_n, a_ms = plan.timing(sb.SB_KCLASS_APPLY_A)
+    plan.set_timing(0)
+    a_us = 1e3 * a_ms / n_apply
+    alg = (16 + 8 * v.ncoils) * n
+    impl = (48 * v.ncoils + 24) * n
+    achieved = alg / (a_us / 1e6) / 1e9
+    roofline = {"bound": "hbm", "kernel": "q = A p: k_g3_fwd_y + k_g3_z + k_g3_inv_y", "achieved": achieved,
+                "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback",
+                "algorithmic_bytes_per_launch": alg, "bytes_rule": "(16 + 8 Nc) N: p and S read, q written",
+                "implementation_bytes_per_launch": impl, "implementation_over_algorithmic": impl / alg,
+                "mean_launch_us": a_us,
+                "timing": f"timed alone: {n_apply} applications ({a_n} launches), CUDA events on the plan stream"}
+
+    extra = {}
+    if rank == 0 and not args.no_cpu_baseline:
+        # the oracle as it stands on the same volume, bounded sample: the operator work of one PCG
+        # iteration (one application of A and one of M^{-1}, FP64 numpy on one host core)
+        from oracle import operators, precond
+        k = precond.clamp_k(precond.k_diag(s.sens, s.mask, v.mu, v.lam, v.gam, 3))
+        p0 = x[0].cpu().numpy().astype(np.complex128)
+        t0 = time.perf_counter()
+        operators.apply_A(p0, s.sens, s.mask, v.mu, v.lam, v.gam, 3)
+        precond.apply_precond(p0, k, 3)
+        t_it = time.perf_counter() - t0
+        extra["cpu_baseline"] = {"value": 1.0 / t_it, "unit": UNIT, "cores": host_threads(), "kind": "oracle",
+                                 "sample": "the operator work of one PCG iteration on the full volume (one "
+                                           "application of A and one of M^{-1}), FP64 numpy"}
+
+    e2e = None
+    if not args.no_e2e:
+        # end to end with host buffers: every step uploads the coil maps, the mask and the k-space
+        # data from pinned memory and reads the image back, all inside the timed region
+        hs = torch.from_numpy(sens_h).pin_memory()
+        hm = torch.from_numpy(mask_h).pin_memory()
+        hy = torch.from_numpy(y_h).pin_memory()
+        hx = torch.empty(tuple(x.shape), dtype=torch.complex64).pin_memory()
+        es, em, ey = torch.empty_like(d_sens), torch.empty_like(d_mask), torch.empty_like(d_y)
+        h2d = hs.numel() * 8 + hm.numel() + hy.numel() * 8
+        d2h = hx.numel() * 8
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        e_it = 0
+        for _ in range(args.steps):
+            es.copy_(hs, non_blocking=True)
+            em.copy_(hm, non_blocking=True)
+            ey.copy_(hy, non_blocking=True)
+            e_it += step(es, em, ey)
+            hx.copy_(x, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e_el = e0.elapsed_time(e1) / 1e3
+        if dist:
+            e_el, e_it = reduce_over_ranks(dist, dev, e_el, e_it)
+        e2e = {"value": e_it / e_el, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
     plan.close()
     if rank == 0:
         line = {"metric": METRIC, "value": total_all / elapsed_max, "unit": UNIT, "n_gpus": world,
@@ -815,8 +957,9 @@ def run_volume(args, torch, sb, synth, world, rank, local, dist):
                            "l2": "inputs larger than L2 (1.1 GB of coil maps)",
                            "parallelism": f"{world} ranks x independent volumes"},
                 "recon_per_s": args.steps * world / elapsed_max,
-                "pcg_iters_per_step": total_all / args.steps, "roofline": None,
-                "kernel_time_breakdown": breakdown, "gpu_launches": int(launches), "clocks": clocks, "e2e": None}
+                "pcg_iters_per_step": total_all / args.steps, "roofline": roofline,
+                "step_split": split, "gpu_launches": int(launches), "clocks": clocks, "e2e": e2e}
+        line.update(extra)
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

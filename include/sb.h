@@ -21,12 +21,17 @@
  *    they return (they report iteration counts to the host).
  *  - Errors are returned as sb_status, never by abort; sb_plan_last_error() gives a message.
  *    A CUDA error leaves the plan in an undefined numerical state (destroy it).
- *  - The mask must be constant along the readout (x) axis: Cartesian phase-encode line masks,
- *    the sampling of the paper's Methods ("Undersampling", random lines).  Other masks are
- *    rejected with SB_ERR_UNSUPPORTED.
- *  - Supported sizes: ndim = 2; nx, ny in {32, 64, 128, 192, 224, 256, 320, 384, 512}
- *    (powers of two and 16 x {12, 14, 20, 24}, mixed-radix transforms); ncoils >= 1; nbatch >= 1;
- *    wavelet_levels in [0, 5] (Haar blocks stay inside the 32 x 32 update tiles).
+ *  - Masks (sb_set_mask): a 2D mask constant along the readout (x) axis (Cartesian
+ *    phase-encode lines, the paper's first scheme in Methods, "Undersampling") takes the fast
+ *    path, DFTs along y only; any other 2D mask (the paper's random 2D sampling) takes the
+ *    general path, a per-point mask between DFTs along y and x.  Volumes (ndim = 3) need a mask
+ *    constant along x (sampled (k_y, k_z) lines); split-precision plans need line masks; other
+ *    combinations are refused with SB_ERR_UNSUPPORTED.
+ *  - Supported sizes: ndim = 2 (slices) or 3 (volumes of nz planes); nx, ny (and nz for
+ *    volumes) in {32, 64, 128, 192, 224, 256, 320, 384, 512} (powers of two and
+ *    16 x {12, 14, 20, 24}, mixed-radix transforms); ncoils >= 1; nbatch >= 1; wavelet_levels in
+ *    [0, 5] for slices (Haar blocks stay inside the 32 x 32 update tiles) and [0, 4] for volumes
+ *    (16^3 tiles).  Further limits of a precision mode or schedule are stated at its field.
  */
 #ifndef SB_H
 #define SB_H
@@ -47,7 +52,7 @@ typedef enum {
     SB_ERR_NONFINITE = 5,     /* NaN or Inf met in a CG scalar (rho, p^H A p, ||r||) */
     SB_ERR_BREAKDOWN = 6,     /* Re(p^H A p) <= 0: A not positive definite on the data */
     SB_ERR_NOT_CONVERGED = 7, /* maxit reached before the tolerance */
-    SB_ERR_TIMEOUT = 8        /* reserved for bounded device-side waits */
+    SB_ERR_TIMEOUT = 8        /* a bounded device-side wait gave up (a TMA tile never arrived) */
 } sb_status;
 
 typedef enum { SB_PREC_FP32 = 0, SB_PREC_SPLIT_BF16 = 1, SB_PREC_SPLIT_FP16 = 2 } sb_precision;
@@ -188,13 +193,18 @@ sb_status sb_split_bregman_many(const sb_plan* plans, int nplans, const void* co
  * buffers, hosts whose framework owns the memory pool).  The paper has no counterpart; this is
  * a deployment variant of the same operation.
  *   d_r, d_z: complex64 [nbatch][ny][nx] (may be equal); d_k: float32 [nbatch][ny][nx], the
- *   diagonal k as returned by sb_get_k; cuda_stream: a cudaStream_t (NULL = legacy stream).
- *   nx, ny in {32, 64, 128, 256}; nbatch * ny * nx <= 1048576, else SB_ERR_INVALID_ARG.
+ *   diagonal k, every entry positive and finite, e.g. as returned by sb_get_k (whose entries
+ *   are already floored at 1e-12 max k); d_k is divided by as given, so a zero entry gives a
+ *   non-finite z there.  cuda_stream: a cudaStream_t (NULL = legacy stream).
+ *   nx, ny in {32, 64, 128, 256}, else SB_ERR_UNSUPPORTED; nbatch >= 1 and
+ *   nbatch * ny * nx <= 1048576 (the fixed scratch), else SB_ERR_INVALID_ARG.
  * The intermediate lives in one fixed 8 MiB device array that this library defines and every
  * GPU using it keeps until the process exits.  The first call on a device sets that array up
- * (resolves its address, writes the DFT twiddle tables with a synchronous copy), so make it
- * before any stream capture.  All calls share the array: calls whose kernels overlap on the
- * GPU race with each other and must be ordered by the caller.  Asynchronous after set-up. */
+ * (resolves its address, writes the DFT twiddle tables and synchronises the device), so make it
+ * before any stream capture.  The set-up is kept per device: the entry point serves the
+ * device's primary context (the CUDA runtime's) and is not valid after cudaDeviceReset.  All
+ * calls share the array: calls whose kernels overlap on the GPU race with each other and must
+ * be ordered by the caller.  Asynchronous after set-up. */
 sb_status sb_apply_precond_noalloc(const void* d_r, const float* d_k, void* d_z, int nx, int ny,
                                    int nbatch, void* cuda_stream);
 
@@ -257,6 +267,18 @@ sb_status sb_get_tuning(sb_plan plan, sb_tuning* tuning);
  * are bitwise identical either way.  enable: 0 = direct launches, 1 = graphs.  Synchronises the
  * plan's stream; SB_ERR_INVALID_ARG for a null plan. */
 sb_status sb_set_graphs(sb_plan plan, int enable);
+
+/* Check of the bounded device waits (no counterpart in the paper).  Every wait of a kernel for
+ * a TMA tile polls an mbarrier at most a fixed number of times (about half a second by
+ * default), then records a timeout in the plan's device error word and lets the kernel finish;
+ * sb_pcg_solve and sb_split_bregman read that word at each convergence poll and return
+ * SB_ERR_TIMEOUT.  wait_polls: the poll limit (1 .. 4194304; 0 restores the default).
+ * withhold_coil_tiles != 0: the coil-tile kernels of the 2D line path in FP32 (q = A p and the
+ * Split Bregman right-hand side) request no tile at all, so nothing is in flight and every wait
+ * for a tile runs out after wait_polls polls; what the plan computes while it is set is
+ * meaningless (switch it off and start the solve again, or destroy the plan).  Clears the error
+ * word, drops captured graphs, synchronises the device.  SB_ERR_INVALID_ARG for a null plan or wait_polls above the default. */
+sb_status sb_set_wait_check(sb_plan plan, unsigned wait_polls, int withhold_coil_tiles);
 
 /* Kernel classes for the event timer below. */
 typedef enum {

@@ -41,6 +41,8 @@ class SbResult:
     x: np.ndarray
     iters: list[int]          # PCG iterations of every solve, in order
     rel_resid: list[float]    # final relative residual of every solve
+    shrink_nonzero: list[float] = dataclasses.field(default_factory=list)  # per solve: fraction of
+    # non-zero shrink outputs (TV d's and wavelet d_w together), a record of how active steps 6-8 are
 
 
 def split_bregman(y, sens, mask, mu, lam, gam, levels, ndim, n_outer, n_inner=1,
@@ -79,7 +81,7 @@ def split_bregman(y, sens, mask, mu, lam, gam, levels, ndim, n_outer, n_inner=1,
     bb = [zero.copy() for _ in range(ndim)]
     d_w = zero.copy()
     b_w = zero.copy()
-    iters, resid = [], []
+    iters, resid, active = [], [], []
     for _j in range(n_outer):                                   # step 2
         for _k in range(n_inner):                               # step 3
             b = operators.rhs(yj, sens, mask, mu, lam, gam, d, bb, d_w, b_w, levels, ndim, wavelet)  # 4
@@ -95,5 +97,7 @@ def split_bregman(y, sens, mask, mu, lam, gam, levels, ndim, n_outer, n_inner=1,
                 wx = operators.wavelet(x, levels, ndim, wavelet)
                 d_w = shrink(wx + b_w, tau_w)                                                # 8
                 b_w = b_w + wx - d_w                                                         # 11
+            outs = (d if lam != 0.0 else []) + ([d_w] if gam != 0.0 else [])
+            active.append(float(np.mean([np.count_nonzero(v) / v.size for v in outs])) if outs else 0.0)
         yj = yj + y1 - operators.encode(x, sens, mask, ndim)                                 # 12-14
-    return SbResult(x, iters, resid)
+    return SbResult(x, iters, resid, active)

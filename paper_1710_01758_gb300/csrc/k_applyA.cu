@@ -123,7 +123,9 @@ k_apply_A(const __grid_constant__ CUtensorMap smap, const float2* __restrict__ p
         mbar_init_fence();
     }
     __syncthreads();
-    if (tid == 0)
+    // kRedWithholdCoilTiles: no tile is requested, so the waits below run out (nothing in flight)
+    const bool loads = !(red.flags & kRedWithholdCoilTiles);
+    if (tid == 0 && loads)
         for (int c = 0; c < 2 && c < nc; ++c) load_coil_tile<NY>(sbuf + c * NY * TX, &smap, x0, b, nc, c, &full[c]);
     for (int i = tid; i < NY; i += NT) {
         tw[i] = tw_g[i];
@@ -140,7 +142,7 @@ k_apply_A(const __grid_constant__ CUtensorMap smap, const float2* __restrict__ p
     for (int c = 0; c < nc; ++c) {
         const int stage = c & 1;
         const uint32_t phase = (c >> 1) & 1;
-        mbar_wait(&full[stage], phase, red.err);
+        mbar_wait(&full[stage], phase, red.err, red.wait_limit);
         const float2* S = sbuf + stage * NY * TX;
         float2 u[16];
 #pragma unroll
@@ -156,8 +158,8 @@ k_apply_A(const __grid_constant__ CUtensorMap smap, const float2* __restrict__ p
         if (lane == 0) mbar_arrive(&empty[stage]);  // this warp is done with the stage
         gbar();                                     // ... and the group with ex
         if (tid == 0 && c + 2 < nc) {
-            mbar_wait(&empty[stage], phase, red.err);
-            load_coil_tile<NY>(sbuf + stage * NY * TX, &smap, x0, b, nc, c + 2, &full[stage]);
+            mbar_wait(&empty[stage], phase, red.err, red.wait_limit);
+            if (loads) load_coil_tile<NY>(sbuf + stage * NY * TX, &smap, x0, b, nc, c + 2, &full[stage]);
         }
     }
     // periodic 5-point stencil for lambda (D_x^H D_x + D_y^H D_y) p; p tile in stage 0

@@ -206,7 +206,7 @@ k_apply_A_tc(const __grid_constant__ CUtensorMap smap8, const float2* __restrict
             umma_commit(&mma_bar);
             if (prefetch >= 0) load_tile(prefetch);  // the other stage's tile is no longer read
         }
-        mbar_wait(&mma_bar, mph, red.err);
+        mbar_wait(&mma_bar, mph, red.err, red.wait_limit);
         mph ^= 1u;
         tc_fence_after();
     };
@@ -214,7 +214,7 @@ k_apply_A_tc(const __grid_constant__ CUtensorMap smap8, const float2* __restrict
     float d[16];
     for (int c = 0; c < nc; ++c) {
         const float2* S = sbuf + (c & 1) * NY * TX;
-        mbar_wait(&full[c & 1], (c >> 1) & 1, red.err);
+        mbar_wait(&full[c & 1], (c >> 1) & 1, red.err, red.wait_limit);
         float2 u[8];
         // stage 1: row (j, s) holds u[s + 16 e], e < 16 (this thread: e = 8 h + i)
 #pragma unroll
@@ -471,7 +471,7 @@ k_apply_A_tc512(const __grid_constant__ CUtensorMap smap8, const float2* __restr
             umma_commit(&mma_bar);
             if (prefetch >= 0) load_tile(prefetch);
         }
-        mbar_wait(&mma_bar, mph, red.err);
+        mbar_wait(&mma_bar, mph, red.err, red.wait_limit);
         mph ^= 1u;
         tc_fence_after();
     };
@@ -479,7 +479,7 @@ k_apply_A_tc512(const __grid_constant__ CUtensorMap smap8, const float2* __restr
     float d[32];
     for (int c = 0; c < nc; ++c) {
         const float2* S = sbuf + (c & 1) * NY * TX;
-        mbar_wait(&full[c & 1], (c >> 1) & 1, red.err);
+        mbar_wait(&full[c & 1], (c >> 1) & 1, red.err, red.wait_limit);
         float2 u[16];
         // stage 1: row (j1, s) holds u[s + 32 e], e < 16
 #pragma unroll

@@ -9,9 +9,13 @@
 // of fixed size that every GPU loading this library holds until the process exits.
 //
 // Set-up: the first call on each device resolves the array's device address with
-// cudaGetSymbolAddress (the array's name in host code is only a host-side stand-in) and writes
-// the DFT twiddle tables into it with a synchronous cudaMemcpy; so that first call must not be
-// made while a stream is being captured.  Later calls only enqueue three kernels on `stream`.
+// cudaGetSymbolAddress (the array's name in host code is only a host-side stand-in), writes
+// the DFT twiddle tables into it and waits for the device to finish that copy (a copy from
+// pageable host memory may return before the data has landed, and the caller's stream need not
+// be ordered after the copy's stream); so that first call must not be made while a stream is
+// being captured.  Later calls only enqueue three kernels on `stream`.  The set-up is kept per
+// device ordinal: the entry point serves the device's primary context (the one the CUDA
+// runtime uses) and does not survive cudaDeviceReset.
 // Every call shares the array and leaves its contents behind; nothing in it has to start at
 // zero (the intermediate is fully written before it is read).  Calls whose kernels overlap on
 // the GPU (different streams, or different threads without ordering) race on the array.
@@ -113,6 +117,9 @@ cudaError_t setup_device(int dev, float2** base) {
                     tw[twiddle_offset(n) + r * 16 + j] = make_float2((float)std::cos(a), (float)std::sin(a));
                 }
         e = cudaMemcpy(p, tw.data(), sizeof(float2) * tw.size(), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return e;
+        // the tables must be in device memory before any stream, blocking or not, reads them
+        e = cudaDeviceSynchronize();
         if (e != cudaSuccess) return e;
         d.base = p;
         d.ready = true;

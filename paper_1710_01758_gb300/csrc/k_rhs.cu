@@ -76,7 +76,9 @@ k_rhs(const __grid_constant__ CUtensorMap smap, const __grid_constant__ CUtensor
         mbar_init_fence();
     }
     __syncthreads();
-    if (tid == 0)
+    // kRedWithholdCoilTiles: no tile is requested, so the waits below run out (nothing in flight)
+    const bool loads = !(red.flags & kRedWithholdCoilTiles);
+    if (tid == 0 && loads)
         for (int c = 0; c < NST && c < nc; ++c) issue(c, c);
     for (int i = tid; i < NY; i += NT) {
         tw[i] = tw_g[i];
@@ -94,7 +96,7 @@ k_rhs(const __grid_constant__ CUtensorMap smap, const __grid_constant__ CUtensor
     const float sc = rsqrtf((float)NY);
     for (int c = 0; c < nc; ++c) {
         const int stage = c % NST;
-        mbar_wait(&bars[stage], (c / NST) & 1, red.err);
+        mbar_wait(&bars[stage], (c / NST) & 1, red.err, red.wait_limit);
         const float2* S = stages + stage * stage_elems;
         const float2* Yt = S + NY * TX;
         const float2* Y1 = Yt + ms * TX;
@@ -125,7 +127,7 @@ k_rhs(const __grid_constant__ CUtensorMap smap, const __grid_constant__ CUtensor
 #pragma unroll
         for (int e = 0; e < 16; ++e) racc[e] = cfmac(racc[e], S[idx(t + T * e)], cscale(u[e], sc));
         __syncthreads();  // this stage's tiles and xbuf are free
-        if (tid == 0 && c + NST < nc) issue(c + NST, stage);
+        if (tid == 0 && loads && c + NST < nc) issue(c + NST, stage);
     }
     // bd' = (racc + bd + bd1) / 2 after an outer update (else bd' = bd);
     // b = mu bd' + g ;  r = mu racc + g - lam D^H D x - gam x

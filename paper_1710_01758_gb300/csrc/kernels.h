@@ -47,12 +47,22 @@ struct Dims {
     int nx, ny, nc, nb;
 };
 
+// polls of a bounded mbarrier wait before it gives up (about half a second with the back-off)
+constexpr uint32_t kWaitLimit = 1u << 22;
+// Red::flags bit: the coil-tile kernels of the line path (q = A p, the right-hand side) issue
+// no TMA load, so their waits for a tile run out (a check of the bounded waits; results are
+// meaningless while it is set)
+constexpr uint32_t kRedWithholdCoilTiles = 1u;
+
 // Workspace of the cross-CTA reductions: part[nb][maxparts][K] doubles, counter[nb]; err is
-// the device error word (bit kErrTmaTimeout: a bounded TMA wait gave up).
+// the device error word (bit kErrTmaTimeout: a bounded TMA wait gave up); wait_limit: polls of
+// each bounded wait; flags: kRedWithholdCoilTiles or 0.
 struct Red {
     double* part;
     unsigned* counter;
     unsigned* err;
+    uint32_t wait_limit = kWaitLimit;
+    uint32_t flags = 0;
 };
 
 // minimum per-slice capacity of Red::part (plans raise it to their widest launch: rows / 16,

@@ -150,6 +150,8 @@ struct sb_plan_s {
     unsigned* counter = nullptr;
     unsigned* kmax = nullptr;
     unsigned* derr = nullptr;  // device error word
+    uint32_t wait_limit = kWaitLimit;  // polls of each bounded device wait (sb_set_wait_check)
+    uint32_t red_flags = 0;            // Red::flags of every launch (sb_set_wait_check)
     // k construction scratch (kept after the first sb_set_mask so later calls do not allocate)
     float2 *spec = nullptr, *gb = nullptr, *rb = nullptr;
     int *line_val = nullptr, *line_uni = nullptr;
@@ -327,7 +329,7 @@ void bind_exec(sb_plan pl, Exec& ex, int b0, int nb, cudaStream_t s) {
     ex.s = s;
     ex.st = pl->st + b0;
     ex.h_st = pl->h_st + b0;
-    ex.red = Red{pl->part + (size_t)b0 * pl->maxparts * 2, pl->counter + b0, pl->derr};
+    ex.red = Red{pl->part + (size_t)b0 * pl->maxparts * 2, pl->counter + b0, pl->derr, pl->wait_limit, pl->red_flags};
 }
 
 // pointer to slice b0 of an array whose slices hold `per` elements
@@ -497,7 +499,8 @@ sb_status pcg_run(Exec& ex, const sb_pcg_opts& o, float2* x_full, sb_pcg_result*
             ce = cudaGraphInstantiate(&exec, graph, 0);
             cudaGraphDestroy(graph);
             if (ce != cudaSuccess) return xfail(ex, SB_ERR_CUDA, cuda_msg("cudaGraphInstantiate", ce));
-            if (ex.graphs.size() >= 8) {  // a bounded cache: drop the oldest
+            if (ex.graphs.size() >= 8) {  // a bounded cache: drop the oldest, once nothing of it runs
+                cudaStreamSynchronize(s);
                 cudaGraphExecDestroy(ex.graphs.front().exec);
                 ex.graphs.erase(ex.graphs.begin());
             }
@@ -1234,6 +1237,25 @@ sb_status sb_set_graphs(sb_plan pl, int enable) {
     SB_CK(pl, pl->stream ? cudaStreamSynchronize(pl->stream) : cudaDeviceSynchronize());
     pl->graphs = enable != 0;
     drop_graphs(pl);
+    return SB_OK;
+}
+
+sb_status sb_set_wait_check(sb_plan pl, unsigned wait_polls, int withhold_coil_tiles) {
+    if (!pl) return SB_ERR_INVALID_ARG;
+    if (wait_polls > kWaitLimit) return fail(pl, SB_ERR_INVALID_ARG, "wait_polls above the default limit");
+    SB_CK(pl, pl->stream ? cudaStreamSynchronize(pl->stream) : cudaDeviceSynchronize());
+    for (Exec& ex : pl->groups) SB_CK(pl, cudaStreamSynchronize(ex.s));
+    pl->wait_limit = wait_polls ? wait_polls : kWaitLimit;
+    pl->red_flags = withhold_coil_tiles ? kRedWithholdCoilTiles : 0u;
+    auto rebind = [pl](Exec& ex) {
+        ex.red.wait_limit = pl->wait_limit;
+        ex.red.flags = pl->red_flags;
+    };
+    rebind(pl->whole);
+    for (Exec& ex : pl->groups) rebind(ex);
+    drop_graphs(pl);  // captured launches hold the old Red by value
+    SB_CK(pl, cudaMemset(pl->derr, 0, sizeof(unsigned)));
+    SB_CK(pl, cudaDeviceSynchronize());
     return SB_OK;
 }
 

@@ -2,9 +2,9 @@
 //
 // A tile is fetched by one elected thread with cp.async.bulk.tensor.2d into shared memory; the
 // mbarrier of its pipeline stage receives the byte count (expect_tx) and completes when the
-// bytes have landed.  Every wait is bounded: after kWaitLimit polls it gives up, records
-// kErrTmaTimeout in the caller's error word and returns false, so a lost transfer ends the
-// kernel with an error status instead of a hang.
+// bytes have landed.  Every wait is bounded: after the caller's poll limit (kWaitLimit by
+// default, kernels.h) it gives up, records kErrTmaTimeout in the caller's error word and
+// returns false, so a lost transfer ends the kernel with an error status instead of a hang.
 #pragma once
 
 #include <cuda.h>
@@ -14,7 +14,6 @@
 namespace sb {
 
 constexpr unsigned kErrTmaTimeout = 1u;
-constexpr uint32_t kWaitLimit = 1u << 22;
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -55,9 +54,10 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     return done != 0;
 }
 
-// Bounded wait for phase `parity` of `bar`; on timeout flags `err` and returns false.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, unsigned* err) {
-    for (uint32_t i = 0; i < kWaitLimit; ++i) {
+// Bounded wait for phase `parity` of `bar` (at most `limit` polls); on timeout flags `err`
+// and returns false.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, unsigned* err, uint32_t limit) {
+    for (uint32_t i = 0; i < limit; ++i) {
         if (mbar_try_wait(bar, parity)) return true;
         if (i >= 32) __nanosleep(128);
     }

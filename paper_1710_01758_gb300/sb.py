@@ -79,6 +79,7 @@ SIGNATURES = [
     ("sb_plan_last_error", ctypes.c_char_p, [_P]),
     ("sb_kernel_launches", ctypes.c_uint64, []),
     ("sb_apply_precond_noalloc", ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P]),
+    ("sb_set_wait_check", ctypes.c_int, [_P, ctypes.c_uint, ctypes.c_int]),
     ("sb_split_bregman_many", ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(_P),
                                              ctypes.POINTER(_P), ctypes.POINTER(sb_sb_opts),
                                              ctypes.POINTER(ctypes.POINTER(sb_pcg_result))]),
@@ -351,6 +352,11 @@ class Plan:
 
     def set_timing(self, class_mask: int):
         sb_plan_set_timing(self.handle, class_mask)
+
+    def set_wait_check(self, wait_polls: int = 0, withhold_coil_tiles: bool = False):
+        """Poll limit of the bounded device waits (0 = default) and, for checking them, whether
+        the line-path coil-tile kernels withhold their TMA requests (see include/sb.h)."""
+        _check(_lib.sb_set_wait_check(_P(self.handle), wait_polls, 1 if withhold_coil_tiles else 0), self.handle)
 
     def timing(self, kernel_class: int):
         return sb_plan_get_timing(self.handle, kernel_class)

@@ -213,10 +213,10 @@ class Volume:
     seed: int = SEED_BASE + 5
 
 
-# 256 x 256 x 128 volume, 16 coils, (k_y, k_z) lines at R = 8 with a 24 x 24 centre, TV + 4-level
-# Haar, 20 SB iterations, PCG to 1e-3.
-VOLUME_256 = Volume("256x256x128 Nc16 R8 TV+Haar4 20SB PCG-tol1e-3", 128, 256, 256, 16, 8.0, 24,
-                    1.0, 0.05, 0.05, 4, 20, 1, 1e-3, 200, 0)
+# 256 x 256 x 128 volume, 16 coils, (k_y, k_z) lines at R = 8 with a 24 x 24 centre, 3D TV +
+# 3-level 3D Haar, 15 SB iterations, PCG to 1e-3.
+VOLUME_256 = Volume("256x256x128 Nc16 R8 TV+Haar3 15SB PCG-tol1e-3", 128, 256, 256, 16, 8.0, 24,
+                    1.0, 0.05, 0.05, 3, 15, 1, 1e-3, 200, 0)
 
 
 def make_volume(v: Volume, seed: int | None = None) -> "Slice":
@@ -250,6 +250,7 @@ class Workload:
     pcg_fixed_iters: int          # > 0: run exactly this many PCG iterations per solve
     sigma: float = 1e-3
     seed: int = SEED_BASE
+    tau: float = 0.0              # shrink thresholds of steps 6-8; <= 0: 1/lambda and 1/gamma
 
 
 # 128x128, 4 coils, R=4 lines + 16 centre lines, TV only, 10 SB x 20 fixed PCG iterations.
@@ -264,6 +265,17 @@ METRIC_256 = Workload("256x256 Nc12 R4 TV+Haar4 20SB PCG-tol1e-3", 256, 256, 12,
 # Haar, 20 SB, PCG to 1e-3 (the paper's second sampling scheme).
 RANDOM_256 = Workload("256x256 Nc12 R4 random-2D TV+Haar4 20SB PCG-tol1e-3", 256, 256, 12, 4.0, 24, "random",
                       1.0, 0.05, 0.05, 4, 20, 1, 1e-3, 200, 0, seed=SEED_BASE + 6)
+# The benchmark geometry with active shrinkage: thresholds 0.02 instead of 1/lambda = 1/gamma = 20
+# (at which, for images in [0, 1], every shrink output stays zero and steps 6-11 do no work).
+SHRINK_256 = dataclasses.replace(METRIC_256, name="256x256 Nc12 R4 TV+Haar4 tau0.02 20SB PCG-tol1e-3",
+                                 tau=0.02, seed=SEED_BASE + 7)
+# The paper's parameter sets 1-3 (Methods, "Reconstruction") on the benchmark geometry, thresholds
+# 0.02 so that shrinkage is active on these synthetic images.
+PARAM_SETS = {"set1": (1e-3, 4e-3, 1e-3), "set2": (1e-2, 4e-3, 1e-3), "set3": (1e-3, 4e-3, 4e-3)}
+PARAM_256 = {k: dataclasses.replace(METRIC_256, name=f"256x256 Nc12 R4 TV+Haar4 {k} mu{mu:g} lam{lam:g} gam{gam:g} "
+                                                     "tau0.02 20SB PCG-tol1e-3",
+                                    mu=mu, lam=lam, gam=gam, tau=0.02, seed=SEED_BASE + 8 + i)
+             for i, (k, (mu, lam, gam)) in enumerate(PARAM_SETS.items())}
 # 512x512, 32 coils, R=6 variable-density lines + 32 centre lines, TV + 4-level Haar, 20 SB.
 LARGE_512 = Workload("512x512 Nc32 R6vd TV+Haar4 20SB PCG-tol1e-3", 512, 512, 32, 6.0, 32, "variable",
                      1.0, 0.05, 0.05, 4, 20, 1, 1e-3, 200, 0, seed=SEED_BASE + 3)

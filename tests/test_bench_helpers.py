@@ -39,8 +39,20 @@ def test_alu_side_of_the_roofline():
     """Two length-256 transforms at 5 log2(256) flops per point, plus 16 flops of products and
     mask: 96 per pixel and coil; the peak is 152 x 128 x 2 flops per clock."""
     wl = synth.METRIC_256
-    r = bench.alu_side(wl, 64, 12, 168.0, {"sm_mhz": 2070.0}, general=False)
+    r = bench.alu_side(wl, 64, 12, 168.0, {"sm_mhz": 2070.0}, general=False, sms=152)
     assert r["flops_per_launch"] == 64 * 256 * 256 * 12 * 96
     assert abs(r["peak_tflops"] - 152 * 128 * 2 * 2.07 / 1e3) < 1e-9
     assert abs(r["achieved_tflops"] - r["flops_per_launch"] / 168e-6 / 1e12) < 1e-9
-    assert r["floor_us"] < 168.0 and bench.alu_side(wl, 64, 12, 168.0, None, general=True) is None
+    assert r["floor_us"] < 168.0 and bench.alu_side(wl, 64, 12, 168.0, None, general=True, sms=152) is None
+
+
+def test_workload_names_resolve():
+    """Every --workload name maps to a synth workload; the active-shrink and parameter-set lines
+    keep the headline geometry and set explicit thresholds."""
+    for name in bench.WORKLOADS:
+        assert bench.workload_of(synth, name).nx > 0
+    for name in ("shrink256", "set1", "set2", "set3"):
+        wl = bench.workload_of(synth, name)
+        assert (wl.nx, wl.ny, wl.ncoils, wl.tau) == (256, 256, 12, 0.02)
+    assert (bench.workload_of(synth, "set2").mu, bench.workload_of(synth, "set2").lam) == (1e-2, 4e-3)
+    assert synth.VOLUME_256.wavelet_levels == 3 and synth.VOLUME_256.n_outer == 15

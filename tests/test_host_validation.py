@@ -74,3 +74,12 @@ def test_null_arguments_refused():
     assert sb._lib.sb_coil_compress(p, p, 64, 33, 1, 4, ctypes.c_void_p(32), ctypes.c_void_p(48), None, None,
                                     None) == sb.SB_ERR_INVALID_ARG
     assert sb._lib.sb_apply_precond_noalloc(None, None, None, 64, 64, 1, None) == sb.SB_ERR_INVALID_ARG
+    # the allocation-free preconditioner: lengths outside {32, 64, 128, 256} are unsupported,
+    # sizes beyond its fixed scratch and empty batches are invalid; all refused before device work
+    q = ctypes.c_void_p(64)
+    assert sb._lib.sb_apply_precond_noalloc(p, q, p, 48, 64, 1, None) == sb.SB_ERR_UNSUPPORTED
+    assert sb._lib.sb_apply_precond_noalloc(p, q, p, 64, 512, 1, None) == sb.SB_ERR_UNSUPPORTED
+    assert sb._lib.sb_apply_precond_noalloc(p, q, p, 256, 256, 17, None) == sb.SB_ERR_INVALID_ARG
+    assert sb._lib.sb_apply_precond_noalloc(p, q, p, 256, 256, 0, None) == sb.SB_ERR_INVALID_ARG
+    # the wait check needs a plan
+    assert sb._lib.sb_set_wait_check(None, 1024, 1) == sb.SB_ERR_INVALID_ARG

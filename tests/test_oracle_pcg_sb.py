@@ -122,6 +122,28 @@ def test_rss_single_unit_coil():
     np.testing.assert_allclose(sb.rss(y, 2).real, np.abs(x), atol=1e-12)
 
 
+def test_rss_several_coils_hand_values():
+    """Step 1's root-sum-of-squares over several coils against values worked out by hand: coil
+    images 3 and 4i give 5 (not 7 = |3| + |4i|, nor 25); images that differ per pixel combine per
+    pixel; three constant coils 1, 2, -2 give 3."""
+    shape = (4, 4)
+    u = np.zeros((2,) + shape, complex)
+    u[0] = 3.0
+    u[1] = 4.0j
+    np.testing.assert_allclose(sb.rss(fourier.fft(u, 2), 2).real, np.full(shape, 5.0), atol=1e-12)
+    u = np.zeros((2,) + shape, complex)
+    u[0, 0, 0], u[1, 0, 0] = 3.0, -4.0      # pixel (0, 0): sqrt(9 + 16) = 5
+    u[1, 2, 1] = 1.0 - 1.0j                 # pixel (2, 1): sqrt(2), only coil 1
+    u[0, 3, 3], u[1, 3, 3] = 0.6j, 0.8      # pixel (3, 3): sqrt(0.36 + 0.64) = 1
+    want = np.zeros(shape)
+    want[0, 0], want[2, 1], want[3, 3] = 5.0, np.sqrt(2.0), 1.0
+    got = sb.rss(fourier.fft(u, 2), 2)
+    np.testing.assert_allclose(got.real, want, atol=1e-12)
+    np.testing.assert_allclose(got.imag, 0.0, atol=0)
+    u = np.stack([np.full(shape, 1.0 + 0j), np.full(shape, 2.0 + 0j), np.full(shape, -2.0 + 0j)])
+    np.testing.assert_allclose(sb.rss(fourier.fft(u, 2), 2).real, np.full(shape, 3.0), atol=1e-12)
+
+
 def _denoise_setup(rng, shape=(16, 16)):
     x_true = synth.random_complex(shape, rng)
     sens = np.ones((1,) + shape, complex)
