@@ -9,8 +9,22 @@
 namespace sb {
 
 // ------------------------------------------------------------------ complex helpers
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// Complex addition and subtraction as packed FP32 pair instructions (add / sub .f32x2, sm_100+):
+// one instruction for both components, each rounded exactly like the scalar operation, so the
+// results are bitwise those of two scalar adds; the transforms are bound by instruction issue,
+// and most of their arithmetic is these adds.
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) {
+    unsigned long long ra, rb, rd;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(ra) : "f"(a.x), "f"(a.y));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(rb) : "f"(b.x), "f"(b.y));
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(rd) : "l"(ra), "l"(rb));
+    float2 d;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(d.x), "=f"(d.y) : "l"(rd));
+    return d;
+}
+// a * (s, s) for a pair (s, s) held as one float2 (packed multiply)
+__device__ __forceinline__ float2 cscale2(float2 a, float2 ss) { return __fmul2_rn(a, ss); }
 __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
@@ -27,6 +41,14 @@ __device__ __forceinline__ float cabs2(float2 a) { return fmaf(a.x, a.x, a.y * a
 // multiply by W4 = -i (forward) or +i (inverse)
 template <bool INV> __device__ __forceinline__ float2 mul_w4(float2 a) {
     return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+}
+// a + W4 x and a - W4 x without forming W4 x: the product swaps x's components, which a packed
+// add could only take after two moves; two scalar adds each are as cheap and give the same bits.
+template <bool INV> __device__ __forceinline__ float2 add_w4(float2 a, float2 x) {
+    return INV ? make_float2(a.x - x.y, a.y + x.x) : make_float2(a.x + x.y, a.y - x.x);
+}
+template <bool INV> __device__ __forceinline__ float2 sub_w4(float2 a, float2 x) {
+    return INV ? make_float2(a.x + x.y, a.y - x.x) : make_float2(a.x - x.y, a.y + x.x);
 }
 // cos(2 pi m / 16) and sin(2 pi m / 16): cos(pi/8), sin(pi/8) and sqrt(1/2) are the only
 // irrational values needed.
@@ -65,11 +87,21 @@ template <bool INV> __device__ __forceinline__ void dft2(float2& a0, float2& a1)
 
 template <bool INV> __device__ __forceinline__ void dft4(float2& a0, float2& a1, float2& a2, float2& a3) {
     const float2 t0 = cadd(a0, a2), t1 = csub(a0, a2);
-    const float2 t2 = cadd(a1, a3), t3 = mul_w4<INV>(csub(a1, a3));
+    const float2 t2 = cadd(a1, a3), d = csub(a1, a3);
     a0 = cadd(t0, t2);
     a2 = csub(t0, t2);
-    a1 = cadd(t1, t3);
-    a3 = csub(t1, t3);
+    a1 = add_w4<INV>(t1, d);
+    a3 = sub_w4<INV>(t1, d);
+}
+
+// dft4 of (a0, a1, W4 r2, a3): the third input arrives before its multiplication by W4
+template <bool INV> __device__ __forceinline__ void dft4_w4in2(float2& a0, float2& a1, float2& r2, float2& a3) {
+    const float2 t0 = add_w4<INV>(a0, r2), t1 = sub_w4<INV>(a0, r2);
+    const float2 t2 = cadd(a1, a3), d = csub(a1, a3);
+    a0 = cadd(t0, t2);
+    r2 = csub(t0, t2);
+    a1 = add_w4<INV>(t1, d);
+    a3 = sub_w4<INV>(t1, d);
 }
 
 template <bool INV> __device__ __forceinline__ void dft8(float2 (&a)[8]) {
@@ -78,11 +110,10 @@ template <bool INV> __device__ __forceinline__ void dft8(float2 (&a)[8]) {
     dft4<INV>(e0, e1, e2, e3);
     dft4<INV>(o0, o1, o2, o3);
     o1 = mul_w16<INV, 2>(o1);
-    o2 = mul_w16<INV, 4>(o2);
     o3 = mul_w16<INV, 6>(o3);
     a[0] = cadd(e0, o0); a[4] = csub(e0, o0);
     a[1] = cadd(e1, o1); a[5] = csub(e1, o1);
-    a[2] = cadd(e2, o2); a[6] = csub(e2, o2);
+    a[2] = add_w4<INV>(e2, o2); a[6] = sub_w4<INV>(e2, o2);  // o2 times W16^4 = W4
     a[3] = cadd(e3, o3); a[7] = csub(e3, o3);
 }
 
@@ -91,9 +122,9 @@ template <bool INV> __device__ __forceinline__ void dft16(float2 (&a)[16]) {
     // length-4 DFTs over n1 for each n2 (in place: a[n2 + 4 k1] holds Y[n2][k1])
 #pragma unroll
     for (int n2 = 0; n2 < 4; ++n2) dft4<INV>(a[n2], a[n2 + 4], a[n2 + 8], a[n2 + 12]);
-    // twiddles W16^(n2 k1)
+    // twiddles W16^(n2 k1) (a[10]'s, W16^4 = W4, is folded into its length-4 DFT below)
     a[5] = mul_w16<INV, 1>(a[5]);  a[9] = mul_w16<INV, 2>(a[9]);   a[13] = mul_w16<INV, 3>(a[13]);
-    a[6] = mul_w16<INV, 2>(a[6]);  a[10] = mul_w16<INV, 4>(a[10]); a[14] = mul_w16<INV, 6>(a[14]);
+    a[6] = mul_w16<INV, 2>(a[6]);                                  a[14] = mul_w16<INV, 6>(a[14]);
     a[7] = mul_w16<INV, 3>(a[7]);  a[11] = mul_w16<INV, 6>(a[11]); a[15] = mul_w16<INV, 9>(a[15]);
     // length-4 DFTs over n2 for each k1: inputs a[4 k1 + n2], outputs X[k1 + 4 k2]
     float2 y[16];
@@ -101,7 +132,8 @@ template <bool INV> __device__ __forceinline__ void dft16(float2 (&a)[16]) {
     for (int k1 = 0; k1 < 4; ++k1) {
         // element (n2, k1) sits at a[n2 + 4 k1]
         float2 b0 = a[4 * k1], b1 = a[1 + 4 * k1], b2 = a[2 + 4 * k1], b3 = a[3 + 4 * k1];
-        dft4<INV>(b0, b1, b2, b3);
+        if (k1 == 2) dft4_w4in2<INV>(b0, b1, b2, b3);
+        else dft4<INV>(b0, b1, b2, b3);
         y[k1] = b0; y[k1 + 4] = b1; y[k1 + 8] = b2; y[k1 + 12] = b3;
     }
 #pragma unroll

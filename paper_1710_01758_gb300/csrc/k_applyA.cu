@@ -26,6 +26,7 @@
 #include "kernels.h"
 #include "tiles.cuh"
 #include "tma.cuh"
+#include "umma.cuh"
 
 namespace sb {
 namespace {
@@ -80,7 +81,7 @@ k_apply_A(const __grid_constant__ CUtensorMap smap, const float2* __restrict__ p
     float2* xbuf2 = xbuf + ExIdx<NY>::kStride * TX;
     float2* tw = xbuf2 + kEx2;
     float2* halo = tw + NY;                           // [2][NY]: columns x0-1 and x0+TX
-    float* mk = reinterpret_cast<float*>(halo + 2 * NY);
+    float2* mk = halo + 2 * NY;                       // [NY] mask weight w of each row as (w, w)
     double* red_s = reinterpret_cast<double*>(mk + NY);
     __shared__ __align__(8) uint64_t full[2], empty[2];
     __shared__ int flag;
@@ -129,7 +130,8 @@ k_apply_A(const __grid_constant__ CUtensorMap smap, const float2* __restrict__ p
         for (int c = 0; c < 2 && c < nc; ++c) load_coil_tile<NY>(sbuf + c * NY * TX, &smap, x0, b, nc, c, &full[c]);
     for (int i = tid; i < NY; i += NT) {
         tw[i] = tw_g[i];
-        mk[i] = maskw[(size_t)b * NY + i];
+        const float w = maskw[(size_t)b * NY + i];
+        mk[i] = make_float2(w, w);
     }
     const size_t img = (size_t)b * NY * nx;
     float2 pv[16], acc[16];
@@ -149,7 +151,7 @@ k_apply_A(const __grid_constant__ CUtensorMap smap, const float2* __restrict__ p
         for (int e = 0; e < 16; ++e) u[e] = cmul(S[rows(e)], pv[e]);
         fft_bar2<NY, false>(u, t, ex, xbuf2, idx, tw, gbar);
 #pragma unroll
-        for (int e = 0; e < 16; ++e) u[e] = cscale(u[e], mk[t + T * e]);
+        for (int e = 0; e < 16; ++e) u[e] = cscale2(u[e], mk[t + T * e]);
         gbar();  // the group's forward reads of ex are done
         fft_bar2<NY, true>(u, t, ex, xbuf2, idx, tw, gbar);
 #pragma unroll
@@ -208,11 +210,230 @@ k_apply_A(const __grid_constant__ CUtensorMap smap, const float2* __restrict__ p
     }
 }
 
+// ---------------------------------------------------------------- 256 rows: k_apply_A8
+// The same operator for ny = 256 with the per-thread state moved out of the register file, so
+// that more warps fit on an SM (the kernel above holds p, the coil accumulator and the transform
+// in 128 registers and two 110 KB CTAs fill an SM: 16 warps, and it is bound by issue latency):
+//  * a CTA owns 8 columns (128 threads, one per tensor-memory lane; a warp holds two whole
+//    columns, 16 rows x 2 columns, so the transforms' exchanges are warp-local as above);
+//  * its p values and the coil accumulator live in tensor memory (TMEM, 64 columns of 32 bits
+//    per CTA), read and written with one tcgen05.ld / tcgen05.st per 16 values;
+//  * the coil tile (256 rows x 8 columns, 64-byte TMA swizzle) has ONE stage: every thread copies
+//    its 16 sensitivities to registers as soon as the tile lands and the stage is refilled with
+//    the next coil at once (the last warp to release it issues the TMA), so the load of coil
+//    c + 1 overlaps the transforms of coil c.
+// Shared memory is ~39 KB and registers <= 96 per thread: five CTAs (20 warps) per SM.
+constexpr int TX8 = 8;
+
+// float2 index of (row, col) in an 8-column tile written by TMA with the 64-byte swizzle
+// (16-byte chunk index XOR (row >> 1) & 3)
+__device__ __forceinline__ int swz64(int row, int col) {
+    return row * TX8 + ((((col >> 1) ^ ((row >> 1) & 3)) << 1) | (col & 1));
+}
+
+// bytes from `p` to the next 512-byte boundary of the shared window (the 64-byte swizzle repeats
+// every 512 bytes)
+__device__ __forceinline__ uint32_t pad_to_512(const void* p) { return (512u - (smem_addr(p) & 511u)) & 511u; }
+
+template <bool PCG>
+__global__ void __launch_bounds__(128, 5)
+k_apply_A8(const __grid_constant__ CUtensorMap smap8, const float2* __restrict__ p, float2* __restrict__ q,
+           const float* __restrict__ maskw, const float2* __restrict__ tw_g, int nx, int nc, float mu, float lam,
+           float gam, SliceState* st, Red red) {
+    constexpr int NY = 256, T = 16, NT = 128, NW = 4;
+    const int b = blockIdx.y;
+    if (PCG && st[b].state != ST_ACTIVE) return;
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* smem = smem_raw + pad_to_512(smem_raw);
+    float2* sbuf = reinterpret_cast<float2*>(smem);  // [NY][8] coil tile; the p tile in the epilogue
+    float2* xbuf = sbuf + NY * TX8;                  // [8][ExIdx::kStride] exchanges; halo in the epilogue
+    float2* tw = xbuf + ExIdx<NY>::kStride * TX8;
+    float2* mk = tw + NY;                            // mask weight w of each row as (w, w)
+    double* red_s = reinterpret_cast<double*>(mk + NY);
+    __shared__ __align__(8) uint64_t full, empty;
+    __shared__ uint32_t tmem_s;
+    __shared__ unsigned ticket;
+    __shared__ int flag;
+
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int t = (lane & 7) + 8 * (lane >> 4), col = 2 * w + ((lane >> 3) & 1);
+    const int x0 = blockIdx.x * TX8, x = x0 + col;
+    const ExIdx<NY> idx{col * ExIdx<NY>::kStride};
+    const int sb0 = swz64(t, col);  // rows t + 16 e share the swizzle term of t
+    auto gbar = []() { __syncwarp(); };
+    const bool loads = !(red.flags & kRedWithholdCoilTiles);
+    auto load_tile = [&](int c) {
+        mbar_arrive_expect_tx(&full, NY * TX8 * sizeof(float2));
+        tma_load_2d(sbuf, &smap8, 2 * x0, (b * nc + c) * NY, &full);
+    };
+
+    if (w == 0) tmem_alloc(&tmem_s, 64);
+    if (tid == 0) {
+        mbar_init(&full, 1);
+        mbar_init(&empty, NW);
+        ticket = 0;
+        mbar_init_fence();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (tid == 0 && loads) load_tile(0);
+    // this warp's TMEM lanes 32 w .. 32 w + 31: columns 0-31 hold p, 32-63 the accumulator
+    const uint32_t t_pv = tmem_s + ((uint32_t)(32 * w) << 16), t_acc = t_pv + 32;
+    for (int i = tid; i < NY; i += NT) {
+        tw[i] = tw_g[i];
+        const float wt = maskw[(size_t)b * NY + i];
+        mk[i] = make_float2(wt, wt);
+    }
+    const size_t img = (size_t)b * NY * nx;
+    {
+        float v[32];
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+            const float2 pv = p[img + (size_t)(t + T * e) * nx + x];
+            v[2 * e] = pv.x;
+            v[2 * e + 1] = pv.y;
+        }
+        tmem_st32(t_pv, v);
+    }
+    __syncthreads();
+    for (int c = 0; c < nc; ++c) {
+        const uint32_t ph = c & 1;
+        mbar_wait(&full, ph, red.err, red.wait_limit);
+        float2 sv[16];
+#pragma unroll
+        for (int e = 0; e < 16; ++e) sv[e] = sbuf[sb0 + e * T * TX8];
+        __syncwarp();
+        if (lane == 0) {  // this warp is done with the tile; the last warp refills it
+            mbar_arrive(&empty);
+            if (atomicAdd(&ticket, 1u) % NW == NW - 1 && c + 1 < nc) {
+                mbar_wait(&empty, ph, red.err, red.wait_limit);  // every warp arrived before its ticket
+                if (loads) load_tile(c + 1);
+            }
+        }
+        __syncwarp();  // the tcgen05 loads and stores below are warp-wide
+        float2 u[16];
+        {
+            float v[32];
+            if (c == 0) tmem_wait_st();
+            tmem_ld32(t_pv, v);
+#pragma unroll
+            for (int e = 0; e < 16; ++e) u[e] = cmul(sv[e], make_float2(v[2 * e], v[2 * e + 1]));
+        }
+        fft_bar2<NY, false>(u, t, xbuf, xbuf, idx, tw, gbar);
+#pragma unroll
+        for (int e = 0; e < 16; ++e) u[e] = cscale2(u[e], mk[t + T * e]);
+        gbar();  // the warp's forward reads of its exchange region are done
+        fft_bar2<NY, true>(u, t, xbuf, xbuf, idx, tw, gbar);
+        // acc += conj(S) u, in two halves of 8 values (16 TMEM columns each)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            float a[16];
+            if (c > 0) {
+                tmem_wait_st();
+                tmem_ld16(t_acc + 16 * h, a);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) a[i] = 0.f;
+            }
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const float2 r = cfmac(make_float2(a[2 * i], a[2 * i + 1]), sv[8 * h + i], u[8 * h + i]);
+                a[2 * i] = r.x;
+                a[2 * i + 1] = r.y;
+            }
+            tmem_st16(t_acc + 16 * h, a);
+        }
+        gbar();  // ... and its inverse reads
+    }
+    // periodic 5-point stencil for lambda (D_x^H D_x + D_y^H D_y) p; p tile in the stage buffer
+    __syncthreads();  // every warp left the coil loop: the stage and the exchange regions are free
+    float2 pv[16], acc[16];
+    {
+        float v[32];
+        tmem_wait_st();
+        tmem_ld32(t_pv, v);
+#pragma unroll
+        for (int e = 0; e < 16; ++e) pv[e] = make_float2(v[2 * e], v[2 * e + 1]);
+        tmem_ld32(t_acc, v);
+#pragma unroll
+        for (int e = 0; e < 16; ++e) acc[e] = make_float2(v[2 * e], v[2 * e + 1]);
+    }
+    float2* pt = sbuf;
+    float2* halo = xbuf;  // [2][NY]: columns x0-1 and x0+8
+#pragma unroll
+    for (int e = 0; e < 16; ++e) pt[sb0 + e * T * TX8] = pv[e];
+    for (int i = tid; i < NY; i += NT) {
+        halo[i] = p[img + (size_t)i * nx + (x0 == 0 ? nx - 1 : x0 - 1)];
+        halo[NY + i] = p[img + (size_t)i * nx + (x0 + TX8 == nx ? 0 : x0 + TX8)];
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (w == 0) tmem_dealloc(tmem_s, 64);  // every warp's TMEM reads are complete
+    float dot = 0.f;
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+        const int y = t + T * e;
+        const float2 up = pt[swz64(y == 0 ? NY - 1 : y - 1, col)];
+        const float2 dn = pt[swz64(y == NY - 1 ? 0 : y + 1, col)];
+        const float2 lf = col > 0 ? pt[swz64(y, col - 1)] : halo[y];
+        const float2 rt = col < TX8 - 1 ? pt[swz64(y, col + 1)] : halo[NY + y];
+        const float tvx = 4.f * pv[e].x - up.x - dn.x - lf.x - rt.x;
+        const float tvy = 4.f * pv[e].y - up.y - dn.y - lf.y - rt.y;
+        float2 o;
+        o.x = fmaf(mu, acc[e].x, fmaf(lam, tvx, gam * pv[e].x));
+        o.y = fmaf(mu, acc[e].y, fmaf(lam, tvy, gam * pv[e].y));
+        q[img + (size_t)y * nx + x] = o;
+        dot = fmaf(pv[e].x, o.x, fmaf(pv[e].y, o.y, dot));
+    }
+    if constexpr (PCG) {
+        double v[1] = {(double)dot}, tot[1];
+        const int np = gridDim.x;
+        if (last_block_total<1>(v, red.part, np, b * np + blockIdx.x, red.counter + b, tot, red_s, &flag) &&
+            threadIdx.x == 0) {
+            SliceState& S = st[b];
+            const double pq = tot[0];
+            S.pq = pq;
+            if (!isfinite(pq) || !isfinite(S.rho)) {
+                S.state = ST_NONFINITE;
+            } else if (!(pq > 0.0)) {
+                S.state = ST_BREAKDOWN;
+            } else {
+                S.alpha = S.rho / pq;
+                S.iters += 1;
+            }
+        }
+    }
+}
+
+constexpr size_t smem_apply_A8() {
+    return 512 + ((size_t)256 * TX8 + (size_t)ExIdx<256>::kStride * TX8 + 2 * 256) * sizeof(float2) +
+           32 * sizeof(double);
+}
+
+cudaError_t apply_A8(const Dims& d, const CUtensorMap& smap8, const float2* p, float2* q, const float* maskw,
+                     const float2* tw, float mu, float lam, float gam, SliceState* st, Red red, cudaStream_t s) {
+    const dim3 grid(d.nx / TX8, d.nb), block(128);
+    constexpr size_t sm = smem_apply_A8();
+    static_assert(2 * 256 * sizeof(float2) <= (size_t)ExIdx<256>::kStride * TX8 * sizeof(float2),
+                  "the halo fits in the exchange regions");
+    cudaError_t e;
+    if (st) {
+        if ((e = set_smem_limit(k_apply_A8<true>, (int)sm)) != cudaSuccess) return e;
+        k_apply_A8<true><<<grid, block, sm, s>>>(smap8, p, q, maskw, tw, d.nx, d.nc, mu, lam, gam, st, red);
+    } else {
+        if ((e = set_smem_limit(k_apply_A8<false>, (int)sm)) != cudaSuccess) return e;
+        k_apply_A8<false><<<grid, block, sm, s>>>(smap8, p, q, maskw, tw, d.nx, d.nc, mu, lam, gam, st, red);
+    }
+    return cudaGetLastError();
+}
+
 template <int NY>
 size_t smem_apply_A() {
-    return 1024 + (2 * (size_t)NY * TX + (is_pow2(NY) ? 1 : 2) * (size_t)ExIdx<NY>::kStride * TX + 3 * NY) *
+    return 1024 + (2 * (size_t)NY * TX + (is_pow2(NY) ? 1 : 2) * (size_t)ExIdx<NY>::kStride * TX + 4 * NY) *
                       sizeof(float2) +
-           NY * sizeof(float) + 64 * sizeof(double);
+           64 * sizeof(double);
 }
 
 template <int NY>
@@ -237,14 +458,14 @@ cudaError_t apply_A_n(const Dims& d, const CUtensorMap& smap, const float2* p, f
 
 }  // namespace
 
-cudaError_t launch_apply_A(const Dims& d, const CUtensorMap& smap, const float2* p, float2* q, const float* maskw,
-                           const float2* tw_y, float mu, float lam, float gam, SliceState* st, Red red,
-                           cudaStream_t s) {
+cudaError_t launch_apply_A(const Dims& d, const CUtensorMap& smap, const CUtensorMap& smap8, const float2* p,
+                           float2* q, const float* maskw, const float2* tw_y, float mu, float lam, float gam,
+                           SliceState* st, Red red, cudaStream_t s) {
     switch (d.ny) {
         case 32: return apply_A_n<32>(d, smap, p, q, maskw, tw_y, mu, lam, gam, st, red, s);
         case 64: return apply_A_n<64>(d, smap, p, q, maskw, tw_y, mu, lam, gam, st, red, s);
         case 128: return apply_A_n<128>(d, smap, p, q, maskw, tw_y, mu, lam, gam, st, red, s);
-        case 256: return apply_A_n<256>(d, smap, p, q, maskw, tw_y, mu, lam, gam, st, red, s);
+        case 256: return apply_A8(d, smap8, p, q, maskw, tw_y, mu, lam, gam, st, red, s);
         case 512: return apply_A_n<512>(d, smap, p, q, maskw, tw_y, mu, lam, gam, st, red, s);
         case 192: return apply_A_n<192>(d, smap, p, q, maskw, tw_y, mu, lam, gam, st, red, s);
         case 224: return apply_A_n<224>(d, smap, p, q, maskw, tw_y, mu, lam, gam, st, red, s);

@@ -74,9 +74,11 @@ constexpr int kVecPerThread = 8;
 // ------------------------------------------------------------------ PCG kernels (k_pcg.cu)
 // q = A p (readout-axis shortcut of the data term); st == nullptr: plain application;
 // otherwise PCG mode: skips inactive slices, accumulates Re(p^H q) and sets alpha = rho/pq.
-// smap: TMA map of the sensitivities viewed as float32 [nb*nc*ny][2*nx], box [ny][2*kColTile].
-cudaError_t launch_apply_A(const Dims& d, const CUtensorMap& smap, const float2* p, float2* q,
-                           const float* maskw, const float2* tw_y, float mu, float lam, float gam,
+// smap: TMA map of the sensitivities viewed as float32 [nb*nc*ny][2*nx], box [ny][2*kColTile]
+// with the 128-byte swizzle; smap8: the same rows as 8-column boxes of 256 rows with the 64-byte
+// swizzle (read at ny = 256).
+cudaError_t launch_apply_A(const Dims& d, const CUtensorMap& smap, const CUtensorMap& smap8, const float2* p,
+                           float2* q, const float* maskw, const float2* tw_y, float mu, float lam, float gam,
                            SliceState* st, Red red, cudaStream_t s);
 
 // q = A p with the radix-16 DFT stages on the tensor cores, operands split in two bf16 or fp16

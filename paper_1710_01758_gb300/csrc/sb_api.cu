@@ -347,7 +347,7 @@ cudaError_t apply_A_2d(const sb_plan_s* pl, const Exec& ex, const Dims& d, const
         const TcOperands tc{&ex.smap_sw64, pl->tw_full, pl->bmat, pl->d.prec == SB_PREC_SPLIT_BF16};
         return launch_apply_A_tc(d, tc, p, q, maskw, mu, lam, gam, st, red, s);
     }
-    return launch_apply_A(d, ex.smap_sw, p, q, maskw, pl->tw_y, mu, lam, gam, st, red, s);
+    return launch_apply_A(d, ex.smap_sw, ex.smap_sw64, p, q, maskw, pl->tw_y, mu, lam, gam, st, red, s);
 }
 
 // ---- volumes (nz > 1) and 2D arbitrary masks: the data term as three passes through the coil
@@ -924,7 +924,7 @@ sb_status sb_set_coils(sb_plan pl, const void* d_sens) {
         const size_t rows = (size_t)ex.d.nb * d.nc * d.ny;
         const int box = coil_box_rows(d.ny);  // a TMA box spans at most 256 rows
         return encode_rows(&ex.smap, base, d.nx, rows, box) && encode_rows(&ex.smap_sw, base, d.nx, rows, box, true) &&
-               (pl->d.prec == SB_PREC_FP32 ||
+               ((pl->d.prec == SB_PREC_FP32 && d.ny != 256) ||
                 encode_rows(&ex.smap_sw64, base, d.nx, rows, 256, true, 8, CU_TENSOR_MAP_SWIZZLE_64B));
     };
     bool ok = true;

@@ -47,11 +47,12 @@ def _rel(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
-def test_withheld_tiles_give_timeout_and_context_survives(torch):
+@pytest.mark.parametrize("nx,ny", [(128, 128), (64, 256)])
+def test_withheld_tiles_give_timeout_and_context_survives(torch, nx, ny):
     from paper_1710_01758_gb300 import sb
 
     mu, lam, gam = 1.0, 0.05, 0.05
-    sens, mask, rng = _problem()
+    sens, mask, rng = _problem(nx=nx, ny=ny)
     nb, nc, ny, nx = sens.shape
     b = synth.random_complex((nb, ny, nx), rng)
     d_b = torch.from_numpy(b).to(torch.complex64).cuda()
