@@ -70,7 +70,14 @@ template <bool INV, int M> __device__ __forceinline__ float2 mul_w16(float2 a) {
     else if constexpr (m == 4) return mul_w4<INV>(a);
     else if constexpr (m == 8) return make_float2(-a.x, -a.y);
     else if constexpr (m == 12) return mul_w4<!INV>(a);
-    else {
+    else if constexpr ((m & 3) == 2) {
+        // W16^m = r (c' + i s') with r = sqrt(1/2) and c', s' = +-1: two adds and one packed
+        // multiply by (r, r) instead of two multiplies and two fused multiply-adds
+        constexpr float cs = w16_cos(m) > 0.f ? 1.f : -1.f;
+        constexpr float sn = (INV ? w16_sin(m) : -w16_sin(m)) > 0.f ? 1.f : -1.f;
+        const float2 t = make_float2(cs * a.x - sn * a.y, sn * a.x + cs * a.y);
+        return __fmul2_rn(t, make_float2(0.70710678118654752f, 0.70710678118654752f));
+    } else {
         constexpr float c = w16_cos(m);
         constexpr float s = INV ? w16_sin(m) : -w16_sin(m);
         return make_float2(fmaf(a.x, c, -a.y * s), fmaf(a.x, s, a.y * c));

@@ -300,6 +300,10 @@ k_apply_A8(const __grid_constant__ CUtensorMap smap8, const float2* __restrict__
     for (int c = 0; c < nc; ++c) {
         const uint32_t ph = c & 1;
         mbar_wait(&full, ph, red.err, red.wait_limit);
+        __syncwarp();  // the tcgen05 load below is warp-wide
+        uint32_t pr[32];  // p, loaded from TMEM while the sensitivities come from shared memory
+        if (c == 0) tmem_wait_st();
+        tmem_ld32_issue(t_pv, pr);
         float2 sv[16];
 #pragma unroll
         for (int e = 0; e < 16; ++e) sv[e] = sbuf[sb0 + e * T * TX8];
@@ -311,15 +315,11 @@ k_apply_A8(const __grid_constant__ CUtensorMap smap8, const float2* __restrict__
                 if (loads) load_tile(c + 1);
             }
         }
-        __syncwarp();  // the tcgen05 loads and stores below are warp-wide
+        __syncwarp();  // the tcgen05 wait below is warp-wide
+        tmem_ld_wait(pr);
         float2 u[16];
-        {
-            float v[32];
-            if (c == 0) tmem_wait_st();
-            tmem_ld32(t_pv, v);
 #pragma unroll
-            for (int e = 0; e < 16; ++e) u[e] = cmul(sv[e], make_float2(v[2 * e], v[2 * e + 1]));
-        }
+        for (int e = 0; e < 16; ++e) u[e] = cmul(sv[e], make_float2(__uint_as_float(pr[2 * e]), __uint_as_float(pr[2 * e + 1])));
         fft_bar2<NY, false>(u, t, xbuf, xbuf, idx, tw, gbar);
 #pragma unroll
         for (int e = 0; e < 16; ++e) u[e] = cscale2(u[e], mk[t + T * e]);
