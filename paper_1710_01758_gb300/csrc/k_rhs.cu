@@ -15,7 +15,9 @@
 // the SM computes meanwhile).
 #include "common.cuh"
 #include "kernels.h"
+#include "tiles.cuh"
 #include "tma.cuh"
+#include "umma.cuh"
 
 namespace sb {
 namespace {
@@ -180,6 +182,271 @@ k_rhs(const __grid_constant__ CUtensorMap smap, const __grid_constant__ CUtensor
     }
 }
 
+// ---------------------------------------------------------------- 256 rows: k_rhs8
+// The same pass for ny = 256 in the layout of k_apply_A8 (k_applyA.cu): 8 columns per CTA, 128
+// threads, a warp holds two whole columns (16 rows x 2 columns) so the transforms' exchanges are
+// warp-local; x and the data-term accumulator live in tensor memory (64 columns per CTA); the
+// coil tile and the compact k-space rows (yt, yt1) arrive by TMA with the 64-byte swizzle into
+// one stage each, released as soon as every warp has read them (the sensitivities into
+// registers at the start of the coil, the k-space rows after the forward transform) and refilled
+// at once by the last warp to release them.  The epilogue's rows of g, bd and bd1 are prefetched
+// into L2 during the last coil.
+constexpr int TX8 = 8;
+using tiles::ExIdx;
+
+__device__ __forceinline__ int swz64(int row, int col) {
+    return row * TX8 + ((((col >> 1) ^ ((row >> 1) & 3)) << 1) | (col & 1));
+}
+__device__ __forceinline__ uint32_t pad_to_512(const void* p) { return (512u - (smem_addr(p) & 511u)) & 511u; }
+__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
+// rows of the k-space stage reserved for yt (rounded up to 8 rows so that yt1 starts on a
+// 512-byte boundary, as the 64-byte swizzle requires)
+__host__ __device__ constexpr int ms_rows8(int ms) { return (ms + 7) & ~7; }
+
+size_t rhs8_smem_bytes(int ms) {
+    return 512 + ((size_t)256 * TX8 + 2 * (size_t)ms_rows8(ms) * TX8 + (size_t)ExIdx<256>::kStride * TX8 + 256) *
+                     sizeof(float2) +
+           256 * sizeof(int) + 32 * sizeof(double);
+}
+
+template <bool ADDBACK>
+__global__ void __launch_bounds__(128, 4)
+k_rhs8(const __grid_constant__ CUtensorMap smap8, const __grid_constant__ CUtensorMap ymap8,
+       const __grid_constant__ CUtensorMap y1map8, SbFields f, int nx, int nc, const float2* __restrict__ xin,
+       float2* __restrict__ r, const float2* __restrict__ tw_g, float mu, float lam, float gam, SliceState* st,
+       double tol2, Red red) {
+    constexpr int NY = 256, T = 16, NT = 128, NW = 4;
+    const int b = blockIdx.y;
+    const int ms = f.ms;
+    const int msr = ms_rows8(ms);
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* smem = smem_raw + pad_to_512(smem_raw);
+    float2* sA = reinterpret_cast<float2*>(smem);  // [NY][8] coil tile; the x tile in the epilogue
+    float2* sB = sA + NY * TX8;                      // [msr][8] yt rows, then [msr][8] yt1 rows
+    float2* xbuf = sB + 2 * msr * TX8;               // [8][ExIdx::kStride] exchanges; halo in the epilogue
+    float2* tw = xbuf + ExIdx<NY>::kStride * TX8;
+    int* sl = reinterpret_cast<int*>(tw + NY);
+    double* red_s = reinterpret_cast<double*>(sl + NY);
+    __shared__ __align__(8) uint64_t fullA, emptyA, fullB, emptyB;
+    __shared__ uint32_t tmem_s;
+    __shared__ unsigned ticketA, ticketB;
+    __shared__ int flag;
+
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int t = (lane & 7) + 8 * (lane >> 4), col = 2 * w + ((lane >> 3) & 1);
+    const int x0 = blockIdx.x * TX8, xg = x0 + col;
+    const ExIdx<NY> idx{col * ExIdx<NY>::kStride};
+    const int sb0 = swz64(t, col);
+    auto gbar = []() { __syncwarp(); };
+    const bool loads = !(red.flags & kRedWithholdCoilTiles);
+    auto load_S = [&](int c) {
+        mbar_arrive_expect_tx(&fullA, NY * TX8 * sizeof(float2));
+        tma_load_2d(sA, &smap8, 2 * x0, (b * nc + c) * NY, &fullA);
+    };
+    auto load_Y = [&](int c) {
+        mbar_arrive_expect_tx(&fullB, (ADDBACK ? 2u : 1u) * (uint32_t)ms * TX8 * sizeof(float2));
+        tma_load_2d(sB, &ymap8, 2 * x0, (b * nc + c) * ms, &fullB);
+        if (ADDBACK) tma_load_2d(sB + msr * TX8, &y1map8, 2 * x0, (b * nc + c) * ms, &fullB);
+    };
+
+    if (w == 0) tmem_alloc(&tmem_s, 64);
+    if (tid == 0) {
+        mbar_init(&fullA, 1);
+        mbar_init(&emptyA, NW);
+        mbar_init(&fullB, 1);
+        mbar_init(&emptyB, NW);
+        ticketA = ticketB = 0;
+        mbar_init_fence();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (tid == 0 && loads) {
+        load_S(0);
+        load_Y(0);
+    }
+    // this warp's TMEM lanes: columns 0-31 hold x, 32-63 the data-term accumulator
+    const uint32_t t_x = tmem_s + ((uint32_t)(32 * w) << 16), t_acc = t_x + 32;
+    for (int i = tid; i < NY; i += NT) {
+        tw[i] = tw_g[i];
+        sl[i] = f.slot[(size_t)b * NY + i];
+    }
+    const size_t img = (size_t)b * NY * nx;
+    {
+        float v[32];
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+            const float2 xv = xin[img + (size_t)(t + T * e) * nx + xg];
+            v[2 * e] = xv.x;
+            v[2 * e + 1] = xv.y;
+        }
+        tmem_st32(t_x, v);
+    }
+    __syncthreads();
+    const float sc = rsqrtf((float)NY);
+    for (int c = 0; c < nc; ++c) {
+        const uint32_t ph = c & 1;
+        if (c == nc - 1) {  // the epilogue's rows of g, bd (and bd1) into L2
+            for (int i = tid; i < NY * (ADDBACK ? 3 : 2); i += NT) {
+                const int a = i / NY, y = i % NY;
+                const float2* base = a == 0 ? f.g : (a == 1 ? f.bd : f.bd1);
+                prefetch_l2(base + img + (size_t)y * nx + x0);
+            }
+        }
+        mbar_wait(&fullA, ph, red.err, red.wait_limit);
+        __syncwarp();
+        uint32_t xr[32];
+        if (c == 0) tmem_wait_st();
+        tmem_ld32_issue(t_x, xr);
+        float2 sv[16];
+#pragma unroll
+        for (int e = 0; e < 16; ++e) sv[e] = sA[sb0 + e * T * TX8];
+        __syncwarp();
+        if (lane == 0) {  // this warp is done with the coil tile; the last warp refills it
+            mbar_arrive(&emptyA);
+            if (atomicAdd(&ticketA, 1u) % NW == NW - 1 && c + 1 < nc) {
+                mbar_wait(&emptyA, ph, red.err, red.wait_limit);
+                if (loads) load_S(c + 1);
+            }
+        }
+        __syncwarp();
+        tmem_ld_wait(xr);
+        float2 u[16];
+#pragma unroll
+        for (int e = 0; e < 16; ++e) u[e] = cmul(sv[e], make_float2(__uint_as_float(xr[2 * e]), __uint_as_float(xr[2 * e + 1])));
+        fft_bar2<NY, false>(u, t, xbuf, xbuf, idx, tw, gbar);
+        // on sampled lines: tt = R F S x (unitary scale), yv = y^[j] after the outer update,
+        // u <- yv - tt; zero elsewhere
+        mbar_wait(&fullB, ph, red.err, red.wait_limit);
+        const float2* Yt = sB;
+        const float2* Y1 = sB + msr * TX8;
+        const size_t ybase = ((size_t)b * nc + c) * ms * nx;
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+            const int s = sl[t + T * e];
+            if (s >= 0) {
+                const float2 tt = cscale(u[e], sc);
+                float2 yv = Yt[swz64(s, col)];
+                if (ADDBACK) {
+                    yv = csub(cadd(yv, Y1[swz64(s, col)]), tt);
+                    f.yt[ybase + (size_t)s * nx + xg] = yv;
+                }
+                u[e] = csub(yv, tt);
+            } else {
+                u[e] = make_float2(0.f, 0.f);
+            }
+        }
+        __syncwarp();
+        if (lane == 0) {  // ... and with the k-space rows
+            mbar_arrive(&emptyB);
+            if (atomicAdd(&ticketB, 1u) % NW == NW - 1 && c + 1 < nc) {
+                mbar_wait(&emptyB, ph, red.err, red.wait_limit);
+                if (loads) load_Y(c + 1);
+            }
+        }
+        gbar();
+        fft_bar2<NY, true>(u, t, xbuf, xbuf, idx, tw, gbar);
+        // racc += conj(S) (sc u), in two halves of 8 values
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            float a[16];
+            if (c > 0) {
+                tmem_wait_st();
+                tmem_ld16(t_acc + 16 * h, a);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) a[i] = 0.f;
+            }
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const float2 rr = cfmac(make_float2(a[2 * i], a[2 * i + 1]), sv[8 * h + i], cscale(u[8 * h + i], sc));
+                a[2 * i] = rr.x;
+                a[2 * i + 1] = rr.y;
+            }
+            tmem_st16(t_acc + 16 * h, a);
+        }
+        gbar();
+    }
+    // bd' = (racc + bd + bd1) / 2 after an outer update (else bd' = bd);
+    // b = mu bd' + g ;  r = mu racc + g - lam D^H D x - gam x
+    __syncthreads();  // the stages and the exchange regions are free
+    float2 xv[16], racc[16];
+    {
+        float v[32];
+        tmem_wait_st();
+        tmem_ld32(t_x, v);
+#pragma unroll
+        for (int e = 0; e < 16; ++e) xv[e] = make_float2(v[2 * e], v[2 * e + 1]);
+        tmem_ld32(t_acc, v);
+#pragma unroll
+        for (int e = 0; e < 16; ++e) racc[e] = make_float2(v[2 * e], v[2 * e + 1]);
+    }
+    float2* xt = sA;
+    float2* halo = xbuf;  // [2][NY]: columns x0-1 and x0+8
+#pragma unroll
+    for (int e = 0; e < 16; ++e) xt[sb0 + e * T * TX8] = xv[e];
+    for (int i = tid; i < NY; i += NT) {
+        halo[i] = xin[img + (size_t)i * nx + (x0 == 0 ? nx - 1 : x0 - 1)];
+        halo[NY + i] = xin[img + (size_t)i * nx + (x0 + TX8 == nx ? 0 : x0 + TX8)];
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (w == 0) tmem_dealloc(tmem_s, 64);
+    float bb = 0.f, rr = 0.f;
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+        const int yy = t + T * e;
+        const size_t gi = img + (size_t)yy * nx + xg;
+        const float2 gv = f.g[gi];
+        const float2 up = xt[swz64(yy == 0 ? NY - 1 : yy - 1, col)];
+        const float2 dn = xt[swz64(yy == NY - 1 ? 0 : yy + 1, col)];
+        const float2 lf = col > 0 ? xt[swz64(yy, col - 1)] : halo[yy];
+        const float2 rt = col < TX8 - 1 ? xt[swz64(yy, col + 1)] : halo[NY + yy];
+        const float tvx = 4.f * xv[e].x - up.x - dn.x - lf.x - rt.x;
+        const float tvy = 4.f * xv[e].y - up.y - dn.y - lf.y - rt.y;
+        float2 bdv = f.bd[gi];
+        if (ADDBACK) {
+            const float2 b1 = f.bd1[gi];
+            bdv = make_float2(0.5f * (racc[e].x + bdv.x + b1.x), 0.5f * (racc[e].y + bdv.y + b1.y));
+            f.bd[gi] = bdv;
+        }
+        const float2 bvec = make_float2(fmaf(mu, bdv.x, gv.x), fmaf(mu, bdv.y, gv.y));
+        float2 rv;
+        rv.x = fmaf(mu, racc[e].x, gv.x) - fmaf(lam, tvx, gam * xv[e].x);
+        rv.y = fmaf(mu, racc[e].y, gv.y) - fmaf(lam, tvy, gam * xv[e].y);
+        r[gi] = rv;
+        bb += cabs2(bvec);
+        rr += cabs2(rv);
+    }
+    double vv[2] = {(double)bb, (double)rr}, tot[2];
+    const int np = gridDim.x;
+    if (last_block_total<2>(vv, red.part, np, b * np + blockIdx.x, red.counter + b, tot, red_s, &flag) &&
+        threadIdx.x == 0) {
+        SliceState& S = st[b];
+        S.bnorm2 = tot[0];
+        S.rnorm2 = tot[1];
+        S.iters = 0;
+        S.rho = S.alpha = S.beta = S.pq = 0.0;
+        if (!isfinite(tot[0]) || !isfinite(tot[1])) S.state = ST_NONFINITE;
+        else if (tot[0] == 0.0) S.state = ST_ZERO;
+        else if (tot[1] <= tol2 * tot[0]) S.state = ST_DONE;
+        else S.state = ST_ACTIVE;
+    }
+}
+
+template <bool AB>
+cudaError_t rhs8(const Dims& d, const RhsMaps& m, const SbFields& f, const float2* x, float2* r, const float2* tw,
+                 float mu, float lam, float gam, SliceState* st, double tol2, Red red, cudaStream_t s) {
+    const size_t sm = rhs8_smem_bytes(f.ms);
+    cudaError_t e = set_smem_limit(k_rhs8<AB>, (int)rhs8_smem_bytes(256));  // the fixed maximum (see rhs_n)
+    if (e != cudaSuccess) return e;
+    k_rhs8<AB><<<dim3(d.nx / TX8, d.nb), 128, sm, s>>>(*m.smap8, *m.ymap8, *m.y1map8, f, d.nx, d.nc, x, r, tw, mu, lam,
+                                                      gam, st, tol2, red);
+    return cudaGetLastError();
+}
+
 template <int NY, bool AB>
 cudaError_t rhs_n(const Dims& d, const CUtensorMap& smap, const CUtensorMap& ymap, const CUtensorMap& y1map,
                   const SbFields& f, const float2* x, float2* r, const float2* tw, float mu, float lam, float gam,
@@ -197,15 +464,17 @@ cudaError_t rhs_n(const Dims& d, const CUtensorMap& smap, const CUtensorMap& yma
 }  // namespace
 
 size_t rhs_smem_bytes(int ny, int ms) {
+    if (ny == 256) return rhs8_smem_bytes(ms);
     const size_t nst = 1;
     const size_t xbufs = is_pow2(ny) ? 1 : 2;  // exchange regions (two for the out-of-place mixed-radix stages)
     return (nst * (size_t)(ny + 2 * ms) * TX + xbufs * (size_t)ny * TX + 3 * (size_t)ny) * sizeof(float2) +
            ny * sizeof(int) + 64 * sizeof(double);
 }
 
-cudaError_t launch_rhs(const Dims& d, const CUtensorMap& smap, const CUtensorMap& ymap, const CUtensorMap& y1map,
-                       const SbFields& f, int addback, const float2* x, float2* r, const float2* tw_y, float mu,
-                       float lam, float gam, SliceState* st, double tol2, Red red, cudaStream_t s) {
+cudaError_t launch_rhs(const Dims& d, const RhsMaps& m, const SbFields& f, int addback, const float2* x, float2* r,
+                       const float2* tw_y, float mu, float lam, float gam, SliceState* st, double tol2, Red red,
+                       cudaStream_t s) {
+    const CUtensorMap &smap = *m.smap, &ymap = *m.ymap, &y1map = *m.y1map;
 #define CALL(N)                                                                                        \
     return addback ? rhs_n<N, true>(d, smap, ymap, y1map, f, x, r, tw_y, mu, lam, gam, st, tol2, red, s) \
                    : rhs_n<N, false>(d, smap, ymap, y1map, f, x, r, tw_y, mu, lam, gam, st, tol2, red, s);
@@ -213,7 +482,9 @@ cudaError_t launch_rhs(const Dims& d, const CUtensorMap& smap, const CUtensorMap
         case 32: CALL(32)
         case 64: CALL(64)
         case 128: CALL(128)
-        case 256: CALL(256)
+        case 256:
+            return addback ? rhs8<true>(d, m, f, x, r, tw_y, mu, lam, gam, st, tol2, red, s)
+                           : rhs8<false>(d, m, f, x, r, tw_y, mu, lam, gam, st, tol2, red, s);
         case 512: CALL(512)
         case 192: CALL(192)
         case 224: CALL(224)

@@ -197,9 +197,13 @@ cudaError_t launch_rss(const Dims& d, const SbFields& f, float2* x, int write_x,
 // Right-hand side and initial residual: optional outer data update yt += yt1 - R F S x,
 // b = mu bd + g with bd advanced by linearity, r = b - A x; ||b||^2, ||r||^2, state.
 // smap: as for launch_apply_A; ymap / y1map: TMA maps of yt / yt1 viewed as float32
-// [nb*nc*ms][2*nx] with box [ms][2*kColTile].
-cudaError_t launch_rhs(const Dims& d, const CUtensorMap& smap, const CUtensorMap& ymap,
-                       const CUtensorMap& y1map, const SbFields& f, int addback, const float2* x,
+// [nb*nc*ms][2*nx] with box [ms][2*kColTile]; at ny = 256 the 8-column maps with the 64-byte
+// swizzle are read instead (smap8 as for launch_apply_A, ymap8 / y1map8 with box [ms][16]).
+struct RhsMaps {
+    const CUtensorMap *smap, *ymap, *y1map;
+    const CUtensorMap *smap8, *ymap8, *y1map8;
+};
+cudaError_t launch_rhs(const Dims& d, const RhsMaps& maps, const SbFields& f, int addback, const float2* x,
                        float2* r, const float2* tw_y, float mu, float lam, float gam, SliceState* st,
                        double tol2, Red red, cudaStream_t s);
 // Shared memory the right-hand-side kernel needs for ny and ms (bytes).

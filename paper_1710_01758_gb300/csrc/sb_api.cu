@@ -87,6 +87,7 @@ struct Exec {
     cudaStream_t s = nullptr;
     bool own_stream = false;
     CUtensorMap smap{}, ymap{}, y1map{};  // TMA maps whose first row belongs to slice b0
+    CUtensorMap ymap8{}, y1map8{};        // compact k-space rows as 8-column boxes, 64-byte swizzle (ny = 256)
     CUtensorMap smap_sw{};                // coil tiles with the 128-byte swizzle (q = A p)
     CUtensorMap smap_sw64{};              // 8-column coil tiles, 64-byte swizzle (split-precision q = A p)
     SliceState* st = nullptr;             // device state of the range
@@ -690,9 +691,9 @@ sb_status sb_run(Exec& ex, const sb_sb_opts& o, const float2* y_full, float2* x_
                           launch_g3_inv_y(dp, pl->nz, 1, addback, U, f1, x, r, 0, pl->tw_y, mu, lam, gam, ex.st, tol2,
                                           ex.red, s));
             } else {
+                const RhsMaps maps{&ex.smap, &ex.ymap, &ex.y1map, &ex.smap_sw64, &ex.ymap8, &ex.y1map8};
                 SB_LAUNCH(ex, SB_KCLASS_RHS, 1,
-                          launch_rhs(d, ex.smap, ex.ymap, ex.y1map, fields(), addback, x, r, pl->tw_y, mu, lam, gam,
-                                     ex.st, tol2, ex.red, s));
+                          launch_rhs(d, maps, fields(), addback, x, r, pl->tw_y, mu, lam, gam, ex.st, tol2, ex.red, s));
             }
             sb_status ps = pcg_run(ex, o.pcg, x_full, h_last, iters + solve, nsolve);
             if (ps == SB_ERR_TIMEOUT || ps == SB_ERR_CUDA) return ps;
@@ -1068,7 +1069,10 @@ sb_status sb_set_mask(sb_plan pl, const uint8_t* d_mask) {
         const size_t rows = (size_t)e2.d.nb * d.nc * ms;
         if (ms > 256 || pl->passes()) return true;  // no compact-row maps (2D line RHS kernel only)
         return encode_rows(&e2.ymap, pl->yt + e2.b0 * yrow, d.nx, rows, ms) &&
-               encode_rows(&e2.y1map, pl->yt1 + e2.b0 * yrow, d.nx, rows, ms);
+               encode_rows(&e2.y1map, pl->yt1 + e2.b0 * yrow, d.nx, rows, ms) &&
+               (d.ny != 256 ||
+                (encode_rows(&e2.ymap8, pl->yt + e2.b0 * yrow, d.nx, rows, ms, true, 8, CU_TENSOR_MAP_SWIZZLE_64B) &&
+                 encode_rows(&e2.y1map8, pl->yt1 + e2.b0 * yrow, d.nx, rows, ms, true, 8, CU_TENSOR_MAP_SWIZZLE_64B)));
     };
     bool ok = enc(pl->whole);
     for (Exec& e2 : pl->groups) ok = ok && enc(e2);
