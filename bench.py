@@ -100,6 +100,8 @@ def parse():
                     help="choose slice groups, the preconditioner's column tile and the poll interval with the "
                          "library's autotuner (timed before the measured region, cached per geometry)")
     ap.add_argument("--groups", type=int, default=0, help="concurrent slice groups (0 = library default)")
+    ap.add_argument("--no-graphs", action="store_true",
+                    help="launch the PCG iteration blocks directly instead of replaying captured CUDA graphs")
     ap.add_argument("--prec", choices=list(PRECS), default="fp32",
                     help="fp32, or a split-precision mode: the radix-16 DFT stages of q = A p on the tensor cores "
                          "with operands split in two bf16 / fp16 terms and FP32 accumulation (ny = 256 or 512)")
@@ -363,8 +365,11 @@ def run_ours(args):
         groups = tuned["groups"]
     plan = sb.Plan(wl.nx, wl.ny, ncv, B, wl.mu, wl.lam, wl.gam, wl.wavelet_levels, stream=stream,
                    groups=groups, wavelet=wav, prec=prec)
+    if args.no_graphs:
+        plan.set_graphs(False)
     if tuned:
-        plan.set_tuning(col_tile=tuned["col_tile"], poll_every=tuned["poll_every"])
+        plan.set_tuning(col_tile=tuned["col_tile"], poll_every=tuned["poll_every"],
+                        apply_tile=tuned.get("apply_tile", 0))
 
     def step(ys=d_y, ss=d_sens, ms=d_mask, xx=x):
         if ncv < wl.ncoils:  # coil compression (Methods, "Coil Compression") is part of the step
@@ -408,7 +413,8 @@ def run_ours(args):
         one = sb.Plan(wl.nx, wl.ny, ncv, B, wl.mu, wl.lam, wl.gam, wl.wavelet_levels, stream=stream, groups=1,
                       wavelet=wav, prec=prec)
         if tuned:
-            one.set_tuning(col_tile=tuned["col_tile"], poll_every=tuned["poll_every"])
+            one.set_tuning(col_tile=tuned["col_tile"], poll_every=tuned["poll_every"],
+                           apply_tile=tuned.get("apply_tile", 0))
         one.set_timing((1 << sb.SB_KCLASS_COUNT) - 1)
         torch.cuda.synchronize()
         s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -586,7 +592,8 @@ def run_ours(args):
                 "scaling": "weak", "vs_baseline": None, "dtype": dtype_label, "scalars": "fp64", "data": "synthetic",
                 "config": workload_config(wl, B, {"parallelism": f"{world} ranks x independent batches",
                                                   "wavelet": args.wavelet, "virtual_coils": ncv,
-                                                  "precision": args.prec, "autotune": tuned}),
+                                                  "precision": args.prec, "autotune": tuned,
+                                                  "graphs": not args.no_graphs}),
                 "recon_per_s": recon_per_s,
                 "pcg_iters_per_step": total_all / args.steps,
                 "roofline": {"bound": "hbm", "kernel": a_label,

@@ -245,7 +245,10 @@ uint64_t sb_kernel_launches(void);
  * the FP64 partial sums).  col_tile: columns per CTA of the preconditioner's column pass (the
  * length-ny DFTs of M^{-1} = F^H diag(k)^{-1} F, Eq. precon): 8, 16 (default) or 32.  poll_every:
  * PCG iterations between two polls of the slices' convergence state, which is also the length
- * of a captured graph block (default 4, 1..64).  A zero field keeps the current value.  The
+ * of a captured graph block (default 4, 1..64).  apply_tile: columns per CTA of q = A p (Eq.
+ * system) on 2D line-mask plans in FP32 with ny = 256: 8 (default; p and the coil accumulator in
+ * tensor memory, five CTAs per SM) or 16 (both in registers, a two-stage coil-tile ring, two
+ * CTAs per SM); other geometries ignore it.  A zero field keeps the current value.  The
  * library's autotuner (paper_1710_01758_gb300.autotune) times the choices per geometry and
  * caches the fastest.  SB_ERR_UNSUPPORTED when col_tile does not divide nx or does not fit the
  * column pass (at most 1024 threads, 160 KB of exchange buffers); SB_ERR_INVALID_ARG for other
@@ -253,6 +256,7 @@ uint64_t sb_kernel_launches(void);
 typedef struct {
     int col_tile;
     int poll_every;
+    int apply_tile;
 } sb_tuning;
 sb_status sb_set_tuning(sb_plan plan, const sb_tuning* tuning);
 sb_status sb_get_tuning(sb_plan plan, sb_tuning* tuning);

@@ -460,12 +460,14 @@ cudaError_t apply_A_n(const Dims& d, const CUtensorMap& smap, const float2* p, f
 
 cudaError_t launch_apply_A(const Dims& d, const CUtensorMap& smap, const CUtensorMap& smap8, const float2* p,
                            float2* q, const float* maskw, const float2* tw_y, float mu, float lam, float gam,
-                           SliceState* st, Red red, cudaStream_t s) {
+                           SliceState* st, Red red, cudaStream_t s, int tile) {
     switch (d.ny) {
         case 32: return apply_A_n<32>(d, smap, p, q, maskw, tw_y, mu, lam, gam, st, red, s);
         case 64: return apply_A_n<64>(d, smap, p, q, maskw, tw_y, mu, lam, gam, st, red, s);
         case 128: return apply_A_n<128>(d, smap, p, q, maskw, tw_y, mu, lam, gam, st, red, s);
-        case 256: return apply_A8(d, smap8, p, q, maskw, tw_y, mu, lam, gam, st, red, s);
+        case 256:
+            return tile == 16 ? apply_A_n<256>(d, smap, p, q, maskw, tw_y, mu, lam, gam, st, red, s)
+                              : apply_A8(d, smap8, p, q, maskw, tw_y, mu, lam, gam, st, red, s);
         case 512: return apply_A_n<512>(d, smap, p, q, maskw, tw_y, mu, lam, gam, st, red, s);
         case 192: return apply_A_n<192>(d, smap, p, q, maskw, tw_y, mu, lam, gam, st, red, s);
         case 224: return apply_A_n<224>(d, smap, p, q, maskw, tw_y, mu, lam, gam, st, red, s);

@@ -114,6 +114,7 @@ struct sb_plan_s {
     bool graphs = true;          // PCG iteration blocks replayed as CUDA graphs
     int col_tile = kColTile;     // columns per CTA of the preconditioner's column pass (tuning)
     int poll_every = kPollEvery; // PCG iterations between convergence polls (tuning)
+    int apply_tile = 8;          // columns per CTA of q = A p at ny = 256 (tuning: 8 or 16)
     // volumes: dims is the rows view {nx, ny nz, Nc, nb}; the planes are ny_plane x nx, nz of them
     int nz = 1, ny_plane = 0;
     size_t maxparts = kMaxParts;  // per-slice capacity of the cross-CTA partial sums
@@ -348,7 +349,8 @@ cudaError_t apply_A_2d(const sb_plan_s* pl, const Exec& ex, const Dims& d, const
         const TcOperands tc{&ex.smap_sw64, pl->tw_full, pl->bmat, pl->d.prec == SB_PREC_SPLIT_BF16};
         return launch_apply_A_tc(d, tc, p, q, maskw, mu, lam, gam, st, red, s);
     }
-    return launch_apply_A(d, ex.smap_sw, ex.smap_sw64, p, q, maskw, pl->tw_y, mu, lam, gam, st, red, s);
+    return launch_apply_A(d, ex.smap_sw, ex.smap_sw64, p, q, maskw, pl->tw_y, mu, lam, gam, st, red, s,
+                          pl->apply_tile);
 }
 
 // ---- volumes (nz > 1) and 2D arbitrary masks: the data term as three passes through the coil
@@ -1222,9 +1224,12 @@ sb_status sb_set_tuning(sb_plan pl, const sb_tuning* t) {
     if (t->col_tile != 0 && !col_tile_ok(pl->ny_plane, pl->dims.nx, t->col_tile))
         return fail(pl, SB_ERR_UNSUPPORTED, "col_tile must be 8, 16 or 32, divide nx and fit the column pass");
     if (t->poll_every < 0 || t->poll_every > 64) return fail(pl, SB_ERR_INVALID_ARG, "poll_every must be 0..64");
+    if (t->apply_tile != 0 && t->apply_tile != 8 && t->apply_tile != 16)
+        return fail(pl, SB_ERR_INVALID_ARG, "apply_tile must be 0, 8 or 16");
     SB_CK(pl, pl->stream ? cudaStreamSynchronize(pl->stream) : cudaDeviceSynchronize());
     if (t->col_tile) pl->col_tile = t->col_tile;
     if (t->poll_every) pl->poll_every = t->poll_every;
+    if (t->apply_tile) pl->apply_tile = t->apply_tile;
     drop_graphs(pl);
     return SB_OK;
 }
@@ -1233,6 +1238,7 @@ sb_status sb_get_tuning(sb_plan pl, sb_tuning* t) {
     if (!pl || !t) return SB_ERR_INVALID_ARG;
     t->col_tile = pl->col_tile;
     t->poll_every = pl->poll_every;
+    t->apply_tile = pl->apply_tile;
     return SB_OK;
 }
 

@@ -38,6 +38,10 @@ def test_candidates_and_default_groups():
     assert {ct for _, ct, _ in autotune.candidates(256, 256, 1, nz=128)} == {16}
     # the library's groups = 0: max(1, min(4, nb / 8)), at most nb
     assert [autotune.default_groups(n) for n in (1, 3, 8, 16, 31, 32, 64, 200)] == [1, 1, 1, 2, 3, 4, 4, 4]
+    # two q = A p kernels only for 2D FP32 plans with 256 rows
+    assert autotune.apply_tiles(256, 256) == [8, 16] and autotune.apply_tiles(128, 256) == [8, 16]
+    assert autotune.apply_tiles(256, 128) == [8] and autotune.apply_tiles(256, 256, prec=2) == [8]
+    assert autotune.apply_tiles(256, 256, nz=128) == [8]
 
 
 def test_select_fastest_with_stable_ties():

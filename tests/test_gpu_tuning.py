@@ -5,7 +5,7 @@ caches it."""
 import numpy as np
 import pytest
 
-from oracle import precond
+from oracle import operators, precond
 from paper_1710_01758_gb300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -114,3 +114,30 @@ def test_autotuner_choice_and_cache(torch, sbm, tmp_path):
     assert t["ms"] > 0 and t["ms"] <= t["default_ms"]
     t2 = autotune.tune(make, nx, ny, nc, nb, reps=1, path=path)
     assert t2["cached"] and t2["col_tile"] == t["col_tile"] and t2["groups"] == t["groups"]
+
+
+def test_apply_tile_kernels_agree(torch, sbm):
+    """The two q = A p kernels at 256 rows (8 columns per CTA with tensor-memory state, 16 columns
+    with register state) compute the same values: one application bitwise; a PCG solve to the
+    same iterates up to the order of the FP64 partial sums of p^H q."""
+    nx, ny, nc, nb = 64, 256, 5, 3
+    plan, sens, mask, rng = setup(sbm, torch, nx, ny, nc, nb, seed=21)
+    p = dev(torch, synth.random_complex((nb, ny, nx), rng))
+    q = {}
+    xs = {}
+    for at in (8, 16):
+        plan.set_tuning(apply_tile=at)
+        assert plan.tuning()["apply_tile"] == at
+        q[at] = plan.apply_A(p).cpu().numpy()
+        x = torch.zeros((nb, ny, nx), dtype=torch.complex64, device="cuda")
+        st, _ = plan.pcg_solve(p, x, fixed_iters=6)
+        assert st == sbm.SB_OK
+        xs[at] = x.cpu().numpy()
+    assert np.array_equal(q[8], q[16])
+    assert np.linalg.norm(xs[8] - xs[16]) / np.linalg.norm(xs[16]) <= 1e-6
+    for s in range(nb):
+        ref = operators.apply_A(p[s].cpu().numpy().astype(np.complex128), sens[s], mask[s], 1.0, 0.05, 0.05, 2)
+        assert np.linalg.norm(q[8][s] - ref) / np.linalg.norm(ref) <= 1e-5
+    with pytest.raises(sbm.SbError) as ei:
+        plan.set_tuning(apply_tile=12)
+    assert ei.value.status == sbm.SB_ERR_INVALID_ARG
