@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB_DIR = os.path.join(HERE, "lib")
 LIB_PATH = os.path.join(LIB_DIR, "libsbpcg.so")
-SOURCES = ["sb_api.cu", "k_applyA.cu", "k_pcg.cu", "k_setup.cu", "k_sb.cu", "k_rhs.cu", "k_sbupd.cu", "k_noalloc.cu", "k_precond_fused.cu", "k_vol.cu", "k_wave.cu", "k_coilcomp.cu", "k_applyA_tc.cu"]
+SOURCES = ["sb_api.cu", "k_applyA.cu", "k_pcg.cu", "k_setup.cu", "k_sb.cu", "k_rhs.cu", "k_sbupd.cu", "k_noalloc.cu", "k_precond_fused.cu", "k_vol.cu", "k_wave.cu", "k_coilcomp.cu", "k_applyA_tc.cu", "k_general.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

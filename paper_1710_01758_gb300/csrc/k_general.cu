@@ -1,0 +1,353 @@
+// q = A p (Eq. system) on 2D slices whose mask varies along x (the paper's random 2D sampling,
+// Methods, "Undersampling"), where the data term needs the whole 2D transform of every coil:
+//
+//   q = mu sum_c conj(S_c) F^H R F (S_c p) + lambda (D_x^H D_x + D_y^H D_y) p + gamma p.
+//
+// One launch per batch and no coil scratch in HBM: each slice belongs to a thread-block cluster
+// of C CTAs (8 at 256 x 256).  CTA r holds rows [r RY, (r+1) RY) for the transforms along x and
+// columns [r W, (r+1) W) for the transforms along y, and for every coil
+//   rows:     u = S_c p, DFT_x; each value stored straight into the column buffer of the CTA
+//             that owns its column (distributed shared memory)
+//   columns:  DFT_y, the per-point mask, IDFT_y; each value stored into the row buffer of the
+//             CTA that owns its row
+//   rows:     IDFT_x, acc += conj(S_c) u.
+// The exchanges are remote stores (no thread waits on a remote load); a cluster barrier after
+// each makes them visible.
+// HBM sees p and S read once and q written once, (2 + Nc) 8 N bytes per slice, where the three
+// passes through a coil scratch move (48 Nc + 24) N.  p and the accumulator live in tensor
+// memory, and so do the current coil's sensitivities between their two uses; the next coil's
+// sensitivities are loaded into registers while the current coil's columns are transformed.  PCG mode: inactive slices are skipped, Re(p^H q) is reduced over the cluster's
+// CTAs in fixed order and the last of them sets alpha = rho / p^H q.
+//
+// Cluster barriers: every CTA of a cluster passes the same two barriers per coil; no remote access
+// follows the last one, so no CTA reuses or releases shared memory that another still writes.
+#include <cooperative_groups.h>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "umma.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace sb {
+namespace {
+
+// launch shape of a slice of NX x NY pixels: 16 values per thread, up to 512 threads per CTA
+template <int NX, int NY>
+struct Gen {
+    static constexpr int kPix = NX * NY / 16;
+    static constexpr int C = kPix / 512 < 1 ? 1 : kPix / 512;  // CTAs per slice (cluster size)
+    static constexpr int RY = NY / C;                            // rows per CTA
+    static constexpr int W = NX / C;                             // columns per CTA
+    static constexpr int TXr = NX / 16;                          // threads per row transform
+    static constexpr int TYc = NY / 16;                          // threads per column transform
+    static constexpr int NT = RY * TXr;                          // threads per CTA
+    static constexpr int NW = NT / 32;
+    static constexpr int RS = NX + NX / 16;                      // padded row stride
+    // tensor memory: 96 columns per thread (p, the accumulator, the coil's sensitivities); warps
+    // w, w + 4, ... share lanes and take consecutive 96-column ranges
+    static constexpr int kWarpsPerLane = (NW + 3) / 4;
+    static constexpr int kTmemCols = kWarpsPerLane <= 1 ? 128 : (kWarpsPerLane <= 2 ? 256 : 512);
+    static_assert(96 * kWarpsPerLane <= kTmemCols, "tensor memory holds every warp's columns");
+    static_assert(NT == W * TYc, "row and column phases use the same threads");
+    static_assert(NT % 32 == 0 && 32 % TXr == 0, "a row transform lies within one warp");
+    static_assert(C >= 1 && C <= 8 && W >= 16, "portable cluster sizes only");
+    static constexpr size_t smem = 32 * sizeof(double) + ((size_t)RY * RS + (size_t)NY * W + NX + NY) * sizeof(float2);
+};
+
+struct RowPos {
+    int base;
+    __device__ __forceinline__ int operator()(int pos) const { return base + pos + (pos >> 4); }
+};
+template <int W>
+struct ColPos {
+    int col;
+    __device__ __forceinline__ int operator()(int pos) const { return pos * W + col; }
+};
+
+// the shared-memory address `saddr` of this CTA in the cluster CTA `rank` (32-bit, shared::cluster)
+__device__ __forceinline__ uint32_t mapa_rank(uint32_t saddr, int rank) {
+    uint32_t r;
+    asm("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void st_cluster(uint32_t addr, float2 v) {
+    asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(addr), "f"(v.x), "f"(v.y) : "memory");
+}
+
+template <int NX, int NY, bool PCG>
+__global__ void __launch_bounds__(Gen<NX, NY>::NT, 1)
+k_apply_A_cl(const float2* __restrict__ sens, const float2* __restrict__ p, float2* __restrict__ q,
+             const uint8_t* __restrict__ mask, const float2* __restrict__ twx_g, const float2* __restrict__ twy_g,
+             int nc, float mu_n, float lam, float gam, SliceState* st, Red red) {
+    using G = Gen<NX, NY>;
+    constexpr int C = G::C, RY = G::RY, W = G::W, TXr = G::TXr, TYc = G::TYc, NT = G::NT, RS = G::RS;
+    const int b = blockIdx.y;
+    // the slice state is written only by the last CTA of the reduction at the very end, so every
+    // CTA of the cluster takes the same branch here, before any cluster barrier
+    if (PCG && st[b].state != ST_ACTIVE) return;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank();
+
+    extern __shared__ __align__(16) unsigned char smem[];
+    double* red_s = reinterpret_cast<double*>(smem);           // block_sum scratch
+    float2* rbuf = reinterpret_cast<float2*>(red_s + 32);      // [RY][RS] rows
+    float2* cbuf = rbuf + RY * RS;                             // [NY][W] columns
+    float2* twx = cbuf + NY * W;
+    float2* twy = twx + NX;
+    __shared__ uint32_t tmem_s;
+    __shared__ int flag;
+
+    const int tid = threadIdx.x, w = tid >> 5;
+    const int row = tid / TXr, t = tid % TXr;   // row phases
+    const int cl = tid % W, ty = tid / W;       // column phase
+    const int yg = rank * RY + row, kx = rank * W + cl, kxo = kx + (kx >> 4);
+    const size_t img = (size_t)b * NX * NY;
+    const RowPos rpos{row * RS};
+    const ColPos<W> cpos{cl};
+    // the exchanges: value e of a thread belongs to cluster CTA (e C) / 16 in both phases
+    // (ty < TYc, t < TXr); that CTA's buffers as shared::cluster addresses
+    uint32_t rb[C], cb[C];
+#pragma unroll
+    for (int k = 0; k < C; ++k) {
+        rb[k] = mapa_rank(smem_addr(rbuf), k);
+        cb[k] = mapa_rank(smem_addr(cbuf), k);
+    }
+    auto wbar = []() { __syncwarp(); };
+
+    if (w == 0) tmem_alloc(&tmem_s, G::kTmemCols);
+    for (int i = tid; i < NX; i += NT) twx[i] = twx_g[i];
+    for (int i = tid; i < NY; i += NT) twy[i] = twy_g[i];
+    uint32_t mbits = 0;  // the mask at this thread's (k_y, k_x) points of the column phase
+#pragma unroll
+    for (int e = 0; e < 16; ++e)
+        mbits |= (mask[img + (size_t)(ty + TYc * e) * NX + kx] != 0 ? 1u : 0u) << e;
+    // sensitivities of coil 0 at this thread's row positions
+    auto sidx = [&](int c, int e) { return (((size_t)b * nc + c) * NY + yg) * NX + t + TXr * e; };
+    float2 sn[16];
+#pragma unroll
+    for (int e = 0; e < 16; ++e) sn[e] = __ldg(sens + sidx(0, e));
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t t_pv = tmem_s + ((uint32_t)(32 * (w & 3)) << 16) + (uint32_t)(96 * (w >> 2));
+    const uint32_t t_acc = t_pv + 32, t_s = t_pv + 64;
+    {
+        float v[32];
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+            const float2 pv = p[img + (size_t)yg * NX + t + TXr * e];
+            v[2 * e] = pv.x;
+            v[2 * e + 1] = pv.y;
+        }
+        tmem_st32(t_pv, v);
+    }
+    for (int c = 0; c < nc; ++c) {
+        // ---- rows: u = S_c p, DFT along x; S_c parked in tensor memory until the accumulation
+        uint32_t pr[32];
+        if (c == 0) tmem_wait_st();
+        tmem_ld32_issue(t_pv, pr);
+        {
+            float v[32];
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+                v[2 * e] = sn[e].x;
+                v[2 * e + 1] = sn[e].y;
+            }
+            tmem_st32(t_s, v);
+        }
+        tmem_ld_wait(pr);
+        float2 u[16];
+#pragma unroll
+        for (int e = 0; e < 16; ++e) u[e] = cmul(sn[e], make_float2(__uint_as_float(pr[2 * e]), __uint_as_float(pr[2 * e + 1])));
+        fft_bar<NX, false>(u, t, rbuf, rpos, twx, wbar);
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {  // (yg, kx) -> column buffer of the CTA owning kx
+            const int k = (e * C) / 16;
+            const int xc = t + TXr * e - k * W;
+            st_cluster(cb[k] + (uint32_t)((yg * W + xc) * sizeof(float2)), u[e]);
+        }
+        cluster.sync();  // every CTA's row spectra sit in the column buffers
+        // the next coil's sensitivities: loaded here, right after a cluster barrier, so that they
+        // have landed by the next one (a barrier's release waits for the loads in flight)
+        if (c + 1 < nc) {
+#pragma unroll
+            for (int e = 0; e < 16; ++e) sn[e] = __ldg(sens + sidx(c + 1, e));
+        }
+        // ---- columns: DFT along y, per-point mask, inverse DFT along y
+#pragma unroll
+        for (int e = 0; e < 16; ++e) u[e] = cbuf[cpos(ty + TYc * e)];
+        __syncthreads();  // every column is in registers before the transform's exchange writes
+        fft<NY, false>(u, ty, cbuf, cpos, twy);
+#pragma unroll
+        for (int e = 0; e < 16; ++e)
+            if (!((mbits >> e) & 1u)) u[e] = make_float2(0.f, 0.f);
+        __syncthreads();  // the forward transform's exchange reads are done before the inverse writes
+        fft<NY, true>(u, ty, cbuf, cpos, twy);
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {  // (ky, kx) -> row buffer of the CTA owning ky
+            const int k = (e * C) / 16;
+            const int yr = ty + TYc * e - k * RY;
+            st_cluster(rb[k] + (uint32_t)((yr * RS + kxo) * sizeof(float2)), u[e]);
+        }
+        cluster.sync();  // every column result sits in the row buffers
+        // ---- rows: inverse DFT along x, acc += conj(S_c) u
+#pragma unroll
+        for (int e = 0; e < 16; ++e) u[e] = rbuf[rpos(t + TXr * e)];
+        wbar();  // the row is in registers before the transform's exchange writes (the row's threads share a warp)
+        fft_bar<NX, true>(u, t, rbuf, rpos, twx, wbar);
+        tmem_wait_st();  // this coil's sensitivities (and the last accumulator) have landed
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            float a[16], sh[16];
+            tmem_ld16(t_s + 16 * h, sh);
+            if (c > 0) {
+                tmem_ld16(t_acc + 16 * h, a);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) a[i] = 0.f;
+            }
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const float2 r = cfmac(make_float2(a[2 * i], a[2 * i + 1]), make_float2(sh[2 * i], sh[2 * i + 1]),
+                                       u[8 * h + i]);
+                a[2 * i] = r.x;
+                a[2 * i + 1] = r.y;
+            }
+            tmem_st16(t_acc + 16 * h, a);
+        }
+        wbar();  // the row transform's exchange reads are done before the next coil's writes
+    }
+    // no remote store follows the last cluster barrier, so every CTA may now reuse its buffers
+    // ---- q = (mu / N) acc + lambda (4 p - neighbours) + gamma p on this CTA's rows
+    float2 pv[16], acc[16];
+    {
+        float v[32];
+        tmem_wait_st();
+        tmem_ld32(t_pv, v);
+#pragma unroll
+        for (int e = 0; e < 16; ++e) pv[e] = make_float2(v[2 * e], v[2 * e + 1]);
+        tmem_ld32(t_acc, v);
+#pragma unroll
+        for (int e = 0; e < 16; ++e) acc[e] = make_float2(v[2 * e], v[2 * e + 1]);
+    }
+#pragma unroll
+    for (int e = 0; e < 16; ++e) rbuf[rpos(t + TXr * e)] = pv[e];  // this row of p (own warp)
+    wbar();
+    const size_t up_row = img + (size_t)(yg == 0 ? NY - 1 : yg - 1) * NX;
+    const size_t dn_row = img + (size_t)(yg == NY - 1 ? 0 : yg + 1) * NX;
+    float dot = 0.f;
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+        const int xx = t + TXr * e;
+        const float2 up = p[up_row + xx], dn = p[dn_row + xx];
+        const float2 lf = rbuf[rpos(xx == 0 ? NX - 1 : xx - 1)];
+        const float2 rt = rbuf[rpos(xx == NX - 1 ? 0 : xx + 1)];
+        const float tvx = 4.f * pv[e].x - up.x - dn.x - lf.x - rt.x;
+        const float tvy = 4.f * pv[e].y - up.y - dn.y - lf.y - rt.y;
+        float2 o;
+        o.x = fmaf(mu_n, acc[e].x, fmaf(lam, tvx, gam * pv[e].x));
+        o.y = fmaf(mu_n, acc[e].y, fmaf(lam, tvy, gam * pv[e].y));
+        q[img + (size_t)yg * NX + xx] = o;
+        dot = fmaf(pv[e].x, o.x, fmaf(pv[e].y, o.y, dot));
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (w == 0) tmem_dealloc(tmem_s, G::kTmemCols);
+    if constexpr (PCG) {
+        double vv[1] = {(double)dot}, tot[1];
+        if (last_block_total<1>(vv, red.part, C, b * C + rank, red.counter + b, tot, red_s, &flag) &&
+            threadIdx.x == 0) {
+            SliceState& S = st[b];
+            const double pq = tot[0];
+            S.pq = pq;
+            if (!isfinite(pq) || !isfinite(S.rho)) {
+                S.state = ST_NONFINITE;
+            } else if (!(pq > 0.0)) {
+                S.state = ST_BREAKDOWN;
+            } else {
+                S.alpha = S.rho / pq;
+                S.iters += 1;
+            }
+        }
+    }
+}
+
+template <int NX, int NY, bool PCG>
+cudaError_t general_n(const Dims& d, const float2* sens, const float2* p, float2* q, const uint8_t* mask,
+                      const float2* twx, const float2* twy, float mu, float lam, float gam, SliceState* st, Red red,
+                      cudaStream_t s, int* clusters) {
+    using G = Gen<NX, NY>;
+    auto kern = k_apply_A_cl<NX, NY, PCG>;
+    cudaError_t e = set_smem_limit(kern, (int)G::smem);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(G::C, d.nb);
+    cfg.blockDim = dim3(G::NT);
+    cfg.dynamicSmemBytes = G::smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = G::C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (clusters) return cudaOccupancyMaxActiveClusters(clusters, kern, &cfg);
+    const float mu_n = mu / (float)(NX * NY);  // both transforms are unnormalised
+    return cudaLaunchKernelEx(&cfg, kern, sens, p, q, mask, twx, twy, d.nc, mu_n, lam, gam, st, red);
+}
+
+template <int NX>
+cudaError_t general_ny(const Dims& d, const float2* sens, const float2* p, float2* q, const uint8_t* mask,
+                       const float2* twx, const float2* twy, float mu, float lam, float gam, SliceState* st, Red red,
+                       cudaStream_t s, int* clusters) {
+#define GEN(NY)                                                                                          \
+    return st ? general_n<NX, NY, true>(d, sens, p, q, mask, twx, twy, mu, lam, gam, st, red, s, clusters) \
+              : general_n<NX, NY, false>(d, sens, p, q, mask, twx, twy, mu, lam, gam, st, red, s, clusters);
+    switch (d.ny) {
+        case 64: GEN(64)
+        case 128: GEN(128)
+        case 256: GEN(256)
+        default: return cudaErrorInvalidValue;
+    }
+#undef GEN
+}
+
+cudaError_t general_dispatch(const Dims& d, const float2* sens, const float2* p, float2* q, const uint8_t* mask,
+                             const float2* twx, const float2* twy, float mu, float lam, float gam, SliceState* st,
+                             Red red, cudaStream_t s, int* clusters) {
+    switch (d.nx) {
+        case 64: return general_ny<64>(d, sens, p, q, mask, twx, twy, mu, lam, gam, st, red, s, clusters);
+        case 128: return general_ny<128>(d, sens, p, q, mask, twx, twy, mu, lam, gam, st, red, s, clusters);
+        case 256: return general_ny<256>(d, sens, p, q, mask, twx, twy, mu, lam, gam, st, red, s, clusters);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace
+
+bool apply_A_general_ok(const Dims& d) {
+    auto ok = [](int n) { return n == 64 || n == 128 || n == 256; };
+    if (!ok(d.nx) || !ok(d.ny)) return false;
+    int n0 = 0, n1 = 0;
+    const Red none{nullptr, nullptr, nullptr};
+    SliceState* fake = reinterpret_cast<SliceState*>(16);  // only selects the PCG instantiation
+    if (general_dispatch(d, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 1.f, 0.f, 0.f, nullptr, none,
+                         nullptr, &n0) != cudaSuccess ||
+        general_dispatch(d, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 1.f, 0.f, 0.f, fake, none,
+                         nullptr, &n1) != cudaSuccess) {
+        cudaGetLastError();  // a refused query is an answer, not a sticky error
+        return false;
+    }
+    return n0 > 0 && n1 > 0;
+}
+
+cudaError_t launch_apply_A_general(const Dims& d, const float2* sens, const float2* p, float2* q, const uint8_t* mask,
+                                   const float2* tw_x, const float2* tw_y, float mu, float lam, float gam,
+                                   SliceState* st, Red red, cudaStream_t s) {
+    return general_dispatch(d, sens, p, q, mask, tw_x, tw_y, mu, lam, gam, st, red, s, nullptr);
+}
+
+}  // namespace sb

@@ -166,6 +166,7 @@ k_precond_fused(float2* __restrict__ x, float2* __restrict__ r, float2* __restri
         rz = fmaf(cabs2(v[e]), w, rz);
         v[e] = cscale(v[e], w);
     }
+    __syncthreads();  // a column's threads span warps: the forward exchange reads end before the inverse writes
     fft<NY, true>(v, ty, cbuf, cpos, twy);
     __syncthreads();
 #pragma unroll

@@ -81,6 +81,15 @@ cudaError_t launch_apply_A(const Dims& d, const CUtensorMap& smap, const CUtenso
                            float2* q, const float* maskw, const float2* tw_y, float mu, float lam, float gam,
                            SliceState* st, Red red, cudaStream_t s, int tile = 8);
 
+// q = A p on 2D slices with an arbitrary mask (mask: u8 [nb][ny][nx]) in one launch: a thread-block
+// cluster per slice keeps every coil's 2D spectrum in distributed shared memory (k_general.cu).
+// st == nullptr: plain application; otherwise PCG mode as launch_apply_A.  nx, ny in {64, 128,
+// 256}; apply_A_general_ok tells whether the device can run the shape.
+bool apply_A_general_ok(const Dims& d);
+cudaError_t launch_apply_A_general(const Dims& d, const float2* sens, const float2* p, float2* q, const uint8_t* mask,
+                                   const float2* tw_x, const float2* tw_y, float mu, float lam, float gam,
+                                   SliceState* st, Red red, cudaStream_t s);
+
 // q = A p with the radix-16 DFT stages on the tensor cores, operands split in two bf16 or fp16
 // terms with FP32 accumulation (the split-precision modes; ny = 256 or 512, nx a multiple of 8).
 // smap8: the coil maps as 8-column x 256-row boxes with the 64-byte swizzle; tw: W_256^m, m < 256;

@@ -125,6 +125,8 @@ struct sb_plan_s {
     // 2D slices whose mask varies along x (the paper's random 2D sampling): the data term runs
     // as the three passes of the volumes with a per-point mask (copied here)
     bool general = false;
+    bool general_cluster = false;  // q = A p of the general path as one cluster launch (k_general.cu)
+    int general_passes = 1;        // tuning: 1 = the cluster launch where the shape allows, 3 = three passes
     uint8_t* mask8 = nullptr;
     float2* wb = nullptr;  // Daubechies-4 coefficient scratch [nb][ny][nx]
     bool passes() const { return nz > 1 || general; }
@@ -368,6 +370,12 @@ sb_status vol_apply_A(Exec& ex, const float2* v, float2* out, bool pcg) {
     SbFields f{};
     f.sens = sens;
     const float mu = (float)pl->d.mu, lam = (float)pl->d.lambda, gam = (float)pl->d.gamma;
+    if (pl->general_cluster && pl->general_passes == 1) {  // one launch, spectra in distributed shared memory
+        SB_LAUNCH(ex, SB_KCLASS_APPLY_A, 1,
+                  launch_apply_A_general(dp, sens, v, out, at(pl->mask8, ex, n), pl->tw_x, pl->tw_y, mu, lam, gam,
+                                         pcg ? ex.st : nullptr, ex.red, ex.s));
+        return SB_OK;
+    }
     SB_LAUNCH(ex, SB_KCLASS_APPLY_A, 1, launch_g3_fwd_y(dp, pl->nz, sens, v, U, pl->tw_y, stf, ex.s));
     if (pl->general)
         SB_LAUNCH(ex, SB_KCLASS_APPLY_A, 1,
@@ -977,6 +985,7 @@ sb_status sb_set_mask(sb_plan pl, const uint8_t* d_mask) {
     if (!lines_only && pl->d.prec != SB_PREC_FP32)
         return fail(pl, SB_ERR_UNSUPPORTED, "the split-precision modes need a mask constant along the readout (x) axis");
     pl->general = !lines_only;
+    pl->general_cluster = pl->general && pl->nz == 1 && apply_A_general_ok(Dims{d.nx, d.ny, d.nc, 1});
     int ms = 1;
     std::vector<float> hw(nb * d.ny);
     std::vector<int> hs(nb * d.ny), hl;
@@ -1226,10 +1235,13 @@ sb_status sb_set_tuning(sb_plan pl, const sb_tuning* t) {
     if (t->poll_every < 0 || t->poll_every > 64) return fail(pl, SB_ERR_INVALID_ARG, "poll_every must be 0..64");
     if (t->apply_tile != 0 && t->apply_tile != 8 && t->apply_tile != 16)
         return fail(pl, SB_ERR_INVALID_ARG, "apply_tile must be 0, 8 or 16");
+    if (t->general_passes != 0 && t->general_passes != 1 && t->general_passes != 3)
+        return fail(pl, SB_ERR_INVALID_ARG, "general_passes must be 0, 1 or 3");
     SB_CK(pl, pl->stream ? cudaStreamSynchronize(pl->stream) : cudaDeviceSynchronize());
     if (t->col_tile) pl->col_tile = t->col_tile;
     if (t->poll_every) pl->poll_every = t->poll_every;
     if (t->apply_tile) pl->apply_tile = t->apply_tile;
+    if (t->general_passes) pl->general_passes = t->general_passes;
     drop_graphs(pl);
     return SB_OK;
 }
@@ -1239,6 +1251,7 @@ sb_status sb_get_tuning(sb_plan pl, sb_tuning* t) {
     t->col_tile = pl->col_tile;
     t->poll_every = pl->poll_every;
     t->apply_tile = pl->apply_tile;
+    t->general_passes = pl->general_passes;
     return SB_OK;
 }
 

@@ -45,7 +45,8 @@ class sb_plan_desc(ctypes.Structure):
 
 
 class sb_tuning(ctypes.Structure):
-    _fields_ = [("col_tile", ctypes.c_int), ("poll_every", ctypes.c_int), ("apply_tile", ctypes.c_int)]
+    _fields_ = [("col_tile", ctypes.c_int), ("poll_every", ctypes.c_int), ("apply_tile", ctypes.c_int),
+                ("general_passes", ctypes.c_int)]
 
 
 class sb_pcg_opts(ctypes.Structure):
@@ -335,17 +336,18 @@ class Plan:
     def pcg_solve(self, b, x, **kw):
         return sb_pcg_solve(self.handle, self._c64(b), self._c64(x), pcg_opts(**kw), self.nbatch)
 
-    def set_tuning(self, col_tile: int = 0, poll_every: int = 0, apply_tile: int = 0):
+    def set_tuning(self, col_tile: int = 0, poll_every: int = 0, apply_tile: int = 0, general_passes: int = 0):
         """Columns per CTA of the preconditioner's column pass (8, 16, 32), PCG iterations per
-        convergence poll and columns per CTA of q = A p at 256 rows (8, 16); 0 keeps the current
-        value."""
-        t = sb_tuning(col_tile, poll_every, apply_tile)
+        convergence poll, columns per CTA of q = A p at 256 rows (8, 16) and the general path's
+        q = A p schedule (1 = one cluster launch, 3 = three passes); 0 keeps the current value."""
+        t = sb_tuning(col_tile, poll_every, apply_tile, general_passes)
         _check(_lib.sb_set_tuning(_P(self.handle), ctypes.byref(t)), self.handle)
 
     def tuning(self) -> dict:
-        t = sb_tuning(0, 0, 0)
+        t = sb_tuning(0, 0, 0, 0)
         _check(_lib.sb_get_tuning(_P(self.handle), ctypes.byref(t)), self.handle)
-        return {"col_tile": t.col_tile, "poll_every": t.poll_every, "apply_tile": t.apply_tile}
+        return {"col_tile": t.col_tile, "poll_every": t.poll_every, "apply_tile": t.apply_tile,
+                "general_passes": t.general_passes}
 
     def set_graphs(self, enable: bool):
         """Replay the PCG iteration blocks from CUDA graphs (default) or launch directly."""

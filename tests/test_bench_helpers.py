@@ -43,7 +43,17 @@ def test_alu_side_of_the_roofline():
     assert r["flops_per_launch"] == 64 * 256 * 256 * 12 * 96
     assert abs(r["peak_tflops"] - 152 * 128 * 2 * 2.07 / 1e3) < 1e-9
     assert abs(r["achieved_tflops"] - r["flops_per_launch"] / 168e-6 / 1e12) < 1e-9
-    assert r["floor_us"] < 168.0 and bench.alu_side(wl, 64, 12, 168.0, None, general=True, sms=152) is None
+    assert r["floor_us"] < 168.0
+    g = bench.alu_side(wl, 64, 12, 168.0, None, general=True, sms=152)
+    assert g["flops_per_launch"] == 64 * 256 * 256 * 12 * (2 * 5 * 16 + 16)
+
+
+def test_roofline_takes_the_binding_floor():
+    alu = {"floor_us": 110.0, "achieved_tflops": 20.0, "peak_tflops": 80.0, "frac": 0.25, "peak_kind": "derived"}
+    r = bench.roofline_line("k", 700.0, 6700.0, alu, 70.0, {"frac": 700 / 6700, "traffic": None, "peak_kind": "m"})
+    assert r["bound"] == "alu" and r["unit"] == "TFLOP/s" and r["frac"] == 0.25 and r["hbm"]["floor_us"] == 70.0
+    r = bench.roofline_line("k", 3000.0, 6700.0, dict(alu, floor_us=60.0), 70.0, {"frac": 3000 / 6700})
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s" and abs(r["frac"] - 3000 / 6700) < 1e-12
 
 
 def test_workload_names_resolve():

@@ -439,6 +439,39 @@ def test_random_mask_operators(torch, sbm, nx, ny, nc, nb):
         assert rel(z[b], precond.apply_precond(x[b], kref, 2)) <= OP_TOL
 
 
+@pytest.mark.parametrize("nx,ny,nc,nb", [(256, 256, 6, 3), (64, 128, 3, 2), (256, 64, 2, 2), (128, 128, 12, 1)])
+def test_random_mask_cluster_and_three_passes(torch, sbm, nx, ny, nc, nb):
+    # the general path's q = A p as one cluster launch (spectra in distributed shared memory) and
+    # as three passes through the coil scratch: both against the oracle, one application and a
+    # fixed PCG schedule (p^H q and alpha in the cluster kernel)
+    sens, mask, rng = random_mask_problem(nx, ny, nc, nb, seed=3 * nx + ny + nc)
+    mu, lam, gam = 1.0, 0.05, 0.05
+    plan = make_plan(sbm, torch, sens, mask, mu, lam, gam)
+    x = synth.random_complex((nb, ny, nx), rng)
+    b = synth.random_complex((nb, ny, nx), rng)
+    out = {}
+    for passes in (1, 3):
+        plan.set_tuning(general_passes=passes)
+        assert plan.tuning()["general_passes"] == passes
+        q = plan.apply_A(to_dev(torch, x)).cpu().numpy()
+        xd = torch.zeros((nb, ny, nx), dtype=torch.complex64, device="cuda")
+        st, _ = plan.pcg_solve(to_dev(torch, b), xd, fixed_iters=6)
+        assert st == sbm.SB_OK
+        out[passes] = (q, xd.cpu().numpy())
+    for s_ in range(nb):
+        qref = operators.apply_A(x[s_], sens[s_], mask[s_], mu, lam, gam, 2)
+        k = precond.clamp_k(precond.k_diag(sens[s_], mask[s_], mu, lam, gam, 2))
+        A = lambda v, s_=s_: operators.apply_A(v, sens[s_], mask[s_], mu, lam, gam, 2)  # noqa: E731
+        xref = pcg.pcg(A, b[s_], np.zeros((ny, nx), complex), lambda v: precond.apply_precond(v, k, 2),
+                       fixed_iters=6).x
+        for passes in (1, 3):
+            assert rel(out[passes][0][s_], qref) <= OP_TOL, (passes, s_)
+            assert rel(out[passes][1][s_], xref) <= IMG_TOL, (passes, s_)
+    with pytest.raises(sbm.SbError) as ei:
+        plan.set_tuning(general_passes=2)
+    assert ei.value.status == sbm.SB_ERR_INVALID_ARG
+
+
 @pytest.mark.parametrize("kind", ["circulant", "jacobi"])
 def test_random_mask_pcg_and_mixed_batch(torch, sbm, kind):
     # slice 0 random points, slice 1 Cartesian lines: one plan in the general mode
