@@ -246,9 +246,9 @@ uint64_t sb_kernel_launches(void);
  * length-ny DFTs of M^{-1} = F^H diag(k)^{-1} F, Eq. precon): 8, 16 (default) or 32.  poll_every:
  * PCG iterations between two polls of the slices' convergence state, which is also the length
  * of a captured graph block (default 4, 1..64).  apply_tile: columns per CTA of q = A p (Eq.
- * system) on 2D line-mask plans in FP32 with ny = 256: 8 (default; p and the coil accumulator in
- * tensor memory, five CTAs per SM) or 16 (both in registers, a two-stage coil-tile ring, two
- * CTAs per SM); other geometries ignore it.  general_passes: how q = A p runs on 2D plans whose
+ * system) on 2D line-mask plans in FP32 with ny = 256 or 512: 8 (default; p and the coil
+ * accumulator in tensor memory) or 16 (both in registers, a two-stage coil-tile ring); other
+ * geometries ignore it.  general_passes: how q = A p runs on 2D plans whose
  * mask varies along x (the general path): 1 (default) = one launch per batch, a thread-block
  * cluster per slice keeping every coil's 2D spectrum in distributed shared memory (nx, ny in
  * {64, 128, 256}; other sizes use three passes), 3 = three passes through a coil scratch in

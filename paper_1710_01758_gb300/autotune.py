@@ -6,9 +6,9 @@ Choices (none changes the arithmetic of a slice, only the launch shapes and the 
               M^{-1} = F^H diag(k)^{-1} F): 8, 16 or 32, where they fit;
   poll_every  PCG iterations between convergence polls (and per replayed CUDA-graph block);
   apply_tile  columns per CTA of q = A p where the library has two kernels (2D line masks in
-              FP32 at ny = 256): 8 (p and the accumulator in tensor memory, 5 CTAs per SM) or 16
-              (registers, a two-stage coil-tile ring, 2 CTAs per SM); tuned after the other
-              three, with their best values.
+              FP32 at ny = 256 and 512): 8 (p and the accumulator in tensor memory) or 16
+              (registers, a two-stage coil-tile ring); tuned after the other three, with their
+              best values.
 The objective is the wall time of a PCG solve to a relative residual of 1e-3 from x = 0 on the
 caller's coils and mask (q = A p and the preconditioner are the whole PCG iteration; the call
 returns when the solve has finished), best of `reps` after a warm-up.  Results are cached under
@@ -76,7 +76,7 @@ def candidates(nx: int, ny: int, nbatch: int, nz: int = 1):
 def apply_tiles(nx: int, ny: int, prec: int = 0, nz: int = 1) -> list:
     """q = A p tiles the library offers for this geometry (the default alone where there is one
     kernel)."""
-    return list(APPLY_TILES) if (ny == 256 and nz == 1 and prec == 0) else [APPLY_TILES[0]]
+    return list(APPLY_TILES) if (ny in (256, 512) and nz == 1 and prec == 0) else [APPLY_TILES[0]]
 
 
 def default_groups(nbatch: int) -> int:

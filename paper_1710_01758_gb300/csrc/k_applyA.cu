@@ -210,19 +210,22 @@ k_apply_A(const __grid_constant__ CUtensorMap smap, const float2* __restrict__ p
     }
 }
 
-// ---------------------------------------------------------------- 256 rows: k_apply_A8
-// The same operator for ny = 256 with the per-thread state moved out of the register file, so
-// that more warps fit on an SM (the kernel above holds p, the coil accumulator and the transform
-// in 128 registers and two 110 KB CTAs fill an SM: 16 warps, and it is bound by issue latency):
-//  * a CTA owns 8 columns (128 threads, one per tensor-memory lane; a warp holds two whole
-//    columns, 16 rows x 2 columns, so the transforms' exchanges are warp-local as above);
+// ---------------------------------------------------------------- 256 and 512 rows: k_apply_A8
+// The same operator for ny = 256 and 512 with the per-thread state moved out of the register
+// file, so that more warps fit on an SM (the kernel above holds p, the coil accumulator and the
+// transform in 128 registers; at 256 rows two 110 KB CTAs fill an SM, 16 warps, and it is bound by
+// issue latency; at 512 rows one CTA of 16 warps spills):
+//  * a CTA owns 8 columns, ny / 16 threads per column (128 threads at 256 rows: a warp holds two
+//    whole columns, 16 rows x 2 columns; 256 threads at 512 rows: a warp is one column), so the
+//    transforms' exchanges are warp-local;
 //  * its p values and the coil accumulator live in tensor memory (TMEM, 64 columns of 32 bits
-//    per CTA), read and written with one tcgen05.ld / tcgen05.st per 16 values;
-//  * the coil tile (256 rows x 8 columns, 64-byte TMA swizzle) has ONE stage: every thread copies
+//    per thread; warps w and w + 4 share lanes), one tcgen05.ld / tcgen05.st per 16 values;
+//  * the coil tile (ny rows x 8 columns, 64-byte TMA swizzle) has ONE stage: every thread copies
 //    its 16 sensitivities to registers as soon as the tile lands and the stage is refilled with
 //    the next coil at once (the last warp to release it issues the TMA), so the load of coil
 //    c + 1 overlaps the transforms of coil c.
-// Shared memory is ~39 KB and registers <= 96 per thread: five CTAs (20 warps) per SM.
+// 256 rows: ~39 KB of shared memory and <= 96 registers, five CTAs (20 warps) per SM; 512 rows:
+// ~77 KB and <= 128 registers, two CTAs (16 warps) per SM.
 constexpr int TX8 = 8;
 
 // float2 index of (row, col) in an 8-column tile written by TMA with the 64-byte swizzle
@@ -235,12 +238,14 @@ __device__ __forceinline__ int swz64(int row, int col) {
 // every 512 bytes)
 __device__ __forceinline__ uint32_t pad_to_512(const void* p) { return (512u - (smem_addr(p) & 511u)) & 511u; }
 
-template <bool PCG>
-__global__ void __launch_bounds__(128, 5)
+template <int NY, bool PCG>
+__global__ void __launch_bounds__(TX8 * NY / 16, NY == 256 ? 5 : 2)
 k_apply_A8(const __grid_constant__ CUtensorMap smap8, const float2* __restrict__ p, float2* __restrict__ q,
            const float* __restrict__ maskw, const float2* __restrict__ tw_g, int nx, int nc, float mu, float lam,
            float gam, SliceState* st, Red red) {
-    constexpr int NY = 256, T = 16, NT = 128, NW = 4;
+    static_assert(NY == 256 || NY == 512, "16 or 32 threads per column");
+    constexpr int T = NY / 16, NT = TX8 * T, NW = NT / 32;
+    constexpr uint32_t kTmemCols = NW > 4 ? 128 : 64;
     const int b = blockIdx.y;
     if (PCG && st[b].state != ST_ACTIVE) return;
     extern __shared__ unsigned char smem_raw[];
@@ -256,18 +261,22 @@ k_apply_A8(const __grid_constant__ CUtensorMap smap8, const float2* __restrict__
     __shared__ int flag;
 
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    const int t = (lane & 7) + 8 * (lane >> 4), col = 2 * w + ((lane >> 3) & 1);
+    // T = 16: a warp = 16 rows x 2 columns, a half-warp 8 rows x 2 columns; T = 32: a warp = a column
+    const int t = T == 16 ? (lane & 7) + 8 * (lane >> 4) : lane;
+    const int col = T == 16 ? 2 * w + ((lane >> 3) & 1) : w;
     const int x0 = blockIdx.x * TX8, x = x0 + col;
     const ExIdx<NY> idx{col * ExIdx<NY>::kStride};
-    const int sb0 = swz64(t, col);  // rows t + 16 e share the swizzle term of t
+    const int sb0 = swz64(t, col);  // rows t + T e share the swizzle term of t
     auto gbar = []() { __syncwarp(); };
     const bool loads = !(red.flags & kRedWithholdCoilTiles);
     auto load_tile = [&](int c) {
         mbar_arrive_expect_tx(&full, NY * TX8 * sizeof(float2));
-        tma_load_2d(sbuf, &smap8, 2 * x0, (b * nc + c) * NY, &full);
+#pragma unroll
+        for (int r0 = 0; r0 < NY; r0 += 256)  // a TMA box spans at most 256 rows
+            tma_load_2d(sbuf + r0 * TX8, &smap8, 2 * x0, (b * nc + c) * NY + r0, &full);
     };
 
-    if (w == 0) tmem_alloc(&tmem_s, 64);
+    if (w == 0) tmem_alloc(&tmem_s, kTmemCols);
     if (tid == 0) {
         mbar_init(&full, 1);
         mbar_init(&empty, NW);
@@ -278,8 +287,9 @@ k_apply_A8(const __grid_constant__ CUtensorMap smap8, const float2* __restrict__
     __syncthreads();
     tc_fence_after();
     if (tid == 0 && loads) load_tile(0);
-    // this warp's TMEM lanes 32 w .. 32 w + 31: columns 0-31 hold p, 32-63 the accumulator
-    const uint32_t t_pv = tmem_s + ((uint32_t)(32 * w) << 16), t_acc = t_pv + 32;
+    // this warp's TMEM lanes 32 (w mod 4) .. +31; columns 64 (w / 4) + 0-31 hold p, + 32-63 the
+    // accumulator
+    const uint32_t t_pv = tmem_s + ((uint32_t)(32 * (w & 3)) << 16) + (uint32_t)(64 * (w >> 2)), t_acc = t_pv + 32;
     for (int i = tid; i < NY; i += NT) {
         tw[i] = tw_g[i];
         const float wt = maskw[(size_t)b * NY + i];
@@ -370,7 +380,7 @@ k_apply_A8(const __grid_constant__ CUtensorMap smap8, const float2* __restrict__
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (w == 0) tmem_dealloc(tmem_s, 64);  // every warp's TMEM reads are complete
+    if (w == 0) tmem_dealloc(tmem_s, kTmemCols);  // every warp's TMEM reads are complete
     float dot = 0.f;
 #pragma unroll
     for (int e = 0; e < 16; ++e) {
@@ -407,24 +417,26 @@ k_apply_A8(const __grid_constant__ CUtensorMap smap8, const float2* __restrict__
     }
 }
 
+template <int NY>
 constexpr size_t smem_apply_A8() {
-    return 512 + ((size_t)256 * TX8 + (size_t)ExIdx<256>::kStride * TX8 + 2 * 256) * sizeof(float2) +
+    return 512 + ((size_t)NY * TX8 + (size_t)ExIdx<NY>::kStride * TX8 + 2 * NY) * sizeof(float2) +
            32 * sizeof(double);
 }
 
+template <int NY>
 cudaError_t apply_A8(const Dims& d, const CUtensorMap& smap8, const float2* p, float2* q, const float* maskw,
                      const float2* tw, float mu, float lam, float gam, SliceState* st, Red red, cudaStream_t s) {
-    const dim3 grid(d.nx / TX8, d.nb), block(128);
-    constexpr size_t sm = smem_apply_A8();
-    static_assert(2 * 256 * sizeof(float2) <= (size_t)ExIdx<256>::kStride * TX8 * sizeof(float2),
+    const dim3 grid(d.nx / TX8, d.nb), block(TX8 * NY / 16);
+    constexpr size_t sm = smem_apply_A8<NY>();
+    static_assert(2 * NY * sizeof(float2) <= (size_t)ExIdx<NY>::kStride * TX8 * sizeof(float2),
                   "the halo fits in the exchange regions");
     cudaError_t e;
     if (st) {
-        if ((e = set_smem_limit(k_apply_A8<true>, (int)sm)) != cudaSuccess) return e;
-        k_apply_A8<true><<<grid, block, sm, s>>>(smap8, p, q, maskw, tw, d.nx, d.nc, mu, lam, gam, st, red);
+        if ((e = set_smem_limit(k_apply_A8<NY, true>, (int)sm)) != cudaSuccess) return e;
+        k_apply_A8<NY, true><<<grid, block, sm, s>>>(smap8, p, q, maskw, tw, d.nx, d.nc, mu, lam, gam, st, red);
     } else {
-        if ((e = set_smem_limit(k_apply_A8<false>, (int)sm)) != cudaSuccess) return e;
-        k_apply_A8<false><<<grid, block, sm, s>>>(smap8, p, q, maskw, tw, d.nx, d.nc, mu, lam, gam, st, red);
+        if ((e = set_smem_limit(k_apply_A8<NY, false>, (int)sm)) != cudaSuccess) return e;
+        k_apply_A8<NY, false><<<grid, block, sm, s>>>(smap8, p, q, maskw, tw, d.nx, d.nc, mu, lam, gam, st, red);
     }
     return cudaGetLastError();
 }
@@ -467,8 +479,10 @@ cudaError_t launch_apply_A(const Dims& d, const CUtensorMap& smap, const CUtenso
         case 128: return apply_A_n<128>(d, smap, p, q, maskw, tw_y, mu, lam, gam, st, red, s);
         case 256:
             return tile == 16 ? apply_A_n<256>(d, smap, p, q, maskw, tw_y, mu, lam, gam, st, red, s)
-                              : apply_A8(d, smap8, p, q, maskw, tw_y, mu, lam, gam, st, red, s);
-        case 512: return apply_A_n<512>(d, smap, p, q, maskw, tw_y, mu, lam, gam, st, red, s);
+                              : apply_A8<256>(d, smap8, p, q, maskw, tw_y, mu, lam, gam, st, red, s);
+        case 512:
+            return tile == 16 ? apply_A_n<512>(d, smap, p, q, maskw, tw_y, mu, lam, gam, st, red, s)
+                              : apply_A8<512>(d, smap8, p, q, maskw, tw_y, mu, lam, gam, st, red, s);
         case 192: return apply_A_n<192>(d, smap, p, q, maskw, tw_y, mu, lam, gam, st, red, s);
         case 224: return apply_A_n<224>(d, smap, p, q, maskw, tw_y, mu, lam, gam, st, red, s);
         case 320: return apply_A_n<320>(d, smap, p, q, maskw, tw_y, mu, lam, gam, st, red, s);

@@ -76,7 +76,7 @@ constexpr int kVecPerThread = 8;
 // otherwise PCG mode: skips inactive slices, accumulates Re(p^H q) and sets alpha = rho/pq.
 // smap: TMA map of the sensitivities viewed as float32 [nb*nc*ny][2*nx], box [ny][2*kColTile]
 // with the 128-byte swizzle; smap8: the same rows as 8-column boxes of 256 rows with the 64-byte
-// swizzle (read at ny = 256).  tile: columns per CTA at ny = 256, 8 (tensor-memory kernel) or 16.
+// swizzle (read at ny = 256 and 512).  tile: columns per CTA there, 8 (tensor-memory kernel) or 16.
 cudaError_t launch_apply_A(const Dims& d, const CUtensorMap& smap, const CUtensorMap& smap8, const float2* p,
                            float2* q, const float* maskw, const float2* tw_y, float mu, float lam, float gam,
                            SliceState* st, Red red, cudaStream_t s, int tile = 8);

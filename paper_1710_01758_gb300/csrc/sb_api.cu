@@ -935,7 +935,7 @@ sb_status sb_set_coils(sb_plan pl, const void* d_sens) {
         const size_t rows = (size_t)ex.d.nb * d.nc * d.ny;
         const int box = coil_box_rows(d.ny);  // a TMA box spans at most 256 rows
         return encode_rows(&ex.smap, base, d.nx, rows, box) && encode_rows(&ex.smap_sw, base, d.nx, rows, box, true) &&
-               ((pl->d.prec == SB_PREC_FP32 && d.ny != 256) ||
+               ((pl->d.prec == SB_PREC_FP32 && d.ny != 256 && d.ny != 512) ||
                 encode_rows(&ex.smap_sw64, base, d.nx, rows, 256, true, 8, CU_TENSOR_MAP_SWIZZLE_64B));
     };
     bool ok = true;

@@ -41,6 +41,7 @@ def test_candidates_and_default_groups():
     # two q = A p kernels only for 2D FP32 plans with 256 rows
     assert autotune.apply_tiles(256, 256) == [8, 16] and autotune.apply_tiles(128, 256) == [8, 16]
     assert autotune.apply_tiles(256, 128) == [8] and autotune.apply_tiles(256, 256, prec=2) == [8]
+    assert autotune.apply_tiles(512, 512) == [8, 16] and autotune.apply_tiles(320, 320) == [8]
     assert autotune.apply_tiles(256, 256, nz=128) == [8]
 
 

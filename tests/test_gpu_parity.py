@@ -64,6 +64,7 @@ def make_plan(sbm, torch, sens, mask, mu, lam, gam, levels=0, passes=0):
 
 
 SHAPES = [(32, 64, 3, 2), (64, 32, 2, 3), (128, 128, 4, 1), (256, 256, 12, 1), (256, 128, 5, 2), (32, 256, 3, 2),
+          (64, 512, 3, 2),
           (512, 512, 32, 1), (512, 128, 3, 2),
           # mixed-radix lengths 16 x {12, 14, 20, 24}
           (192, 192, 8, 2), (256, 224, 12, 1), (320, 320, 16, 1), (384, 320, 32, 1), (224, 384, 3, 1)]

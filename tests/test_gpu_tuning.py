@@ -116,11 +116,12 @@ def test_autotuner_choice_and_cache(torch, sbm, tmp_path):
     assert t2["cached"] and t2["col_tile"] == t["col_tile"] and t2["groups"] == t["groups"]
 
 
-def test_apply_tile_kernels_agree(torch, sbm):
-    """The two q = A p kernels at 256 rows (8 columns per CTA with tensor-memory state, 16 columns
-    with register state) compute the same values: one application bitwise; a PCG solve to the
-    same iterates up to the order of the FP64 partial sums of p^H q."""
-    nx, ny, nc, nb = 64, 256, 5, 3
+@pytest.mark.parametrize("ny", [256, 512])
+def test_apply_tile_kernels_agree(torch, sbm, ny):
+    """The two q = A p kernels at 256 and 512 rows (8 columns per CTA with tensor-memory state, 16
+    columns with register state) compute the same values: one application bitwise; a PCG solve to
+    the same iterates up to the order of the FP64 partial sums of p^H q."""
+    nx, nc, nb = 64, 5, 3
     plan, sens, mask, rng = setup(sbm, torch, nx, ny, nc, nb, seed=21)
     p = dev(torch, synth.random_complex((nb, ny, nx), rng))
     q = {}
