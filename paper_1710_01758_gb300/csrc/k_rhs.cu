@@ -189,8 +189,10 @@ k_rhs(const __grid_constant__ CUtensorMap smap, const __grid_constant__ CUtensor
 // coil tile and the compact k-space rows (yt, yt1) arrive by TMA with the 64-byte swizzle into
 // one stage each, released as soon as every warp has read them (the sensitivities into
 // registers at the start of the coil, the k-space rows after the forward transform) and refilled
-// at once by the last warp to release them.  The epilogue's rows of g, bd and bd1 are prefetched
-// into L2 during the last coil.
+// at once by the last warp to release them.  Between the transforms a warp handles the sampled
+// lines of its two columns densely (its lanes over the compact slots, through the exchange
+// region) instead of each thread testing its own 16 rows, which left most lanes idle on every
+// row.  The epilogue's rows of g, bd and bd1 are prefetched into L2 during the last coil.
 constexpr int TX8 = 8;
 using tiles::ExIdx;
 
@@ -207,7 +209,7 @@ __host__ __device__ constexpr int ms_rows8(int ms) { return (ms + 7) & ~7; }
 size_t rhs8_smem_bytes(int ms) {
     return 512 + ((size_t)256 * TX8 + 2 * (size_t)ms_rows8(ms) * TX8 + (size_t)ExIdx<256>::kStride * TX8 + 256) *
                      sizeof(float2) +
-           256 * sizeof(int) + 32 * sizeof(double);
+           2 * 256 * sizeof(int) + 32 * sizeof(double);
 }
 
 template <bool ADDBACK>
@@ -226,8 +228,9 @@ k_rhs8(const __grid_constant__ CUtensorMap smap8, const __grid_constant__ CUtens
     float2* sB = sA + NY * TX8;                      // [msr][8] yt rows, then [msr][8] yt1 rows
     float2* xbuf = sB + 2 * msr * TX8;               // [8][ExIdx::kStride] exchanges; halo in the epilogue
     float2* tw = xbuf + ExIdx<NY>::kStride * TX8;
-    int* sl = reinterpret_cast<int*>(tw + NY);
-    double* red_s = reinterpret_cast<double*>(sl + NY);
+    int* sl = reinterpret_cast<int*>(tw + NY);  // [NY] slot of each row (-1: not sampled)
+    int* ln = sl + NY;                          // [ms] line of each slot
+    double* red_s = reinterpret_cast<double*>(ln + NY);
     __shared__ __align__(8) uint64_t fullA, emptyA, fullB, emptyB;
     __shared__ uint32_t tmem_s;
     __shared__ unsigned ticketA, ticketB;
@@ -272,6 +275,7 @@ k_rhs8(const __grid_constant__ CUtensorMap smap8, const __grid_constant__ CUtens
         tw[i] = tw_g[i];
         sl[i] = f.slot[(size_t)b * NY + i];
     }
+    for (int i = tid; i < ms; i += NT) ln[i] = f.lines[(size_t)b * ms + i];
     const size_t img = (size_t)b * NY * nx;
     {
         float v[32];
@@ -284,6 +288,9 @@ k_rhs8(const __grid_constant__ CUtensorMap smap8, const __grid_constant__ CUtens
         tmem_st32(t_x, v);
     }
     __syncthreads();
+    uint32_t mb = 0;  // which of this thread's rows t + 16 e are sampled
+#pragma unroll
+    for (int e = 0; e < 16; ++e) mb |= (sl[t + T * e] >= 0 ? 1u : 0u) << e;
     const float sc = rsqrtf((float)NY);
     for (int c = 0; c < nc; ++c) {
         const uint32_t ph = c & 1;
@@ -317,26 +324,35 @@ k_rhs8(const __grid_constant__ CUtensorMap smap8, const __grid_constant__ CUtens
         for (int e = 0; e < 16; ++e) u[e] = cmul(sv[e], make_float2(__uint_as_float(xr[2 * e]), __uint_as_float(xr[2 * e + 1])));
         fft_bar2<NY, false>(u, t, xbuf, xbuf, idx, tw, gbar);
         // on sampled lines: tt = R F S x (unitary scale), yv = y^[j] after the outer update,
-        // u <- yv - tt; zero elsewhere
-        mbar_wait(&fullB, ph, red.err, red.wait_limit);
-        const float2* Yt = sB;
-        const float2* Y1 = sB + msr * TX8;
-        const size_t ybase = ((size_t)b * nc + c) * ms * nx;
+        // u <- yv - tt; zero elsewhere.  The warp's two columns go through the exchange region:
+        // every thread stores its 16 values, the lanes then walk the compact slots of both columns
+        // (lane l: column 2 w + (l & 1), slots l / 2 + 16 i), and every thread reads its rows back.
+        gbar();  // the forward transform's exchange reads are done
 #pragma unroll
-        for (int e = 0; e < 16; ++e) {
-            const int s = sl[t + T * e];
-            if (s >= 0) {
-                const float2 tt = cscale(u[e], sc);
-                float2 yv = Yt[swz64(s, col)];
+        for (int e = 0; e < 16; ++e) xbuf[idx(t + T * e)] = u[e];
+        mbar_wait(&fullB, ph, red.err, red.wait_limit);
+        __syncwarp();
+        {
+            const float2* Yt = sB;
+            const float2* Y1 = sB + msr * TX8;
+            const size_t ybase = ((size_t)b * nc + c) * ms * nx;
+            const int cc = 2 * w + (lane & 1);  // the column this lane serves in the dense walk
+            const ExIdx<NY> cidx{cc * ExIdx<NY>::kStride};
+            for (int s = lane >> 1; s < ms; s += 16) {
+                const int yrow = ln[s];
+                const float2 tt = cscale(xbuf[cidx(yrow)], sc);
+                float2 yv = Yt[swz64(s, cc)];
                 if (ADDBACK) {
-                    yv = csub(cadd(yv, Y1[swz64(s, col)]), tt);
-                    f.yt[ybase + (size_t)s * nx + xg] = yv;
+                    yv = csub(cadd(yv, Y1[swz64(s, cc)]), tt);
+                    f.yt[ybase + (size_t)s * nx + x0 + cc] = yv;
                 }
-                u[e] = csub(yv, tt);
-            } else {
-                u[e] = make_float2(0.f, 0.f);
+                xbuf[cidx(yrow)] = csub(yv, tt);
             }
         }
+        __syncwarp();
+#pragma unroll
+        for (int e = 0; e < 16; ++e)
+            u[e] = ((mb >> e) & 1u) ? xbuf[idx(t + T * e)] : make_float2(0.f, 0.f);
         __syncwarp();
         if (lane == 0) {  // ... and with the k-space rows
             mbar_arrive(&emptyB);

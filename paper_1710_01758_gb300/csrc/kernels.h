@@ -181,6 +181,7 @@ struct SbFields {
     const float2* sens;
     const float* maskw;   // [nb][ny]: 1/ny on sampled lines, 0 elsewhere
     const int* slot;      // [nb][ny]: compact index of a sampled line, -1 elsewhere
+    const int* lines;     // [nb][ms]: the line of each compact index (2D line path)
     float2* yt;           // [nb][nc][ms][nx]: F_x^H y^[j] on sampled lines
     const float2* yt1;    // [nb][nc][ms][nx]: F_x^H y^[1]
     int ms;               // slots per slice

@@ -648,6 +648,7 @@ sb_status sb_run(Exec& ex, const sb_sb_opts& o, const float2* y_full, float2* x_
         f.sens = at(pl->sens, ex, (size_t)d.nc * n);
         f.maskw = at(pl->maskw, ex, (size_t)d.ny);
         f.slot = at(pl->slot, ex, (size_t)d.ny);
+        f.lines = pl->lines ? at(pl->lines, ex, ms) : nullptr;
         f.yt = at(pl->yt, ex, yrow);
         f.yt1 = at(pl->yt1, ex, yrow);
         f.ms = (int)ms;
