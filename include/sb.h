@@ -24,9 +24,11 @@
  *  - Masks (sb_set_mask): a 2D mask constant along the readout (x) axis (Cartesian
  *    phase-encode lines, the paper's first scheme in Methods, "Undersampling") takes the fast
  *    path, DFTs along y only; any other 2D mask (the paper's random 2D sampling) takes the
- *    general path, a per-point mask between DFTs along y and x.  Volumes (ndim = 3) need a mask
- *    constant along x (sampled (k_y, k_z) lines); split-precision plans need line masks; other
- *    combinations are refused with SB_ERR_UNSUPPORTED.
+ *    general path, a per-point mask between DFTs along y and x.  On volumes (ndim = 3) a mask
+ *    constant along x (sampled (k_y, k_z) lines) takes three passes per data-term operation and
+ *    any other mask the general path's five (DFTs along y and z, the per-point mask between DFTs
+ *    along x, inverse DFTs along z and y).  Split-precision plans need 2D line masks
+ *    (SB_ERR_UNSUPPORTED otherwise).
  *  - Supported sizes: ndim = 2 (slices) or 3 (volumes of nz planes); nx, ny (and nz for
  *    volumes) in {32, 64, 128, 192, 224, 256, 320, 384, 512} (powers of two and
  *    16 x {12, 14, 20, 24}, mixed-radix transforms); ncoils >= 1; nbatch >= 1; wavelet_levels in
@@ -115,9 +117,10 @@ sb_status sb_set_coils(sb_plan plan, const void* d_sens);
  * DFT order, and build k of Eq. Kdiag by FFTs (Eq. diagonalelements and the k_d paragraph of
  * "Efficient Implementation of the Preconditioner").  Requires sb_set_coils.  d_mask is read
  * during this call only.  Synchronises the stream.  A 2D mask that varies along x (the paper's
- * random sampling, Methods, "Undersampling") switches the plan to the general path: the data
- * term in three passes with a per-point mask.  Returns SB_ERR_UNSUPPORTED for such a mask on a
- * volume plan or on a split-precision plan. */
+ * random sampling, Methods, "Undersampling") switches the plan to the general path: q = A p in
+ * one cluster launch (nx, ny in {64, 128, 256}) or three passes with a per-point mask, the
+ * right-hand side in three passes; a volume mask that varies along x does too (five passes).
+ * Returns SB_ERR_UNSUPPORTED for such a mask on a split-precision plan. */
 sb_status sb_set_mask(sb_plan plan, const uint8_t* d_mask);
 
 /* Copy k (float32 [nbatch][ny][nx], DFT order, before inversion) into d_k. */

@@ -359,6 +359,25 @@ cudaError_t apply_A_2d(const sb_plan_s* pl, const Exec& ex, const Dims& d, const
 // scratch (k_vol.cu)
 Dims plane_dims(const Exec& ex) { return Dims{ex.d.nx, ex.pl->ny_plane, ex.d.nc, ex.d.nb}; }
 
+// The middle of the general path (a mask that varies along x) on the coil scratch U, after DFT_y
+// of every plane: DFT_z (volumes), then along x the per-point mask operation `mode` of k_g2_x
+// over the rows of every plane, then IDFT_z.  mode 2 (back-projection) reads no U, so it skips
+// the forward DFT_z.  The z passes run over every volume of the context (converged ones too: U
+// is scratch).
+sb_status general_mid(Exec& ex, int cls, int mode, int addback, float2* U, float2* yt, const float2* yt1,
+                      const SliceState* stf) {
+    sb_plan pl = ex.pl;
+    const Dims dp = plane_dims(ex);
+    const Dims rows{dp.nx, dp.ny * pl->nz, dp.nc, dp.nb};  // the rows of all planes
+    const int ncols = dp.nx * dp.ny, nimg = dp.nb * dp.nc;
+    if (pl->nz > 1 && mode != 2)
+        SB_LAUNCH(ex, cls, 1, launch_fft_cols(ncols, pl->nz, nimg, U, pl->tw_z, false, ex.s));
+    SB_LAUNCH(ex, cls, 1,
+              launch_g2_x(rows, mode, addback, U, at(pl->mask8, ex, pl->n), yt, yt1, pl->tw_x, stf, ex.s));
+    if (pl->nz > 1) SB_LAUNCH(ex, cls, 1, launch_fft_cols(ncols, pl->nz, nimg, U, pl->tw_z, true, ex.s));
+    return SB_OK;
+}
+
 // out = A v on the context's volumes; pcg: PCG mode (inactive volumes skipped, p^H q, alpha)
 sb_status vol_apply_A(Exec& ex, const float2* v, float2* out, bool pcg) {
     sb_plan pl = ex.pl;
@@ -377,10 +396,9 @@ sb_status vol_apply_A(Exec& ex, const float2* v, float2* out, bool pcg) {
         return SB_OK;
     }
     SB_LAUNCH(ex, SB_KCLASS_APPLY_A, 1, launch_g3_fwd_y(dp, pl->nz, sens, v, U, pl->tw_y, stf, ex.s));
-    if (pl->general)
-        SB_LAUNCH(ex, SB_KCLASS_APPLY_A, 1,
-                  launch_g2_x(dp, 0, 0, U, at(pl->mask8, ex, n), nullptr, nullptr, pl->tw_x, stf, ex.s));
-    else
+    if (pl->general) {
+        if (sb_status e = general_mid(ex, SB_KCLASS_APPLY_A, 0, 0, U, nullptr, nullptr, stf)) return e;
+    } else
         SB_LAUNCH(ex, SB_KCLASS_APPLY_A, 1,
                   launch_g3_z(dp, pl->nz, 0, 0, U, at(pl->slot, ex, (size_t)ex.d.ny), nullptr, nullptr, pl->ms,
                               pl->tw_z, stf, ex.s));
@@ -667,14 +685,14 @@ sb_status sb_run(Exec& ex, const sb_sb_opts& o, const float2* y_full, float2* x_
     const Dims dp = plane_dims(ex);
     float2* U = at(pl->spec, ex, (size_t)d.nc * n);
     const bool passes = pl->passes();
-    const uint8_t* mask8 = pl->general ? at(pl->mask8, ex, n) : nullptr;
     if (passes) {
         SbFields f0 = fields();
-        if (pl->general)
-            SB_LAUNCH(ex, SB_KCLASS_OTHER, 1, launch_g2_x(dp, 2, 0, U, mask8, f0.yt, f0.yt1, pl->tw_x, nullptr, s));
-        else
+        if (pl->general) {
+            if (sb_status e = general_mid(ex, SB_KCLASS_OTHER, 2, 0, U, f0.yt, f0.yt1, nullptr)) return e;
+        } else {
             SB_LAUNCH(ex, SB_KCLASS_OTHER, 1,
                       launch_g3_z(dp, pl->nz, 2, 0, U, f0.slot, f0.yt, f0.yt1, (int)ms, pl->tw_z, nullptr, s));
+        }
         SB_LAUNCH(ex, SB_KCLASS_OTHER, 1,
                   launch_g3_inv_y(dp, pl->nz, 2, 0, U, f0, nullptr, x, o.init_rss ? 1 : 0, pl->tw_y, mu, lam, gam,
                                   ex.st, 0.0, ex.red, s));
@@ -691,10 +709,9 @@ sb_status sb_run(Exec& ex, const sb_sb_opts& o, const float2* y_full, float2* x_
             if (passes) {
                 SbFields f1 = fields();
                 SB_LAUNCH(ex, SB_KCLASS_RHS, 1, launch_g3_fwd_y(dp, pl->nz, f1.sens, x, U, pl->tw_y, nullptr, s));
-                if (pl->general)
-                    SB_LAUNCH(ex, SB_KCLASS_RHS, 1,
-                              launch_g2_x(dp, 1, addback, U, mask8, f1.yt, f1.yt1, pl->tw_x, nullptr, s));
-                else
+                if (pl->general) {
+                    if (sb_status e = general_mid(ex, SB_KCLASS_RHS, 1, addback, U, f1.yt, f1.yt1, nullptr)) return e;
+                } else
                     SB_LAUNCH(ex, SB_KCLASS_RHS, 1,
                               launch_g3_z(dp, pl->nz, 1, addback, U, f1.slot, f1.yt, f1.yt1, (int)ms, pl->tw_z, nullptr,
                                           s));
@@ -981,8 +998,6 @@ sb_status sb_set_mask(sb_plan pl, const uint8_t* d_mask) {
     SB_CK(pl, cudaStreamSynchronize(s));
     bool lines_only = true;
     for (size_t i = 0; i < hu.size(); ++i) lines_only = lines_only && hu[i];
-    if (!lines_only && pl->nz > 1)
-        return fail(pl, SB_ERR_UNSUPPORTED, "a volume mask must be constant along the readout (x) axis");
     if (!lines_only && pl->d.prec != SB_PREC_FP32)
         return fail(pl, SB_ERR_UNSUPPORTED, "the split-precision modes need a mask constant along the readout (x) axis");
     pl->general = !lines_only;
