@@ -221,6 +221,27 @@ __device__ __forceinline__ void fft_2stage_bar(float2 (&v)[16], int t, float2* b
     }
 }
 
+// fft_2stage_bar for N = 256 (16 threads per transform, t < 16) with the thread's stage-2
+// twiddles held in registers, twr[r - 1] = W_256^{r t} for r = 1 .. 15: it saves the transform's
+// 15 shared-memory twiddle loads, at the cost of 30 registers.
+template <bool INV, class Idx, class Bar>
+__device__ __forceinline__ void fft256_bar_rtw(float2 (&v)[16], int t, float2* buf, Idx idx, const float2 (&twr)[15],
+                                               Bar bar) {
+    dft16<INV>(v);
+#pragma unroll
+    for (int r = 0; r < 16; ++r) buf[idx(16 * t + r)] = v[r];
+    bar();
+#pragma unroll
+    for (int r = 0; r < 16; ++r) v[r] = buf[idx(t + 16 * r)];
+#pragma unroll
+    for (int r = 1; r < 16; ++r) {
+        float2 w = twr[r - 1];
+        if (INV) w.y = -w.y;
+        v[r] = cmul(v[r], w);
+    }
+    dft16<INV>(v);
+}
+
 // Three-stage transform for N = 16 * 16 * R3 (N = 512: R3 = 2), T = N / 16 threads per
 // transform, the same register layout (thread t holds x[t + T e] in and X[t + T e] out).
 // Stage 1: radix 16 on registers; stage 2: radix 16 over the 256-point sub-transforms (span 16,

@@ -224,7 +224,9 @@ k_apply_A(const __grid_constant__ CUtensorMap smap, const float2* __restrict__ p
 //    its 16 sensitivities to registers as soon as the tile lands and the stage is refilled with
 //    the next coil at once (the last warp to release it issues the TMA), so the load of coil
 //    c + 1 overlaps the transforms of coil c.
-// 256 rows: ~39 KB of shared memory and <= 96 registers, five CTAs (20 warps) per SM; 512 rows:
+//  * at 256 rows a thread's 15 stage-2 twiddles W_256^{r t} stay in registers for the whole
+//    kernel (30 shared-memory loads fewer per coil).
+// 256 rows: ~39 KB of shared memory and <= 128 registers, four CTAs (16 warps) per SM; 512 rows:
 // ~77 KB and <= 128 registers, two CTAs (16 warps) per SM.
 constexpr int TX8 = 8;
 
@@ -239,7 +241,7 @@ __device__ __forceinline__ int swz64(int row, int col) {
 __device__ __forceinline__ uint32_t pad_to_512(const void* p) { return (512u - (smem_addr(p) & 511u)) & 511u; }
 
 template <int NY, bool PCG>
-__global__ void __launch_bounds__(TX8 * NY / 16, NY == 256 ? 5 : 2)
+__global__ void __launch_bounds__(TX8 * NY / 16, NY == 256 ? 4 : 2)
 k_apply_A8(const __grid_constant__ CUtensorMap smap8, const float2* __restrict__ p, float2* __restrict__ q,
            const float* __restrict__ maskw, const float2* __restrict__ tw_g, int nx, int nc, float mu, float lam,
            float gam, SliceState* st, Red red) {
@@ -307,6 +309,9 @@ k_apply_A8(const __grid_constant__ CUtensorMap smap8, const float2* __restrict__
         tmem_st32(t_pv, v);
     }
     __syncthreads();
+    float2 twr[15];  // used at 256 rows only
+#pragma unroll
+    for (int r = 1; r < 16; ++r) twr[r - 1] = tw[r * 16 + (t & 15)];
     for (int c = 0; c < nc; ++c) {
         const uint32_t ph = c & 1;
         mbar_wait(&full, ph, red.err, red.wait_limit);
@@ -330,11 +335,13 @@ k_apply_A8(const __grid_constant__ CUtensorMap smap8, const float2* __restrict__
         float2 u[16];
 #pragma unroll
         for (int e = 0; e < 16; ++e) u[e] = cmul(sv[e], make_float2(__uint_as_float(pr[2 * e]), __uint_as_float(pr[2 * e + 1])));
-        fft_bar2<NY, false>(u, t, xbuf, xbuf, idx, tw, gbar);
+        if constexpr (NY == 256) fft256_bar_rtw<false>(u, t, xbuf, idx, twr, gbar);
+        else fft_bar2<NY, false>(u, t, xbuf, xbuf, idx, tw, gbar);
 #pragma unroll
         for (int e = 0; e < 16; ++e) u[e] = cscale2(u[e], mk[t + T * e]);
         gbar();  // the warp's forward reads of its exchange region are done
-        fft_bar2<NY, true>(u, t, xbuf, xbuf, idx, tw, gbar);
+        if constexpr (NY == 256) fft256_bar_rtw<true>(u, t, xbuf, idx, twr, gbar);
+        else fft_bar2<NY, true>(u, t, xbuf, xbuf, idx, tw, gbar);
         // acc += conj(S) u, in two halves of 8 values (16 TMEM columns each)
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
