@@ -46,9 +46,9 @@ HBM_FALLBACK_GBS = 6800.0
 # FP32 lanes per SM (the FP32 CUDA-core peak is SMs x lanes x 2 flops (FMA) x the SM clock)
 FP32_LANES_PER_SM = 128
 # DRAM bytes (read + write) of one q = A p launch (k_apply_A8) over the full 64-slice 256x256x12
-# batch: an ncu capture of a 32-slice launch (232.95 MB read + 11.77 MB written) scaled by the
+# batch: an ncu capture of a 32-slice launch (231.62 MB read + 10.63 MB written) scaled by the
 # slices processed.  Set to None whenever the kernel changes until it is captured again.
-TRAFFIC_K1 = 2 * (232.95e6 + 11.77e6)
+TRAFFIC_K1 = 2 * (231.62e6 + 10.63e6)
 # --prec: (sb_precision, dtype label of the JSON line)
 PRECS = {"fp32": (0, "fp32"), "split-bf16": (1, "bf16x2 split, fp32 accumulate (tensor-core DFT stages)"),
          "split-fp16": (2, "fp16x2 split, fp32 accumulate (tensor-core DFT stages)")}
@@ -125,7 +125,8 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms while active."""
+    """nvidia-smi clocks and throttle reasons sampled every 100 ms while active; only the rows
+    written after start() returns (the timed region) are summarised."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -135,14 +136,25 @@ class ClockSampler:
         self.gpu = gpu_index
         self.proc = None
         self.path = None
+        self.skip = 0
+
+    def _rows_written(self) -> int:
+        with open(self.path) as fh:
+            return sum(1 for _ in fh)
 
     def start(self):
         try:
             fd, self.path = tempfile.mkstemp(suffix=".csv")
             os.close(fd)
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            # nvidia-smi takes a moment to start: wait for its first row, so that the rows written
+            # from here on fall inside the timed region that follows
+            t0 = time.time()
+            while time.time() - t0 < 3.0 and self.proc.poll() is None and self._rows_written() == 0:
+                time.sleep(0.02)
+            self.skip = self._rows_written()
         except Exception:
             self.proc = None
 
@@ -160,6 +172,8 @@ class ClockSampler:
             if len(parts) >= 9:
                 rows.append(parts)
         os.unlink(self.path)
+        if len(rows) > self.skip:  # else keep every row (a region shorter than one interval)
+            rows = rows[self.skip:]
         if not rows:
             return None
         sm = sorted(float(r[1]) for r in rows if r[1].replace(".", "").isdigit())

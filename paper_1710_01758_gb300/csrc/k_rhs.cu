@@ -185,7 +185,9 @@ k_rhs(const __grid_constant__ CUtensorMap smap, const __grid_constant__ CUtensor
 // ---------------------------------------------------------------- 256 rows: k_rhs8
 // The same pass for ny = 256 in the layout of k_apply_A8 (k_applyA.cu): 8 columns per CTA, 128
 // threads, a warp holds two whole columns (16 rows x 2 columns) so the transforms' exchanges are
-// warp-local; x and the data-term accumulator live in tensor memory (64 columns per CTA); the
+// warp-local; x, the data-term accumulator and the coil's sensitivities (between the forward
+// product and the conjugate product) live in tensor memory (128 columns per CTA), and the
+// thread's 15 stage-2 twiddles W_256^{r t} in the registers that this frees; the
 // coil tile and the compact k-space rows (yt, yt1) arrive by TMA with the 64-byte swizzle into
 // one stage each, released as soon as every warp has read them (the sensitivities into
 // registers at the start of the coil, the k-space rows after the forward transform) and refilled
@@ -253,7 +255,7 @@ k_rhs8(const __grid_constant__ CUtensorMap smap8, const __grid_constant__ CUtens
         if (ADDBACK) tma_load_2d(sB + msr * TX8, &y1map8, 2 * x0, (b * nc + c) * ms, &fullB);
     };
 
-    if (w == 0) tmem_alloc(&tmem_s, 64);
+    if (w == 0) tmem_alloc(&tmem_s, 128);
     if (tid == 0) {
         mbar_init(&fullA, 1);
         mbar_init(&emptyA, NW);
@@ -269,8 +271,8 @@ k_rhs8(const __grid_constant__ CUtensorMap smap8, const __grid_constant__ CUtens
         load_S(0);
         load_Y(0);
     }
-    // this warp's TMEM lanes: columns 0-31 hold x, 32-63 the data-term accumulator
-    const uint32_t t_x = tmem_s + ((uint32_t)(32 * w) << 16), t_acc = t_x + 32;
+    // this warp's TMEM lanes: columns 0-31 hold x, 32-63 the data-term accumulator, 64-95 S
+    const uint32_t t_x = tmem_s + ((uint32_t)(32 * w) << 16), t_acc = t_x + 32, t_sv = t_x + 64;
     for (int i = tid; i < NY; i += NT) {
         tw[i] = tw_g[i];
         sl[i] = f.slot[(size_t)b * NY + i];
@@ -292,6 +294,9 @@ k_rhs8(const __grid_constant__ CUtensorMap smap8, const __grid_constant__ CUtens
 #pragma unroll
     for (int e = 0; e < 16; ++e) mb |= (sl[t + T * e] >= 0 ? 1u : 0u) << e;
     const float sc = rsqrtf((float)NY);
+    float2 twr[15];
+#pragma unroll
+    for (int r = 1; r < 16; ++r) twr[r - 1] = tw[r * 16 + t];
     for (int c = 0; c < nc; ++c) {
         const uint32_t ph = c & 1;
         if (c == nc - 1) {  // the epilogue's rows of g, bd (and bd1) into L2
@@ -322,7 +327,16 @@ k_rhs8(const __grid_constant__ CUtensorMap smap8, const __grid_constant__ CUtens
         float2 u[16];
 #pragma unroll
         for (int e = 0; e < 16; ++e) u[e] = cmul(sv[e], make_float2(__uint_as_float(xr[2 * e]), __uint_as_float(xr[2 * e + 1])));
-        fft_bar2<NY, false>(u, t, xbuf, xbuf, idx, tw, gbar);
+        {
+            float v[32];
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+                v[2 * e] = sv[e].x;
+                v[2 * e + 1] = sv[e].y;
+            }
+            tmem_st32(t_sv, v);
+        }
+        fft256_bar_rtw<false>(u, t, xbuf, idx, twr, gbar);
         // on sampled lines: tt = R F S x (unitary scale), yv = y^[j] after the outer update,
         // u <- yv - tt; zero elsewhere.  The warp's two columns go through the exchange region:
         // every thread stores its 16 values, the lanes then walk the compact slots of both columns
@@ -362,13 +376,14 @@ k_rhs8(const __grid_constant__ CUtensorMap smap8, const __grid_constant__ CUtens
             }
         }
         gbar();
-        fft_bar2<NY, true>(u, t, xbuf, xbuf, idx, tw, gbar);
+        fft256_bar_rtw<true>(u, t, xbuf, idx, twr, gbar);
         // racc += conj(S) (sc u), in two halves of 8 values
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            float a[16];
+            float a[16], s16[16];
+            tmem_wait_st();
+            tmem_ld16(t_sv + 16 * h, s16);
             if (c > 0) {
-                tmem_wait_st();
                 tmem_ld16(t_acc + 16 * h, a);
             } else {
 #pragma unroll
@@ -376,7 +391,7 @@ k_rhs8(const __grid_constant__ CUtensorMap smap8, const __grid_constant__ CUtens
             }
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
-                const float2 rr = cfmac(make_float2(a[2 * i], a[2 * i + 1]), sv[8 * h + i], cscale(u[8 * h + i], sc));
+                const float2 rr = cfmac(make_float2(a[2 * i], a[2 * i + 1]), make_float2(s16[2 * i], s16[2 * i + 1]), cscale(u[8 * h + i], sc));
                 a[2 * i] = rr.x;
                 a[2 * i + 1] = rr.y;
             }
@@ -409,7 +424,7 @@ k_rhs8(const __grid_constant__ CUtensorMap smap8, const __grid_constant__ CUtens
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (w == 0) tmem_dealloc(tmem_s, 64);
+    if (w == 0) tmem_dealloc(tmem_s, 128);
     float bb = 0.f, rr = 0.f;
 #pragma unroll
     for (int e = 0; e < 16; ++e) {
