@@ -381,10 +381,19 @@ k_rhs8(const __grid_constant__ CUtensorMap smap8, const __grid_constant__ CUtens
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             float a[16], s16[16];
+            uint32_t ra[16], rs[16];
             tmem_wait_st();
-            tmem_ld16(t_sv + 16 * h, s16);
+            tmem_ld16_issue(t_sv + 16 * h, rs);
+            if (c > 0) tmem_ld16_issue(t_acc + 16 * h, ra);
+            else
+#pragma unroll
+                for (int i = 0; i < 16; ++i) ra[i] = 0u;
+            tmem_ld_wait2(ra, rs);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) s16[i] = __uint_as_float(rs[i]);
             if (c > 0) {
-                tmem_ld16(t_acc + 16 * h, a);
+#pragma unroll
+                for (int i = 0; i < 16; ++i) a[i] = __uint_as_float(ra[i]);
             } else {
 #pragma unroll
                 for (int i = 0; i < 16; ++i) a[i] = 0.f;
@@ -426,30 +435,46 @@ k_rhs8(const __grid_constant__ CUtensorMap smap8, const __grid_constant__ CUtens
     tc_fence_after();
     if (w == 0) tmem_dealloc(tmem_s, 128);
     float bb = 0.f, rr = 0.f;
+    // the rows' g, bd (and bd1) loads are issued EC rows at a time: in one loop with the stores
+    // of bd and r they could not be moved above the previous row's stores (the arrays may alias
+    // as far as the compiler knows), and each row would wait for its loads in turn; 8 rows spill
+    constexpr int EC = 4;
 #pragma unroll
-    for (int e = 0; e < 16; ++e) {
-        const int yy = t + T * e;
-        const size_t gi = img + (size_t)yy * nx + xg;
-        const float2 gv = f.g[gi];
-        const float2 up = xt[swz64(yy == 0 ? NY - 1 : yy - 1, col)];
-        const float2 dn = xt[swz64(yy == NY - 1 ? 0 : yy + 1, col)];
-        const float2 lf = col > 0 ? xt[swz64(yy, col - 1)] : halo[yy];
-        const float2 rt = col < TX8 - 1 ? xt[swz64(yy, col + 1)] : halo[NY + yy];
-        const float tvx = 4.f * xv[e].x - up.x - dn.x - lf.x - rt.x;
-        const float tvy = 4.f * xv[e].y - up.y - dn.y - lf.y - rt.y;
-        float2 bdv = f.bd[gi];
-        if (ADDBACK) {
-            const float2 b1 = f.bd1[gi];
-            bdv = make_float2(0.5f * (racc[e].x + bdv.x + b1.x), 0.5f * (racc[e].y + bdv.y + b1.y));
-            f.bd[gi] = bdv;
+    for (int e0 = 0; e0 < 16; e0 += EC) {
+        float2 gq[EC], bq[EC], b1q[EC];
+#pragma unroll
+        for (int k = 0; k < EC; ++k) {
+            const size_t gi = img + (size_t)(t + T * (e0 + k)) * nx + xg;
+            gq[k] = f.g[gi];
+            bq[k] = f.bd[gi];
+            if (ADDBACK) b1q[k] = f.bd1[gi];
         }
-        const float2 bvec = make_float2(fmaf(mu, bdv.x, gv.x), fmaf(mu, bdv.y, gv.y));
-        float2 rv;
-        rv.x = fmaf(mu, racc[e].x, gv.x) - fmaf(lam, tvx, gam * xv[e].x);
-        rv.y = fmaf(mu, racc[e].y, gv.y) - fmaf(lam, tvy, gam * xv[e].y);
-        r[gi] = rv;
-        bb += cabs2(bvec);
-        rr += cabs2(rv);
+#pragma unroll
+        for (int k = 0; k < EC; ++k) {
+            const int e = e0 + k;
+            const int yy = t + T * e;
+            const size_t gi = img + (size_t)yy * nx + xg;
+            const float2 gv = gq[k];
+            const float2 up = xt[swz64(yy == 0 ? NY - 1 : yy - 1, col)];
+            const float2 dn = xt[swz64(yy == NY - 1 ? 0 : yy + 1, col)];
+            const float2 lf = col > 0 ? xt[swz64(yy, col - 1)] : halo[yy];
+            const float2 rt = col < TX8 - 1 ? xt[swz64(yy, col + 1)] : halo[NY + yy];
+            const float tvx = 4.f * xv[e].x - up.x - dn.x - lf.x - rt.x;
+            const float tvy = 4.f * xv[e].y - up.y - dn.y - lf.y - rt.y;
+            float2 bdv = bq[k];
+            if (ADDBACK) {
+                const float2 b1 = b1q[k];
+                bdv = make_float2(0.5f * (racc[e].x + bdv.x + b1.x), 0.5f * (racc[e].y + bdv.y + b1.y));
+                f.bd[gi] = bdv;
+            }
+            const float2 bvec = make_float2(fmaf(mu, bdv.x, gv.x), fmaf(mu, bdv.y, gv.y));
+            float2 rv;
+            rv.x = fmaf(mu, racc[e].x, gv.x) - fmaf(lam, tvx, gam * xv[e].x);
+            rv.y = fmaf(mu, racc[e].y, gv.y) - fmaf(lam, tvy, gam * xv[e].y);
+            r[gi] = rv;
+            bb += cabs2(bvec);
+            rr += cabs2(rv);
+        }
     }
     double vv[2] = {(double)bb, (double)rr}, tot[2];
     const int np = gridDim.x;

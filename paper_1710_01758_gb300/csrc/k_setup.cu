@@ -42,9 +42,10 @@ __global__ void k_mask_lines(const uint8_t* __restrict__ mask, int nx, int* line
     }
 }
 
+// src == dst transforms in place (each thread writes back only the values it read)
 template <int NX, bool INV>
 __global__ void __launch_bounds__(RY * NX / 16)
-k_fft_rows(float2* __restrict__ data, int nrows_total, const float2* __restrict__ tw_g) {
+k_fft_rows(const float2* src, float2* dst, int nrows_total, const float2* __restrict__ tw_g) {
     constexpr int T = NX / 16;
     constexpr int NT = RY * T;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -57,12 +58,12 @@ k_fft_rows(float2* __restrict__ data, int nrows_total, const float2* __restrict_
     const bool ok = grow < nrows_total;
     const size_t base = (size_t)(ok ? grow : 0) * NX;
 #pragma unroll
-    for (int e = 0; e < 16; ++e) v[e] = data[base + t + T * e];
+    for (int e = 0; e < 16; ++e) v[e] = src[base + t + T * e];
     __syncthreads();
     fft<NX, INV>(v, t, buf, RowIdx<NX>{row}, tw);
     if (ok)
 #pragma unroll
-        for (int e = 0; e < 16; ++e) data[base + t + T * e] = v[e];
+        for (int e = 0; e < 16; ++e) dst[base + t + T * e] = v[e];
 }
 
 template <int NY, bool INV>
@@ -86,16 +87,47 @@ k_fft_cols(float2* __restrict__ data, int nx, const float2* __restrict__ tw_g) {
     for (int e = 0; e < 16; ++e) data[img + (size_t)(t + T * e) * nx + x] = v[e];
 }
 
-__global__ void k_coil_power(const float2* __restrict__ spec, float2* __restrict__ g, int n, int nc, double inv_n2) {
+// (a sum of nc non-negative FP32 terms: relative error below nc * 2^-24, no cancellation)
+__global__ void k_coil_power(const float2* __restrict__ spec, float2* __restrict__ g, int n, int nc, float inv_n2) {
     const int b = blockIdx.y;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        double acc = 0.0;
-        for (int c = 0; c < nc; ++c) {
-            const float2 v = spec[((size_t)b * nc + c) * n + i];
-            acc += (double)v.x * v.x + (double)v.y * v.y;
-        }
-        g[(size_t)b * n + i] = make_float2((float)(acc * inv_n2), 0.f);
+        float acc = 0.f;
+        for (int c = 0; c < nc; ++c) acc += cabs2(spec[((size_t)b * nc + c) * n + i]);
+        g[(size_t)b * n + i] = make_float2(acc * inv_n2, 0.f);
     }
+}
+
+// 2D planes: the column DFTs of every coil's row-transformed sensitivities and the coil power
+// sum in one pass (the coil spectra are never written): per column tile of a slice, coil by coil,
+// g += |DFT_y(column)|^2, then g / N^2
+template <int NY>
+__global__ void __launch_bounds__(TX * NY / 16)
+k_coil_power_cols(const float2* __restrict__ spec, float2* __restrict__ g, int nx, int nc, float inv_n2,
+                  const float2* __restrict__ tw_g) {
+    constexpr int T = NY / 16;
+    constexpr int NT = TX * T;
+    extern __shared__ __align__(128) unsigned char smem[];
+    float2* buf = reinterpret_cast<float2*>(smem);
+    float2* tw = buf + NY * TX;
+    const int tid = threadIdx.x, col = tid % TX, t = tid / TX;
+    const int x = blockIdx.x * TX + col, b = blockIdx.y;
+    for (int i = tid; i < NY; i += NT) tw[i] = tw_g[i];
+    float acc[16];
+#pragma unroll
+    for (int e = 0; e < 16; ++e) acc[e] = 0.f;
+    for (int c = 0; c < nc; ++c) {
+        const size_t img = ((size_t)b * nc + c) * NY * nx;
+        float2 v[16];
+#pragma unroll
+        for (int e = 0; e < 16; ++e) v[e] = spec[img + (size_t)(t + T * e) * nx + x];
+        __syncthreads();  // the twiddles are in place; the previous coil's exchange reads are done
+        fft<NY, false>(v, t, buf, ColIdx{col}, tw);
+#pragma unroll
+        for (int e = 0; e < 16; ++e) acc[e] += cabs2(v[e]);
+    }
+    const size_t out = (size_t)b * NY * nx;
+#pragma unroll
+    for (int e = 0; e < 16; ++e) g[out + (size_t)(t + T * e) * nx + x] = make_float2(acc[e] * inv_n2, 0.f);
 }
 
 __global__ void k_mask_to_complex(const uint8_t* __restrict__ mask, float2* __restrict__ out, size_t n) {
@@ -126,7 +158,9 @@ __global__ void k_form_k(const float2* __restrict__ kc_raw, int nx, int ny, int 
         k[(size_t)b * n + i] = v;
         local = fmaxf(local, v);
     }
-    atomicMax(kmax + b, __float_as_uint(fmaxf(local, 0.f)));
+    // one atomic per warp (every thread of the block reaches this point)
+    const unsigned wmax = __reduce_max_sync(0xffffffffu, __float_as_uint(fmaxf(local, 0.f)));
+    if ((threadIdx.x & 31) == 0) atomicMax(kmax + b, wmax);
 }
 
 // clamp k below at 1e-12 max(k) and store 1/(k N), the scale that turns the unnormalised
@@ -165,18 +199,29 @@ __global__ void k_jacobi_diag(const float2* __restrict__ sens, const float* __re
 }
 
 template <int NX>
-cudaError_t fft_rows_n(int ny, int nimg, float2* data, const float2* tw, bool inv, cudaStream_t s) {
+cudaError_t fft_rows_n(int ny, int nimg, const float2* src, float2* dst, const float2* tw, bool inv, cudaStream_t s) {
     const int rows = ny * nimg;
     const dim3 grid((rows + RY - 1) / RY), block(RY * NX / 16);
     const size_t sm = (RY * (NX + NX / 16) + NX) * sizeof(float2);
     cudaError_t e;
     if (inv) {
         if (sm > 48 * 1024 && (e = set_smem_limit(k_fft_rows<NX, true>, (int)sm)) != cudaSuccess) return e;
-        k_fft_rows<NX, true><<<grid, block, sm, s>>>(data, rows, tw);
+        k_fft_rows<NX, true><<<grid, block, sm, s>>>(src, dst, rows, tw);
     } else {
         if (sm > 48 * 1024 && (e = set_smem_limit(k_fft_rows<NX, false>, (int)sm)) != cudaSuccess) return e;
-        k_fft_rows<NX, false><<<grid, block, sm, s>>>(data, rows, tw);
+        k_fft_rows<NX, false><<<grid, block, sm, s>>>(src, dst, rows, tw);
     }
+    return cudaGetLastError();
+}
+
+template <int NY>
+cudaError_t coil_power_cols_n(const Dims& d, const float2* spec, float2* g, const float2* tw, cudaStream_t s) {
+    const dim3 grid(d.nx / TX, d.nb), block(TX * NY / 16);
+    const size_t sm = (NY * TX + NY) * sizeof(float2);
+    cudaError_t e;
+    if (sm > 48 * 1024 && (e = set_smem_limit(k_coil_power_cols<NY>, (int)sm)) != cudaSuccess) return e;
+    const float n = (float)d.nx * (float)NY;
+    k_coil_power_cols<NY><<<grid, block, sm, s>>>(spec, g, d.nx, d.nc, 1.f / (n * n), tw);
     return cudaGetLastError();
 }
 
@@ -207,17 +252,37 @@ cudaError_t launch_mask_lines(const Dims& d, const uint8_t* mask, int* line_val,
     return cudaGetLastError();
 }
 
-cudaError_t launch_fft_rows(int nx, int ny, int nimg, float2* data, const float2* tw_x, bool inv, cudaStream_t s) {
+cudaError_t launch_fft_rows_from(int nx, int ny, int nimg, const float2* src, float2* dst, const float2* tw_x,
+                                 bool inv, cudaStream_t s) {
     switch (nx) {
-        case 32: return fft_rows_n<32>(ny, nimg, data, tw_x, inv, s);
-        case 64: return fft_rows_n<64>(ny, nimg, data, tw_x, inv, s);
-        case 128: return fft_rows_n<128>(ny, nimg, data, tw_x, inv, s);
-        case 256: return fft_rows_n<256>(ny, nimg, data, tw_x, inv, s);
-        case 512: return fft_rows_n<512>(ny, nimg, data, tw_x, inv, s);
-        case 192: return fft_rows_n<192>(ny, nimg, data, tw_x, inv, s);
-        case 224: return fft_rows_n<224>(ny, nimg, data, tw_x, inv, s);
-        case 320: return fft_rows_n<320>(ny, nimg, data, tw_x, inv, s);
-        case 384: return fft_rows_n<384>(ny, nimg, data, tw_x, inv, s);
+        case 32: return fft_rows_n<32>(ny, nimg, src, dst, tw_x, inv, s);
+        case 64: return fft_rows_n<64>(ny, nimg, src, dst, tw_x, inv, s);
+        case 128: return fft_rows_n<128>(ny, nimg, src, dst, tw_x, inv, s);
+        case 256: return fft_rows_n<256>(ny, nimg, src, dst, tw_x, inv, s);
+        case 512: return fft_rows_n<512>(ny, nimg, src, dst, tw_x, inv, s);
+        case 192: return fft_rows_n<192>(ny, nimg, src, dst, tw_x, inv, s);
+        case 224: return fft_rows_n<224>(ny, nimg, src, dst, tw_x, inv, s);
+        case 320: return fft_rows_n<320>(ny, nimg, src, dst, tw_x, inv, s);
+        case 384: return fft_rows_n<384>(ny, nimg, src, dst, tw_x, inv, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_fft_rows(int nx, int ny, int nimg, float2* data, const float2* tw_x, bool inv, cudaStream_t s) {
+    return launch_fft_rows_from(nx, ny, nimg, data, data, tw_x, inv, s);
+}
+
+cudaError_t launch_coil_power_cols(const Dims& d, const float2* spec, float2* g, const float2* tw_y, cudaStream_t s) {
+    switch (d.ny) {
+        case 32: return coil_power_cols_n<32>(d, spec, g, tw_y, s);
+        case 64: return coil_power_cols_n<64>(d, spec, g, tw_y, s);
+        case 128: return coil_power_cols_n<128>(d, spec, g, tw_y, s);
+        case 256: return coil_power_cols_n<256>(d, spec, g, tw_y, s);
+        case 512: return coil_power_cols_n<512>(d, spec, g, tw_y, s);
+        case 192: return coil_power_cols_n<192>(d, spec, g, tw_y, s);
+        case 224: return coil_power_cols_n<224>(d, spec, g, tw_y, s);
+        case 320: return coil_power_cols_n<320>(d, spec, g, tw_y, s);
+        case 384: return coil_power_cols_n<384>(d, spec, g, tw_y, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -239,7 +304,7 @@ cudaError_t launch_fft_cols(int nx, int ny, int nimg, float2* data, const float2
 
 cudaError_t launch_coil_power(const Dims& d, const float2* data, float2* g, cudaStream_t s) {
     const int n = d.nx * d.ny;
-    const double inv_n2 = 1.0 / ((double)n * (double)n);
+    const float inv_n2 = (float)(1.0 / ((double)n * (double)n));
     k_coil_power<<<dim3(elem_blocks(n), d.nb), 256, 0, s>>>(data, g, n, d.nc, inv_n2);
     return cudaGetLastError();
 }

@@ -162,11 +162,17 @@ cudaError_t launch_mask_lines(const Dims& d, const uint8_t* mask, int* line_val,
 // [nbatch_images][ny][nx] arrays, in place; inv selects the sign.
 cudaError_t launch_fft_rows(int nx, int ny, int nimg, float2* data, const float2* tw_x, bool inv,
                             cudaStream_t s);
+// the same row transform from src into dst (src == dst: in place)
+cudaError_t launch_fft_rows_from(int nx, int ny, int nimg, const float2* src, float2* dst, const float2* tw_x,
+                                 bool inv, cudaStream_t s);
 cudaError_t launch_fft_cols(int nx, int ny, int nimg, float2* data, const float2* tw_y, bool inv,
                             cudaStream_t s);
 // g[b] = sum_c |data[b][c]|^2 / N^2 (data: [nb][nc][N], the DFTs of the sensitivities);
 // out as complex (imaginary part 0) for the next FFT.
 cudaError_t launch_coil_power(const Dims& d, const float2* data, float2* g, cudaStream_t s);
+// 2D planes: g[b] = sum_c |DFT_y(spec[b][c])|^2 / N^2 with spec the row-transformed sensitivities
+// (the column transforms and the coil sum in one pass; spec is read only).
+cudaError_t launch_coil_power_cols(const Dims& d, const float2* spec, float2* g, const float2* tw_y, cudaStream_t s);
 // Pack the mask as complex: out[b][i] = (mask != 0, 0).
 cudaError_t launch_mask_to_complex(const Dims& d, const uint8_t* mask, float2* out, cudaStream_t s);
 // prod[b][i] = R[b][i] * conj(G[b][i])  (the spectra of r and g), in place in R.

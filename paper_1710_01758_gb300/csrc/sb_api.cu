@@ -1051,7 +1051,6 @@ sb_status sb_set_mask(sb_plan pl, const uint8_t* d_mask) {
     // 2. k = mu k_c + lam k_d + gam by FFTs (Eq. Kdiag, Eq. diagonalelements)
     float2 *spec = pl->spec, *gb = pl->gb, *rb = pl->rb;
     const int nimg_c = d.nb * d.nc;
-    SB_CK(pl, cudaMemcpyAsync(spec, pl->sens, sizeof(float2) * nb * d.nc * n, cudaMemcpyDeviceToDevice, s));
     // unnormalised 2D / 3D DFT of nimg images: rows (x), per-plane columns (y), z columns
     const int nyp = pl->ny_plane, nz = pl->nz;
     const Dims dp{d.nx, nyp, d.nc, d.nb};  // plane dims
@@ -1062,8 +1061,15 @@ sb_status sb_set_mask(sb_plan pl, const uint8_t* d_mask) {
         return SB_OK;
     };
     auto build_k = [&]() -> sb_status {
-        if (sb_status e2 = fft_nd(spec, nimg_c, false)) return e2;
-        SB_LAUNCH(ex, SB_KCLASS_OTHER, 1, launch_coil_power(d, spec, gb, s));
+        if (nz == 1) {  // rows out of place from the sensitivities, then columns + coil sum in one pass
+            SB_LAUNCH(ex, SB_KCLASS_OTHER, 1,
+                      launch_fft_rows_from(d.nx, d.ny, nimg_c, pl->sens, spec, pl->tw_x, false, s));
+            SB_LAUNCH(ex, SB_KCLASS_OTHER, 1, launch_coil_power_cols(d, spec, gb, pl->tw_y, s));
+        } else {
+            SB_CK(pl, cudaMemcpyAsync(spec, pl->sens, sizeof(float2) * nb * d.nc * n, cudaMemcpyDeviceToDevice, s));
+            if (sb_status e2 = fft_nd(spec, nimg_c, false)) return e2;
+            SB_LAUNCH(ex, SB_KCLASS_OTHER, 1, launch_coil_power(d, spec, gb, s));
+        }
         SB_LAUNCH(ex, SB_KCLASS_OTHER, 1, launch_mask_to_complex(d, d_mask, rb, s));
         if (sb_status e2 = fft_nd(gb, d.nb, false)) return e2;
         if (sb_status e2 = fft_nd(rb, d.nb, false)) return e2;
