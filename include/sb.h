@@ -139,7 +139,9 @@ typedef struct {
     int maxit;           /* iteration cap (>= 1) */
     int fixed_iters;     /* > 0: run exactly this many iterations, no tolerance test */
     sb_precond precond;  /* SB_PRECOND_CIRCULANT (Eq. precon), SB_PRECOND_NONE (plain CG) or
-                            SB_PRECOND_JACOBI (diag(A)^{-1}, the comparison of the Results) */
+                            SB_PRECOND_JACOBI (diag(A)^{-1}, the comparison of the Results; its
+                            weights are built on the plan stream by the first Jacobi solve after
+                            sb_set_coils / sb_set_mask) */
 } sb_pcg_opts;
 
 typedef struct {

@@ -7,6 +7,8 @@
 // the DFT of the first row of D_x^H D_x + D_y^H D_y, 4 - 2 cos(2 pi kx/nx) - 2 cos(2 pi ky/ny),
 // and k_w = 1.  The generic row / column FFT kernels here reuse the register-resident Stockham
 // transform of common.cuh.
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -141,26 +143,28 @@ __global__ void k_mul_conj(float2* __restrict__ R, const float2* __restrict__ G,
 }
 
 // k = mu kc + lam kd + gam (first pass) and its per-slice maximum (non-negative floats compare
-// as integers)
-// (volumes: k_d = 6 - 2 cos - 2 cos - 2 cos; with nz = 1 the z term vanishes and this is the 2D
-// formula)
-__global__ void k_form_k(const float2* __restrict__ kc_raw, int nx, int ny, int nz, float mu, float lam, float gam,
-                         float inv_n, float* __restrict__ k, unsigned* __restrict__ kmax) {
+// as integers); kd is the geometry's table (volumes: k_d = 6 - 2 cos - 2 cos - 2 cos; with nz = 1
+// the z term is 2 and this is the 2D formula), computed once per plan on the host
+__global__ void k_form_k(const float2* __restrict__ kc_raw, const float* __restrict__ kd, int n, float mu, float lam,
+                         float gam, float inv_n, float* __restrict__ k, unsigned* __restrict__ kmax) {
     const int b = blockIdx.y;
-    const int n = nx * ny * nz;
     float local = 0.f;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const int kx = i % nx, ky = (i / nx) % ny, kz = i / (nx * ny);
-        const float kd = 6.f - 2.f * cospif(2.f * kx / nx) - 2.f * cospif(2.f * ky / ny) -
-                         2.f * cospif(2.f * kz / nz);
         const float kc = kc_raw[(size_t)b * n + i].x * inv_n;
-        const float v = fmaf(mu, kc, fmaf(lam, kd, gam));
+        const float v = fmaf(mu, kc, fmaf(lam, kd[i], gam));
         k[(size_t)b * n + i] = v;
         local = fmaxf(local, v);
     }
-    // one atomic per warp (every thread of the block reaches this point)
-    const unsigned wmax = __reduce_max_sync(0xffffffffu, __float_as_uint(fmaxf(local, 0.f)));
-    if ((threadIdx.x & 31) == 0) atomicMax(kmax + b, wmax);
+    // one atomic per block: atomics on one address serialise in L2 (one per warp over a 64-slice
+    // batch, 2048 per slice, took 90 us), so the warps' maxima meet in shared memory first
+    __shared__ unsigned wmax[32];
+    const unsigned m = __reduce_max_sync(0xffffffffu, __float_as_uint(fmaxf(local, 0.f)));
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const unsigned v = __reduce_max_sync(0xffffffffu, threadIdx.x < (blockDim.x >> 5) ? wmax[threadIdx.x] : 0u);
+        if (threadIdx.x == 0) atomicMax(kmax + b, v);
+    }
 }
 
 // clamp k below at 1e-12 max(k) and store 1/(k N), the scale that turns the unnormalised
@@ -329,13 +333,14 @@ cudaError_t launch_jacobi_diag(const Dims& d, int nz, const float2* sens, const 
     return cudaGetLastError();
 }
 
-cudaError_t launch_finish_k(const Dims& d, int nz, const float2* kc_raw, float mu, float lam, float gam, float* k,
-                            float* invk, unsigned* kmax, cudaStream_t s) {
+cudaError_t launch_finish_k(const Dims& d, int nz, const float2* kc_raw, const float* kd, float mu, float lam,
+                            float gam, float* k, float* invk, unsigned* kmax, cudaStream_t s) {
     const int n = d.nx * d.ny * nz;
     cudaError_t e = cudaMemsetAsync(kmax, 0, sizeof(unsigned) * d.nb, s);
     if (e != cudaSuccess) return e;
     const dim3 grid(elem_blocks(n), d.nb);
-    k_form_k<<<grid, 256, 0, s>>>(kc_raw, d.nx, d.ny, nz, mu, lam, gam, 1.f / n, k, kmax);
+    // at most 64 blocks per slice for the maximum (each block one atomic; threads loop)
+    k_form_k<<<dim3(std::min(elem_blocks(n), 64u), d.nb), 256, 0, s>>>(kc_raw, kd, n, mu, lam, gam, 1.f / n, k, kmax);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_clamp_invert<<<grid, 256, 0, s>>>(k, invk, n, kmax);
     return cudaGetLastError();

@@ -177,10 +177,10 @@ cudaError_t launch_coil_power_cols(const Dims& d, const float2* spec, float2* g,
 cudaError_t launch_mask_to_complex(const Dims& d, const uint8_t* mask, float2* out, cudaStream_t s);
 // prod[b][i] = R[b][i] * conj(G[b][i])  (the spectra of r and g), in place in R.
 cudaError_t launch_mul_conj(const Dims& d, float2* R, const float2* G, cudaStream_t s);
-// k = mu Re(kc)/N + lam k_d + gam, clamped; invk = 1 / (k N).
-// kmax: nb words of scratch.
-cudaError_t launch_finish_k(const Dims& d, int nz, const float2* kc_unscaled, float mu, float lam, float gam,
-                            float* k, float* invk, unsigned* kmax, cudaStream_t s);
+// k = mu Re(kc)/N + lam k_d + gam, clamped; invk = 1 / (k N).  kd: [N] k_d of the geometry
+// (shared by the slices); kmax: nb words of scratch.
+cudaError_t launch_finish_k(const Dims& d, int nz, const float2* kc_unscaled, const float* kd, float mu, float lam,
+                            float gam, float* k, float* invk, unsigned* kmax, cudaStream_t s);
 
 // ------------------------------------------------------------------ Split Bregman (k_sb.cu)
 struct SbFields {

@@ -140,7 +140,9 @@ struct sb_plan_s {
     int ms = 0;
     float* k = nullptr;      // [nb][N]
     float* invk = nullptr;   // [nb][N]
+    float* kd = nullptr;     // [N] k_d of the geometry (the same for every slice)
     float* jw = nullptr;     // [nb][N] 1 / diag(A) (Jacobi)
+    bool jw_ready = false;   // jw matches the current coils and mask (built by the first Jacobi solve)
     float2 *r = nullptr, *p = nullptr, *q = nullptr, *tb = nullptr;
     float2* bx[2] = {nullptr, nullptr};
     float2* by[2] = {nullptr, nullptr};
@@ -838,6 +840,7 @@ sb_status sb_plan_create(const sb_plan_desc* desc, void* cuda_stream, sb_plan* o
     ALLOC(pl->slot, nb * d.ny * nz);
     ALLOC(pl->k, nb * n);
     ALLOC(pl->invk, nb * n);
+    ALLOC(pl->kd, n);
     ALLOC(pl->r, nb * n);
     ALLOC(pl->p, nb * n);
     ALLOC(pl->q, nb * n);
@@ -857,6 +860,21 @@ sb_status sb_plan_create(const sb_plan_desc* desc, void* cuda_stream, sb_plan* o
         return bail("cudaMemcpy twiddles");
     if ((e = cudaMemcpy(pl->tw_z, tz.data(), sizeof(float2) * nz, cudaMemcpyHostToDevice)) != cudaSuccess)
         return bail("cudaMemcpy twiddles");
+    {  // k_d = 2 ndim - 2 cos(2 pi kx / nx) - 2 cos(2 pi ky / ny) (- 2 cos(2 pi kz / nz)), in double
+        auto c2 = [](int len) {
+            std::vector<double> c(len);
+            for (int m = 0; m < len; ++m) c[m] = 2.0 * std::cos(2.0 * M_PI * m / len);
+            return c;
+        };
+        const std::vector<double> cx = c2(d.nx), cy = c2(d.ny), cz = c2(nz);
+        std::vector<float> hk(n);
+        for (int z = 0; z < nz; ++z)
+            for (int y = 0; y < d.ny; ++y)
+                for (int x = 0; x < d.nx; ++x)
+                    hk[((size_t)z * d.ny + y) * d.nx + x] = (float)(6.0 - cx[x] - cy[y] - cz[z]);
+        if ((e = cudaMemcpy(pl->kd, hk.data(), sizeof(float) * n, cudaMemcpyHostToDevice)) != cudaSuccess)
+            return bail("cudaMemcpy k_d");
+    }
     if (pl->tw_full) {
         std::vector<float2> tf(d.ny);
         for (int m = 0; m < d.ny; ++m) {
@@ -901,7 +919,7 @@ sb_status sb_plan_destroy(sb_plan pl) {
     if (pl->stream) cudaStreamSynchronize(pl->stream);
     else cudaDeviceSynchronize();
     for (void* p : {(void*)pl->tw_x, (void*)pl->tw_y, (void*)pl->maskw, (void*)pl->slot, (void*)pl->lines,
-                    (void*)pl->k, (void*)pl->invk, (void*)pl->r, (void*)pl->p, (void*)pl->q, (void*)pl->tb,
+                    (void*)pl->k, (void*)pl->invk, (void*)pl->kd, (void*)pl->r, (void*)pl->p, (void*)pl->q, (void*)pl->tb,
                     (void*)pl->bx[0], (void*)pl->bx[1], (void*)pl->by[0], (void*)pl->by[1], (void*)pl->bw,
                     (void*)pl->g, (void*)pl->bd, (void*)pl->bd1, (void*)pl->yt, (void*)pl->yt1, (void*)pl->st,
                     (void*)pl->part, (void*)pl->counter, (void*)pl->kmax, (void*)pl->derr, (void*)pl->spec,
@@ -964,6 +982,7 @@ sb_status sb_set_coils(sb_plan pl, const void* d_sens) {
     if (!ok) return fail(pl, SB_ERR_CUDA, "cuTensorMapEncodeTiled failed for the sensitivities");
     pl->sens = static_cast<const float2*>(d_sens);
     pl->have_coils = true;
+    pl->jw_ready = false;
     pl->have_mask = false;  // k depends on the coils: rebuilt by sb_set_mask
     return SB_OK;
 }
@@ -1076,11 +1095,9 @@ sb_status sb_set_mask(sb_plan pl, const uint8_t* d_mask) {
         SB_LAUNCH(ex, SB_KCLASS_OTHER, 1, launch_mul_conj(d, rb, gb, s));
         if (sb_status e2 = fft_nd(rb, d.nb, true)) return e2;
         SB_LAUNCH(ex, SB_KCLASS_OTHER, 2,
-                  launch_finish_k(dp, nz, rb, (float)pl->d.mu, (float)pl->d.lambda, (float)pl->d.gamma, pl->k,
+                  launch_finish_k(dp, nz, rb, pl->kd, (float)pl->d.mu, (float)pl->d.lambda, (float)pl->d.gamma, pl->k,
                                   pl->invk, pl->kmax, s));
-        SB_LAUNCH(ex, SB_KCLASS_OTHER, 1,
-                  launch_jacobi_diag(dp, nz, pl->sens, pl->maskw, (float)pl->d.mu, (float)pl->d.lambda,
-                                     (float)pl->d.gamma, pl->jw, s));
+        pl->jw_ready = false;  // the Jacobi weights are built by the first solve that uses them
         return SB_OK;
     };
     if ((st = build_k()) != SB_OK) return fail(pl, st, ex.err);
@@ -1175,9 +1192,23 @@ sb_status sb_apply_precond(sb_plan pl, const void* d_r, void* d_z) {
     return st == SB_OK ? st : fail(pl, st, ex.err);
 }
 
+// the Jacobi weights 1 / diag(A) for the current coils and mask, on the plan stream before the
+// solve's work (only solves that ask for the Jacobi preconditioner need them)
+sb_status ensure_jacobi(sb_plan pl, int precond) {
+    if (precond != SB_PRECOND_JACOBI || pl->jw_ready) return SB_OK;
+    Exec& ex = pl->whole;
+    const Dims dp{pl->dims.nx, pl->ny_plane, pl->dims.nc, pl->dims.nb};
+    SB_LAUNCH(ex, SB_KCLASS_OTHER, 1,
+              launch_jacobi_diag(dp, pl->nz, pl->sens, pl->maskw, (float)pl->d.mu, (float)pl->d.lambda,
+                                 (float)pl->d.gamma, pl->jw, ex.s));
+    pl->jw_ready = true;
+    return SB_OK;
+}
+
 sb_status sb_pcg_solve(sb_plan pl, const void* d_b, void* d_x, const sb_pcg_opts* o, sb_pcg_result* h_results) {
     if (sb_status s = check_ready(pl)) return s;
     if (sb_status s = check_opts(pl, o)) return s;
+    if (sb_status s = ensure_jacobi(pl, o->precond)) return s;
     if (!d_b || !d_x || d_b == d_x) return fail(pl, SB_ERR_INVALID_ARG, "need distinct non-null b and x");
     float2* x_full = static_cast<float2*>(d_x);
     const float2* b_full = static_cast<const float2*>(d_b);
@@ -1205,6 +1236,7 @@ sb_status sb_split_bregman(sb_plan pl, const void* d_y, void* d_x, const sb_sb_o
         return fail(pl, SB_ERR_INVALID_ARG, "the image buffer must be 16-byte aligned");
     if (o->n_outer < 1 || o->n_inner < 1) return fail(pl, SB_ERR_INVALID_ARG, "n_outer and n_inner must be >= 1");
     if (sb_status s = check_opts(pl, &o->pcg)) return s;
+    if (sb_status s = ensure_jacobi(pl, o->pcg.precond)) return s;
     if (!pl->passes() && (pl->ms > 256 || rhs_smem_bytes(pl->dims.ny, pl->ms) > 227 * 1024))
         return fail(pl, SB_ERR_UNSUPPORTED, "too many sampled lines for the shared-memory pipeline of this size");
     const int nsolve = o->n_outer * o->n_inner;
