@@ -138,6 +138,40 @@ def test_pcg_fixed_iterations(torch, sbm, kind):
         assert rel(xg[i], ref.x) <= IMG_TOL
 
 
+def test_jacobi_weights_follow_new_coils_and_mask(torch, sbm):
+    """The Jacobi weights are built by the first Jacobi solve after sb_set_mask: a solve after
+    new coils (not normalised, so diag(A) changes) and after a new mask must use the new
+    weights, checked against the oracle's Jacobi PCG each time."""
+    nx, ny, nc, nb = 128, 128, 4, 2
+    sens, mask, rng = problem(nx, ny, nc, nb, seed=29)
+    mu, lam, gam = 1.0, 0.05, 0.05
+    plan = make_plan(sbm, torch, sens, mask, mu, lam, gam)
+    b = synth.random_complex((nb, ny, nx), rng)
+    yy, xx = np.mgrid[0:ny, 0:nx]
+    gain = 1.0 + 0.8 * np.cos(2 * np.pi * xx / nx) * np.sin(2 * np.pi * yy / ny)  # |S| no longer normalised
+    sens2 = sens * gain
+    mask2 = np.stack([synth.line_mask(ny, nx, 3.0, 8, rng) for _ in range(nb)])
+
+    def check(s, m):
+        xd = torch.zeros((nb, ny, nx), dtype=torch.complex64, device="cuda")
+        st, res = plan.pcg_solve(to_dev(torch, b), xd, fixed_iters=10, precond=sbm.SB_PRECOND_JACOBI)
+        assert st == sbm.SB_OK and all(r[0] == 10 for r in res)
+        xg = xd.cpu().numpy()
+        for i in range(nb):
+            A = lambda v: operators.apply_A(v, s[i], m[i], mu, lam, gam, 2)  # noqa: E731
+            M = oracle_M("jacobi", s[i], m[i], mu, lam, gam, None)
+            ref = pcg.pcg(A, b[i], np.zeros((ny, nx), complex), M, fixed_iters=10)
+            assert rel(xg[i], ref.x) <= IMG_TOL
+
+    check(sens, mask)
+    s2 = to_dev(torch, sens2)
+    plan.set_coils(s2)  # new coils need sb_set_mask again before a solve (k depends on both)
+    plan.set_mask(torch.from_numpy(mask).cuda())
+    check(sens2, mask)
+    plan.set_mask(torch.from_numpy(mask2).cuda())
+    check(sens2, mask2)
+
+
 @pytest.mark.parametrize("kind", ["circulant", "none", "jacobi"])
 def test_pcg_tolerance_iteration_counts(torch, sbm, kind):
     nx, ny, nc, nb = 256, 256, 8, 2
