@@ -299,6 +299,47 @@ __device__ __forceinline__ void fft_3stage_bar(float2 (&v)[16], int t, float2* b
     }
 }
 
+// fft_3stage_bar for N = 512 (32 threads per transform) with the thread's stage-2 twiddles in
+// registers, twr[r - 1] = W_256^{r (t mod 16)} for r = 1 .. 15
+template <bool INV, class Idx, class Bar>
+__device__ __forceinline__ void fft512_bar_rtw(float2 (&v)[16], int t, float2* buf, Idx idx, const float2* tw,
+                                               const float2 (&twr)[15], Bar bar) {
+    constexpr int T = 32;
+    dft16<INV>(v);
+#pragma unroll
+    for (int r = 0; r < 16; ++r) buf[idx(16 * t + r)] = v[r];
+    bar();
+    {
+        const int k = t & 15;
+        float2 a[16];
+#pragma unroll
+        for (int r = 0; r < 16; ++r) a[r] = buf[idx(t + T * r)];
+#pragma unroll
+        for (int r = 1; r < 16; ++r) {
+            float2 w = twr[r - 1];
+            if (INV) w.y = -w.y;
+            a[r] = cmul(a[r], w);
+        }
+        dft16<INV>(a);
+        bar();  // every stage-2 read is done before the stage-2 writes
+        const int base = (t >> 4) * 256 + k;
+#pragma unroll
+        for (int r = 0; r < 16; ++r) buf[idx(base + 16 * r)] = a[r];
+    }
+    bar();
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+        const int j = t + T * m;
+        float2 a0 = buf[idx(j)], a1 = buf[idx(j + 256)];
+        float2 w = tw[256 + j];
+        if (INV) w.y = -w.y;
+        a1 = cmul(a1, w);
+        dft2<INV>(a0, a1);
+        v[m] = a0;
+        v[m + 8] = a1;
+    }
+}
+
 // ------------------------------------------------------------------ lengths 16 x {12, 14, 20, 24}
 // cos and sin of 2 pi m / R for the odd radices (values of the functions, to float precision)
 template <int R> __host__ __device__ constexpr float cos_r(int m);

@@ -219,17 +219,18 @@ k_apply_A(const __grid_constant__ CUtensorMap smap, const float2* __restrict__ p
 //    whole columns, 16 rows x 2 columns; 256 threads at 512 rows: a warp is one column), so the
 //    transforms' exchanges are warp-local;
 //  * its p values and the coil accumulator live in tensor memory (TMEM, 32-bit columns of the
-//    thread's lane; warps w and w + 4 share lanes), one tcgen05.ld / tcgen05.st per 16 values;
-//    at 256 rows the coil's 16 sensitivities are parked there too between the forward product
-//    and the conjugate product (128 columns per CTA: p, accumulator, S);
+//    thread's lane; warps w and w + 4 share lanes and take 96-column ranges 96 (w / 4) apart),
+//    one tcgen05.ld / tcgen05.st per 16 values; the coil's 16 sensitivities are parked there too
+//    between the forward product and the conjugate product (p, accumulator, S: 128 columns per
+//    CTA at 256 rows, 256 at 512);
 //  * the coil tile (ny rows x 8 columns, 64-byte TMA swizzle) has ONE stage: every thread copies
 //    its 16 sensitivities to registers as soon as the tile lands and the stage is refilled with
 //    the next coil at once (the last warp to release it issues the TMA), so the load of coil
 //    c + 1 overlaps the transforms of coil c.
-//  * at 256 rows a thread's 15 stage-2 twiddles W_256^{r t} stay in registers for the whole
-//    kernel (30 shared-memory loads fewer per coil), in the registers that parking S frees.
+//  * a thread's 15 stage-2 twiddles W_256^{r (t mod 16)} stay in registers for the whole kernel
+//    (30 shared-memory loads fewer per coil), in the registers that parking S frees.
 // 256 rows: ~39 KB of shared memory and <= 128 registers, four CTAs (16 warps) per SM, 4 x 128
-// TMEM columns; 512 rows: ~77 KB and <= 128 registers, two CTAs (16 warps) per SM.
+// TMEM columns; 512 rows: ~77 KB and <= 128 registers, two CTAs (16 warps) per SM, 2 x 256.
 constexpr int TX8 = 8;
 
 // float2 index of (row, col) in an 8-column tile written by TMA with the 64-byte swizzle
@@ -249,7 +250,7 @@ k_apply_A8(const __grid_constant__ CUtensorMap smap8, const float2* __restrict__
            float gam, SliceState* st, Red red) {
     static_assert(NY == 256 || NY == 512, "16 or 32 threads per column");
     constexpr int T = NY / 16, NT = TX8 * T, NW = NT / 32;
-    constexpr uint32_t kTmemCols = 128;
+    constexpr uint32_t kTmemCols = NY == 512 ? 256 : 128;
     const int b = blockIdx.y;
     if (PCG && st[b].state != ST_ACTIVE) return;
     extern __shared__ unsigned char smem_raw[];
@@ -291,9 +292,9 @@ k_apply_A8(const __grid_constant__ CUtensorMap smap8, const float2* __restrict__
     __syncthreads();
     tc_fence_after();
     if (tid == 0 && loads) load_tile(0);
-    // this warp's TMEM lanes 32 (w mod 4) .. +31; columns 64 (w / 4) + 0-31 hold p, + 32-63 the
-    // accumulator (at 256 rows, one warp per lane group: + 64-95 the coil's sensitivities)
-    const uint32_t t_pv = tmem_s + ((uint32_t)(32 * (w & 3)) << 16) + (uint32_t)(64 * (w >> 2));
+    // this warp's TMEM lanes 32 (w mod 4) .. +31; columns 96 (w / 4) + 0-31 hold p, + 32-63 the
+    // accumulator, + 64-95 the coil's sensitivities
+    const uint32_t t_pv = tmem_s + ((uint32_t)(32 * (w & 3)) << 16) + (uint32_t)(96 * (w >> 2));
     const uint32_t t_acc = t_pv + 32, t_sv = t_pv + 64;
     for (int i = tid; i < NY; i += NT) {
         tw[i] = tw_g[i];
@@ -312,7 +313,7 @@ k_apply_A8(const __grid_constant__ CUtensorMap smap8, const float2* __restrict__
         tmem_st32(t_pv, v);
     }
     __syncthreads();
-    float2 twr[15];  // used at 256 rows only
+    float2 twr[15];
 #pragma unroll
     for (int r = 1; r < 16; ++r) twr[r - 1] = tw[r * 16 + (t & 15)];
     for (int c = 0; c < nc; ++c) {
@@ -338,7 +339,7 @@ k_apply_A8(const __grid_constant__ CUtensorMap smap8, const float2* __restrict__
         float2 u[16];
 #pragma unroll
         for (int e = 0; e < 16; ++e) u[e] = cmul(sv[e], make_float2(__uint_as_float(pr[2 * e]), __uint_as_float(pr[2 * e + 1])));
-        if constexpr (NY == 256) {
+        {
             float v[32];
 #pragma unroll
             for (int e = 0; e < 16; ++e) {
@@ -348,26 +349,18 @@ k_apply_A8(const __grid_constant__ CUtensorMap smap8, const float2* __restrict__
             tmem_st32(t_sv, v);
         }
         if constexpr (NY == 256) fft256_bar_rtw<false>(u, t, xbuf, idx, twr, gbar);
-        else fft_bar2<NY, false>(u, t, xbuf, xbuf, idx, tw, gbar);
+        else fft512_bar_rtw<false>(u, t, xbuf, idx, tw, twr, gbar);
 #pragma unroll
         for (int e = 0; e < 16; ++e) u[e] = cscale2(u[e], mk[t + T * e]);
         gbar();  // the warp's forward reads of its exchange region are done
         if constexpr (NY == 256) fft256_bar_rtw<true>(u, t, xbuf, idx, twr, gbar);
-        else fft_bar2<NY, true>(u, t, xbuf, xbuf, idx, tw, gbar);
+        else fft512_bar_rtw<true>(u, t, xbuf, idx, tw, twr, gbar);
         // acc += conj(S) u, in two halves of 8 values (16 TMEM columns each)
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             float a[16], s16[16];
-            if (NY == 256 || c > 0) tmem_wait_st();
-            if constexpr (NY == 256) {
-                tmem_ld16(t_sv + 16 * h, s16);
-            } else {
-#pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    s16[2 * i] = sv[8 * h + i].x;
-                    s16[2 * i + 1] = sv[8 * h + i].y;
-                }
-            }
+            tmem_wait_st();
+            tmem_ld16(t_sv + 16 * h, s16);
             if (c > 0) {
                 tmem_ld16(t_acc + 16 * h, a);
             } else {
