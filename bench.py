@@ -46,9 +46,9 @@ HBM_FALLBACK_GBS = 6800.0
 # FP32 lanes per SM (the FP32 CUDA-core peak is SMs x lanes x 2 flops (FMA) x the SM clock)
 FP32_LANES_PER_SM = 128
 # DRAM bytes (read + write) of one q = A p launch (k_apply_A8) over the full 64-slice 256x256x12
-# batch: an ncu capture of a 32-slice launch (231.62 MB read + 10.63 MB written) scaled by the
+# batch: an ncu capture of a 32-slice launch (231.76 MB read + 10.52 MB written) scaled by the
 # slices processed.  Set to None whenever the kernel changes until it is captured again.
-TRAFFIC_K1 = 2 * (231.62e6 + 10.63e6)
+TRAFFIC_K1 = 2 * (231.76e6 + 10.52e6)
 # --prec: (sb_precision, dtype label of the JSON line)
 PRECS = {"fp32": (0, "fp32"), "split-bf16": (1, "bf16x2 split, fp32 accumulate (tensor-core DFT stages)"),
          "split-fp16": (2, "fp16x2 split, fp32 accumulate (tensor-core DFT stages)")}
