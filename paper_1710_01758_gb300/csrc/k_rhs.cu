@@ -182,17 +182,18 @@ k_rhs(const __grid_constant__ CUtensorMap smap, const __grid_constant__ CUtensor
     }
 }
 
-// ---------------------------------------------------------------- 256 rows: k_rhs8
-// The same pass for ny = 256 in the layout of k_apply_A8 (k_applyA.cu): 8 columns per CTA, 128
-// threads, a warp holds two whole columns (16 rows x 2 columns) so the transforms' exchanges are
-// warp-local; x, the data-term accumulator and the coil's sensitivities (between the forward
-// product and the conjugate product) live in tensor memory (128 columns per CTA), and the
-// thread's 15 stage-2 twiddles W_256^{r t} in the registers that this frees; the
-// coil tile and the compact k-space rows (yt, yt1) arrive by TMA with the 64-byte swizzle into
-// one stage each, released as soon as every warp has read them (the sensitivities into
-// registers at the start of the coil, the k-space rows after the forward transform) and refilled
-// at once by the last warp to release them.  Between the transforms a warp handles the sampled
-// lines of its two columns densely (its lanes over the compact slots, through the exchange
+// ---------------------------------------------------------------- 256 and 512 rows: k_rhs8
+// The same pass for ny = 256 and 512 in the layout of k_apply_A8 (k_applyA.cu): 8 columns per
+// CTA, ny / 16 threads per column (128 threads at 256 rows: a warp holds two whole columns, 16
+// rows x 2 columns; 256 threads at 512 rows: a warp is one column), so the transforms' exchanges
+// are warp-local; x, the data-term accumulator and the coil's sensitivities (between the forward
+// product and the conjugate product) live in tensor memory (128 columns per CTA at 256 rows, 256
+// at 512), and the thread's 15 stage-2 twiddles W_256^{r (t mod 16)} in the registers that this
+// frees; the coil tile and the compact k-space rows (yt, yt1) arrive by TMA with the 64-byte
+// swizzle into one stage each, released as soon as every warp has read them (the sensitivities
+// into registers at the start of the coil, the k-space rows after the forward transform) and
+// refilled at once by the last warp to release them.  Between the transforms a warp handles the
+// sampled lines of its columns densely (its lanes over the compact slots, through the exchange
 // region) instead of each thread testing its own 16 rows, which left most lanes idle on every
 // row.  The epilogue's rows of g, bd and bd1 are prefetched into L2 during the last coil.
 constexpr int TX8 = 8;
@@ -208,19 +209,22 @@ __device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefe
 // 512-byte boundary, as the 64-byte swizzle requires)
 __host__ __device__ constexpr int ms_rows8(int ms) { return (ms + 7) & ~7; }
 
-size_t rhs8_smem_bytes(int ms) {
-    return 512 + ((size_t)256 * TX8 + 2 * (size_t)ms_rows8(ms) * TX8 + (size_t)ExIdx<256>::kStride * TX8 + 256) *
-                     sizeof(float2) +
-           2 * 256 * sizeof(int) + 32 * sizeof(double);
+size_t rhs8_smem_bytes(int ny, int ms) {
+    const size_t stride = ny == 512 ? ExIdx<512>::kStride : ExIdx<256>::kStride;
+    return 512 + ((size_t)ny * TX8 + 2 * (size_t)ms_rows8(ms) * TX8 + stride * TX8 + ny) * sizeof(float2) +
+           2 * (size_t)ny * sizeof(int) + 32 * sizeof(double);
 }
 
-template <bool ADDBACK>
-__global__ void __launch_bounds__(128, 4)
+template <int NY, bool ADDBACK>
+__global__ void __launch_bounds__(TX8 * NY / 16, NY == 256 ? 4 : 2)
 k_rhs8(const __grid_constant__ CUtensorMap smap8, const __grid_constant__ CUtensorMap ymap8,
        const __grid_constant__ CUtensorMap y1map8, SbFields f, int nx, int nc, const float2* __restrict__ xin,
        float2* __restrict__ r, const float2* __restrict__ tw_g, float mu, float lam, float gam, SliceState* st,
        double tol2, Red red) {
-    constexpr int NY = 256, T = 16, NT = 128, NW = 4;
+    static_assert(NY == 256 || NY == 512, "16 or 32 threads per column");
+    // T = 16: a warp = 16 rows x 2 columns; T = 32: a warp = one column
+    constexpr int T = NY / 16, NT = TX8 * T, NW = NT / 32, CPW = 32 / T;
+    constexpr uint32_t kTmemCols = NY == 512 ? 256 : 128;
     const int b = blockIdx.y;
     const int ms = f.ms;
     const int msr = ms_rows8(ms);
@@ -239,7 +243,8 @@ k_rhs8(const __grid_constant__ CUtensorMap smap8, const __grid_constant__ CUtens
     __shared__ int flag;
 
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    const int t = (lane & 7) + 8 * (lane >> 4), col = 2 * w + ((lane >> 3) & 1);
+    const int t = T == 16 ? (lane & 7) + 8 * (lane >> 4) : lane;
+    const int col = T == 16 ? 2 * w + ((lane >> 3) & 1) : w;
     const int x0 = blockIdx.x * TX8, xg = x0 + col;
     const ExIdx<NY> idx{col * ExIdx<NY>::kStride};
     const int sb0 = swz64(t, col);
@@ -247,7 +252,9 @@ k_rhs8(const __grid_constant__ CUtensorMap smap8, const __grid_constant__ CUtens
     const bool loads = !(red.flags & kRedWithholdCoilTiles);
     auto load_S = [&](int c) {
         mbar_arrive_expect_tx(&fullA, NY * TX8 * sizeof(float2));
-        tma_load_2d(sA, &smap8, 2 * x0, (b * nc + c) * NY, &fullA);
+#pragma unroll
+        for (int r0 = 0; r0 < NY; r0 += 256)  // a TMA box spans at most 256 rows
+            tma_load_2d(sA + r0 * TX8, &smap8, 2 * x0, (b * nc + c) * NY + r0, &fullA);
     };
     auto load_Y = [&](int c) {
         mbar_arrive_expect_tx(&fullB, (ADDBACK ? 2u : 1u) * (uint32_t)ms * TX8 * sizeof(float2));
@@ -255,7 +262,7 @@ k_rhs8(const __grid_constant__ CUtensorMap smap8, const __grid_constant__ CUtens
         if (ADDBACK) tma_load_2d(sB + msr * TX8, &y1map8, 2 * x0, (b * nc + c) * ms, &fullB);
     };
 
-    if (w == 0) tmem_alloc(&tmem_s, 128);
+    if (w == 0) tmem_alloc(&tmem_s, kTmemCols);
     if (tid == 0) {
         mbar_init(&fullA, 1);
         mbar_init(&emptyA, NW);
@@ -271,8 +278,10 @@ k_rhs8(const __grid_constant__ CUtensorMap smap8, const __grid_constant__ CUtens
         load_S(0);
         load_Y(0);
     }
-    // this warp's TMEM lanes: columns 0-31 hold x, 32-63 the data-term accumulator, 64-95 S
-    const uint32_t t_x = tmem_s + ((uint32_t)(32 * w) << 16), t_acc = t_x + 32, t_sv = t_x + 64;
+    // this warp's TMEM lanes 32 (w mod 4) .. +31; columns 96 (w / 4) + 0-31 hold x, + 32-63 the
+    // data-term accumulator, + 64-95 S
+    const uint32_t t_x = tmem_s + ((uint32_t)(32 * (w & 3)) << 16) + (uint32_t)(96 * (w >> 2));
+    const uint32_t t_acc = t_x + 32, t_sv = t_x + 64;
     for (int i = tid; i < NY; i += NT) {
         tw[i] = tw_g[i];
         sl[i] = f.slot[(size_t)b * NY + i];
@@ -290,13 +299,13 @@ k_rhs8(const __grid_constant__ CUtensorMap smap8, const __grid_constant__ CUtens
         tmem_st32(t_x, v);
     }
     __syncthreads();
-    uint32_t mb = 0;  // which of this thread's rows t + 16 e are sampled
+    uint32_t mb = 0;  // which of this thread's rows t + T e are sampled
 #pragma unroll
     for (int e = 0; e < 16; ++e) mb |= (sl[t + T * e] >= 0 ? 1u : 0u) << e;
     const float sc = rsqrtf((float)NY);
     float2 twr[15];
 #pragma unroll
-    for (int r = 1; r < 16; ++r) twr[r - 1] = tw[r * 16 + t];
+    for (int r = 1; r < 16; ++r) twr[r - 1] = tw[r * 16 + (t & 15)];
     for (int c = 0; c < nc; ++c) {
         const uint32_t ph = c & 1;
         if (c == nc - 1) {  // the epilogue's rows of g, bd (and bd1) into L2
@@ -336,11 +345,13 @@ k_rhs8(const __grid_constant__ CUtensorMap smap8, const __grid_constant__ CUtens
             }
             tmem_st32(t_sv, v);
         }
-        fft256_bar_rtw<false>(u, t, xbuf, idx, twr, gbar);
+        if constexpr (NY == 256) fft256_bar_rtw<false>(u, t, xbuf, idx, twr, gbar);
+        else fft512_bar_rtw<false>(u, t, xbuf, idx, tw, twr, gbar);
         // on sampled lines: tt = R F S x (unitary scale), yv = y^[j] after the outer update,
-        // u <- yv - tt; zero elsewhere.  The warp's two columns go through the exchange region:
-        // every thread stores its 16 values, the lanes then walk the compact slots of both columns
-        // (lane l: column 2 w + (l & 1), slots l / 2 + 16 i), and every thread reads its rows back.
+        // u <- yv - tt; zero elsewhere.  The warp's columns go through the exchange region: every
+        // thread stores its 16 values, the lanes then walk the compact slots of the warp's columns
+        // (T = 16, two columns: lane l serves column 2 w + (l & 1), slots l / 2 + 16 i; T = 32:
+        // slots l + 32 i of column w), and every thread reads its rows back.
         gbar();  // the forward transform's exchange reads are done
 #pragma unroll
         for (int e = 0; e < 16; ++e) xbuf[idx(t + T * e)] = u[e];
@@ -350,9 +361,9 @@ k_rhs8(const __grid_constant__ CUtensorMap smap8, const __grid_constant__ CUtens
             const float2* Yt = sB;
             const float2* Y1 = sB + msr * TX8;
             const size_t ybase = ((size_t)b * nc + c) * ms * nx;
-            const int cc = 2 * w + (lane & 1);  // the column this lane serves in the dense walk
+            const int cc = CPW == 2 ? 2 * w + (lane & 1) : w;  // the column this lane serves in the walk
             const ExIdx<NY> cidx{cc * ExIdx<NY>::kStride};
-            for (int s = lane >> 1; s < ms; s += 16) {
+            for (int s = lane / CPW; s < ms; s += 32 / CPW) {
                 const int yrow = ln[s];
                 const float2 tt = cscale(xbuf[cidx(yrow)], sc);
                 float2 yv = Yt[swz64(s, cc)];
@@ -376,7 +387,8 @@ k_rhs8(const __grid_constant__ CUtensorMap smap8, const __grid_constant__ CUtens
             }
         }
         gbar();
-        fft256_bar_rtw<true>(u, t, xbuf, idx, twr, gbar);
+        if constexpr (NY == 256) fft256_bar_rtw<true>(u, t, xbuf, idx, twr, gbar);
+        else fft512_bar_rtw<true>(u, t, xbuf, idx, tw, twr, gbar);
         // racc += conj(S) (sc u), in two halves of 8 values
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
@@ -433,7 +445,7 @@ k_rhs8(const __grid_constant__ CUtensorMap smap8, const __grid_constant__ CUtens
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (w == 0) tmem_dealloc(tmem_s, 128);
+    if (w == 0) tmem_dealloc(tmem_s, kTmemCols);
     float bb = 0.f, rr = 0.f;
     // the rows' g, bd (and bd1) loads are issued EC rows at a time: in one loop with the stores
     // of bd and r they could not be moved above the previous row's stores (the arrays may alias
@@ -492,14 +504,15 @@ k_rhs8(const __grid_constant__ CUtensorMap smap8, const __grid_constant__ CUtens
     }
 }
 
-template <bool AB>
+template <int NY, bool AB>
 cudaError_t rhs8(const Dims& d, const RhsMaps& m, const SbFields& f, const float2* x, float2* r, const float2* tw,
                  float mu, float lam, float gam, SliceState* st, double tol2, Red red, cudaStream_t s) {
-    const size_t sm = rhs8_smem_bytes(f.ms);
-    cudaError_t e = set_smem_limit(k_rhs8<AB>, (int)rhs8_smem_bytes(256));  // the fixed maximum (see rhs_n)
+    const size_t sm = rhs8_smem_bytes(NY, f.ms);
+    // the fixed maximum (see rhs_n)
+    cudaError_t e = set_smem_limit(k_rhs8<NY, AB>, (int)rhs8_smem_bytes(NY, 256));
     if (e != cudaSuccess) return e;
-    k_rhs8<AB><<<dim3(d.nx / TX8, d.nb), 128, sm, s>>>(*m.smap8, *m.ymap8, *m.y1map8, f, d.nx, d.nc, x, r, tw, mu, lam,
-                                                      gam, st, tol2, red);
+    k_rhs8<NY, AB><<<dim3(d.nx / TX8, d.nb), TX8 * NY / 16, sm, s>>>(*m.smap8, *m.ymap8, *m.y1map8, f, d.nx, d.nc, x,
+                                                                    r, tw, mu, lam, gam, st, tol2, red);
     return cudaGetLastError();
 }
 
@@ -520,7 +533,7 @@ cudaError_t rhs_n(const Dims& d, const CUtensorMap& smap, const CUtensorMap& yma
 }  // namespace
 
 size_t rhs_smem_bytes(int ny, int ms) {
-    if (ny == 256) return rhs8_smem_bytes(ms);
+    if (ny == 256 || ny == 512) return rhs8_smem_bytes(ny, ms);
     const size_t nst = 1;
     const size_t xbufs = is_pow2(ny) ? 1 : 2;  // exchange regions (two for the out-of-place mixed-radix stages)
     return (nst * (size_t)(ny + 2 * ms) * TX + xbufs * (size_t)ny * TX + 3 * (size_t)ny) * sizeof(float2) +
@@ -539,9 +552,11 @@ cudaError_t launch_rhs(const Dims& d, const RhsMaps& m, const SbFields& f, int a
         case 64: CALL(64)
         case 128: CALL(128)
         case 256:
-            return addback ? rhs8<true>(d, m, f, x, r, tw_y, mu, lam, gam, st, tol2, red, s)
-                           : rhs8<false>(d, m, f, x, r, tw_y, mu, lam, gam, st, tol2, red, s);
-        case 512: CALL(512)
+            return addback ? rhs8<256, true>(d, m, f, x, r, tw_y, mu, lam, gam, st, tol2, red, s)
+                           : rhs8<256, false>(d, m, f, x, r, tw_y, mu, lam, gam, st, tol2, red, s);
+        case 512:
+            return addback ? rhs8<512, true>(d, m, f, x, r, tw_y, mu, lam, gam, st, tol2, red, s)
+                           : rhs8<512, false>(d, m, f, x, r, tw_y, mu, lam, gam, st, tol2, red, s);
         case 192: CALL(192)
         case 224: CALL(224)
         case 320: CALL(320)

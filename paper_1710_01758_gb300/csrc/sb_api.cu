@@ -87,7 +87,7 @@ struct Exec {
     cudaStream_t s = nullptr;
     bool own_stream = false;
     CUtensorMap smap{}, ymap{}, y1map{};  // TMA maps whose first row belongs to slice b0
-    CUtensorMap ymap8{}, y1map8{};        // compact k-space rows as 8-column boxes, 64-byte swizzle (ny = 256)
+    CUtensorMap ymap8{}, y1map8{};        // compact k-space rows as 8-column boxes, 64-byte swizzle (ny 256, 512)
     CUtensorMap smap_sw{};                // coil tiles with the 128-byte swizzle (q = A p)
     CUtensorMap smap_sw64{};              // 8-column coil tiles, 64-byte swizzle (split-precision q = A p)
     SliceState* st = nullptr;             // device state of the range
@@ -1120,7 +1120,7 @@ sb_status sb_set_mask(sb_plan pl, const uint8_t* d_mask) {
         if (ms > 256 || pl->passes()) return true;  // no compact-row maps (2D line RHS kernel only)
         return encode_rows(&e2.ymap, pl->yt + e2.b0 * yrow, d.nx, rows, ms) &&
                encode_rows(&e2.y1map, pl->yt1 + e2.b0 * yrow, d.nx, rows, ms) &&
-               (d.ny != 256 ||
+               ((d.ny != 256 && d.ny != 512) ||
                 (encode_rows(&e2.ymap8, pl->yt + e2.b0 * yrow, d.nx, rows, ms, true, 8, CU_TENSOR_MAP_SWIZZLE_64B) &&
                  encode_rows(&e2.y1map8, pl->yt1 + e2.b0 * yrow, d.nx, rows, ms, true, 8, CU_TENSOR_MAP_SWIZZLE_64B)));
     };
