@@ -75,17 +75,24 @@ __device__ __forceinline__ void st_cluster(uint32_t addr, float2 v) {
     asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(addr), "f"(v.x), "f"(v.y) : "memory");
 }
 
-template <int NX, int NY, bool PCG>
+// MODE 0: q = A p (PCG: PCG mode, p^H q and alpha in the last CTA); mu_n = mu / N.
+// MODE 1: the Split Bregman right-hand side and initial residual of the same data term (the
+// passes of k_vol.cu in one launch): at the sampled points of the 2D spectrum tt = F S_c x /
+// sqrt(N), the outer data update yt <- yt + yt1 - tt (PCG = ADDBACK, written back) and yt - tt
+// instead of the mask; the epilogue is k_g3_inv_y's (bd', b = mu bd' + g, r = b - A x and the
+// initial convergence test); mu_n = mu.  q is r, p is x, f carries g, bd, bd1, yt and yt1.
+template <int NX, int NY, int MODE, bool PCG>
 __global__ void __launch_bounds__(Gen<NX, NY>::NT, 1)
 k_apply_A_cl(const float2* __restrict__ sens, const float2* __restrict__ p, float2* __restrict__ q,
              const uint8_t* __restrict__ mask, const float2* __restrict__ twx_g, const float2* __restrict__ twy_g,
-             int nc, float mu_n, float lam, float gam, SliceState* st, Red red) {
+             int nc, float mu_n, float lam, float gam, SliceState* st, Red red, SbFields f, double tol2) {
     using G = Gen<NX, NY>;
     constexpr int C = G::C, RY = G::RY, W = G::W, TXr = G::TXr, TYc = G::TYc, NT = G::NT, RS = G::RS;
     const int b = blockIdx.y;
     // the slice state is written only by the last CTA of the reduction at the very end, so every
-    // CTA of the cluster takes the same branch here, before any cluster barrier
-    if (PCG && st[b].state != ST_ACTIVE) return;
+    // CTA of the cluster takes the same branch here, before any cluster barrier (the right-hand
+    // side runs for every slice)
+    if (MODE == 0 && PCG && st[b].state != ST_ACTIVE) return;
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (int)cluster.block_rank();
 
@@ -179,9 +186,43 @@ k_apply_A_cl(const float2* __restrict__ sens, const float2* __restrict__ p, floa
         for (int e = 0; e < 16; ++e) u[e] = cbuf[cpos(ty + TYc * e)];
         __syncthreads();  // every column is in registers before the transform's exchange writes
         fft<NY, false>(u, ty, cbuf, cpos, twy);
+        if constexpr (MODE == 0) {
 #pragma unroll
-        for (int e = 0; e < 16; ++e)
-            if (!((mbits >> e) & 1u)) u[e] = make_float2(0.f, 0.f);
+            for (int e = 0; e < 16; ++e)
+                if (!((mbits >> e) & 1u)) u[e] = make_float2(0.f, 0.f);
+        } else {  // the sampled points: outer data update and the data-term residual yt - tt
+            const float isq = rsqrtf((float)NX * (float)NY);
+            const size_t kb = ((size_t)b * nc + c) * NY * NX + kx;
+            // four points' loads at a time: in one loop with the stores of yt they could not be
+            // moved above the previous point's store (yt may alias as far as the compiler knows)
+#pragma unroll
+            for (int e0 = 0; e0 < 16; e0 += 4) {
+                float2 yq[4], y1q[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const size_t ki = kb + (size_t)(ty + TYc * (e0 + k)) * NX;
+                    if ((mbits >> (e0 + k)) & 1u) {
+                        yq[k] = f.yt[ki];
+                        if (PCG) y1q[k] = __ldg(f.yt1 + ki);
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int e = e0 + k;
+                    if (!((mbits >> e) & 1u)) {
+                        u[e] = make_float2(0.f, 0.f);
+                    } else {
+                        const float2 tt = cscale(u[e], isq);
+                        float2 yv = yq[k];
+                        if (PCG) {
+                            yv = csub(cadd(yv, y1q[k]), tt);
+                            f.yt[kb + (size_t)(ty + TYc * e) * NX] = yv;
+                        }
+                        u[e] = cscale(csub(yv, tt), isq);
+                    }
+                }
+            }
+        }
         __syncthreads();  // the forward transform's exchange reads are done before the inverse writes
         fft<NY, true>(u, ty, cbuf, cpos, twy);
 #pragma unroll
@@ -236,7 +277,7 @@ k_apply_A_cl(const float2* __restrict__ sens, const float2* __restrict__ p, floa
     wbar();
     const size_t up_row = img + (size_t)(yg == 0 ? NY - 1 : yg - 1) * NX;
     const size_t dn_row = img + (size_t)(yg == NY - 1 ? 0 : yg + 1) * NX;
-    float dot = 0.f;
+    float dot = 0.f, v1 = 0.f;  // MODE 0: Re(p^H q); MODE 1: ||b||^2, ||r||^2
 #pragma unroll
     for (int e = 0; e < 16; ++e) {
         const int xx = t + TXr * e;
@@ -245,17 +286,49 @@ k_apply_A_cl(const float2* __restrict__ sens, const float2* __restrict__ p, floa
         const float2 rt = rbuf[rpos(xx == NX - 1 ? 0 : xx + 1)];
         const float tvx = 4.f * pv[e].x - up.x - dn.x - lf.x - rt.x;
         const float tvy = 4.f * pv[e].y - up.y - dn.y - lf.y - rt.y;
-        float2 o;
-        o.x = fmaf(mu_n, acc[e].x, fmaf(lam, tvx, gam * pv[e].x));
-        o.y = fmaf(mu_n, acc[e].y, fmaf(lam, tvy, gam * pv[e].y));
-        q[img + (size_t)yg * NX + xx] = o;
-        dot = fmaf(pv[e].x, o.x, fmaf(pv[e].y, o.y, dot));
+        const size_t gi = img + (size_t)yg * NX + xx;
+        if constexpr (MODE == 0) {
+            float2 o;
+            o.x = fmaf(mu_n, acc[e].x, fmaf(lam, tvx, gam * pv[e].x));
+            o.y = fmaf(mu_n, acc[e].y, fmaf(lam, tvy, gam * pv[e].y));
+            q[gi] = o;
+            dot = fmaf(pv[e].x, o.x, fmaf(pv[e].y, o.y, dot));
+        } else {  // bd' = (racc + bd + bd1) / 2 after an outer update; b = mu bd' + g; r = mu racc + g - ...
+            const float2 gv = __ldg(f.g + gi);
+            float2 bdv = f.bd[gi];
+            if (PCG) {
+                const float2 b1 = __ldg(f.bd1 + gi);
+                bdv = make_float2(0.5f * (acc[e].x + bdv.x + b1.x), 0.5f * (acc[e].y + bdv.y + b1.y));
+                f.bd[gi] = bdv;
+            }
+            const float2 bvec = make_float2(fmaf(mu_n, bdv.x, gv.x), fmaf(mu_n, bdv.y, gv.y));
+            float2 rv;
+            rv.x = fmaf(mu_n, acc[e].x, gv.x) - fmaf(lam, tvx, gam * pv[e].x);
+            rv.y = fmaf(mu_n, acc[e].y, gv.y) - fmaf(lam, tvy, gam * pv[e].y);
+            q[gi] = rv;
+            dot += cabs2(bvec);
+            v1 += cabs2(rv);
+        }
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     if (w == 0) tmem_dealloc(tmem_s, G::kTmemCols);
-    if constexpr (PCG) {
+    if constexpr (MODE == 1) {
+        double vv[2] = {(double)dot, (double)v1}, tot[2];
+        if (last_block_total<2>(vv, red.part, C, b * C + rank, red.counter + b, tot, red_s, &flag) &&
+            threadIdx.x == 0) {
+            SliceState& S = st[b];
+            S.bnorm2 = tot[0];
+            S.rnorm2 = tot[1];
+            S.iters = 0;
+            S.rho = S.alpha = S.beta = S.pq = 0.0;
+            if (!isfinite(tot[0]) || !isfinite(tot[1])) S.state = ST_NONFINITE;
+            else if (tot[0] == 0.0) S.state = ST_ZERO;
+            else if (tot[1] <= tol2 * tot[0]) S.state = ST_DONE;
+            else S.state = ST_ACTIVE;
+        }
+    } else if constexpr (PCG) {
         double vv[1] = {(double)dot}, tot[1];
         if (last_block_total<1>(vv, red.part, C, b * C + rank, red.counter + b, tot, red_s, &flag) &&
             threadIdx.x == 0) {
@@ -274,12 +347,12 @@ k_apply_A_cl(const float2* __restrict__ sens, const float2* __restrict__ p, floa
     }
 }
 
-template <int NX, int NY, bool PCG>
+template <int NX, int NY, int MODE, bool PCG>
 cudaError_t general_n(const Dims& d, const float2* sens, const float2* p, float2* q, const uint8_t* mask,
                       const float2* twx, const float2* twy, float mu, float lam, float gam, SliceState* st, Red red,
-                      cudaStream_t s, int* clusters) {
+                      cudaStream_t s, int* clusters, const SbFields& f = SbFields{}, double tol2 = 0.0) {
     using G = Gen<NX, NY>;
-    auto kern = k_apply_A_cl<NX, NY, PCG>;
+    auto kern = k_apply_A_cl<NX, NY, MODE, PCG>;
     cudaError_t e = set_smem_limit(kern, (int)G::smem);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
@@ -295,17 +368,18 @@ cudaError_t general_n(const Dims& d, const float2* sens, const float2* p, float2
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     if (clusters) return cudaOccupancyMaxActiveClusters(clusters, kern, &cfg);
-    const float mu_n = mu / (float)(NX * NY);  // both transforms are unnormalised
-    return cudaLaunchKernelEx(&cfg, kern, sens, p, q, mask, twx, twy, d.nc, mu_n, lam, gam, st, red);
+    // q = A p: both transforms are unnormalised; the right-hand side scales each by 1 / sqrt(N)
+    const float mu_n = MODE == 0 ? mu / (float)(NX * NY) : mu;
+    return cudaLaunchKernelEx(&cfg, kern, sens, p, q, mask, twx, twy, d.nc, mu_n, lam, gam, st, red, f, tol2);
 }
 
 template <int NX>
 cudaError_t general_ny(const Dims& d, const float2* sens, const float2* p, float2* q, const uint8_t* mask,
                        const float2* twx, const float2* twy, float mu, float lam, float gam, SliceState* st, Red red,
                        cudaStream_t s, int* clusters) {
-#define GEN(NY)                                                                                          \
-    return st ? general_n<NX, NY, true>(d, sens, p, q, mask, twx, twy, mu, lam, gam, st, red, s, clusters) \
-              : general_n<NX, NY, false>(d, sens, p, q, mask, twx, twy, mu, lam, gam, st, red, s, clusters);
+#define GEN(NY)                                                                                             \
+    return st ? general_n<NX, NY, 0, true>(d, sens, p, q, mask, twx, twy, mu, lam, gam, st, red, s, clusters) \
+              : general_n<NX, NY, 0, false>(d, sens, p, q, mask, twx, twy, mu, lam, gam, st, red, s, clusters);
     switch (d.ny) {
         case 64: GEN(64)
         case 128: GEN(128)
@@ -326,22 +400,63 @@ cudaError_t general_dispatch(const Dims& d, const float2* sens, const float2* p,
     }
 }
 
+// the right-hand side (MODE 1); clusters != nullptr: occupancy query of both instantiations
+template <int NX>
+cudaError_t rhs_general_ny(const Dims& d, const SbFields& f, const float2* x, float2* r, const uint8_t* mask,
+                           const float2* twx, const float2* twy, float mu, float lam, float gam, SliceState* st,
+                           double tol2, Red red, int addback, cudaStream_t s, int* clusters) {
+#define GEN(NY)                                                                                                    \
+    return addback ? general_n<NX, NY, 1, true>(d, f.sens, x, r, mask, twx, twy, mu, lam, gam, st, red, s, clusters, \
+                                                f, tol2)                                                          \
+                   : general_n<NX, NY, 1, false>(d, f.sens, x, r, mask, twx, twy, mu, lam, gam, st, red, s, clusters, \
+                                                 f, tol2);
+    switch (d.ny) {
+        case 64: GEN(64)
+        case 128: GEN(128)
+        case 256: GEN(256)
+        default: return cudaErrorInvalidValue;
+    }
+#undef GEN
+}
+
+cudaError_t rhs_general_dispatch(const Dims& d, const SbFields& f, const float2* x, float2* r, const uint8_t* mask,
+                                 const float2* twx, const float2* twy, float mu, float lam, float gam, SliceState* st,
+                                 double tol2, Red red, int addback, cudaStream_t s, int* clusters) {
+    switch (d.nx) {
+        case 64: return rhs_general_ny<64>(d, f, x, r, mask, twx, twy, mu, lam, gam, st, tol2, red, addback, s, clusters);
+        case 128: return rhs_general_ny<128>(d, f, x, r, mask, twx, twy, mu, lam, gam, st, tol2, red, addback, s, clusters);
+        case 256: return rhs_general_ny<256>(d, f, x, r, mask, twx, twy, mu, lam, gam, st, tol2, red, addback, s, clusters);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 }  // namespace
 
 bool apply_A_general_ok(const Dims& d) {
     auto ok = [](int n) { return n == 64 || n == 128 || n == 256; };
     if (!ok(d.nx) || !ok(d.ny)) return false;
-    int n0 = 0, n1 = 0;
+    int n0 = 0, n1 = 0, n2 = 0, n3 = 0;
     const Red none{nullptr, nullptr, nullptr};
     SliceState* fake = reinterpret_cast<SliceState*>(16);  // only selects the PCG instantiation
+    const SbFields nof{};
     if (general_dispatch(d, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 1.f, 0.f, 0.f, nullptr, none,
                          nullptr, &n0) != cudaSuccess ||
         general_dispatch(d, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 1.f, 0.f, 0.f, fake, none,
-                         nullptr, &n1) != cudaSuccess) {
+                         nullptr, &n1) != cudaSuccess ||
+        rhs_general_dispatch(d, nof, nullptr, nullptr, nullptr, nullptr, nullptr, 1.f, 0.f, 0.f, nullptr, 0.0, none,
+                             0, nullptr, &n2) != cudaSuccess ||
+        rhs_general_dispatch(d, nof, nullptr, nullptr, nullptr, nullptr, nullptr, 1.f, 0.f, 0.f, nullptr, 0.0, none,
+                             1, nullptr, &n3) != cudaSuccess) {
         cudaGetLastError();  // a refused query is an answer, not a sticky error
         return false;
     }
-    return n0 > 0 && n1 > 0;
+    return n0 > 0 && n1 > 0 && n2 > 0 && n3 > 0;
+}
+
+cudaError_t launch_rhs_general(const Dims& d, const SbFields& f, int addback, const float2* x, float2* r,
+                               const uint8_t* mask, const float2* tw_x, const float2* tw_y, float mu, float lam,
+                               float gam, SliceState* st, double tol2, Red red, cudaStream_t s) {
+    return rhs_general_dispatch(d, f, x, r, mask, tw_x, tw_y, mu, lam, gam, st, tol2, red, addback, s, nullptr);
 }
 
 cudaError_t launch_apply_A_general(const Dims& d, const float2* sens, const float2* p, float2* q, const uint8_t* mask,

@@ -203,6 +203,13 @@ struct SbFields {
     float2* bd1;          // [nb][N]: the same for y^[1]
 };
 
+// The right-hand side and initial residual of launch_rhs for 2D slices with an arbitrary mask
+// (mask: u8 [nb][ny][nx]; f.yt, f.yt1: the whole k-space [nb][nc][ny][nx]) in one launch of the
+// thread-block clusters of launch_apply_A_general (k_general.cu); the same shapes.
+cudaError_t launch_rhs_general(const Dims& d, const SbFields& f, int addback, const float2* x, float2* r,
+                               const uint8_t* mask, const float2* tw_x, const float2* tw_y, float mu, float lam,
+                               float gam, SliceState* st, double tol2, Red red, cudaStream_t s);
+
 // yt1[b][c][s][:] = F_x^H y[b][c][line(s)][:] (unitary).
 cudaError_t launch_ytilde(const Dims& d, const float2* y, const int* lines, int ms, float2* yt1,
                           const float2* tw_x, cudaStream_t s);

@@ -708,7 +708,12 @@ sb_status sb_run(Exec& ex, const sb_sb_opts& o, const float2* y_full, float2* x_
     for (int j = 0; j < o.n_outer; ++j) {
         for (int k = 0; k < o.n_inner; ++k, ++solve) {
             const int addback = (j > 0 && k == 0);
-            if (passes) {
+            if (passes && pl->general_cluster && pl->general_passes == 1) {  // one cluster launch
+                SbFields f1 = fields();
+                SB_LAUNCH(ex, SB_KCLASS_RHS, 1,
+                          launch_rhs_general(dp, f1, addback, x, r, at(pl->mask8, ex, n), pl->tw_x, pl->tw_y, mu, lam,
+                                             gam, ex.st, tol2, ex.red, s));
+            } else if (passes) {
                 SbFields f1 = fields();
                 SB_LAUNCH(ex, SB_KCLASS_RHS, 1, launch_g3_fwd_y(dp, pl->nz, f1.sens, x, U, pl->tw_y, nullptr, s));
                 if (pl->general) {
