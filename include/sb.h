@@ -253,11 +253,11 @@ uint64_t sb_kernel_launches(void);
  * of a captured graph block (default 4, 1..64).  apply_tile: columns per CTA of q = A p (Eq.
  * system) on 2D line-mask plans in FP32 with ny = 256 or 512: 8 (default; p and the coil
  * accumulator in tensor memory) or 16 (both in registers, a two-stage coil-tile ring); other
- * geometries ignore it.  general_passes: how q = A p runs on 2D plans whose
- * mask varies along x (the general path): 1 (default) = one launch per batch, a thread-block
- * cluster per slice keeping every coil's 2D spectrum in distributed shared memory (nx, ny in
- * {64, 128, 256}; other sizes use three passes), 3 = three passes through a coil scratch in
- * device memory.  A zero field keeps the current value.  The
+ * geometries ignore it.  general_passes: how q = A p and the Split Bregman right-hand side run
+ * on 2D plans whose mask varies along x (the general path): 1 (default) = one launch per batch
+ * each, a thread-block cluster per slice keeping every coil's 2D spectrum in distributed shared
+ * memory (nx, ny in {64, 128, 256}; other sizes use three passes), 3 = three passes through a
+ * coil scratch in device memory.  A zero field keeps the current value.  The
  * library's autotuner (paper_1710_01758_gb300.autotune) times the choices per geometry and
  * caches the fastest.  SB_ERR_UNSUPPORTED when col_tile does not divide nx or does not fit the
  * column pass (at most 1024 threads, 160 KB of exchange buffers); SB_ERR_INVALID_ARG for other
