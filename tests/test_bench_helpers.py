@@ -1,6 +1,7 @@
 """Host-side helpers of bench.py on CPU: the tensor-core work per launch for both stage shapes
 (counted by hand from the stage structure), the precision labels, and the workload config that
 the reference arm and our arm share."""
+import os
 import types
 
 import bench
@@ -66,3 +67,23 @@ def test_workload_names_resolve():
         assert (wl.nx, wl.ny, wl.ncoils, wl.tau) == (256, 256, 12, 0.02)
     assert (bench.workload_of(synth, "set2").mu, bench.workload_of(synth, "set2").lam) == (1e-2, 4e-3)
     assert synth.VOLUME_256.wavelet_levels == 3 and synth.VOLUME_256.n_outer == 15
+
+
+def test_clock_sampler_keeps_only_rows_of_the_timed_region(tmp_path, monkeypatch):
+    """bench.ClockSampler waits for nvidia-smi's first row before the timed region and keeps only
+    the rows written after that: a fake nvidia-smi writes five idle rows at once, then, while the
+    region runs, three rows at full clock with the power-cap reason active."""
+    import time
+    fake = tmp_path / "nvidia-smi"
+    idle = "0, 1000, 2070, 100.0, 0x0, Not Active, Not Active, Not Active, Not Active"
+    busy = "0, 2070, 2070, 900.0, 0x4, Not Active, Not Active, Not Active, Active"
+    fake.write_text("#!/bin/bash\n" + "".join(f"echo '{idle}'\n" for _ in range(5)) + "sleep 0.5\n" +
+                    "".join(f"echo '{busy}'\nsleep 0.05\n" for _ in range(3)) + "exec sleep 30\n")
+    fake.chmod(0o755)
+    monkeypatch.setenv("PATH", f"{tmp_path}:{os.environ['PATH']}")
+    s = bench.ClockSampler(0)
+    s.start()
+    assert s.proc is not None and s.skip == 5
+    time.sleep(1.2)
+    c = s.stop()
+    assert c == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
