@@ -338,8 +338,9 @@ class Plan:
 
     def set_tuning(self, col_tile: int = 0, poll_every: int = 0, apply_tile: int = 0, general_passes: int = 0):
         """Columns per CTA of the preconditioner's column pass (8, 16, 32), PCG iterations per
-        convergence poll, columns per CTA of q = A p at 256 rows (8, 16) and the general path's
-        q = A p schedule (1 = one cluster launch, 3 = three passes); 0 keeps the current value."""
+        convergence poll, columns per CTA of q = A p at 256 and 512 rows (8, 16) and the general
+        path's schedule of q = A p and of the right-hand side (1 = one cluster launch each, 3 =
+        three passes); 0 keeps the current value."""
         t = sb_tuning(col_tile, poll_every, apply_tile, general_passes)
         _check(_lib.sb_set_tuning(_P(self.handle), ctypes.byref(t)), self.handle)
 
